@@ -1,0 +1,377 @@
+"""FP64 oracle of the DD-alpha-AMG pieces (test infrastructure only).
+
+Eq. 1 of arXiv:1710.06198 gives the two-level error propagation
+
+    eps <- (I - M D)^k (I - P D_c^-1 P^dag D) eps,
+
+with M the SAP smoother (Sec. 1.1, Luescher's Schwarz alternating procedure), P the
+aggregation-based prolongation built from N_v test vectors, Gamma5-compatible (G5 P = P G5_c), and
+D_c = P^dag D P.  The paper fixes only this structure; the details below are the readings this
+project adopts (listed with their reasons in the design notes):
+
+* SAP: lattice cut into blocks; a block's colour is the parity of its block coordinates.  One sweep
+  visits colour 0 then colour 1; for every block of the colour, r_B = (b - D x)|_B, then n_mr
+  minimal-residual steps on D_B (D restricted to the block with zero Dirichlet data outside; clover
+  and twist included), then x_B += e_B.
+* Aggregation: aggregates are lattice blocks.  Each test vector is split into its chirality halves
+  (spins 0,1 = +, spins 2,3 = -); within each (aggregate, chirality) the N_v pieces are
+  orthonormalised by modified Gram-Schmidt, applied twice, in the order j = 0..N_v-1.  Coarse
+  degrees of freedom per coarse site are ordered [+: 0..N_v-1, -: 0..N_v-1], so
+  G5_c = diag(+1 x N_v, -1 x N_v).
+* D_c is stored as a 9-point stencil: a self block and one block per face (+mu, -mu), each built
+  from the fine hops that cross that face.  The twist is excluded from the stored blocks and added
+  as +i mu G5_c on application (D_c(mu) = D_c + i mu G5_c, Sec. 1.1).
+* Cycle (right preconditioner of FGMRES): from z = 0, coarse correction first,
+  z = P D_c^-1 P^dag r, with D_c^-1 replaced by one GMRES cycle from zero (at most m_c steps,
+  stopping at relative residual rtol_c), then k SAP sweeps on D z = r.  This is Eq. 1 applied to
+  the error of the zero initial guess.
+* Setup: N_v caller-given random vectors; n_init passes of v_j <- normalise(M_SAP^k v_j) from
+  x = 0; build P and D_c; then n_iter passes of v_j <- normalise(cycle(v_j)) with P and D_c
+  rebuilt after each pass (the adaptive setup iterations of Sec. 2).
+
+Pinned by (tests/test_oracle_mg.py): P^dag P = I, G5 P = P G5_c, D_c x_c = P^dag D P x_c,
+D_c(mu) - D_c(0) = i mu G5_c, D_c^dag = G5_c D_c G5_c, the dense SAP error propagator, exact
+coarse correction with full-rank P, and dense LU solutions.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import dirac, krylov
+
+# ---------------------------------------------------------------- block geometry
+
+
+def _lat(shape_tail_dims, f):
+    return f.shape[f.ndim - 4 - shape_tail_dims: f.ndim - shape_tail_dims]
+
+
+def to_blocks(f, bdims, ntail):
+    """f[..., T, Z, Y, X, *tail] -> f[..., nT, nZ, nY, nX, bt, bz, by, bx, *tail]."""
+    bx, by, bz, bt = bdims
+    lead = f.shape[: f.ndim - 4 - ntail]
+    T, Z, Y, X = f.shape[f.ndim - 4 - ntail: f.ndim - ntail]
+    tail = f.shape[f.ndim - ntail:]
+    g = f.reshape(lead + (T // bt, bt, Z // bz, bz, Y // by, by, X // bx, bx) + tail)
+    nl = len(lead)
+    perm = list(range(nl)) + [nl + 0, nl + 2, nl + 4, nl + 6, nl + 1, nl + 3, nl + 5, nl + 7] + \
+        list(range(nl + 8, nl + 8 + ntail))
+    return g.transpose(perm)
+
+
+def from_blocks(g, ntail):
+    nl = g.ndim - 8 - ntail
+    lead = g.shape[:nl]
+    nT, nZ, nY, nX, bt, bz, by, bx = g.shape[nl: nl + 8]
+    tail = g.shape[nl + 8:]
+    perm = list(range(nl)) + [nl + 0, nl + 4, nl + 1, nl + 5, nl + 2, nl + 6, nl + 3, nl + 7] + \
+        list(range(nl + 8, nl + 8 + ntail))
+    return g.transpose(perm).reshape(lead + (nT * bt, nZ * bz, nY * by, nX * bx) + tail)
+
+
+def coords(lat_shape):
+    """(x, y, z, t) coordinate arrays of a (T, Z, Y, X) lattice."""
+    c = np.indices(lat_shape)
+    return [c[3], c[2], c[1], c[0]]
+
+
+def block_colour(lat_shape, bdims):
+    """Colour (0/1) of the block containing each site: parity of the block coordinates."""
+    c = coords(lat_shape)
+    return sum(c[mu] // bdims[mu] for mu in range(4)) % 2
+
+
+# ---------------------------------------------------------------- SAP (Sec. 1.1, Eq. 1: M)
+def hopping_masked(U, psi, tbc, fwd_mask, bwd_mask):
+    """Hopping term with the hops selected by per-site masks (fwd_mask[mu], bwd_mask[mu])."""
+    out = np.zeros_like(psi)
+    for mu in range(4):
+        Umu = U[..., mu, :, :]
+        fwd = dirac.colour_mul(Umu, dirac.shift_fwd(psi, mu, tbc))
+        bwd = dirac.shift_bwd(dirac.colour_mul_dag(Umu, psi), mu, tbc)
+        out += fwd_mask[mu][..., None, None] * dirac.spin_mul(dirac.I4 - dirac.GAMMA[mu], fwd)
+        out += bwd_mask[mu][..., None, None] * dirac.spin_mul(dirac.I4 + dirac.GAMMA[mu], bwd)
+    return -0.5 * out
+
+
+def inner_masks(lat_shape, bdims):
+    """Masks of the hops that stay inside a block (x_mu+1 resp. x_mu-1 in the same block)."""
+    c = coords(lat_shape)
+    fwd = [(c[mu] % bdims[mu]) != bdims[mu] - 1 for mu in range(4)]
+    bwd = [(c[mu] % bdims[mu]) != 0 for mu in range(4)]
+    return fwd, bwd
+
+
+def apply_D_blocks(U, psi, p: dirac.Params, clover, bdims, mu=None, twist=True):
+    """Block-diagonal Dirichlet operator: sum_B D_B (hops across block faces dropped)."""
+    mu = p.mu if mu is None else mu
+    lat = U.shape[:4]
+    fm, bm = inner_masks(lat, bdims)
+    out = (4.0 + p.m0) * psi + dirac.site_matrix_mul(clover, psi) + hopping_masked(U, psi, p.tbc, fm, bm)
+    if twist:
+        out = out + 1j * mu * dirac.apply_g5(psi)
+    return out
+
+
+def block_inner(a, b, bdims):
+    """Per-block <a, b> over sites and spin-colour: result[..., nT, nZ, nY, nX]."""
+    g = to_blocks(np.conj(a) * b, bdims, 2)
+    return g.sum(axis=(-6, -5, -4, -3, -2, -1))
+
+
+def block_broadcast(vals, bdims):
+    """Per-block scalars -> per-site field [..., T, Z, Y, X, 1, 1]."""
+    bx, by, bz, bt = bdims
+    v = np.repeat(vals, bt, axis=-4)
+    v = np.repeat(v, bz, axis=-3)
+    v = np.repeat(v, by, axis=-2)
+    v = np.repeat(v, bx, axis=-1)
+    return v[..., None, None]
+
+
+def block_mr(U, p, clover, r, bdims, n_mr, mu=None):
+    """n_mr MR steps on every block simultaneously, each block with its own step length."""
+    e = np.zeros_like(r)
+    r = r.copy()
+    for _ in range(n_mr):
+        q = apply_D_blocks(U, r, p, clover, bdims, mu)
+        qq = np.real(block_inner(q, q, bdims))
+        qr = block_inner(q, r, bdims)
+        a = np.where(qq > 0, qr / np.where(qq > 0, qq, 1.0), 0.0)
+        ab = block_broadcast(a, bdims)
+        e += ab * r
+        r -= ab * q
+    return e
+
+
+def sap(U, p, clover, b, bdims, n_sweeps, n_mr, x0=None, mu=None):
+    """Multiplicative SAP: n_sweeps x (colour 0, colour 1) block-MR updates of D x = b.
+
+    Needs an even number (>= 2) of blocks along every direction so that blocks of one colour never
+    touch and every hop that leaves a block really couples two different blocks.
+    """
+    lat = U.shape[:4]
+    for d in range(4):
+        nb = lat[3 - d] // bdims[d]
+        if nb < 2 or nb % 2 or lat[3 - d] % bdims[d]:
+            raise ValueError("SAP needs an even number of blocks >= 2 in every direction")
+    col = block_colour(lat, bdims)
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    for _ in range(n_sweeps):
+        for c in (0, 1):
+            r = b - dirac.apply_D(U, x, p, mu, clover)
+            rc = r * (col == c)[..., None, None]
+            x = x + block_mr(U, p, clover, rc, bdims, n_mr, mu)
+    return x
+
+
+# ---------------------------------------------------------------- aggregation P (Sec. 1.1)
+def orthonormalise(vectors, adims):
+    """Per (aggregate, chirality) modified Gram-Schmidt, twice, over j = 0..N_v-1.
+
+    vectors[Nv, T, Z, Y, X, 4, 3] -> W of the same shape; P e_(a, chi, j) = W_j restricted to
+    aggregate a and to the spins of chirality chi.
+    """
+    nv = vectors.shape[0]
+    b = to_blocks(vectors, adims, 2)                    # [Nv, nT,nZ,nY,nX, bt,bz,by,bx, 4, 3]
+    shp = b.shape
+    b = b.reshape(shp[:5] + (-1, 2, 2, 3))              # [..., sites, chi, 2 spins, 3]
+    b = np.moveaxis(b, -3, 5)                           # [Nv, agg4, chi, sites, 2, 3]
+    w = b.reshape(shp[:5] + (2, -1)).copy()            # [Nv, agg4, chi, n_loc]
+    for _ in range(2):
+        for j in range(nv):
+            for i in range(j):
+                ov = np.sum(np.conj(w[i]) * w[j], axis=-1, keepdims=True)
+                w[j] = w[j] - ov * w[i]
+            nrm = np.sqrt(np.sum(np.abs(w[j]) ** 2, axis=-1, keepdims=True))
+            w[j] = w[j] / nrm
+    w = w.reshape(b.shape)
+    w = np.moveaxis(w, 5, -3).reshape(shp)
+    return from_blocks(w, 2)
+
+
+@dataclass
+class Prolongator:
+    W: np.ndarray          # [Nv, T, Z, Y, X, 4, 3]
+    adims: tuple
+
+    @property
+    def nv(self):
+        return self.W.shape[0]
+
+    @property
+    def coarse_lat(self):
+        T, Z, Y, X = self.W.shape[1:5]
+        ax, ay, az, at = self.adims
+        return (T // at, Z // az, Y // ay, X // ax)
+
+
+def prolong(P: Prolongator, c):
+    """e(x)_chi = sum_j W_j(x)_chi c[a(x), chi, j]; c[..., nT, nZ, nY, nX, 2 Nv]."""
+    nv = P.nv
+    lead = c.shape[:-5]
+    ax, ay, az, at = P.adims
+    cf = np.repeat(np.repeat(np.repeat(np.repeat(c, at, axis=-5), az, axis=-4), ay, axis=-3), ax, axis=-2)
+    cp = cf[..., :nv]   # [..., T, Z, Y, X, Nv]
+    cm = cf[..., nv:]
+    e = np.zeros(lead + P.W.shape[1:], dtype=np.complex128)
+    e[..., 0:2, :] = np.einsum("j...sa,...j->...sa", P.W[..., 0:2, :], cp)
+    e[..., 2:4, :] = np.einsum("j...sa,...j->...sa", P.W[..., 2:4, :], cm)
+    return e
+
+
+def restrict(P: Prolongator, r):
+    """c[a, chi, j] = sum_{x in a} W_j(x)_chi^dag r(x)_chi  (P^dag r)."""
+    nv = P.nv
+    sp = np.einsum("j...sa,...sa->...j", np.conj(P.W[..., 0:2, :]), r[..., 0:2, :])
+    sm = np.einsum("j...sa,...sa->...j", np.conj(P.W[..., 2:4, :]), r[..., 2:4, :])
+    s = np.concatenate([sp, sm], axis=-1)              # [..., T, Z, Y, X, 2Nv]
+    g = to_blocks(s, P.adims, 1)
+    return g.sum(axis=(-5, -4, -3, -2))
+
+
+def coarse_gamma5(nv):
+    return np.concatenate([np.ones(nv), -np.ones(nv)])
+
+
+# ---------------------------------------------------------------- coarse operator D_c = P^dag D P
+@dataclass
+class CoarseOp:
+    self_blk: np.ndarray   # [nT, nZ, nY, nX, nd, nd]
+    fwd: np.ndarray        # [4, nT, nZ, nY, nX, nd, nd]  block coupling a to a+mu
+    bwd: np.ndarray        # [4, nT, nZ, nY, nX, nd, nd]  block coupling a to a-mu
+    nv: int
+    extra: dict = field(default_factory=dict)
+
+
+def build_coarse(U, p: dirac.Params, clover, P: Prolongator):
+    """Stencil blocks of P^dag D_W P (twist excluded), one column per coarse dof l:
+
+    w_l = P e_l on every aggregate at once; self = P^dag (aggregate-Dirichlet D_W) w_l;
+    fwd[mu] = P^dag (hops x -> x+mu crossing the +mu face) w_l;
+    bwd[mu] = P^dag (hops x -> x-mu crossing the -mu face) w_l.
+    """
+    nv = P.nv
+    nd = 2 * nv
+    lat = U.shape[:4]
+    clat = P.coarse_lat
+    c = coords(lat)
+    self_blk = np.zeros(clat + (nd, nd), dtype=np.complex128)
+    fwd = np.zeros((4,) + clat + (nd, nd), dtype=np.complex128)
+    bwd = np.zeros((4,) + clat + (nd, nd), dtype=np.complex128)
+    for l in range(nd):
+        chi, j = divmod(l, nv)
+        w = np.zeros(lat + (4, 3), dtype=np.complex128)
+        sl = slice(0, 2) if chi == 0 else slice(2, 4)
+        w[..., sl, :] = P.W[j][..., sl, :]
+        s = apply_D_blocks(U, w, p, clover, P.adims, mu=0.0, twist=False)
+        self_blk[..., :, l] = restrict(P, s)
+        for mu in range(4):
+            Umu = U[..., mu, :, :]
+            face_f = (c[mu] % P.adims[mu]) == P.adims[mu] - 1
+            face_b = (c[mu] % P.adims[mu]) == 0
+            hf = -0.5 * dirac.spin_mul(dirac.I4 - dirac.GAMMA[mu],
+                                       dirac.colour_mul(Umu, dirac.shift_fwd(w, mu, p.tbc)))
+            hb = -0.5 * dirac.spin_mul(dirac.I4 + dirac.GAMMA[mu],
+                                       dirac.shift_bwd(dirac.colour_mul_dag(Umu, w), mu, p.tbc))
+            fwd[mu][..., :, l] = restrict(P, hf * face_f[..., None, None])
+            bwd[mu][..., :, l] = restrict(P, hb * face_b[..., None, None])
+    return CoarseOp(self_blk, fwd, bwd, nv)
+
+
+def _cshift(c, mu, sign):
+    # coarse fields carry (..., nT, nZ, nY, nX, dof): the axis of direction mu is -2 - mu
+    return np.roll(c, -sign, axis=-2 - mu)
+
+
+def coarse_apply(Dc: CoarseOp, x, mu=0.0):
+    """y(a) = A_self(a) x(a) + sum_mu [A_+mu(a) x(a+mu) + A_-mu(a) x(a-mu)] + i mu G5_c x(a)."""
+    y = np.einsum("...kl,...l->...k", Dc.self_blk, x)
+    for m in range(4):
+        y += np.einsum("...kl,...l->...k", Dc.fwd[m], _cshift(x, m, +1))
+        y += np.einsum("...kl,...l->...k", Dc.bwd[m], _cshift(x, m, -1))
+    return y + 1j * mu * coarse_gamma5(Dc.nv) * x
+
+
+def coarse_apply_definition(U, p, clover, P, x, mu=None):
+    """D_c(mu) x = P^dag D(mu) P x, straight from the definition (Sec. 1.1)."""
+    return restrict(P, dirac.apply_D(U, prolong(P, x), p, mu, clover))
+
+
+def coarse_apply_nd(Dc: CoarseOp, x2, mubar, epsbar):
+    """D_ND,c = D_c x I2 + i mubar G5_c x tau3 - epsbar I x tau1 (Sec. 1.1, Eq. 2 coarsened)."""
+    u = coarse_apply(Dc, x2[0], mubar) - epsbar * x2[1]
+    d = coarse_apply(Dc, x2[1], -mubar) - epsbar * x2[0]
+    return np.stack([u, d])
+
+
+def coarse_dense(Dc: CoarseOp, mu=0.0):
+    shp = Dc.self_blk.shape[:4] + (2 * Dc.nv,)
+    return dirac.dense_matrix(lambda v: coarse_apply(Dc, v, mu), shp)
+
+
+# ---------------------------------------------------------------- cycle, setup, solve
+@dataclass
+class MGParams:
+    block: tuple = (4, 4, 4, 4)       # SAP block (x, y, z, t)
+    agg: tuple = (4, 4, 4, 4)         # aggregate (x, y, z, t)
+    nv: int = 8
+    sap_sweeps: int = 3               # k of Eq. 1
+    sap_mr: int = 4                   # MR steps per block solve
+    coarse_m: int = 30                # max GMRES steps of the coarse solve
+    coarse_rtol: float = 5e-2
+    n_init: int = 5                   # initial SAP inverse-iteration passes
+    n_iter: int = 3                   # adaptive setup iterations
+    restart: int = 10                 # outer FGMRES restart length
+
+
+class Hierarchy:
+    """Two-level DD-alpha-AMG hierarchy: operator data, P and D_c."""
+
+    def __init__(self, U, p: dirac.Params, mg: MGParams, clover=None):
+        self.U, self.p, self.mg = U, p, mg
+        self.clover = dirac.clover_term(U, p.csw) if clover is None else clover
+        self.P = None
+        self.Dc = None
+
+    def D(self, x, mu=None):
+        return dirac.apply_D(self.U, x, self.p, mu, self.clover)
+
+    def smooth(self, b, x0, mu=None):
+        return sap(self.U, self.p, self.clover, b, self.mg.block, self.mg.sap_sweeps, self.mg.sap_mr,
+                   x0, mu)
+
+    def set_vectors(self, v):
+        self.P = Prolongator(orthonormalise(v, self.mg.agg), tuple(self.mg.agg))
+        self.Dc = build_coarse(self.U, self.p, self.clover, self.P)
+
+    def coarse_solve(self, c, mu=None):
+        mu = self.p.mu if mu is None else mu
+        e, _ = krylov.gmres_fixed(lambda v: coarse_apply(self.Dc, v, mu), c, self.mg.coarse_m,
+                                  self.mg.coarse_rtol)
+        return e
+
+    def cycle(self, r, mu=None):
+        """Eq. 1 on the zero initial guess: coarse correction, then k SAP sweeps."""
+        z = prolong(self.P, self.coarse_solve(restrict(self.P, r), mu))
+        return self.smooth(r, z, mu)
+
+    def setup(self, v0):
+        v = np.array(v0, dtype=np.complex128, copy=True)
+        for _ in range(self.mg.n_init):
+            for j in range(v.shape[0]):
+                x = self.smooth(v[j], None)
+                v[j] = x / np.sqrt(dirac.norm2(x))
+        self.set_vectors(v)
+        for _ in range(self.mg.n_iter):
+            for j in range(v.shape[0]):
+                x = self.cycle(v[j])
+                v[j] = x / np.sqrt(dirac.norm2(x))
+            self.set_vectors(v)
+        return v
+
+    def solve(self, b, tol=1e-10, maxiter=2000, mu=None):
+        return krylov.fgmres(lambda x: self.D(x, mu), b, lambda r: self.cycle(r, mu),
+                             m=self.mg.restart, tol=tol, maxiter=maxiter)

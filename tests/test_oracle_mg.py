@@ -1,0 +1,199 @@
+"""Pins of the oracle's multigrid pieces (Eq. 1 and Sec. 1.1 of arXiv:1710.06198).
+
+* P^dag P = I and G5 P = P G5_c (Gamma5-compatible aggregation);
+* the stored 9-point D_c equals the definition P^dag D P;
+* D_c(mu) - D_c(0) = i mu G5_c and D_c^dag = G5_c D_c G5_c;
+* the coarse-grid correction depends only on span(P) (basis invariance);
+* full-rank P makes the coarse-grid correction exact;
+* SAP with converged block solves equals the dense product of block projections;
+* Krylov solvers and the two-level solve agree with dense LU.
+"""
+import numpy as np
+import pytest
+
+from oracle import dirac, krylov, mg
+from synth import fields
+from tests.conftest import rel
+
+
+def _params(m0=-0.2, csw=1.2, mu=0.05, tbc=-1):
+    return dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, mu=mu, tbc=tbc)
+
+
+def _prolongator(dims, adims, nv, seed, eps=0.5):
+    U = fields.gauge_field(dims, eps, seed)
+    v = fields.gaussian_spinor(dims, seed + 1, n=nv)
+    return U, mg.Prolongator(mg.orthonormalise(v, adims), tuple(adims))
+
+
+def test_prolongator_orthonormal_and_gamma5_compatible():
+    dims, adims, nv = (4, 4, 2, 4), (2, 2, 2, 2), 4
+    _, P = _prolongator(dims, adims, nv, 30)
+    clat = P.coarse_lat
+    c = fields.gaussian_coarse((2, 2, 1, 2), 2 * nv, 31)
+    assert c.shape[:4] == clat
+    assert rel(mg.restrict(P, mg.prolong(P, c)), c) < 1e-14           # P^dag P = I
+    g5c = mg.coarse_gamma5(nv)
+    assert rel(dirac.apply_g5(mg.prolong(P, c)), mg.prolong(P, g5c * c)) < 1e-15
+    # dense: P^dag P = identity exactly as a matrix
+    n = int(np.prod(clat)) * 2 * nv
+    Pm = np.stack([mg.prolong(P, e.reshape(clat + (2 * nv,))).ravel() for e in np.eye(n)], axis=1)
+    assert np.abs(Pm.conj().T @ Pm - np.eye(n)).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims,adims", [((6, 4, 4, 6), (2, 2, 2, 2)),   # coarse extent 3
+                                        ((4, 4, 4, 4), (2, 2, 4, 4)),   # coarse extent 1
+                                        ((8, 4, 4, 4), (4, 4, 4, 4))])  # coarse extent 2
+def test_coarse_stencil_equals_definition(dims, adims):
+    nv = 3
+    U, P = _prolongator(dims, adims, nv, 40)
+    p = _params()
+    C = dirac.clover_term(U, p.csw)
+    Dc = mg.build_coarse(U, p, C, P)
+    clat = P.coarse_lat
+    x = fields.gaussian_coarse((clat[3], clat[2], clat[1], clat[0]), 2 * nv, 41)
+    for mu in (0.0, 0.3):
+        want = mg.coarse_apply_definition(U, p, C, P, x, mu)
+        got = mg.coarse_apply(Dc, x, mu)
+        assert rel(got, want) < 1e-13
+    # twist on the coarse grid: D_c(mu) - D_c(0) = i mu G5_c
+    d = mg.coarse_apply_definition(U, p, C, P, x, 0.3) - mg.coarse_apply_definition(U, p, C, P, x, 0.0)
+    assert rel(d, 0.3j * mg.coarse_gamma5(nv) * x) < 1e-13
+
+
+def test_coarse_gamma5_hermiticity():
+    dims, adims, nv = (6, 4, 4, 4), (2, 2, 2, 2), 2
+    U, P = _prolongator(dims, adims, nv, 50)
+    p = _params(mu=0.0)
+    Dc = mg.build_coarse(U, p, dirac.clover_term(U, p.csw), P)
+    A = mg.coarse_dense(Dc, 0.0)
+    g = np.tile(mg.coarse_gamma5(nv), A.shape[0] // (2 * nv))
+    assert np.abs(A.conj().T - (g[:, None] * A * g[None, :])).max() < 1e-13
+
+
+def test_coarse_correction_basis_invariance():
+    """I - P D_c^-1 P^dag D depends on span(P) only: mixing the test vectors by any invertible
+    matrix leaves the coarse-grid correction unchanged."""
+    dims, adims, nv = (4, 4, 2, 4), (2, 2, 2, 2), 3
+    U = fields.gauge_field(dims, 0.5, 60)
+    p = _params(mu=0.1)
+    C = dirac.clover_term(U, p.csw)
+    v = fields.gaussian_spinor(dims, 61, n=nv)
+    rng = np.random.default_rng(62)
+    R = rng.standard_normal((nv, nv)) + 1j * rng.standard_normal((nv, nv))
+    v2 = np.einsum("jk,k...->j...", R, v)
+    e = fields.gaussian_spinor(dims, 63)
+    out = []
+    for vv in (v, v2):
+        P = mg.Prolongator(mg.orthonormalise(vv, adims), adims)
+        Dc = mg.build_coarse(U, p, C, P)
+        A = mg.coarse_dense(Dc, p.mu)
+        c = mg.restrict(P, dirac.apply_D(U, e, p, clover=C))
+        sol = np.linalg.solve(A, c.ravel()).reshape(c.shape)
+        out.append(e - mg.prolong(P, sol))
+    assert rel(out[1], out[0]) < 1e-11
+
+
+def test_full_rank_prolongator_exact_correction():
+    """Aggregates of one site and N_v = 6 per chirality: P is unitary, D_c is unitarily similar to
+    D and FGMRES preconditioned by P D_c^-1 P^dag converges in one step."""
+    dims = (2, 2, 2, 2)
+    U = fields.gauge_field(dims, 0.6, 70)
+    p = _params(mu=0.1)
+    C = dirac.clover_term(U, p.csw)
+    P = mg.Prolongator(mg.orthonormalise(fields.gaussian_spinor(dims, 71, n=6), (1, 1, 1, 1)),
+                       (1, 1, 1, 1))
+    Dc = mg.build_coarse(U, p, C, P)
+    A = mg.coarse_dense(Dc, p.mu)
+    b = fields.gaussian_spinor(dims, 72)
+    prec = lambda r: mg.prolong(P, np.linalg.solve(A, mg.restrict(P, r).ravel()).reshape(
+        P.coarse_lat + (12,)))
+    x, steps, res = krylov.fgmres(lambda v: dirac.apply_D(U, v, p, clover=C), b, prec, m=5, tol=1e-12)
+    assert steps == 1 and res < 1e-12
+    D = dirac.dense_matrix(lambda v: dirac.apply_D(U, v, p, clover=C), fields.lattice_shape(dims) + (4, 3))
+    ev_f = np.sort_complex(np.round(np.linalg.eigvals(D), 10))
+    ev_c = np.sort_complex(np.round(np.linalg.eigvals(A), 10))
+    assert np.abs(ev_f - ev_c).max() < 1e-9
+
+
+def test_sap_converged_equals_block_projection_product():
+    """With converged block solves, one SAP sweep from x = 0 maps b to
+    x = K1 (b - D K0 b) + K0 b, K_c = sum over colour-c blocks of I_B D_B^-1 I_B^T."""
+    dims, bdims = (4, 4, 4, 4), (2, 2, 2, 2)
+    U = fields.gauge_field(dims, 0.3, 80)
+    p = _params(m0=0.4, mu=0.05)
+    C = dirac.clover_term(U, p.csw)
+    shape = fields.lattice_shape(dims) + (4, 3)
+    D = dirac.dense_matrix(lambda v: dirac.apply_D(U, v, p, clover=C), shape)
+    col = mg.block_colour(fields.lattice_shape(dims), bdims)
+    bid = mg.coords(fields.lattice_shape(dims))
+    block_index = sum((bid[mu] // bdims[mu]) * (10 ** mu) for mu in range(4))
+    site_block = np.repeat(block_index.ravel(), 12)
+    site_col = np.repeat(col.ravel(), 12)
+    K = []
+    for c in (0, 1):
+        Kc = np.zeros_like(D)
+        for bval in np.unique(site_block[site_col == c]):
+            idx = np.where(site_block == bval)[0]
+            Kc[np.ix_(idx, idx)] = np.linalg.inv(D[np.ix_(idx, idx)])
+        K.append(Kc)
+    b = fields.gaussian_spinor(dims, 81)
+    bv = b.ravel()
+    x0 = K[0] @ bv
+    want = x0 + K[1] @ (bv - D @ x0)
+    got = mg.sap(U, p, C, b, bdims, n_sweeps=1, n_mr=120)
+    assert rel(got.ravel(), want) < 1e-11
+
+
+def test_block_operator_is_block_diagonal_part_of_D():
+    dims, bdims = (4, 8, 4, 2), (2, 4, 2, 1)
+    U = fields.gauge_field(dims, 0.5, 82)
+    p = _params()
+    C = dirac.clover_term(U, p.csw)
+    shape = fields.lattice_shape(dims) + (4, 3)
+    D = dirac.dense_matrix(lambda v: dirac.apply_D(U, v, p, clover=C), shape)
+    DB = dirac.dense_matrix(lambda v: mg.apply_D_blocks(U, v, p, C, bdims), shape)
+    bid = mg.coords(fields.lattice_shape(dims))
+    blk = np.repeat(sum((bid[mu] // bdims[mu]) * (10 ** mu) for mu in range(4)).ravel(), 12)
+    same = blk[:, None] == blk[None, :]
+    assert np.abs(DB - np.where(same, D, 0)).max() < 1e-15
+
+
+def test_krylov_against_dense_lu():
+    dims = (2, 2, 2, 4)
+    U = fields.gauge_field(dims, 0.6, 90)
+    p = _params(mu=0.05)
+    C = dirac.clover_term(U, p.csw)
+    shape = fields.lattice_shape(dims) + (4, 3)
+    D = dirac.dense_matrix(lambda v: dirac.apply_D(U, v, p, clover=C), shape)
+    b = fields.gaussian_spinor(dims, 91)
+    x_lu = np.linalg.solve(D, b.ravel())
+    Dop = lambda v: dirac.apply_D(U, v, p, clover=C)
+    x_cg, _, r_cg = krylov.cg_normal(Dop, lambda v: dirac.apply_Ddag(U, v, p, clover=C), b, tol=1e-13)
+    x_gm, _, r_gm = krylov.gmres(Dop, b, m=20, tol=1e-13)
+    for x in (x_cg, x_gm):
+        assert rel(x.ravel(), x_lu) < 1e-10
+    e = krylov.mr(Dop, b, 1)
+    a = np.vdot(D @ b.ravel(), b.ravel()) / np.vdot(D @ b.ravel(), D @ b.ravel())
+    assert rel(e.ravel(), a * b.ravel()) < 1e-14
+
+
+def test_two_level_solve_against_dense_lu():
+    dims = (4, 4, 4, 4)
+    U = fields.gauge_field(dims, 0.4, 100)
+    p = _params(m0=-0.3, mu=0.02)
+    m = mg.MGParams(block=(2, 2, 2, 2), agg=(2, 2, 2, 2), nv=4, n_init=2, n_iter=1, restart=10)
+    H = mg.Hierarchy(U, p, m)
+    H.setup(fields.gaussian_spinor(dims, 101, n=m.nv))
+    b = fields.gaussian_spinor(dims, 102)
+    x, steps, res = H.solve(b, tol=1e-12)
+    shape = fields.lattice_shape(dims) + (4, 3)
+    D = dirac.dense_matrix(H.D, shape)
+    x_lu = np.linalg.solve(D, b.ravel())
+    assert res < 1e-12
+    assert rel(x.ravel(), x_lu) < 1e-9
+    # two-step solve of D^dag D (Sec. 1.1): D(-mu) x1 = G5 b, then D(mu) y = G5 x1
+    x1, _, _ = H.solve(dirac.apply_g5(b), tol=1e-12, mu=-p.mu)
+    y, _, _ = H.solve(dirac.apply_g5(x1), tol=1e-12)
+    want = np.linalg.solve(D.conj().T @ D, b.ravel())
+    assert rel(y.ravel(), want) < 1e-8
