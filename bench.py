@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the twisted-mass DD-alpha-AMG solve on one GB300 (arXiv:1710.06198 hot path).
+
+Workload (the mixed-precision fine-level configuration): a 16^3 x 32 lattice, SU(3) links
+U = exp(i 0.35 H) from seed 3, c_sw = 1.5, mu = 0.003, antiperiodic time, kappa from the
+oracle's sigma_min search (synth/kappa.json), two-level DD-alpha-AMG with 4^4 SAP blocks and
+aggregates, N_v = 16 test vectors (setup: 5 SAP passes + 3 cycle iterations, untimed), one
+Gaussian right-hand side (seed 4), solved to a true FP64 relative residual of 1e-10.
+
+One timed step = one mixed-precision solve (FP64 defect correction around FP32 FGMRES with the
+FP32 / FP16-link multigrid cycle), inputs already resident in HBM.  L2 (129 MB) is flushed
+between steps by writing a 512 MB buffer.  The JSON line also carries:
+  * e2e: the same solve through the public API with pinned host buffers (H2D + D2H timed);
+  * roofline: the dominant kernel class of the solve (CUDA events around each of its launches
+    in one instrumented solve) against the measured HBM copy peak;
+  * fp64_solve_s, cg_fp64_s: the plain FP64 multigrid and FP64 CG solves of the same system;
+  * cpu_baseline: the FP64 numpy oracle timed on the host cores on a bounded sample.
+`--impl reference` times the oracle itself (the CPU reference arm) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="tm_clover_16x16x16x32_mixed_2lvl", dims=(16, 16, 16, 32), block=(4, 4, 4, 4), eps=0.35,
+                seed=3, csw=1.5, mu=0.003, nv=16, rhs_seed=4, tol=1e-10, sigma_target=5e-4, setup_seed=103)
+METRIC = "DD-alphaAMG solve s to 1e-10 (mixed+batched vs FP64) ; dslash GB/s vs HBM peak"
+
+
+def workload_kappa(w):
+    path = os.path.join(ROOT, "synth", "kappa.json")
+    with open(path) as f:
+        table = json.load(f)
+    e = table[w["name"]]
+    return e["kappa"], e
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kind, V, nv, nc, nd):
+    """Bytes one launch of a kernel class must move at least (each input read once, each output
+    written once); per-site figures are listed in the design notes."""
+    spinor32, spinor64 = 96, 192
+    if kind == "dslash_f32":
+        return V * (2 * spinor32 + 4 * 48 + 288)
+    if kind == "dslash_f16":
+        return V * (2 * spinor32 + 4 * 24 + 144 + 4)
+    if kind == "dslash_f64":
+        return V * (2 * spinor64 + 4 * 144 + 576)
+    if kind == "sap_f32":       # one colour: b, x read, x written, 4 links and clover of the colour's sites
+        return (V // 2) * (3 * spinor32 + 4 * 48 + 288)
+    if kind == "sap_f16":
+        return (V // 2) * (3 * spinor32 + 4 * 24 + 144 + 4)
+    if kind == "sap_f64":
+        return (V // 2) * (3 * spinor64 + 4 * 144 + 576)
+    if kind == "restrict":
+        return V * spinor32 * (1 + nv) + nc * nd * 8
+    if kind == "prolong":
+        return V * spinor32 * (1 + nv) + nc * nd * 8
+    if kind == "coarse_apply":
+        return nc * (9 * nd * nd * 8 + 2 * nd * 8)
+    return None
+
+
+def run_ours(args):
+    import torch
+    import paper_1710_06198_gb300 as tmg
+    from synth import fields
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    kappa, kinfo = workload_kappa(w)
+    U = fields.gauge_field(w["dims"], w["eps"], w["seed"])
+    b_host = fields.gaussian_spinor(w["dims"], w["rhs_seed"])
+    v0 = fields.gaussian_spinor(w["dims"], w["setup_seed"], n=w["nv"])
+    ctx = tmg.Context(w["dims"], w["block"], device=local)
+    ctx.set_params(kappa, w["csw"], w["mu"])
+    ctx.load_gauge(U, -1)
+    prm = tmg.Context.mg_defaults()
+    prm.nv = w["nv"]
+    prm.prec_fine = tmg.PREC_F16 if args.fine == "f16" else tmg.PREC_F32
+    prm.prec_coarse = tmg.PREC_F32
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.setup(v0, prm)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+
+    dev = torch.device("cuda", local)
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(method=tmg.SOLVE_MG_MIXED):
+        _, st = ctx.solve(b, tol=w["tol"], method=method, out=x)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, iters, stats = [], [], None
+    n0 = tmg.launch_count(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(stats["iterations"])
+    torch.cuda.synchronize()
+    launches = (tmg.launch_count(ctx) - n0) // max(1, args.steps)
+    clocks = sampler.stop()
+    t_step = sum(times) / len(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    # verify the last solve in FP64 on the device (true residual through the FP64 operator)
+    r = (ctx.apply(x, tmg.OP_D, tmg.PREC_F64) - b)
+    true_res = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b))
+
+    # end to end through the public API with pinned host buffers
+    bp = torch.from_numpy(b_host).pin_memory()
+    xp = torch.empty_like(bp).pin_memory()
+    bnp, xnp = bp.numpy(), xp.numpy()
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve(bnp, tol=w["tol"], method=tmg.SOLVE_MG_MIXED, out=xnp)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e) / len(e2e)
+
+    # comparators: plain FP64 multigrid and FP64 CG on the same system
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st64 = ctx.solve(b, tol=w["tol"], method=tmg.SOLVE_MG_F64, out=x)
+    torch.cuda.synchronize()
+    fp64_s = time.perf_counter() - t0
+    cg = None
+    if not args.no_cg:
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, stcg = ctx.solve(b, tol=w["tol"], method=tmg.SOLVE_CG_F64, out=x, maxiter=args.cg_maxiter, check=False)
+        torch.cuda.synchronize()
+        cg = {"s": time.perf_counter() - t0, "iterations": stcg["iterations"], "true_residual": stcg["true_residual"]}
+
+    # one instrumented solve: device time of every kernel class
+    flush.zero_()
+    tmg.profile(ctx, True)
+    step()
+    prof = tmg.profile_read(ctx)
+    tmg.profile(ctx, False)
+    V = int(np.prod(w["dims"]))
+    nd = 2 * w["nv"]
+    nc = V // int(np.prod(w["block"]))
+    kernels = {}
+    for k, (n, ms) in prof.items():
+        if n:
+            ab = algorithmic_bytes(k, V, w["nv"], nc, nd)
+            kernels[k] = {"launches": n, "ms_total": round(ms, 4), "us_per_launch": round(1e3 * ms / n, 3),
+                          "algo_bytes_per_launch": ab,
+                          "gbs": round(ab / (ms / n * 1e-3) / 1e9, 1) if ab else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    peak, peak_src = peaks()
+    # dslash bandwidth of the FP32 operator alone: average of launches with L2 flushed in between
+    dsl = []
+    for _ in range(20):
+        flush.zero_()
+        dsl.append(ctx.bench_dslash(tmg.PREC_F32, 1))
+    dsl_ms = statistics.median(dsl)
+    dsl_gbs = algorithmic_bytes("dslash_f32", V, 0, 0, 0) / (dsl_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": round(kernels[dom]["gbs"] / peak, 3), "peak_source": peak_src, "traffic": traffic}
+
+    line = {
+        "metric": METRIC, "value": round(t_step, 6), "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * t_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.fine == "f32" else "f32+f16",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "lattice": list(w["dims"]), "kappa": kappa,
+                   "kappa_source": kinfo.get("source"), "csw": w["csw"], "mu": w["mu"], "levels": 2,
+                   "sap_block": list(w["block"]), "aggregate": list(w["block"]), "nv": w["nv"],
+                   "fine_precision": args.fine, "tol": w["tol"], "rhs": 1, "l2": "flushed (512 MB write) between steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations": iters[-1], "refinements": stats["refinements"], "coarse_iterations": stats["coarse_iterations"],
+        "true_residual": true_res, "setup_s": round(setup_s, 3),
+        "fp64_solve_s": round(fp64_s, 4), "fp64_iterations": st64["iterations"],
+        "cg_fp64": cg,
+        "dslash_f32": {"us": round(dsl_ms * 1e3, 2), "gbs": round(dsl_gbs, 1), "frac_measured_peak": round(dsl_gbs / peak, 3),
+                       "frac_nominal_8tbs": round(dsl_gbs / 8000.0, 3)},
+        "kernels": kernels,
+        "roofline": roof,
+        "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(b_host.nbytes),
+                "d2h_bytes_per_step": int(b_host.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, kappa, float(np.mean(iters)), args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(w, kappa, gpu_iters, budget_s):
+    """The FP64 numpy oracle on the host cores: time per outer FGMRES iteration (one two-level
+    cycle + one operator application + Gram-Schmidt) measured on a bounded number of iterations,
+    times the outer iterations of the GPU solve.  The oracle's P comes from orthonormalised random
+    vectors (its setup is not part of the timed solve)."""
+    import os as _os
+    from oracle import dirac, mg, krylov
+    from synth import fields
+    cores = len(_os.sched_getaffinity(0))
+    U = fields.gauge_field(w["dims"], w["eps"], w["seed"])
+    p = dirac.Params(kappa=kappa, csw=w["csw"], mu=w["mu"], tbc=-1)
+    b = fields.gaussian_spinor(w["dims"], w["rhs_seed"])
+    mgp = mg.MGParams(block=w["block"], agg=w["block"], nv=w["nv"], coarse_m=30, coarse_rtol=5e-2)
+    H = mg.Hierarchy(U, p, mgp)
+    t0 = time.perf_counter()
+    H.set_vectors(fields.gaussian_spinor(w["dims"], w["setup_seed"], n=w["nv"]))
+    t_build = time.perf_counter() - t0
+    n_it = 1
+    t0 = time.perf_counter()
+    krylov.fgmres(H.D, b, H.cycle, m=n_it, tol=1e-30, maxiter=n_it)
+    t_it = (time.perf_counter() - t0) / n_it
+    est = t_it * gpu_iters
+    return {"value": round(est, 3), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_it} FP64 FGMRES iteration(s) with the two-level cycle on the full 16^3x32 lattice "
+                      f"({t_it:.2f} s each), scaled by the GPU solve's {gpu_iters:.0f} outer iterations; "
+                      f"coarse-operator build ({t_build:.1f} s) not included"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOAD
+    kappa, kinfo = workload_kappa(w)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(w, kappa, 10.0, args.cpu_budget)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "lattice": list(w["dims"]), "kappa": kappa, "nv": w["nv"],
+                       "tol": w["tol"]},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"] + " (10 outer iterations assumed)",
+                             "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fine", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--cg-maxiter", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=30.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * tmg.h -- C ABI of the GB300 twisted-mass DD-alpha-AMG library (libtmg.so).
+ *
+ * Operators and method follow arXiv:1710.06198 ("Multigrid accelerated simulations for Twisted
+ * Mass fermions"):
+ *   - Sec. 1.1: clover-improved Wilson operator D, twisted mass D(+-mu) = D +- i mu G5,
+ *     error propagation of the DD-alpha-AMG preconditioner (Eq. 1): SAP smoother M, aggregation
+ *     prolongation P (G5 P = P G5_c), coarse operator D_c = P^dag D P, D_c(+-mu) = D_c +- i mu G5_c,
+ *     flexible Krylov outer solver.
+ *   - Eq. 2: non-degenerate doublet D_ND(mubar, epsbar) = D x I2 + i mubar G5 x tau3 - epsbar I x tau1.
+ *   - Sec. 1.1: D^dag(mu) D(mu) solved in two steps, D(-mu) x = G5 b then D(mu) y = G5 x.
+ *
+ * Conventions (readings of what the paper leaves open):
+ *   - lattice dims {Lx, Ly, Lz, T}; lexicographic site index x + Lx*(y + Ly*(z + Lz*t));
+ *   - D_W psi(x) = (4 + m0) psi(x) - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                  + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)] + (i c_sw/32) sum_{mu!=nu} sigma_mu_nu
+ *                  (Q_mu_nu - Q_nu_mu) psi(x), with m0 = 1/(2 kappa) - 4 and a Euclidean chiral
+ *                  gamma basis in which g5 = diag(1, 1, -1, -1);
+ *   - periodic in space; the time boundary sign t_bc multiplies every hop across t = T-1 <-> 0;
+ *   - host/device vectors exchanged through this ABI are FP64 complex, interleaved (re, im), in
+ *     lexicographic site order: a fine spinor is [V][4 spins][3 colours], a gauge field is
+ *     [V][4 directions][3][3] (row-major), a coarse vector is [V_c][2 N_v] with the coarse sites in
+ *     lexicographic order of the aggregate coordinates and dofs ordered [+: 0..N_v-1, -: 0..N_v-1].
+ *
+ * Ownership and errors: the library copies what it keeps (gauge field, test vectors).  Caller
+ * buffers are only read or written during a call.  `where` selects host (TMG_HOST, pageable or
+ * pinned memory; the call copies and synchronises) or device pointers (TMG_DEVICE, memory on the
+ * context's device; the call is stream-ordered on the context stream and returns without a
+ * host synchronisation unless it has to read a scalar back).  Every call returns a tmg_status;
+ * no call aborts, traps or prints.  tmg_last_error() gives the text of the last failure.  A
+ * context is not thread-safe.
+ */
+#ifndef TMG_H
+#define TMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tmg_ctx tmg_ctx;
+
+typedef enum {
+  TMG_OK = 0,
+  TMG_ERR_ARG = -1,       /* invalid argument, unsupported geometry or size */
+  TMG_ERR_CUDA = -2,      /* a CUDA runtime call failed (text in tmg_last_error) */
+  TMG_ERR_OOM = -3,       /* device allocation failed */
+  TMG_ERR_NOCONV = -4,    /* solver hit its iteration cap; x holds the last iterate */
+  TMG_ERR_BREAKDOWN = -5, /* NaN/Inf or Krylov breakdown detected */
+  TMG_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+  TMG_ERR_STATE = -7      /* call out of order (e.g. solve before setup) */
+} tmg_status;
+
+enum { TMG_PREC_F64 = 0, TMG_PREC_F32 = 1, TMG_PREC_F16 = 2 };
+enum { TMG_HOST = 0, TMG_DEVICE = 1 };
+
+/* operators for tmg_apply */
+enum {
+  TMG_OP_D = 0,      /* y = D(mu) x                          (Sec. 1.1)            */
+  TMG_OP_DDAG = 1,   /* y = D(mu)^dag x = G5 D(-mu) G5 x     (Sec. 1.1)            */
+  TMG_OP_DND = 2,    /* y = D_ND(mubar, epsbar) x, x = [2 flavours][V][4][3] (Eq. 2) */
+  TMG_OP_HOP = 3     /* y = hopping term only (for tests and bandwidth runs)        */
+};
+
+/* Create a context for a Lx x Ly x Lz x T lattice on `device`.  `block` is the SAP block, which is
+ * also the fine-level aggregate: every dim must divide the lattice, the number of blocks along
+ * every direction must be even and >= 2, and the block volume must be a multiple of 32 and
+ * <= 256 (one CTA of one thread per site works on a block).  `stream` is a cudaStream_t (NULL: the legacy default stream).  Section 1.1 of the
+ * paper uses lattice blocks both as SAP domains and as aggregates. */
+int tmg_create(tmg_ctx **ctx, const int dims[4], const int block[4], int device, void *stream);
+int tmg_destroy(tmg_ctx *ctx);
+const char *tmg_last_error(const tmg_ctx *ctx);
+/* Library version string; needs no context. */
+const char *tmg_version(void);
+
+/* Load the gauge field U (FP64, [V][4][3][3] complex) and set the time boundary sign t_bc
+ * (+1 periodic, -1 antiperiodic).  Rebuilds the clover field on the device (Sec. 1.1: the
+ * clover-improved operator) and the FP32 / FP16 copies of links and clover. */
+int tmg_load_gauge(tmg_ctx *ctx, const double *U, int where, int t_bc);
+
+/* Operator parameters: kappa (m0 = 1/(2 kappa) - 4), c_sw, the twist mu (Sec. 1.1) and the
+ * non-degenerate doublet's mubar, epsbar (Eq. 2).  Must precede tmg_load_gauge's clover build or
+ * be followed by it: changing kappa or c_sw rebuilds the clover field if a gauge field is loaded. */
+int tmg_set_params(tmg_ctx *ctx, double kappa, double csw, double mu, double mubar, double epsbar);
+
+/* y = op x for n_rhs fine spinors ([n_rhs][V][4][3], or [n_rhs][2][V][4][3] for TMG_OP_DND) in
+ * the storage precision `prec` (inputs rounded to it; FP16 storage computes in FP32).
+ * mu_per_col (n_rhs values) overrides the twist per column; NULL uses the context's mu. */
+int tmg_apply(tmg_ctx *ctx, int op, const double *x, double *y, int n_rhs,
+              const double *mu_per_col, int prec, int where);
+
+/* ---- multigrid (Eq. 1) ---- */
+typedef struct {
+  int nv;              /* test vectors N_v (coarse dofs per site = 2 N_v); 2..32 */
+  int sap_sweeps;      /* k of Eq. 1 */
+  int sap_mr;          /* MR steps per SAP block solve */
+  int coarse_m;        /* max GMRES steps of the coarse solve (<= 64) */
+  double coarse_rtol;  /* relative residual target of the coarse solve */
+  int n_init;          /* initial SAP inverse-iteration passes of the setup */
+  int n_iter;          /* adaptive setup iterations (cycle-based) */
+  int restart;         /* outer FGMRES restart length (<= 64) */
+  int prec_fine;       /* TMG_PREC_F64 / F32 / F16 for SAP, P, P^dag inside the cycle */
+  int prec_coarse;     /* TMG_PREC_F64 / F32 for D_c and the coarse solve */
+} tmg_mg_params;
+
+/* Fill p with the defaults (nv 8, k 3, MR 4, coarse GMRES 30 / 5e-2, setup 5 + 3, restart 10,
+ * fine F32, coarse F32). */
+int tmg_mg_defaults(tmg_mg_params *p);
+
+/* Adaptive setup (Sec. 1.1 and Sec. 2): start from the caller's N_v vectors v0 ([nv][V][4][3],
+ * host or device per `where`), run n_init SAP inverse-iteration passes, build P and D_c, then
+ * n_iter cycle-based setup iterations.  With n_init = n_iter = 0 the vectors only get
+ * orthonormalised, which lets a caller impose a given P. */
+int tmg_setup(tmg_ctx *ctx, const tmg_mg_params *p, const double *v0, int where);
+
+/* Copy out the orthonormalised test vectors W ([nv][V][4][3] FP64) that define P. */
+int tmg_get_vectors(tmg_ctx *ctx, double *W, int where);
+
+/* Pieces of the cycle, each in precision `prec` (fine) or the coarse precision:
+ *   tmg_sap:      x <- k SAP sweeps on D x = b starting from the given x (Eq. 1: M);
+ *   tmg_restrict: c = P^dag r;  tmg_prolong: e = P c;
+ *   tmg_coarse_apply: y = D_c(mu) x on coarse vectors ([V_c][2 N_v]);
+ *   tmg_cycle:    z = one application of the preconditioner of Eq. 1 to r (zero start). */
+int tmg_sap(tmg_ctx *ctx, const double *b, double *x, int prec, int where);
+int tmg_restrict(tmg_ctx *ctx, const double *r, double *c, int prec, int where);
+int tmg_prolong(tmg_ctx *ctx, const double *c, double *e, int prec, int where);
+int tmg_coarse_apply(tmg_ctx *ctx, const double *x, double *y, double mu, int prec, int where);
+int tmg_cycle(tmg_ctx *ctx, const double *r, double *z, int where);
+
+/* ---- solves ---- */
+typedef struct {
+  int iterations;        /* outer FGMRES (or CG) iterations summed over restarts/refinements */
+  int refinements;       /* FP64 defect-correction restarts */
+  int coarse_iterations; /* coarse GMRES steps summed over all cycles */
+  double true_residual;  /* ||b - D x|| / ||b|| in FP64 at exit */
+  double seconds;        /* wall time of the call */
+} tmg_stats;
+
+enum {
+  TMG_SOLVE_MG_F64 = 0,   /* FGMRES + DD-alpha-AMG, everything in FP64                     */
+  TMG_SOLVE_MG_MIXED = 1, /* FP64 defect correction around FGMRES + DD-alpha-AMG in the MG   */
+                          /* params' fine/coarse precisions                                 */
+  TMG_SOLVE_CG_F64 = 2    /* CG on D D^dag in FP64 (comparator of Sec. 1.1 / Fig. 1)       */
+};
+
+/* Solve D(mu) x = b (relative FP64 residual tol) for n_rhs right-hand sides, one after another.
+ * mu_per_col may override the twist per column (the same P serves every mu, Sec. 1.1).
+ * x is an output (zero initial guess).  maxiter bounds the outer iterations. */
+int tmg_solve(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double *mu_per_col,
+              double tol, int method, int maxiter, tmg_stats *stats, int where);
+
+/* Time `n_iter` back-to-back launches of the dslash kernel (y = D x, one column, storage
+ * precision prec) on the context stream with CUDA events; writes the mean milliseconds per
+ * launch.  Inputs are the library's internal fields (random data is not needed: the timing
+ * does not depend on values). */
+int tmg_bench_dslash(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_launch);
+
+/* Kernel classes timed by tmg_profile (CUDA events around every launch of the class, on the
+ * context stream).  Not a paper quantity: measurement support. */
+enum {
+  TMG_PK_DSLASH_F64 = 0, TMG_PK_DSLASH_F32 = 1, TMG_PK_DSLASH_F16 = 2,
+  TMG_PK_SAP_F64 = 3, TMG_PK_SAP_F32 = 4, TMG_PK_SAP_F16 = 5,
+  TMG_PK_RESTRICT = 6, TMG_PK_PROLONG = 7, TMG_PK_COARSE = 8, TMG_PK_COUNT = 9
+};
+/* enable != 0: reset the records and start timing every launch of the classes above;
+ * enable == 0: stop (records are kept until the next call). */
+int tmg_profile(tmg_ctx *ctx, int enable);
+/* Launches recorded for class `kind` and their summed device time in milliseconds. */
+int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total);
+
+/* Number of CUDA kernels this context has launched so far (every launcher counts its launches;
+ * lets a caller count the kernels inside a timed region).  Not a paper quantity. */
+int tmg_launch_count(const tmg_ctx *ctx, long long *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMG_H */

@@ -1,0 +1,112 @@
+"""FP64 oracle of the hopping-parameter search (test infrastructure only).
+
+The workloads fix kappa indirectly: "kappa tuned so that sigma_min(D_W) is about a target at
+mu = 0".  sigma_min(D_W) is the smallest singular value of D_W, equal to the smallest |eigenvalue|
+of the Hermitian Q = G5 D_W (Eq. 3 uses Q = G5 D).  This module assembles D_W as a sparse matrix,
+gets min |lambda(Q)| by shift-invert Lanczos around 0 (scipy ``eigsh``, i.e. a sparse LU of Q), and
+runs the search: start at m0 = 0, step m0 down by 0.05 until sigma_min drops below the target, then
+bisect the last step until sigma_min is within +-2 % of the target (the first crossing from above).
+
+Pinned by tests/test_oracle_kappa.py: the sparse matrix equals the matrix-free operator of
+``oracle.dirac`` on random vectors, and on the free field sigma_min equals the closed form
+min_p sqrt(M(p)^2 + sum_mu sin^2 p_mu) over the allowed momenta.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import dirac
+
+
+def sparse_DW(U, p: dirac.Params, clover=None):
+    """Sparse FP64 matrix of D_W (twist excluded); dof index = 12 * lex_site + 3 * spin + colour."""
+    lat = U.shape[:4]
+    V = int(np.prod(lat))
+    if clover is None:
+        clover = dirac.clover_term(U, p.csw)
+    site = np.arange(V).reshape(lat)
+    rows, cols, vals = [], [], []
+
+    def add_blocks(row_site, col_site, blocks):
+        # blocks[V, 12, 12]
+        r = (12 * row_site.reshape(V, 1, 1) + np.arange(12).reshape(1, 12, 1)) + 0 * np.arange(12).reshape(1, 1, 12)
+        c = (12 * col_site.reshape(V, 1, 1) + np.arange(12).reshape(1, 1, 12)) + 0 * np.arange(12).reshape(1, 12, 1)
+        rows.append(r.ravel())
+        cols.append(c.ravel())
+        vals.append(blocks.ravel())
+
+    diag = clover.reshape(V, 12, 12) + (4.0 + p.m0) * np.eye(12)[None]
+    add_blocks(site, site, diag)
+    t_index = np.indices(lat)[0]
+    T = lat[0]
+    for mu in range(4):
+        Umu = U[..., mu, :, :].reshape(V, 3, 3)
+        fwd_site = dirac.shift_fwd(site[..., None, None], mu)[..., 0, 0]    # index of x + mu
+        bwd_site = dirac.shift_bwd(site[..., None, None], mu)[..., 0, 0]    # index of x - mu
+        sgn_f = np.ones(lat)
+        sgn_b = np.ones(lat)
+        if mu == 3 and p.tbc != 1:
+            sgn_f[t_index == T - 1] = p.tbc
+            sgn_b[t_index == 0] = p.tbc
+        Pm = dirac.I4 - dirac.GAMMA[mu]
+        Pp = dirac.I4 + dirac.GAMMA[mu]
+        f = -0.5 * sgn_f.reshape(V, 1, 1, 1, 1) * np.einsum("st,vab->vsatb", Pm, Umu)
+        Ub = dirac.dagger(U[..., mu, :, :])                                  # U_mu(x)^dag at x
+        Ub = dirac.shift_bwd(Ub, mu).reshape(V, 3, 3)                        # U_mu(x - mu)^dag
+        b = -0.5 * sgn_b.reshape(V, 1, 1, 1, 1) * np.einsum("st,vab->vsatb", Pp, Ub)
+        add_blocks(site, fwd_site, f.reshape(V, 12, 12))
+        add_blocks(site, bwd_site, b.reshape(V, 12, 12))
+    n = 12 * V
+    return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def sigma_min(U, p: dirac.Params, clover=None):
+    """Smallest singular value of D_W = smallest |eigenvalue| of Q = G5 D_W."""
+    D = sparse_DW(U, p, clover)
+    n = D.shape[0]
+    g5 = np.tile(np.repeat(np.diag(dirac.GAMMA5).real, 3), n // 12)
+    Q = sp.diags(g5) @ D
+    Q = ((Q + Q.getH()) * 0.5).tocsc()   # exact Hermitian form (removes rounding asymmetry)
+    lu = spla.splu(Q, permc_spec="MMD_AT_PLUS_A")
+    inv = spla.LinearOperator(Q.shape, matvec=lu.solve, dtype=np.complex128)
+    w = spla.eigsh(Q, k=1, sigma=0.0, which="LM", OPinv=inv, return_eigenvectors=False, tol=1e-10)
+    return float(np.min(np.abs(w)))
+
+
+def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, max_steps=80, log=None):
+    """First crossing from above of sigma_min(D_W(m0)) = target, to +-rel_tol.  Returns
+    (m0, sigma_min, evaluations)."""
+    clover = dirac.clover_term(U, csw)
+
+    def s(m0):
+        v = sigma_min(U, dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, tbc=tbc), clover)
+        if log is not None:
+            log.append((m0, v))
+        return v
+
+    hi, s_hi = 0.0, s(0.0)
+    if s_hi < target:
+        raise ValueError("sigma_min already below target at m0 = 0")
+    lo = hi
+    for _ in range(max_steps):
+        lo = hi - step
+        s_lo = s(lo)
+        if s_lo < target:
+            break
+        hi, s_hi = lo, s_lo
+    else:
+        raise ValueError("no crossing found")
+    if abs(s_lo - target) <= rel_tol * target:
+        return lo, s_lo, len(log) if log is not None else None
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        s_mid = s(mid)
+        if abs(s_mid - target) <= rel_tol * target:
+            return mid, s_mid, len(log) if log is not None else None
+        if s_mid < target:
+            lo = mid
+        else:
+            hi = mid
+    raise ValueError("bisection did not reach the tolerance")

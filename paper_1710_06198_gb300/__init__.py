@@ -1,0 +1,295 @@
+"""Python binding of libtmg, the GB300 twisted-mass DD-alpha-AMG library (arXiv:1710.06198).
+
+Argument marshalling only: every operation runs in the library's CUDA kernels through the C ABI
+declared in ``include/tmg.h``.  Arrays are complex128 in lexicographic site order
+(``[..., T, Z, Y, X, 4, 3]`` for spinors, ``[T, Z, Y, X, 4, 3, 3]`` for links, ``[..., Vc, 2 Nv]``
+for coarse vectors).  numpy arrays are passed as host memory; CUDA torch tensors (complex128) are
+passed as device memory on the context's device, and the call is ordered on the context stream.
+
+The library is loaded from this directory (``libtmg.so``, built by ``build.py``).  If it is
+missing, :func:`lib` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmg.so")
+
+PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
+HOST, DEVICE = 0, 1
+OP_D, OP_DDAG, OP_DND, OP_HOP = 0, 1, 2, 3
+SOLVE_MG_F64, SOLVE_MG_MIXED, SOLVE_CG_F64 = 0, 1, 2
+STATUS = {0: "TMG_OK", -1: "TMG_ERR_ARG", -2: "TMG_ERR_CUDA", -3: "TMG_ERR_OOM", -4: "TMG_ERR_NOCONV",
+          -5: "TMG_ERR_BREAKDOWN", -6: "TMG_ERR_TIMEOUT", -7: "TMG_ERR_STATE"}
+
+_lib = None
+
+
+class TmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int), ("sap_sweeps", ctypes.c_int), ("sap_mr", ctypes.c_int),
+                ("coarse_m", ctypes.c_int), ("coarse_rtol", ctypes.c_double), ("n_init", ctypes.c_int),
+                ("n_iter", ctypes.c_int), ("restart", ctypes.c_int), ("prec_fine", ctypes.c_int),
+                ("prec_coarse", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("coarse_iterations", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "tmg_create": [ctypes.POINTER(_P), _P, _P, _I, _P],
+    "tmg_destroy": [_P],
+    "tmg_last_error": [_P],
+    "tmg_version": [],
+    "tmg_load_gauge": [_P, _P, _I, _I],
+    "tmg_set_params": [_P, _D, _D, _D, _D, _D],
+    "tmg_apply": [_P, _I, _P, _P, _I, _P, _I, _I],
+    "tmg_mg_defaults": [ctypes.POINTER(MGParams)],
+    "tmg_setup": [_P, ctypes.POINTER(MGParams), _P, _I],
+    "tmg_get_vectors": [_P, _P, _I],
+    "tmg_sap": [_P, _P, _P, _I, _I],
+    "tmg_restrict": [_P, _P, _P, _I, _I],
+    "tmg_prolong": [_P, _P, _P, _I, _I],
+    "tmg_coarse_apply": [_P, _P, _P, _D, _I, _I],
+    "tmg_cycle": [_P, _P, _P, _I],
+    "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
+    "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
+    "tmg_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "tmg_profile": [_P, _I],
+    "tmg_profile_read": [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)],
+}
+
+PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
+                 "prolong", "coarse_apply"]
+
+
+def lib():
+    """Load libtmg.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libtmg.so not built ({LIB_PATH}); run paper_1710_06198_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("tmg_last_error", "tmg_version") else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _is_torch_cuda(a):
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a):
+    """(pointer, where) of a complex128 numpy array or CUDA torch tensor."""
+    if _is_torch_cuda(a):
+        import torch
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise TypeError("device arrays must be contiguous complex128 torch tensors")
+        return ctypes.c_void_p(a.data_ptr()), DEVICE
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError("host arrays must be C-contiguous complex128 numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+def _empty_like(a, shape):
+    if _is_torch_cuda(a):
+        import torch
+        return torch.empty(shape, dtype=torch.complex128, device=a.device)
+    return np.empty(shape, dtype=np.complex128)
+
+
+def _same_where(*arrays):
+    wh = {_ptr(a)[1] for a in arrays}
+    if len(wh) != 1:
+        raise TypeError("mixing host and device arrays in one call")
+
+
+@dataclass
+class OperatorParams:
+    kappa: float
+    csw: float = 0.0
+    mu: float = 0.0
+    mubar: float = 0.0
+    epsbar: float = 0.0
+
+
+class Context:
+    """One lattice on one GPU: gauge field, operator parameters and multigrid hierarchy."""
+
+    def __init__(self, dims, block, device=0, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.block = tuple(int(b) for b in block)
+        self.lat = (self.dims[3], self.dims[2], self.dims[1], self.dims[0])
+        self.V = int(np.prod(self.dims))
+        self.coarse_lat = tuple(self.lat[i] // self.block[3 - i] for i in range(4))
+        self.nv = None
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.dims)
+        b = (ctypes.c_int * 4)(*self.block)
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        rc = lib().tmg_create(ctypes.byref(h), d, b, int(device), st)
+        if rc != 0:
+            raise TmgError(rc, "tmg_create rejected the geometry or device")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TmgError(rc, lib().tmg_last_error(self._h).decode())
+
+    # ---- operator data
+    def load_gauge(self, U, t_bc=-1):
+        p, wh = _ptr(U)
+        self._check(lib().tmg_load_gauge(self._h, p, wh, int(t_bc)))
+
+    def set_params(self, kappa, csw=0.0, mu=0.0, mubar=0.0, epsbar=0.0):
+        self._check(lib().tmg_set_params(self._h, kappa, csw, mu, mubar, epsbar))
+
+    def apply(self, x, op=OP_D, prec=PREC_F64, mu_per_col=None):
+        """y = op x for x[..., T, Z, Y, X, 4, 3] (TMG_OP_DND: x[..., 2, T, Z, Y, X, 4, 3])."""
+        per = 2 * self.V * 12 if op == OP_DND else self.V * 12
+        n = int(np.prod(x.shape)) // per
+        y = _empty_like(x, x.shape)
+        px, wh = _ptr(x)
+        py, _ = _ptr(y)
+        mp = None
+        if mu_per_col is not None:
+            mu_arr = np.ascontiguousarray(np.asarray(mu_per_col, dtype=np.float64).reshape(n))
+            mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
+        self._check(lib().tmg_apply(self._h, op, px, py, n, mp, prec, wh))
+        return y
+
+    # ---- multigrid
+    @staticmethod
+    def mg_defaults():
+        p = MGParams()
+        lib().tmg_mg_defaults(ctypes.byref(p))
+        return p
+
+    def setup(self, v0, params: MGParams):
+        _same_where(v0)
+        p, wh = _ptr(v0)
+        self._check(lib().tmg_setup(self._h, ctypes.byref(params), p, wh))
+        self.nv = params.nv
+
+    def get_vectors(self, like=None):
+        shape = (self.nv,) + self.lat + (4, 3)
+        W = _empty_like(like, shape) if like is not None else np.empty(shape, np.complex128)
+        p, wh = _ptr(W)
+        self._check(lib().tmg_get_vectors(self._h, p, wh))
+        return W
+
+    def sap(self, b, x0, prec=PREC_F64):
+        x = x0.copy() if not _is_torch_cuda(x0) else x0.clone()
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        self._check(lib().tmg_sap(self._h, pb, px, prec, wh))
+        return x
+
+    def restrict(self, r, prec=PREC_F64):
+        c = _empty_like(r, self.coarse_lat + (2 * self.nv,))
+        pr, wh = _ptr(r)
+        pc, _ = _ptr(c)
+        self._check(lib().tmg_restrict(self._h, pr, pc, prec, wh))
+        return c
+
+    def prolong(self, c, prec=PREC_F64):
+        e = _empty_like(c, self.lat + (4, 3))
+        pc, wh = _ptr(c)
+        pe, _ = _ptr(e)
+        self._check(lib().tmg_prolong(self._h, pc, pe, prec, wh))
+        return e
+
+    def coarse_apply(self, x, mu=0.0, prec=PREC_F64):
+        y = _empty_like(x, x.shape)
+        px, wh = _ptr(x)
+        py, _ = _ptr(y)
+        self._check(lib().tmg_coarse_apply(self._h, px, py, float(mu), prec, wh))
+        return y
+
+    def cycle(self, r):
+        z = _empty_like(r, r.shape)
+        pr, wh = _ptr(r)
+        pz, _ = _ptr(z)
+        self._check(lib().tmg_cycle(self._h, pr, pz, wh))
+        return z
+
+    def solve(self, b, tol=1e-10, method=SOLVE_MG_MIXED, maxiter=10000, mu_per_col=None, out=None,
+              check=True):
+        n = int(np.prod(b.shape)) // (self.V * 12)
+        x = _empty_like(b, b.shape) if out is None else out
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        st = Stats()
+        mp = None
+        if mu_per_col is not None:
+            mu_arr = np.ascontiguousarray(np.asarray(mu_per_col, dtype=np.float64).reshape(n))
+            mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
+        rc = lib().tmg_solve(self._h, pb, px, n, mp, float(tol), int(method), int(maxiter), ctypes.byref(st), wh)
+        if check:
+            self._check(rc)
+        return x, st.as_dict()
+
+    def bench_dslash(self, prec=PREC_F32, n_iter=100):
+        ms = ctypes.c_double()
+        self._check(lib().tmg_bench_dslash(self._h, prec, n_iter, ctypes.byref(ms)))
+        return ms.value
+
+
+def profile(ctx: "Context", enable: bool):
+    ctx._check(lib().tmg_profile(ctx._h, int(bool(enable))))
+
+
+def profile_read(ctx: "Context"):
+    """{kind: (launches, total ms)} of the kernel classes timed since profile(ctx, True)."""
+    out = {}
+    for k, name in enumerate(PROFILE_KINDS):
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        ctx._check(lib().tmg_profile_read(ctx._h, k, ctypes.byref(n), ctypes.byref(ms)))
+        out[name] = (n.value, ms.value)
+    return out
+
+
+def launch_count(ctx: "Context"):
+    n = ctypes.c_longlong()
+    ctx._check(lib().tmg_launch_count(ctx._h, ctypes.byref(n)))
+    return n.value
+
+
+def version():
+    return lib().tmg_version().decode()

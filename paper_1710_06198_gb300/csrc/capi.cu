@@ -1,0 +1,460 @@
+// C ABI of libtmg (declared in include/tmg.h).  Every entry point validates its arguments, runs
+// the work on the context stream and converts exceptions from the launchers into status codes.
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "tmg_host.h"
+#include "solver.h"
+
+using namespace tmg;
+
+struct tmg_ctx {
+  Ctx c;
+  tmg::Field fin, fout;   // per-call conversion buffers
+};
+
+namespace {
+
+int fail(tmg_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->c.err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(tmg_ctx* ctx, F&& f) {
+  if (!ctx) return TMG_ERR_ARG;
+  try {
+    TMG_CUDA(cudaSetDevice(ctx->c.device));
+    return f();
+  } catch (const tmg::Error& e) {
+    return fail(ctx, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, TMG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(ctx, TMG_ERR_CUDA, e.what());
+  }
+}
+
+bool valid_prec(int p) { return p == TMG_PREC_F64 || p == TMG_PREC_F32 || p == TMG_PREC_F16; }
+bool valid_where(int w) { return w == TMG_HOST || w == TMG_DEVICE; }
+
+// Bring an FP64 lexicographic array (host or device) onto the device; returns a device pointer.
+const double* stage_in(Ctx& c, DBuf& stage, const double* p, size_t n_doubles, int where) {
+  if (where == TMG_DEVICE) return p;
+  stage.alloc(n_doubles * sizeof(double));
+  TMG_CUDA(cudaMemcpyAsync(stage.p, p, n_doubles * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  return stage.as<double>();
+}
+
+double* stage_out_ptr(Ctx& c, DBuf& stage, double* p, size_t n_doubles, int where) {
+  if (where == TMG_DEVICE) return p;
+  stage.alloc(n_doubles * sizeof(double));
+  return stage.as<double>();
+}
+
+void stage_out_finish(Ctx& c, DBuf& stage, double* p, size_t n_doubles, int where) {
+  if (where == TMG_DEVICE) return;
+  TMG_CUDA(cudaMemcpyAsync(p, stage.p, n_doubles * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+int storage_of(int prec) { return prec == TMG_PREC_F64 ? TMG_PREC_F64 : TMG_PREC_F32; }
+
+}  // namespace
+
+extern "C" {
+
+const char* tmg_version(void) { return "tmg 0.1 (sm_103a)"; }
+
+const char* tmg_last_error(const tmg_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int tmg_create(tmg_ctx** out, const int dims[4], const int block[4], int device, void* stream) {
+  if (!out || !dims || !block) return TMG_ERR_ARG;
+  *out = nullptr;
+  Geom g{};
+  long long V = 1;
+  int VB = 1, nblk = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    if (dims[mu] <= 0 || block[mu] <= 0 || dims[mu] % block[mu]) return TMG_ERR_ARG;
+    const int nb = dims[mu] / block[mu];
+    if (nb < 2 || nb % 2) return TMG_ERR_ARG;
+    g.L[mu] = dims[mu];
+    g.B[mu] = block[mu];
+    g.NB[mu] = nb;
+    V *= dims[mu];
+    VB *= block[mu];
+    nblk *= nb;
+  }
+  if (V > (1LL << 30) / 12 || VB % 32 || VB > 256) return TMG_ERR_ARG;
+  g.ls[0] = 1; g.bs[0] = 1;
+  for (int mu = 1; mu < 4; mu++) {
+    g.ls[mu] = g.ls[mu - 1] * g.B[mu - 1];
+    g.bs[mu] = g.bs[mu - 1] * g.NB[mu - 1];
+  }
+  g.VB = VB;
+  g.nblk = nblk;
+  g.V = (int)V;
+  g.tbc = -1;
+  tmg_ctx* ctx = new (std::nothrow) tmg_ctx();
+  if (!ctx) return TMG_ERR_OOM;
+  ctx->c.device = device;
+  ctx->c.stream = (cudaStream_t)stream;
+  ctx->c.g = g;
+  tmg_mg_defaults(&ctx->c.mg);
+  const int rc = guarded(ctx, [&]() -> int {
+    int sms = 0;
+    TMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    ctx->c.sms = sms > 0 ? sms : 152;
+    return TMG_OK;
+  });
+  if (rc != TMG_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return TMG_OK;
+}
+
+int tmg_destroy(tmg_ctx* ctx) {
+  if (!ctx) return TMG_ERR_ARG;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  delete ctx;
+  return TMG_OK;
+}
+
+int tmg_set_params(tmg_ctx* ctx, double kappa, double csw, double mu, double mubar, double epsbar) {
+  return guarded(ctx, [&]() -> int {
+    if (!(kappa > 0.0) || !std::isfinite(csw) || !std::isfinite(mu) || !std::isfinite(mubar) || !std::isfinite(epsbar))
+      return fail(ctx, TMG_ERR_ARG, "invalid operator parameters");
+    Ctx& c = ctx->c;
+    const bool rebuild = c.gauge_loaded && (kappa != c.kappa || csw != c.csw);
+    c.kappa = kappa;
+    c.csw = csw;
+    c.mu = mu;
+    c.mubar = mubar;
+    c.epsbar = epsbar;
+    if (rebuild) {
+      build_clover(c);
+      convert_op_precisions(c);
+      c.mg_ready = false;
+    }
+    return TMG_OK;
+  });
+}
+
+int tmg_load_gauge(tmg_ctx* ctx, const double* U, int where, int t_bc) {
+  return guarded(ctx, [&]() -> int {
+    if (!U || !valid_where(where) || (t_bc != 1 && t_bc != -1)) return fail(ctx, TMG_ERR_ARG, "tmg_load_gauge: bad argument");
+    Ctx& c = ctx->c;
+    c.g.tbc = t_bc;
+    const size_t n = (size_t)c.g.V * 72;
+    const double* d = stage_in(c, c.U_lex, U, n, where);
+    gauge_lex_to_internal(c, d);
+    build_clover(c);
+    convert_op_precisions(c);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    c.U_lex.release();
+    c.gauge_loaded = true;
+    c.mg_ready = false;
+    return TMG_OK;
+  });
+}
+
+int tmg_apply(tmg_ctx* ctx, int op, const double* x, double* y, int n_rhs, const double* mu_per_col, int prec,
+              int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!x || !y || n_rhs <= 0 || !valid_prec(prec) || !valid_where(where) || op < 0 || op > 3)
+      return fail(ctx, TMG_ERR_ARG, "tmg_apply: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_apply: no gauge field loaded");
+    const int sp = storage_of(prec);
+    const int nfl = op == TMG_OP_DND ? 2 : 1;
+    const size_t col = (size_t)24 * c.g.V;  // doubles per flavour column
+    ctx->fin.create(c.g, sp, nfl);
+    ctx->fout.create(c.g, sp, nfl);
+    for (int j = 0; j < n_rhs; j++) {
+      const size_t off = (size_t)j * nfl * col;
+      const double* xd = x + off;
+      if (where == TMG_HOST) {
+        c.stage_a.alloc(nfl * col * sizeof(double));
+        TMG_CUDA(cudaMemcpyAsync(c.stage_a.p, x + off, nfl * col * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        xd = c.stage_a.as<double>();
+      }
+      for (int f = 0; f < nfl; f++) spinor_from_lex(c, xd + f * col, ctx->fin.col(c.g, f), sp);
+      const double mu = mu_per_col ? mu_per_col[j] : c.mu;
+      if (op == TMG_OP_D) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 0);
+      else if (op == TMG_OP_DDAG) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 1);
+      else if (op == TMG_OP_HOP) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 2, 0);
+      else dslash_nd(c, prec, ctx->fout.buf.p, ctx->fin.buf.p);
+      double* yd = where == TMG_DEVICE ? y + off : nullptr;
+      if (where == TMG_HOST) {
+        c.stage_b.alloc(nfl * col * sizeof(double));
+        yd = c.stage_b.as<double>();
+      }
+      for (int f = 0; f < nfl; f++) spinor_to_lex(c, ctx->fout.col(c.g, f), sp, yd + f * col);
+      if (where == TMG_HOST) {
+        TMG_CUDA(cudaMemcpyAsync(y + off, yd, nfl * col * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        TMG_CUDA(cudaStreamSynchronize(c.stream));
+      }
+    }
+    return TMG_OK;
+  });
+}
+
+int tmg_bench_dslash(tmg_ctx* ctx, int prec, int n_iter, double* ms) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!ms || n_iter <= 0 || !valid_prec(prec)) return fail(ctx, TMG_ERR_ARG, "tmg_bench_dslash: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_bench_dslash: no gauge field loaded");
+    const int sp = storage_of(prec);
+    ctx->fin.create(c.g, sp, 1);
+    ctx->fout.create(c.g, sp, 1);
+    blas_zero(c, ctx->fin.buf.p, sp, (size_t)12 * c.g.V);
+    for (int i = 0; i < 3; i++) dslash(c, prec, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
+    cudaEvent_t e0, e1;
+    TMG_CUDA(cudaEventCreate(&e0));
+    TMG_CUDA(cudaEventCreate(&e1));
+    TMG_CUDA(cudaEventRecord(e0, c.stream));
+    for (int i = 0; i < n_iter; i++) dslash(c, prec, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
+    TMG_CUDA(cudaEventRecord(e1, c.stream));
+    TMG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    TMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / n_iter;
+    return TMG_OK;
+  });
+}
+
+int tmg_profile(tmg_ctx* ctx, int enable) {
+  return guarded(ctx, [&]() -> int {
+    TMG_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    ctx->c.prof.reset();
+    ctx->c.prof.on = enable != 0;
+    return TMG_OK;
+  });
+}
+
+int tmg_profile_read(tmg_ctx* ctx, int kind, long long* count, double* ms_total) {
+  return guarded(ctx, [&]() -> int {
+    if (kind < 0 || kind >= PK_COUNT || !count || !ms_total) return fail(ctx, TMG_ERR_ARG, "tmg_profile_read: bad argument");
+    TMG_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    double t = 0.0;
+    for (auto& p : ctx->c.prof.recs[kind]) {
+      float ms = 0.f;
+      TMG_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+      t += ms;
+    }
+    *count = (long long)ctx->c.prof.recs[kind].size();
+    *ms_total = t;
+    return TMG_OK;
+  });
+}
+
+int tmg_launch_count(const tmg_ctx* ctx, long long* n) {
+  if (!ctx || !n) return TMG_ERR_ARG;
+  *n = ctx->c.launches;
+  return TMG_OK;
+}
+
+int tmg_mg_defaults(tmg_mg_params* p) {
+  if (!p) return TMG_ERR_ARG;
+  p->nv = 8;
+  p->sap_sweeps = 3;
+  p->sap_mr = 4;
+  p->coarse_m = 30;
+  p->coarse_rtol = 5e-2;
+  p->n_init = 5;
+  p->n_iter = 3;
+  p->restart = 10;
+  p->prec_fine = TMG_PREC_F32;
+  p->prec_coarse = TMG_PREC_F32;
+  return TMG_OK;
+}
+
+int tmg_setup(tmg_ctx* ctx, const tmg_mg_params* p, const double* v0, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!p || !v0 || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_setup: bad argument");
+    if (p->nv < 2 || p->nv > 32 || p->sap_sweeps < 0 || p->sap_mr < 0 || p->coarse_m < 1 || p->coarse_m > 64 ||
+        p->restart < 1 || p->restart > 64 || p->n_init < 0 || p->n_iter < 0 || !valid_prec(p->prec_fine) ||
+        (p->prec_coarse != TMG_PREC_F64 && p->prec_coarse != TMG_PREC_F32) || !(p->coarse_rtol >= 0.0))
+      return fail(ctx, TMG_ERR_ARG, "tmg_setup: invalid multigrid parameters");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_setup: no gauge field loaded");
+    c.mg = *p;
+    const size_t n = (size_t)p->nv * 24 * c.g.V;
+    const double* d = stage_in(c, c.stage_a, v0, n, where);
+    mg_setup(c, d);
+    if (where == TMG_HOST) c.stage_a.release();
+    return TMG_OK;
+  });
+}
+
+int tmg_get_vectors(tmg_ctx* ctx, double* W, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!W || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_get_vectors: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_get_vectors: no setup");
+    const size_t col = (size_t)24 * c.g.V;
+    const size_t n = col * c.cl.nv;
+    double* d = stage_out_ptr(c, c.stage_b, W, n, where);
+    for (int j = 0; j < c.cl.nv; j++)
+      spinor_to_lex(c, c.cl.W64.as<double2>() + (size_t)j * 12 * c.g.V, TMG_PREC_F64, d + j * col);
+    stage_out_finish(c, c.stage_b, W, n, where);
+    return TMG_OK;
+  });
+}
+
+// Fine vector in -> internal field (F64 or F32 storage)
+static void fine_in(tmg_ctx* ctx, const double* x, int where, tmg::Field& f, int sp) {
+  Ctx& c = ctx->c;
+  const size_t col = (size_t)24 * c.g.V;
+  const double* d = stage_in(c, c.stage_a, x, col, where);
+  f.create(c.g, sp, 1);
+  spinor_from_lex(c, d, f.buf.p, sp);
+}
+
+static void fine_out(tmg_ctx* ctx, const tmg::Field& f, int sp, double* y, int where) {
+  Ctx& c = ctx->c;
+  const size_t col = (size_t)24 * c.g.V;
+  double* d = stage_out_ptr(c, c.stage_b, y, col, where);
+  spinor_to_lex(c, f.buf.p, sp, d);
+  stage_out_finish(c, c.stage_b, y, col, where);
+}
+
+int tmg_sap(tmg_ctx* ctx, const double* b, double* x, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || !valid_prec(prec) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_sap: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_sap: no gauge field loaded");
+    const int sp = storage_of(prec);
+    fine_in(ctx, b, where, ctx->fin, sp);
+    fine_in(ctx, x, where, ctx->fout, sp);
+    tmg::Field r;
+    r.create(c.g, sp, 1);
+    sap_sweeps(c, prec, ctx->fout.buf.p, ctx->fin.buf.p, r.buf.p, c.mu, c.mg.sap_sweeps);
+    fine_out(ctx, ctx->fout, sp, x, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_restrict(tmg_ctx* ctx, const double* r, double* cv, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!r || !cv || !valid_prec(prec) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_restrict: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_restrict: no setup");
+    const int sp = storage_of(prec);
+    fine_in(ctx, r, where, ctx->fin, sp);
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    tmg::CField out;
+    out.create(TMG_PREC_F64, n);
+    restrict_(c, prec, ctx->fin.buf.p, out.buf.p, TMG_PREC_F64);
+    double* d = stage_out_ptr(c, c.stage_b, cv, 2 * n, where);
+    blas_copy(c, out.buf.p, d, TMG_PREC_F64, n);
+    stage_out_finish(c, c.stage_b, cv, 2 * n, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_prolong(tmg_ctx* ctx, const double* cv, double* e, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!cv || !e || !valid_prec(prec) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_prolong: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_prolong: no setup");
+    const int sp = storage_of(prec);
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, cv, 2 * n, where);
+    ctx->fout.create(c.g, sp, 1);
+    prolong(c, prec, d, TMG_PREC_F64, ctx->fout.buf.p, 0);
+    fine_out(ctx, ctx->fout, sp, e, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_coarse_apply(tmg_ctx* ctx, const double* x, double* y, double mu, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!x || !y || (prec != TMG_PREC_F64 && prec != TMG_PREC_F32) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_coarse_apply: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_coarse_apply: no setup");
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, x, 2 * n, where);
+    tmg::CField xi, yo;
+    xi.create(prec, n);
+    yo.create(prec, n);
+    convert_field(c, d, TMG_PREC_F64, xi.buf.p, prec, n);
+    coarse_apply(c, prec, xi.buf.p, yo.buf.p, mu);
+    double* o = stage_out_ptr(c, c.stage_b, y, 2 * n, where);
+    convert_field(c, yo.buf.p, prec, o, TMG_PREC_F64, n);
+    stage_out_finish(c, c.stage_b, y, 2 * n, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_cycle(tmg_ctx* ctx, const double* r, double* z, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!r || !z || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_cycle: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_cycle: no setup");
+    const int sp = storage_of(c.mg.prec_fine);
+    fine_in(ctx, r, where, ctx->fin, sp);
+    ctx->fout.create(c.g, sp, 1);
+    mg_cycle(c, ctx->fin.buf.p, ctx->fout.buf.p, c.mu);
+    fine_out(ctx, ctx->fout, sp, z, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double* mu_per_col, double tol, int method,
+              int maxiter, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 2)
+      return fail(ctx, TMG_ERR_ARG, "tmg_solve: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no gauge field loaded");
+    if (method != TMG_SOLVE_CG_F64 && !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no multigrid setup");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    tmg_stats acc{};
+    int rc = TMG_OK;
+    for (int j = 0; j < n_rhs; j++) {
+      const double mu = mu_per_col ? mu_per_col[j] : c.mu;
+      tmg::Field bf, xf;
+      bf.create(c.g, TMG_PREC_F64, 1);
+      const double* bd = b + j * col;
+      if (where == TMG_HOST) {
+        c.stage_a.alloc(col * sizeof(double));
+        TMG_CUDA(cudaMemcpyAsync(c.stage_a.p, b + j * col, col * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        bd = c.stage_a.as<double>();
+      }
+      spinor_from_lex(c, bd, bf.buf.p, TMG_PREC_F64);
+      xf.create(c.g, TMG_PREC_F64, 1);
+      SolveStats st{};
+      const int r = solve_one(c, method, bf.buf.p, xf.buf.p, mu, tol, maxiter, st);
+      if (r != TMG_OK && rc == TMG_OK) rc = r;
+      acc.iterations += st.iterations;
+      acc.refinements += st.refinements;
+      acc.coarse_iterations += st.coarse_iterations;
+      acc.true_residual = std::max(acc.true_residual, st.true_residual);
+      double* out = where == TMG_DEVICE ? x + j * col : nullptr;
+      if (where == TMG_HOST) {
+        c.stage_b.alloc(col * sizeof(double));
+        out = c.stage_b.as<double>();
+      }
+      spinor_to_lex(c, xf.buf.p, TMG_PREC_F64, out);
+      if (where == TMG_HOST) {
+        TMG_CUDA(cudaMemcpyAsync(x + j * col, out, col * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      }
+    }
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = acc;
+    if (rc != TMG_OK && c.err.empty()) c.err = "solver did not converge";
+    return rc;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,421 @@
+// Field layout conversion, clover construction and complex BLAS kernels of libtmg.
+#include <algorithm>
+#include <cmath>
+
+#include "tmg_host.h"
+
+namespace tmg {
+
+static inline int grid_for(const Ctx& c, size_t n, int threads = 256) {
+  size_t b = (n + threads - 1) / threads;
+  size_t cap = (size_t)c.sms * 16;
+  return (int)std::max<size_t>(1, std::min(b, cap));
+}
+
+// ------------------------------------------------------------------ gauge field
+// lex [V][4][9] complex -> internal F64 [4][9][V]
+__global__ void k_gauge_lex_to_f64(Geom g, const double2* __restrict__ lex, double2* __restrict__ out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    for (int k = 0; k < 36; k++) out[(size_t)k * g.V + s] = lex[(size_t)i * 36 + k];
+  }
+}
+
+void gauge_lex_to_internal(Ctx& c, const double* lex_dev) {
+  c.op[0].U.alloc((size_t)36 * c.g.V * sizeof(double2));
+  ++c.launches, k_gauge_lex_to_f64<<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, c.op[0].U.as<double2>());
+  TMG_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ clover
+// Leaves of the clover, all counter-clockwise in the (mu, nu) plane, ending at x.
+struct M3 { cpx<double> m[9]; };
+
+__device__ __forceinline__ M3 m3_load(const Geom& g, const double2* U, int s, int mu) {
+  M3 r;
+  for (int k = 0; k < 9; k++) { double2 v = U[(size_t)(mu * 9 + k) * g.V + s]; r.m[k] = {v.x, v.y}; }
+  return r;
+}
+__device__ __forceinline__ M3 m3_mul(const M3& a, const M3& b) {
+  M3 r;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      cpx<double> acc = mk(0.0, 0.0);
+      for (int k = 0; k < 3; k++) acc = acc + a.m[i * 3 + k] * b.m[k * 3 + j];
+      r.m[i * 3 + j] = acc;
+    }
+  return r;
+}
+__device__ __forceinline__ M3 m3_dag(const M3& a) {
+  M3 r;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) r.m[i * 3 + j] = conj(a.m[j * 3 + i]);
+  return r;
+}
+__device__ __forceinline__ M3 m3_add(const M3& a, const M3& b) {
+  M3 r;
+  for (int k = 0; k < 9; k++) r.m[k] = a.m[k] + b.m[k];
+  return r;
+}
+
+__device__ __forceinline__ int step(const Geom& g, int s, int mu, int dir) {
+  SiteCoord sc = decode_site(g, s);
+  return dir > 0 ? nbr_fwd(g, sc, mu) : nbr_bwd(g, sc, mu);
+}
+
+// sigma_mu_nu restricted to chirality chi (2x2), for mu < nu, in the chiral basis:
+// spatial (j,k): -eps_jkl s_l for both chiralities; (k,t): +s_k for chi = 0, -s_k for chi = 1.
+__device__ __forceinline__ void sigma_block(int mu, int nu, int chi, cpx<double> sg[4]) {
+  int l;
+  double sign;
+  if (nu == 3) { l = mu; sign = chi == 0 ? 1.0 : -1.0; }
+  else {
+    l = 3 - mu - nu;                               // the remaining spatial direction
+    const double eps = (mu == 0 && nu == 1) ? 1.0 : (mu == 0 && nu == 2) ? -1.0 : 1.0;  // eps_{mu nu l}
+    sign = -eps;
+  }
+  // Pauli matrix s_l (l = 0, 1, 2 -> s1, s2, s3)
+  cpx<double> p[4];
+  if (l == 0) { p[0] = mk(0., 0.); p[1] = mk(1., 0.); p[2] = mk(1., 0.); p[3] = mk(0., 0.); }
+  else if (l == 1) { p[0] = mk(0., 0.); p[1] = mk(0., -1.); p[2] = mk(0., 1.); p[3] = mk(0., 0.); }
+  else { p[0] = mk(1., 0.); p[1] = mk(0., 0.); p[2] = mk(0., 0.); p[3] = mk(-1., 0.); }
+  for (int k = 0; k < 4; k++) sg[k] = sign * p[k];
+}
+
+// A(x) = (4 + m0) + (i c_sw / 16) sum_{mu<nu} sigma_mu_nu (x) (Q_mu_nu - Q_mu_nu^dag)
+// (equal to the sum over all ordered pairs with 1/32, since Q_nu_mu = Q_mu_nu^dag).
+__global__ void k_clover_build(Geom g, const double2* __restrict__ U, double diag, double csw,
+                               double2* __restrict__ A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  cpx<double> blk[2][36];  // full 6x6 per chirality
+  for (int chi = 0; chi < 2; chi++)
+    for (int k = 0; k < 36; k++) blk[chi][k] = mk(0.0, 0.0);
+  if (csw != 0.0) {
+    for (int mu = 0; mu < 4; mu++) {
+      for (int nu = mu + 1; nu < 4; nu++) {
+        const int xpm = step(g, s, mu, +1), xpn = step(g, s, nu, +1);
+        const int xmm = step(g, s, mu, -1), xmn = step(g, s, nu, -1);
+        const int xmm_pn = step(g, xmm, nu, +1), xmm_mn = step(g, xmm, nu, -1);
+        const int xpm_mn = step(g, xpm, nu, -1);
+        const M3 Um = m3_load(g, U, s, mu), Un = m3_load(g, U, s, nu);
+        const M3 Un_pm = m3_load(g, U, xpm, nu), Um_pn = m3_load(g, U, xpn, mu);
+        const M3 Um_mm = m3_load(g, U, xmm, mu), Un_mm = m3_load(g, U, xmm, nu);
+        const M3 Um_mm_pn = m3_load(g, U, xmm_pn, mu);
+        const M3 Um_mm_mn = m3_load(g, U, xmm_mn, mu), Un_mm_mn = m3_load(g, U, xmm_mn, nu);
+        const M3 Um_mn = m3_load(g, U, xmn, mu), Un_mn = m3_load(g, U, xmn, nu);
+        const M3 Un_pm_mn = m3_load(g, U, xpm_mn, nu);
+        M3 q = m3_mul(m3_mul(m3_mul(Um, Un_pm), m3_dag(Um_pn)), m3_dag(Un));
+        q = m3_add(q, m3_mul(m3_mul(m3_mul(Un, m3_dag(Um_mm_pn)), m3_dag(Un_mm)), Um_mm));
+        q = m3_add(q, m3_mul(m3_mul(m3_mul(m3_dag(Um_mm), m3_dag(Un_mm_mn)), Um_mm_mn), Un_mn));
+        q = m3_add(q, m3_mul(m3_mul(m3_mul(m3_dag(Un_mn), Um_mn), Un_pm_mn), m3_dag(Um)));
+        // F = Q - Q^dag, then i c_sw / 16 * F
+        cpx<double> f[9];
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) {
+            cpx<double> v = q.m[a * 3 + b] - conj(q.m[b * 3 + a]);
+            f[a * 3 + b] = mul_i((csw / 16.0) * v);
+          }
+        for (int chi = 0; chi < 2; chi++) {
+          cpx<double> sg[4];
+          sigma_block(mu, nu, chi, sg);
+          for (int si = 0; si < 2; si++)
+            for (int ti = 0; ti < 2; ti++)
+              for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                  const int i = si * 3 + a, j = ti * 3 + b;
+                  blk[chi][i * 6 + j] = blk[chi][i * 6 + j] + sg[si * 2 + ti] * f[a * 3 + b];
+                }
+        }
+      }
+    }
+  }
+  for (int chi = 0; chi < 2; chi++) {
+    double v[36];
+    for (int i = 0; i < 6; i++) v[i] = diag + blk[chi][i * 6 + i].re;
+    for (int i = 1; i < 6; i++)
+      for (int j = 0; j < i; j++) {
+        const int t = 6 + 2 * tri_index(i, j);
+        v[t] = blk[chi][i * 6 + j].re;
+        v[t + 1] = blk[chi][i * 6 + j].im;
+      }
+    for (int k = 0; k < 18; k++) A[(size_t)(chi * 18 + k) * g.V + s] = make_double2(v[2 * k], v[2 * k + 1]);
+  }
+}
+
+void build_clover(Ctx& c) {
+  c.op[0].A.alloc((size_t)36 * c.g.V * sizeof(double2));
+  const double m0 = 1.0 / (2.0 * c.kappa) - 4.0;
+  ++c.launches, k_clover_build<<<(c.g.V + 127) / 128, 128, 0, c.stream>>>(c.g, c.op[0].U.as<double2>(), 4.0 + m0, c.csw,
+                                                             c.op[0].A.as<double2>());
+  TMG_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ precision copies
+__global__ void k_gauge_f64_to_low(Geom g, const double2* __restrict__ U, float4* __restrict__ U32,
+                                   short4* __restrict__ U16) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    for (int mu = 0; mu < 4; mu++) {
+      for (int k = 0; k < 3; k++) {  // rows 0, 1 = complex 0..5, two per chunk
+        const double2 a = U[(size_t)(mu * 9 + 2 * k) * g.V + s];
+        const double2 b = U[(size_t)(mu * 9 + 2 * k + 1) * g.V + s];
+        U32[(size_t)(mu * 3 + k) * g.V + s] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        auto q = [](double v) { return (short)__double2int_rn(fmin(1.0, fmax(-1.0, v)) * 32767.0); };
+        U16[(size_t)(mu * 3 + k) * g.V + s] = make_short4(q(a.x), q(a.y), q(b.x), q(b.y));
+      }
+    }
+  }
+}
+
+__global__ void k_clover_f64_to_low(Geom g, const double2* __restrict__ A, float4* __restrict__ A32,
+                                    short4* __restrict__ A16, float* __restrict__ sc16) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int k = 0; k < 36; k++) {
+      const double2 v = A[(size_t)k * g.V + s];
+      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+    const float scale = (float)m;
+    sc16[s] = scale;
+    const double inv = m > 0 ? 32767.0 / (double)scale : 0.0;
+    for (int chi = 0; chi < 2; chi++)
+      for (int k = 0; k < 9; k++) {
+        const double2 a = A[(size_t)(chi * 18 + 2 * k) * g.V + s];
+        const double2 b = A[(size_t)(chi * 18 + 2 * k + 1) * g.V + s];
+        A32[(size_t)(chi * 9 + k) * g.V + s] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        auto q = [inv](double v) { return (short)__double2int_rn(fmin(32767.0, fmax(-32767.0, v * inv))); };
+        A16[(size_t)(chi * 9 + k) * g.V + s] = make_short4(q(a.x), q(a.y), q(b.x), q(b.y));
+      }
+  }
+}
+
+void convert_op_precisions(Ctx& c) {
+  const size_t V = c.g.V;
+  c.op[1].U.alloc(V * 12 * sizeof(float4));
+  c.op[2].U.alloc(V * 12 * sizeof(short4));
+  c.op[1].A.alloc(V * 18 * sizeof(float4));
+  c.op[2].A.alloc(V * 18 * sizeof(short4));
+  c.op[2].Ascale.alloc(V * sizeof(float));
+  ++c.launches, k_gauge_f64_to_low<<<grid_for(c, V), 256, 0, c.stream>>>(c.g, c.op[0].U.as<double2>(), c.op[1].U.as<float4>(),
+                                                           c.op[2].U.as<short4>());
+  TMG_CHECK_LAUNCH();
+  ++c.launches, k_clover_f64_to_low<<<grid_for(c, V), 256, 0, c.stream>>>(c.g, c.op[0].A.as<double2>(), c.op[1].A.as<float4>(),
+                                                            c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>());
+  TMG_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ spinor lex <-> internal
+// internal flat complex index of (site s, component k) = 2 ((k/2) V + s) + (k%2)
+__device__ __forceinline__ size_t spinor_flat(int V, int s, int k) {
+  return 2 * ((size_t)(k >> 1) * V + s) + (k & 1);
+}
+
+template <typename T2>
+__global__ void k_spinor_from_lex(Geom g, const double2* __restrict__ lex, T2* __restrict__ out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    for (int k = 0; k < 12; k++) {
+      const double2 v = lex[(size_t)i * 12 + k];
+      T2 o;
+      o.x = v.x; o.y = v.y;
+      out[spinor_flat(g.V, s, k)] = o;
+    }
+  }
+}
+
+template <typename T2>
+__global__ void k_spinor_to_lex(Geom g, const T2* __restrict__ in, double2* __restrict__ lex) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    for (int k = 0; k < 12; k++) {
+      const T2 v = in[spinor_flat(g.V, s, k)];
+      lex[(size_t)i * 12 + k] = make_double2((double)v.x, (double)v.y);
+    }
+  }
+}
+
+void spinor_from_lex(Ctx& c, const double* lex_dev, void* dst, int prec) {
+  if (prec == TMG_PREC_F64)
+    ++c.launches, k_spinor_from_lex<double2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, (double2*)dst);
+  else
+    ++c.launches, k_spinor_from_lex<float2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, (float2*)dst);
+  TMG_CHECK_LAUNCH();
+}
+
+void spinor_to_lex(Ctx& c, const void* src, int prec, double* lex_dev) {
+  if (prec == TMG_PREC_F64)
+    ++c.launches, k_spinor_to_lex<double2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)src, (double2*)lex_dev);
+  else
+    ++c.launches, k_spinor_to_lex<float2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const float2*)src, (double2*)lex_dev);
+  TMG_CHECK_LAUNCH();
+}
+
+template <typename A2, typename B2>
+__global__ void k_convert(const A2* __restrict__ a, B2* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const A2 v = a[i];
+    B2 o;
+    o.x = v.x; o.y = v.y;
+    b[i] = o;
+  }
+}
+
+void convert_field(Ctx& c, const void* src, int psrc, void* dst, int pdst, size_t n) {
+  const int gr = grid_for(c, n);
+  if (psrc == TMG_PREC_F64 && pdst == TMG_PREC_F32) ++c.launches, k_convert<<<gr, 256, 0, c.stream>>>((const double2*)src, (float2*)dst, n);
+  else if (psrc == TMG_PREC_F32 && pdst == TMG_PREC_F64) ++c.launches, k_convert<<<gr, 256, 0, c.stream>>>((const float2*)src, (double2*)dst, n);
+  else if (psrc == TMG_PREC_F64) ++c.launches, k_convert<<<gr, 256, 0, c.stream>>>((const double2*)src, (double2*)dst, n);
+  else ++c.launches, k_convert<<<gr, 256, 0, c.stream>>>((const float2*)src, (float2*)dst, n);
+  TMG_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ BLAS-1
+template <typename T2>
+__global__ void k_axpy(double ar, double ai, const T2* __restrict__ x, T2* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = x[i];
+    T2 b = y[i];
+    b.x += ar * a.x - ai * a.y;
+    b.y += ar * a.y + ai * a.x;
+    y[i] = b;
+  }
+}
+template <typename T2>
+__global__ void k_xpay(const T2* __restrict__ x, double ar, double ai, T2* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = x[i];
+    T2 b = y[i];
+    T2 o;
+    o.x = a.x + (ar * b.x - ai * b.y);
+    o.y = a.y + (ar * b.y + ai * b.x);
+    y[i] = o;
+  }
+}
+template <typename T2>
+__global__ void k_scale(double ar, double ai, T2* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    T2 b = x[i];
+    T2 o;
+    o.x = ar * b.x - ai * b.y;
+    o.y = ar * b.y + ai * b.x;
+    x[i] = o;
+  }
+}
+template <typename X2, typename Y2>
+__global__ void k_axpy_mixed(double a, const X2* __restrict__ x, Y2* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const X2 v = x[i];
+    Y2 b = y[i];
+    b.x += a * (double)v.x;
+    b.y += a * (double)v.y;
+    y[i] = b;
+  }
+}
+
+
+void blas_zero(Ctx& c, void* x, int prec, size_t n) {
+  TMG_CUDA(cudaMemsetAsync(x, 0, n * (prec == TMG_PREC_F64 ? 16 : 8), c.stream));
+}
+void blas_copy(Ctx& c, const void* x, void* y, int prec, size_t n) {
+  TMG_CUDA(cudaMemcpyAsync(y, x, n * (prec == TMG_PREC_F64 ? 16 : 8), cudaMemcpyDeviceToDevice, c.stream));
+}
+void blas_axpy(Ctx& c, double ar, double ai, const void* x, void* y, int prec, size_t n) {
+  const int gr = grid_for(c, n);
+  if (prec == TMG_PREC_F64) ++c.launches, k_axpy<double2><<<gr, 256, 0, c.stream>>>(ar, ai, (const double2*)x, (double2*)y, n);
+  else ++c.launches, k_axpy<float2><<<gr, 256, 0, c.stream>>>(ar, ai, (const float2*)x, (float2*)y, n);
+  TMG_CHECK_LAUNCH();
+}
+void blas_xpay(Ctx& c, const void* x, double ar, double ai, void* y, int prec, size_t n) {
+  const int gr = grid_for(c, n);
+  if (prec == TMG_PREC_F64) ++c.launches, k_xpay<double2><<<gr, 256, 0, c.stream>>>((const double2*)x, ar, ai, (double2*)y, n);
+  else ++c.launches, k_xpay<float2><<<gr, 256, 0, c.stream>>>((const float2*)x, ar, ai, (float2*)y, n);
+  TMG_CHECK_LAUNCH();
+}
+void blas_scale(Ctx& c, double ar, double ai, void* x, int prec, size_t n) {
+  const int gr = grid_for(c, n);
+  if (prec == TMG_PREC_F64) ++c.launches, k_scale<double2><<<gr, 256, 0, c.stream>>>(ar, ai, (double2*)x, n);
+  else ++c.launches, k_scale<float2><<<gr, 256, 0, c.stream>>>(ar, ai, (float2*)x, n);
+  TMG_CHECK_LAUNCH();
+}
+void blas_axpy_mixed(Ctx& c, double a, const void* x, int px, void* y, int py, size_t n) {
+  const int gr = grid_for(c, n);
+  if (px == TMG_PREC_F32 && py == TMG_PREC_F64) ++c.launches, k_axpy_mixed<<<gr, 256, 0, c.stream>>>(a, (const float2*)x, (double2*)y, n);
+  else if (px == TMG_PREC_F64 && py == TMG_PREC_F32) ++c.launches, k_axpy_mixed<<<gr, 256, 0, c.stream>>>(a, (const double2*)x, (float2*)y, n);
+  else if (px == TMG_PREC_F64) ++c.launches, k_axpy_mixed<<<gr, 256, 0, c.stream>>>(a, (const double2*)x, (double2*)y, n);
+  else ++c.launches, k_axpy_mixed<<<gr, 256, 0, c.stream>>>(a, (const float2*)x, (float2*)y, n);
+  TMG_CHECK_LAUNCH();
+}
+
+// Block-level reduction of two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_reduce2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+    a = l < nw ? sa[l] : 0.0;
+    b = l < nw ? sb[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
+template <typename T2>
+__global__ void k_dot_partial(const T2* __restrict__ x, const T2* __restrict__ y, size_t n, double* __restrict__ part) {
+  double re = 0.0, im = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = x[i], b = y[i];
+    re += (double)a.x * b.x + (double)a.y * b.y;
+    im += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  block_reduce2(re, im);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = re; part[2 * blockIdx.x + 1] = im; }
+}
+
+__global__ void k_reduce_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  double re = 0.0, im = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) { re += part[2 * i]; im += part[2 * i + 1]; }
+  block_reduce2(re, im);
+  if (threadIdx.x == 0) { out[0] = re; out[1] = im; }
+}
+
+void blas_dot_dev(Ctx& c, const void* x, const void* y, int prec, size_t n, double* out_dev) {
+  const int gr = std::min(grid_for(c, n), 2 * c.sms);
+  c.red.alloc((size_t)2 * 4096 * sizeof(double));
+  if (prec == TMG_PREC_F64) ++c.launches, k_dot_partial<double2><<<gr, 256, 0, c.stream>>>((const double2*)x, (const double2*)y, n, c.red.as<double>());
+  else ++c.launches, k_dot_partial<float2><<<gr, 256, 0, c.stream>>>((const float2*)x, (const float2*)y, n, c.red.as<double>());
+  TMG_CHECK_LAUNCH();
+  ++c.launches, k_reduce_final<<<1, 256, 0, c.stream>>>(c.red.as<double>(), gr, out_dev);
+  TMG_CHECK_LAUNCH();
+}
+
+void blas_dot(Ctx& c, const void* x, const void* y, int prec, size_t n, double* re, double* im) {
+  c.red_out.alloc(64 * sizeof(double));
+  blas_dot_dev(c, x, y, prec, n, c.red_out.as<double>());
+  double h[2];
+  TMG_CUDA(cudaMemcpyAsync(h, c.red_out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+  *re = h[0];
+  if (im) *im = h[1];
+}
+
+double blas_norm2(Ctx& c, const void* x, int prec, size_t n) {
+  double re, im;
+  blas_dot(c, x, x, prec, n, &re, &im);
+  return re;
+}
+
+}  // namespace tmg

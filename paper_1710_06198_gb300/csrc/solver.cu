@@ -1,0 +1,546 @@
+// Solver runtime of libtmg: the DD-alpha-AMG cycle of Eq. 1 (coarse-grid correction, then k SAP
+// sweeps), its adaptive setup (Sec. 1.1 and Sec. 2 of arXiv:1710.06198), the coarse solve, and the
+// flexible outer Krylov solver (Sec. 1.1) with FP64 residual recomputation at every restart.
+//
+// The coarse GMRES runs entirely on the device: Hessenberg column, Givens rotations, stopping
+// test and back substitution live in device memory, so a cycle issues its kernels without a
+// single host synchronisation.  Launches after convergence test a device flag and return.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "solver.h"
+
+namespace tmg {
+
+namespace {
+
+constexpr int MAXM = 64;     // largest Krylov cycle
+constexpr int NPART = 64;    // reduction partials per vector
+
+struct GmState {
+  double beta;               // ||b||
+  double rtol;               // stop when |g_{j+1}| <= rtol * beta
+  double hn;                 // ||w|| of the current step
+  int done;                  // 1 once converged (or broken down); later launches return
+  int k;                     // steps taken
+  cpx<double> H[(MAXM + 1) * MAXM];  // column-major, H[j * (MAXM + 1) + i]
+  cpx<double> cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
+};
+
+// ---- multi-vector reductions on flat complex arrays ---------------------------------------------
+// part[i * NPART + b] = partial of <v_i, w> over the chunk of block b (grid: NPART x count)
+template <typename T2>
+__global__ void k_mdot_partial(const T2* __restrict__ Vb, size_t stride, const T2* __restrict__ w, size_t n,
+                               double2* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.y;
+  const T2* v = Vb + (size_t)i * stride;
+  double re = 0.0, im = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = v[e], b = w[e];
+    re += (double)a.x * b.x + (double)a.y * b.y;
+    im += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  __shared__ double sre[32], sim[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (lane == 0) { sre[wp] = re; sim[wp] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { a += sre[k]; b += sim[k]; }
+    part[(size_t)i * NPART + blockIdx.x] = make_double2(a, b);
+  }
+}
+
+// out[i] = sum_b part[i * NPART + b]
+__global__ void k_mdot_final(const double2* __restrict__ part, int np, int count, double2* __restrict__ out,
+                             const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double a = 0, b = 0;
+  for (int k = 0; k < np; k++) { const double2 v = part[(size_t)i * NPART + k]; a += v.x; b += v.y; }
+  out[i] = make_double2(a, b);
+}
+
+// h += h2 (the re-orthogonalisation correction of classical Gram-Schmidt)
+__global__ void k_gm_sum_hcol(double2* __restrict__ h, const double2* __restrict__ h2, int count,
+                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int i = threadIdx.x;
+  if (i < count) h[i] = make_double2(h[i].x + h2[i].x, h[i].y + h2[i].y);
+}
+
+// w -= sum_i coef[i] v_i  (coef on the device); optionally partial ||w||^2 into part[b]
+template <typename T2>
+__global__ void k_mgs_update(const T2* __restrict__ Vb, size_t stride, int count, const double2* __restrict__ coef,
+                             T2* __restrict__ w, size_t n, double2* __restrict__ npart, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double2 cf[MAXM + 1];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) cf[i] = coef[i];
+  __syncthreads();
+  double nn = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double xr = w[e].x, xi = w[e].y;
+    for (int i = 0; i < count; i++) {
+      const T2 v = Vb[(size_t)i * stride + e];
+      xr -= cf[i].x * v.x - cf[i].y * v.y;
+      xi -= cf[i].x * v.y + cf[i].y * v.x;
+    }
+    T2 o;
+    o.x = xr;
+    o.y = xi;
+    w[e] = o;
+    nn += (double)o.x * o.x + (double)o.y * o.y;
+  }
+  if (!npart) return;
+  __shared__ double s[32];
+  for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) a += s[k];
+    npart[blockIdx.x] = make_double2(a, 0.0);
+  }
+}
+
+// x = sum_{i<k} coef[i] z_i   (k read from the device when kdev != null)
+template <typename T2>
+__global__ void k_combine(const T2* __restrict__ Zb, size_t stride, int count, const int* __restrict__ kdev,
+                          const double2* __restrict__ coef, T2* __restrict__ x, size_t n) {
+  const int k = kdev ? *kdev : count;
+  __shared__ double2 cf[MAXM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = coef[i];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double xr = 0, xi = 0;
+    for (int i = 0; i < k; i++) {
+      const T2 v = Zb[(size_t)i * stride + e];
+      xr += cf[i].x * v.x - cf[i].y * v.y;
+      xi += cf[i].x * v.y + cf[i].y * v.x;
+    }
+    T2 o;
+    o.x = xr;
+    o.y = xi;
+    x[e] = o;
+  }
+}
+
+// ---- device GMRES control ---------------------------------------------------------------------
+__global__ void k_gm_init(GmState* st, const double2* __restrict__ npart, int np, double rtol) {
+  double a = 0;
+  for (int k = 0; k < np; k++) a += npart[k].x;
+  st->beta = sqrt(a);
+  st->rtol = rtol;
+  st->k = 0;
+  st->done = !(st->beta > 0.0);
+  for (int i = 0; i <= MAXM; i++) st->g[i] = mk(0.0, 0.0);
+  st->g[0] = mk(st->beta, 0.0);
+}
+
+// v0 = b / beta
+template <typename T2>
+__global__ void k_gm_scale_first(const GmState* __restrict__ st, const T2* __restrict__ b, T2* __restrict__ v0, size_t n) {
+  const double inv = st->beta > 0 ? 1.0 / st->beta : 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = b[e];
+    T2 o;
+    o.x = a.x * inv;
+    o.y = a.y * inv;
+    v0[e] = o;
+  }
+}
+
+// After the orthogonalisation of step j: finish ||w||, store column j, rotate, test.
+__global__ void k_gm_givens(GmState* st, int j, const double2* __restrict__ hcol, const double2* __restrict__ npart,
+                            int np, int last) {
+  if (st->done) return;
+  double nn = 0;
+  for (int k = 0; k < np; k++) nn += npart[k].x;
+  const double hn = sqrt(nn);
+  cpx<double>* h = st->H + (size_t)j * (MAXM + 1);
+  for (int i = 0; i <= j; i++) h[i] = mk(hcol[i].x, hcol[i].y);
+  h[j + 1] = mk(hn, 0.0);
+  for (int i = 0; i < j; i++) {
+    const cpx<double> a = h[i], b = h[i + 1];
+    h[i] = conj(st->cs[i]) * a + conj(st->sn[i]) * b;
+    h[i + 1] = st->sn[i] * a;
+    h[i + 1] = mk(-h[i + 1].re, -h[i + 1].im);
+    h[i + 1] = h[i + 1] + st->cs[i] * b;
+  }
+  const cpx<double> a = h[j], b = h[j + 1];
+  const double den = sqrt(a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im);
+  st->cs[j] = den > 0 ? mk(a.re / den, a.im / den) : mk(1.0, 0.0);
+  st->sn[j] = den > 0 ? mk(b.re / den, b.im / den) : mk(0.0, 0.0);
+  h[j] = mk(den, 0.0);
+  h[j + 1] = mk(0.0, 0.0);
+  const cpx<double> gj = st->g[j];
+  st->g[j + 1] = mk(-(st->sn[j] * gj).re, -(st->sn[j] * gj).im);
+  st->g[j] = conj(st->cs[j]) * gj;
+  st->hn = hn;
+  st->k = j + 1;
+  const double res = sqrt(st->g[j + 1].re * st->g[j + 1].re + st->g[j + 1].im * st->g[j + 1].im);
+  if (res <= st->rtol * st->beta || !(hn > 0.0) || !(den > 0.0) || last) st->done = 1;
+}
+
+// v_{j+1} = w / hn  unless done
+template <typename T2>
+__global__ void k_gm_next(const GmState* __restrict__ st, const T2* __restrict__ w, T2* __restrict__ v, size_t n) {
+  if (st->done) return;
+  const double inv = 1.0 / st->hn;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const T2 a = w[e];
+    T2 o;
+    o.x = a.x * inv;
+    o.y = a.y * inv;
+    v[e] = o;
+  }
+}
+
+__global__ void k_gm_backsolve(GmState* st, double2* __restrict__ ycoef, int* __restrict__ counter) {
+  const int k = st->k;
+  for (int i = k - 1; i >= 0; i--) {
+    cpx<double> acc = st->g[i];
+    for (int l = i + 1; l < k; l++) acc = acc - st->H[(size_t)l * (MAXM + 1) + i] * st->y[l];
+    const cpx<double> d = st->H[(size_t)i * (MAXM + 1) + i];
+    const double dn = d.re * d.re + d.im * d.im;
+    st->y[i] = dn > 0 ? mk((acc.re * d.re + acc.im * d.im) / dn, (acc.im * d.re - acc.re * d.im) / dn) : mk(0.0, 0.0);
+  }
+  for (int i = 0; i < k; i++) ycoef[i] = make_double2(st->y[i].re, st->y[i].im);
+  if (counter) *counter += k;
+}
+
+size_t esize(int prec) { return prec == TMG_PREC_F64 ? 16 : 8; }
+
+int red_grid(size_t n) { return (int)std::min<size_t>(NPART, std::max<size_t>(1, (n + 255) / 256)); }
+
+template <typename F>
+void dispatch(int prec, F&& f) {
+  if (prec == TMG_PREC_F64) f(double2{});
+  else f(float2{});
+}
+
+// grid for element-wise kernels
+int egrid(const Ctx& c, size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)c.sms * 8)); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- coarse solve
+// x ~= D_c(mu)^-1 b by one GMRES cycle from zero (at most coarse_m steps, stop at coarse_rtol),
+// classical Gram-Schmidt with one re-orthogonalisation, all control on the device.
+static void coarse_gmres(Ctx& c, int cp, const void* b, void* x, double mu) {
+  const int m = std::min(c.mg.coarse_m, MAXM);
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  const size_t es = esize(cp);
+  c.cw_V.alloc((m + 1) * n * es);
+  c.cw_w.alloc(n * es);
+  c.cw_state.alloc(sizeof(GmState));
+  c.cw_part.alloc(sizeof(double2) * NPART * (MAXM + 2) + sizeof(double2) * 2 * (MAXM + 1));
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  GmState* st = c.cw_state.as<GmState>();
+  double2* part = c.cw_part.as<double2>();
+  double2* hcol = part + NPART * (MAXM + 2);
+  double2* hcol2 = hcol + (MAXM + 1);
+  const int* skip = &st->done;
+  const int rg = red_grid(n);
+  const int eg = egrid(c, n);
+  dispatch(cp, [&](auto tag) {
+    using T2 = decltype(tag);
+    T2* V = c.cw_V.as<T2>();
+    T2* w = c.cw_w.as<T2>();
+    const T2* bb = (const T2*)b;
+    // beta = ||b||
+    ++c.launches, k_mdot_partial<T2><<<dim3(NPART, 1), 256, 0, c.stream>>>(bb, n, bb, n, part, nullptr);
+    TMG_CHECK_LAUNCH();
+    ++c.launches, k_gm_init<<<1, 1, 0, c.stream>>>(st, part, NPART, c.mg.coarse_rtol);
+    ++c.launches, k_gm_scale_first<T2><<<eg, 256, 0, c.stream>>>(st, bb, V, n);
+    TMG_CHECK_LAUNCH();
+    for (int j = 0; j < m; j++) {
+      coarse_apply(c, cp, V + (size_t)j * n, w, mu, skip);
+      for (int pass = 0; pass < 2; pass++) {
+        double2* hc = pass == 0 ? hcol : hcol2;
+        ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>(V, n, w, n, part, skip);
+        ++c.launches, k_mdot_final<<<1, 128, 0, c.stream>>>(part, rg, j + 1, hc, skip);
+        ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>(V, n, j + 1, hc, w, n, pass == 1 ? part + NPART * (MAXM + 1) : nullptr, skip);
+      }
+      // h column = first pass + correction of the second pass
+      ++c.launches, k_gm_sum_hcol<<<1, 64, 0, c.stream>>>(hcol, hcol2, j + 1, skip);
+      ++c.launches, k_gm_givens<<<1, 1, 0, c.stream>>>(st, j, hcol, part + NPART * (MAXM + 1), rg, j == m - 1);
+      if (j < m - 1) ++c.launches, k_gm_next<T2><<<eg, 256, 0, c.stream>>>(st, w, V + (size_t)(j + 1) * n, n);
+      TMG_CHECK_LAUNCH();
+    }
+    ++c.launches, k_gm_backsolve<<<1, 1, 0, c.stream>>>(st, hcol2, c.coarse_iter_dev.as<int>());
+    ++c.launches, k_combine<T2><<<eg, 256, 0, c.stream>>>(V, n, m, &st->k, hcol2, (T2*)x, n);
+    TMG_CHECK_LAUNCH();
+  });
+}
+
+// ---------------------------------------------------------------- cycle (Eq. 1)
+static int storage(int prec) { return prec == TMG_PREC_F64 ? TMG_PREC_F64 : TMG_PREC_F32; }
+
+// z = P D_c^-1 P^dag r, then k SAP sweeps on D z = r starting from z (pf: fine precision of the
+// SAP / P operations, pc: coarse precision).
+static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu) {
+  const size_t nco = (size_t)c.cl.nc * c.cl.nd;
+  c.cw_cr.alloc(nco * esize(pc));
+  c.cw_ce.alloc(nco * esize(pc));
+  restrict_(c, pf, r, c.cw_cr.p, pc);
+  coarse_gmres(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
+  prolong(c, pf, c.cw_ce.p, pc, z, 0);
+  sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
+}
+
+void mg_cycle(Ctx& c, const void* r, void* z, double mu) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, mu); }
+
+// ---------------------------------------------------------------- setup
+static void set_vectors(Ctx& c, int sp) {
+  const size_t n = (size_t)12 * c.g.V;
+  const size_t es = esize(sp);
+  for (int j = 0; j < c.cl.nv; j++)
+    convert_field(c, (const char*)c.sv_raw.p + j * n * es, sp, c.cl.W64.as<double2>() + j * n, TMG_PREC_F64, n);
+  orthonormalise(c, c.cl.W64.p);
+  convert_field(c, c.cl.W64.p, TMG_PREC_F64, c.cl.W32.p, TMG_PREC_F32, n * c.cl.nv);
+  build_coarse(c);
+}
+
+void mg_setup(Ctx& c, const double* v0_lex) {
+  const int nv = c.mg.nv;
+  c.cl.nv = nv;
+  c.cl.nd = 2 * nv;
+  c.cl.nc = c.g.nblk;
+  for (int mu = 0; mu < 4; mu++) c.cl.cgeom[mu] = c.g.NB[mu];
+  const size_t n = (size_t)12 * c.g.V;
+  const int pf = c.mg.prec_fine, sp = storage(pf);
+  const size_t es = esize(sp);
+  c.cl.W64.alloc(nv * n * 16);
+  c.cl.W32.alloc(nv * n * 8);
+  c.sv_raw.alloc(nv * n * es);
+  c.fw_t.alloc(2 * n * es);
+  char* raw = (char*)c.sv_raw.p;
+  void* xb = c.fw_t.p;
+  void* bb = (char*)c.fw_t.p + n * es;
+  for (int j = 0; j < nv; j++) spinor_from_lex(c, v0_lex + (size_t)j * 24 * c.g.V, raw + j * n * es, sp);
+  for (int pass = 0; pass < c.mg.n_init; pass++) {
+    for (int j = 0; j < nv; j++) {
+      void* vj = raw + j * n * es;
+      blas_copy(c, vj, bb, sp, n);
+      blas_zero(c, xb, sp, n);
+      sap_sweeps(c, pf, xb, bb, nullptr, c.mu, c.mg.sap_sweeps);
+      const double nrm = std::sqrt(blas_norm2(c, xb, sp, n));
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) throw Error{TMG_ERR_BREAKDOWN, "setup: test vector vanished"};
+      blas_copy(c, xb, vj, sp, n);
+      blas_scale(c, 1.0 / nrm, 0.0, vj, sp, n);
+    }
+  }
+  set_vectors(c, sp);
+  c.mg_ready = true;
+  for (int it = 0; it < c.mg.n_iter; it++) {
+    for (int j = 0; j < nv; j++) {
+      void* vj = raw + j * n * es;
+      cycle_p(c, pf, c.mg.prec_coarse, vj, xb, c.mu);
+      const double nrm = std::sqrt(blas_norm2(c, xb, sp, n));
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) throw Error{TMG_ERR_BREAKDOWN, "setup: test vector vanished"};
+      blas_copy(c, xb, vj, sp, n);
+      blas_scale(c, 1.0 / nrm, 0.0, vj, sp, n);
+    }
+    set_vectors(c, sp);
+  }
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// ---------------------------------------------------------------- outer flexible GMRES
+// One FGMRES cycle of at most m steps on D(mu) e = r from zero (vectors in storage sp, operator
+// precision op, preconditioner = cycle in (pf, pc)).  Host-side Givens; dots accumulate in FP64.
+static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, void* e, double mu, int m,
+                         double rtol, int& steps) {
+  const size_t n = (size_t)12 * c.g.V;
+  const size_t es = esize(sp);
+  c.fw_V.alloc((m + 1) * n * es);
+  c.fw_Z.alloc(m * n * es);
+  c.fw_w.alloc(n * es);
+  c.fw_part.alloc(sizeof(double2) * NPART * (MAXM + 2));
+  c.fw_h.alloc(sizeof(double2) * 2 * (MAXM + 1));
+  double2* part = c.fw_part.as<double2>();
+  double2* hdev = c.fw_h.as<double2>();
+  const int rg = red_grid(n);
+  std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  const double beta = std::sqrt(blas_norm2(c, r, sp, n));
+  steps = 0;
+  if (!(beta > 0.0)) {
+    blas_zero(c, e, sp, n);
+    return;
+  }
+  char* V = (char*)c.fw_V.p;
+  char* Z = (char*)c.fw_Z.p;
+  blas_copy(c, r, V, sp, n);
+  blas_scale(c, 1.0 / beta, 0.0, V, sp, n);
+  g[0] = beta;
+  int k = 0;
+  for (int j = 0; j < m; j++) {
+    void* vj = V + j * n * es;
+    void* zj = Z + j * n * es;
+    cycle_p(c, pf, pc, vj, zj, mu);
+    dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
+    std::vector<double2> hc(j + 1), hc2(j + 1);
+    double2 nn_parts[NPART];
+    dispatch(sp, [&](auto tag) {
+      using T2 = decltype(tag);
+      for (int pass = 0; pass < 2; pass++) {
+        ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
+        ++c.launches, k_mdot_final<<<1, 128, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
+        ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + pass * (MAXM + 1), (T2*)c.fw_w.p, n,
+                                                   pass == 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
+        TMG_CHECK_LAUNCH();
+      }
+    });
+    TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaMemcpyAsync(hc2.data(), hdev + (MAXM + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaMemcpyAsync(nn_parts, part + NPART * (MAXM + 1), sizeof(double2) * rg, cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    double nn = 0.0;
+    for (int q = 0; q < rg; q++) nn += nn_parts[q].x;
+    const double hn = std::sqrt(nn);
+    std::complex<double>* h = &H[j * (m + 1)];
+    for (int i = 0; i <= j; i++) h[i] = std::complex<double>(hc[i].x + hc2[i].x, hc[i].y + hc2[i].y);
+    h[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+      const std::complex<double> a = h[i], b = h[i + 1];
+      h[i] = std::conj(cs[i]) * a + std::conj(sn[i]) * b;
+      h[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    const std::complex<double> a = h[j], b = h[j + 1];
+    const double den = std::sqrt(std::norm(a) + std::norm(b));
+    if (!std::isfinite(den)) throw Error{TMG_ERR_BREAKDOWN, "fgmres: non-finite Hessenberg entry"};
+    cs[j] = den > 0 ? a / den : 1.0;
+    sn[j] = den > 0 ? b / den : 0.0;
+    h[j] = den;
+    h[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = std::conj(cs[j]) * g[j];
+    k = j + 1;
+    if (std::abs(g[j + 1]) <= rtol * beta || hn == 0.0) break;
+    blas_copy(c, c.fw_w.p, V + (j + 1) * n * es, sp, n);
+    blas_scale(c, 1.0 / hn, 0.0, V + (j + 1) * n * es, sp, n);
+  }
+  for (int i = k - 1; i >= 0; i--) {
+    std::complex<double> acc = g[i];
+    for (int l = i + 1; l < k; l++) acc -= H[l * (m + 1) + i] * y[l];
+    y[i] = acc / H[i * (m + 1) + i];
+  }
+  std::vector<double2> yc(k);
+  for (int i = 0; i < k; i++) yc[i] = make_double2(y[i].real(), y[i].imag());
+  TMG_CUDA(cudaMemcpyAsync(hdev, yc.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, c.stream));
+  dispatch(sp, [&](auto tag) {
+    using T2 = decltype(tag);
+    ++c.launches, k_combine<T2><<<egrid(c, n), 256, 0, c.stream>>>((const T2*)Z, n, k, nullptr, hdev, (T2*)e, n);
+    TMG_CHECK_LAUNCH();
+  });
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+  steps = k;
+}
+
+// ---------------------------------------------------------------- CG comparator (FP64)
+// CG on D D^dag y = b with x = D^dag y accumulated directly: q = D^dag p, x += a q, r -= a D q.
+static int cg_solve(Ctx& c, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st) {
+  const size_t n = (size_t)12 * c.g.V;
+  c.fw_t.alloc(3 * n * 16);
+  c.fw_r64.alloc(n * 16);
+  void* r = c.fw_r64.p;
+  void* p = c.fw_t.p;
+  void* q = (char*)c.fw_t.p + n * 16;
+  void* Aq = (char*)c.fw_t.p + 2 * n * 16;
+  blas_zero(c, x, TMG_PREC_F64, n);
+  blas_copy(c, b, r, TMG_PREC_F64, n);
+  blas_copy(c, b, p, TMG_PREC_F64, n);
+  const double bn2 = blas_norm2(c, b, TMG_PREC_F64, n);
+  if (!std::isfinite(bn2)) throw Error{TMG_ERR_BREAKDOWN, "cg: right-hand side is not finite"};
+  if (!(bn2 > 0.0)) return TMG_OK;
+  double rr = bn2;
+  int it = 0;
+  while (it < maxiter && rr > tol * tol * bn2) {
+    dslash(c, TMG_PREC_F64, q, p, nullptr, mu, 0, 1);
+    dslash(c, TMG_PREC_F64, Aq, q, nullptr, mu, 0, 0);
+    const double qq = blas_norm2(c, q, TMG_PREC_F64, n);
+    if (!(qq > 0.0) || !std::isfinite(qq)) throw Error{TMG_ERR_BREAKDOWN, "cg: breakdown"};
+    const double a = rr / qq;
+    blas_axpy(c, a, 0.0, q, x, TMG_PREC_F64, n);
+    blas_axpy(c, -a, 0.0, Aq, r, TMG_PREC_F64, n);
+    const double rr_new = blas_norm2(c, r, TMG_PREC_F64, n);
+    blas_xpay(c, r, rr_new / rr, 0.0, p, TMG_PREC_F64, n);
+    rr = rr_new;
+    it++;
+  }
+  dslash(c, TMG_PREC_F64, r, x, b, mu, 1, 0);
+  st.iterations = it;
+  st.true_residual = std::sqrt(blas_norm2(c, r, TMG_PREC_F64, n) / bn2);
+  return st.true_residual <= tol ? TMG_OK : TMG_ERR_NOCONV;
+}
+
+// ---------------------------------------------------------------- solve
+int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st) {
+  if (method == TMG_SOLVE_CG_F64) return cg_solve(c, b, x, mu, tol, maxiter, st);
+  const size_t n = (size_t)12 * c.g.V;
+  const bool f64 = method == TMG_SOLVE_MG_F64;
+  const int pf = f64 ? TMG_PREC_F64 : c.mg.prec_fine;
+  const int pc = f64 ? TMG_PREC_F64 : c.mg.prec_coarse;
+  const int sp = storage(pf);
+  const int op = pf;
+  const size_t es = esize(sp);
+  c.fw_r64.alloc(n * 16);
+  c.fw_e.alloc(n * es);
+  c.fw_x.alloc(n * es);
+  int c0 = 0, c1 = 0;
+  if (c.coarse_iter_dev.p) TMG_CUDA(cudaMemcpyAsync(&c0, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  blas_zero(c, x, TMG_PREC_F64, n);
+  blas_copy(c, b, c.fw_r64.p, TMG_PREC_F64, n);
+  const double bn = std::sqrt(blas_norm2(c, b, TMG_PREC_F64, n));
+  if (!std::isfinite(bn)) throw Error{TMG_ERR_BREAKDOWN, "solve: right-hand side is not finite"};
+  if (!(bn > 0.0)) return TMG_OK;
+  int rc = TMG_OK;
+  while (true) {
+    const double rn = std::sqrt(blas_norm2(c, c.fw_r64.p, TMG_PREC_F64, n));
+    if (!std::isfinite(rn)) {
+      rc = TMG_ERR_BREAKDOWN;
+      break;
+    }
+    st.true_residual = rn / bn;
+    if (rn <= tol * bn) break;
+    if (st.iterations >= maxiter) {
+      rc = TMG_ERR_NOCONV;
+      break;
+    }
+    // unit-norm residual in the working precision
+    convert_field(c, c.fw_r64.p, TMG_PREC_F64, c.fw_x.p, sp, n);
+    blas_scale(c, 1.0 / rn, 0.0, c.fw_x.p, sp, n);
+    double target = tol * bn / rn;
+    if (!f64) target = std::max(target, 1e-6);
+    int k = 0;
+    fgmres_cycle(c, sp, op, pf, pc, c.fw_x.p, c.fw_e.p, mu, std::min(c.mg.restart, MAXM), target, k);
+    st.iterations += k;
+    blas_axpy_mixed(c, rn, c.fw_e.p, sp, x, TMG_PREC_F64, n);
+    dslash(c, TMG_PREC_F64, c.fw_r64.p, x, b, mu, 1, 0);
+    st.refinements++;
+    if (k == 0) {
+      rc = TMG_ERR_BREAKDOWN;
+      break;
+    }
+  }
+  if (c.coarse_iter_dev.p) {
+    TMG_CUDA(cudaMemcpyAsync(&c1, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    st.coarse_iterations = c1 - c0;
+  }
+  return rc;
+}
+
+}  // namespace tmg

@@ -1,0 +1,23 @@
+// Host-side solver runtime of libtmg (internal): adaptive setup, the DD-alpha-AMG cycle of Eq. 1,
+// the device-resident coarse GMRES, the outer flexible GMRES with FP64 defect correction, and the
+// FP64 CG comparator.
+#pragma once
+#include "tmg_host.h"
+
+namespace tmg {
+
+struct SolveStats {
+  int iterations = 0;
+  int refinements = 0;
+  int coarse_iterations = 0;
+  double true_residual = 0.0;
+};
+
+// Adaptive setup from nv FP64 lexicographic vectors on the device (Sec. 1.1, Sec. 2).
+void mg_setup(Ctx& c, const double* v0_lex);
+// z = M_MG r in the fine storage precision of the multigrid parameters (r is not modified).
+void mg_cycle(Ctx& c, const void* r, void* z, double mu);
+// Solve D(mu) x = b on FP64 internal fields (b, x: F64 storage).  Returns a tmg_status.
+int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st);
+
+}  // namespace tmg

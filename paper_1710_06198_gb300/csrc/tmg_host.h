@@ -1,0 +1,206 @@
+// Host-side context and kernel launchers of libtmg (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "tmg_internal.cuh"
+#include "../../include/tmg.h"
+
+namespace tmg {
+
+// Error carried from a launcher up to the C ABI.
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define TMG_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::tmg::Error{e_ == cudaErrorMemoryAllocation ? TMG_ERR_OOM : TMG_ERR_CUDA,       \
+                         std::string(#call) + ": " + cudaGetErrorString(e_)};                \
+  } while (0)
+
+#define TMG_CHECK_LAUNCH() TMG_CUDA(cudaGetLastError())
+
+// Owning device buffer.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void alloc(size_t n) {
+    if (n <= bytes && p) return;
+    release();
+    if (n == 0) return;
+    TMG_CUDA(cudaMalloc(&p, n));
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Fine spinor field (one or more columns) in F64 or F32 storage; complex count per column 12 V.
+struct Field {
+  int prec = 1;       // TMG_PREC_F64 or TMG_PREC_F32
+  int ncol = 1;
+  DBuf buf;
+  size_t col_elems(const Geom& g) const { return (size_t)12 * g.V; }
+  size_t elem_bytes() const { return prec == TMG_PREC_F64 ? 16 : 8; }
+  void create(const Geom& g, int prec_, int ncol_ = 1) {
+    prec = prec_;
+    ncol = ncol_;
+    buf.alloc(col_elems(g) * elem_bytes() * ncol);
+  }
+  void* col(const Geom& g, int j) const { return (char*)buf.p + col_elems(g) * elem_bytes() * j; }
+};
+
+// Coarse vector: [ncoarse][nd] complex in F64 or F32.
+struct CField {
+  int prec = 1;
+  size_t n = 0;       // complex entries per column
+  DBuf buf;
+  void create(int prec_, size_t n_) {
+    prec = prec_;
+    n = n_;
+    buf.alloc(n * (prec == TMG_PREC_F64 ? 16 : 8));
+  }
+};
+
+// Gauge-dependent operator data in one storage precision.
+struct OpData {
+  DBuf U;       // links
+  DBuf A;       // clover (4 + m0 + C)
+  DBuf Ascale;  // F16 clover scale per site
+};
+
+// Multigrid level data (fine level 0 -> coarse level 1).
+struct Coarse {
+  int nv = 0, nd = 0, nc = 0;  // test vectors, dofs per coarse site, coarse sites
+  int cgeom[4];                // coarse lattice dims
+  DBuf W64, W32;               // orthonormalised test vectors, F64 and F32 ([nv] spinor fields)
+  DBuf Dc64, Dc32;             // coarse stencil [nc][9][nd(col l)][nd(row k)]
+};
+
+// Optional per-kernel-class timing with CUDA events on the context stream (tmg_profile).
+enum { PK_DSLASH_F64 = 0, PK_DSLASH_F32, PK_DSLASH_F16, PK_SAP_F64, PK_SAP_F32, PK_SAP_F16, PK_RESTRICT,
+       PK_PROLONG, PK_COARSE, PK_COUNT };
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;             // free events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> recs[PK_COUNT];
+  ~Prof() {
+    for (auto& v : recs)
+      for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    TMG_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  void reset() {
+    for (auto& v : recs) {
+      for (auto& p : v) { pool.push_back(p.first); pool.push_back(p.second); }
+      v.clear();
+    }
+  }
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Geom g{};
+  double kappa = 0.125, csw = 0.0, mu = 0.0, mubar = 0.0, epsbar = 0.0;
+  bool gauge_loaded = false;
+  OpData op[3];          // F64, F32, F16
+  DBuf U_lex;            // staging for a host gauge field
+  tmg_mg_params mg{};
+  bool mg_ready = false;
+  Coarse cl;
+  // solver workspaces (solver.cu)
+  DBuf cw_V, cw_w, cw_state, cw_part, cw_cr, cw_ce;   // coarse GMRES
+  DBuf fw_V, fw_Z, fw_w, fw_r64, fw_e, fw_x, fw_t, fw_part, fw_h;  // outer FGMRES / CG
+  DBuf sv_raw;           // raw (un-orthonormalised) test vectors of the setup
+  DBuf coarse_iter_dev;  // device counter of coarse GMRES steps
+  // scratch
+  DBuf red;              // reduction partials (doubles)
+  DBuf red_out;          // reduction results (doubles)
+  DBuf stage_a, stage_b; // FP64 lex staging for host vectors
+  std::string err;
+  int sms = 152;
+  long long launches = 0;  // kernels launched by this context (all launchers count)
+  Prof prof;
+};
+
+// Records a start event on construction and an end event on destruction when profiling is on.
+struct ProfScope {
+  Ctx& c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(Ctx& c_, int kind_) : c(c_), kind(kind_) {
+    if (c.prof.on) {
+      a = c.prof.get();
+      TMG_CUDA(cudaEventRecord(a, c.stream));
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = c.prof.get();
+      cudaEventRecord(b, c.stream);
+      c.prof.recs[kind].push_back({a, b});
+    }
+  }
+};
+
+// ---------------------------------------------------------------- launchers (k_fields.cu)
+void gauge_lex_to_internal(Ctx& c, const double* lex_dev);
+void build_clover(Ctx& c);
+void convert_op_precisions(Ctx& c);
+// lex FP64 [V][12] complex -> internal field column (prec F64 or F32)
+void spinor_from_lex(Ctx& c, const double* lex_dev, void* dst, int prec);
+void spinor_to_lex(Ctx& c, const void* src, int prec, double* lex_dev);
+void convert_field(Ctx& c, const void* src, int psrc, void* dst, int pdst, size_t n_complex);
+
+// complex BLAS on flat arrays of n complex numbers (prec F64: double2, F32: float2)
+void blas_zero(Ctx& c, void* x, int prec, size_t n);
+void blas_copy(Ctx& c, const void* x, void* y, int prec, size_t n);
+// y = a x + y
+void blas_axpy(Ctx& c, double are, double aim, const void* x, void* y, int prec, size_t n);
+// y = x + a y
+void blas_xpay(Ctx& c, const void* x, double are, double aim, void* y, int prec, size_t n);
+// x = a x
+void blas_scale(Ctx& c, double are, double aim, void* x, int prec, size_t n);
+// y_prec_dst += a * x_prec_src (mixed precision accumulate, F32 -> F64 typical)
+void blas_axpy_mixed(Ctx& c, double a, const void* x, int px, void* y, int py, size_t n);
+// result[0] = re <x, y>, result[1] = im <x, y> into device doubles (FP64 accumulation)
+void blas_dot_dev(Ctx& c, const void* x, const void* y, int prec, size_t n, double* out_dev);
+double blas_norm2(Ctx& c, const void* x, int prec, size_t n);
+void blas_dot(Ctx& c, const void* x, const void* y, int prec, size_t n, double* re, double* im);
+
+// ---------------------------------------------------------------- dslash (k_dslash.cu)
+// mode 0: y = op x ; mode 1: y = b - op x ; mode 2: y = hopping(x)
+void dslash(Ctx& c, int prec, void* y, const void* x, const void* b, double mu, int mode, int dagger);
+// non-degenerate doublet (Eq. 2) on F64 / F32 fields with 2 flavour columns
+void dslash_nd(Ctx& c, int prec, void* y, const void* x);
+
+// ---------------------------------------------------------------- multigrid (k_mg.cu)
+void sap_sweeps(Ctx& c, int prec, void* x, const void* b, void* r_scratch, double mu, int n_sweeps);
+void restrict_(Ctx& c, int prec, const void* r, void* cvec, int cprec);
+void prolong(Ctx& c, int prec, const void* cvec, int cprec, void* e, int accumulate);
+// skip: optional device flag; when it is non-zero the launch does nothing
+void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const int* skip = nullptr);
+void orthonormalise(Ctx& c, void* W64);
+void build_coarse(Ctx& c);
+
+}  // namespace tmg

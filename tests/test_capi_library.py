@@ -1,0 +1,59 @@
+"""Host-side checks of the C-ABI library: it builds for sm_103a, loads without a GPU, exports every
+entry point declared in include/tmg.h, and rejects bad arguments without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1710_06198_gb300 as tmg
+from paper_1710_06198_gb300 import build as tmg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    tmg_build.build()
+    return tmg.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tmg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(tmg._SIGS), "binding lacks a declared entry point"
+
+
+def test_version_without_device(L):
+    assert "sm_103a" in tmg.version()
+
+
+def test_create_rejects_bad_geometry(L):
+    h = ctypes.c_void_p()
+    bad = [((8, 4, 4, 4), (4, 2, 2, 3)),    # block does not divide
+           ((8, 4, 4, 6), (4, 2, 2, 2)),    # odd number of blocks in t
+           ((4, 4, 4, 4), (4, 2, 2, 2)),    # a single block in x
+           ((8, 8, 4, 4), (2, 2, 2, 2))]    # block volume not a multiple of 32
+    for dims, block in bad:
+        d = (ctypes.c_int * 4)(*dims)
+        b = (ctypes.c_int * 4)(*block)
+        assert L.tmg_create(ctypes.byref(h), d, b, 0, None) == -1
+    assert L.tmg_create(None, None, None, 0, None) == -1
+
+
+def test_null_context_calls_fail_cleanly(L):
+    assert L.tmg_destroy(None) == -1
+    assert L.tmg_load_gauge(None, None, 0, -1) == -1
+    assert L.tmg_apply(None, 0, None, None, 1, None, 0, 0) == -1
+    assert L.tmg_solve(None, None, None, 1, None, 1e-10, 0, 10, None, 0) == -1
+    p = tmg.MGParams()
+    assert L.tmg_mg_defaults(ctypes.byref(p)) == 0
+    assert p.nv == 8 and p.sap_sweeps == 3 and p.restart == 10
