@@ -132,6 +132,31 @@ def algorithmic_bytes(kind, V, nv, nc, nd):
     return None
 
 
+def run_kernel_case(args):
+    """A single kernel class on a 24^3 x 48 lattice (working set above the 129 MB L2), for ncu."""
+    import torch
+    import paper_1710_06198_gb300 as tmg
+    from synth import fields
+    from oracle import dirac  # noqa: F401  (kappa conversion only)
+    dims = (24, 24, 24, 48)
+    U = fields.gauge_field(dims, 0.3, 4)
+    ctx = tmg.Context(dims, (4, 4, 4, 4))
+    ctx.set_params(1.0 / (2.0 * (4.0 - 0.4)), 1.6, 0.002)
+    ctx.load_gauge(U, -1)
+    if args.kernel_case == "dslash":
+        ms = ctx.bench_dslash(tmg.PREC_F32, 3)
+        print(json.dumps({"kernel_case": "dslash", "ms": ms}))
+    elif args.kernel_case == "sap":
+        prm = tmg.Context.mg_defaults()
+        prm.nv, prm.n_init, prm.n_iter, prm.sap_sweeps = 2, 0, 0, 1
+        ctx.setup(fields.gaussian_spinor(dims, 5, n=2), prm)
+        b = torch.from_numpy(fields.gaussian_spinor(dims, 6)).cuda()
+        x = torch.zeros_like(b)
+        y = ctx.sap(b, x, tmg.PREC_F32)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": "sap", "norm": float(torch.linalg.vector_norm(y))}))
+
+
 def run_ours(args):
     import torch
     import paper_1710_06198_gb300 as tmg
@@ -170,6 +195,17 @@ def run_ours(args):
     def step(method=tmg.SOLVE_MG_MIXED):
         _, st = ctx.solve(b, tol=w["tol"], method=method, out=x)
         return st
+
+    if args.ncu_solve:
+        # one warm solve, then exactly one solve inside the profiler range (for ncu --profile-from-start off)
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        st = step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_solve": True, "iterations": st["iterations"], "launches_total": tmg.launch_count(ctx)}))
+        return
 
     for _ in range(args.warmup):
         step()
@@ -246,7 +282,7 @@ def run_ours(args):
             kernels[k] = {"launches": n, "ms_total": round(ms, 4), "us_per_launch": round(1e3 * ms / n, 3),
                           "algo_bytes_per_launch": ab,
                           "gbs": round(ab / (ms / n * 1e-3) / 1e9, 1) if ab else None}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    dom = max((k for k in kernels if kernels[k]["algo_bytes_per_launch"]), key=lambda k: kernels[k]["ms_total"])
     peak, peak_src = peaks()
     # dslash bandwidth of the FP32 operator alone: average of launches with L2 flushed in between
     dsl = []
@@ -295,31 +331,37 @@ def run_ours(args):
 
 
 def cpu_baseline(w, kappa, gpu_iters, budget_s):
-    """The FP64 numpy oracle on the host cores: time per outer FGMRES iteration (one two-level
-    cycle + one operator application + Gram-Schmidt) measured on a bounded number of iterations,
-    times the outer iterations of the GPU solve.  The oracle's P comes from orthonormalised random
-    vectors (its setup is not part of the timed solve)."""
+    """The FP64 numpy oracle on the host cores, on a bounded sample: one outer FGMRES iteration
+    (one two-level cycle + one operator application + Gram-Schmidt) on an 8^4 lattice with the
+    same recipe and multigrid parameters, scaled by the volume ratio and by the outer iterations of
+    the GPU solve.  The oracle's P comes from orthonormalised random vectors; its coarse-operator
+    build is not part of the timed sample."""
     import os as _os
     from oracle import dirac, mg, krylov
     from synth import fields
     cores = len(_os.sched_getaffinity(0))
-    U = fields.gauge_field(w["dims"], w["eps"], w["seed"])
+    dims = (8, 8, 8, 8)
+    U = fields.gauge_field(dims, w["eps"], w["seed"])
     p = dirac.Params(kappa=kappa, csw=w["csw"], mu=w["mu"], tbc=-1)
-    b = fields.gaussian_spinor(w["dims"], w["rhs_seed"])
+    b = fields.gaussian_spinor(dims, w["rhs_seed"])
     mgp = mg.MGParams(block=w["block"], agg=w["block"], nv=w["nv"], coarse_m=30, coarse_rtol=5e-2)
     H = mg.Hierarchy(U, p, mgp)
     t0 = time.perf_counter()
-    H.set_vectors(fields.gaussian_spinor(w["dims"], w["setup_seed"], n=w["nv"]))
+    H.set_vectors(fields.gaussian_spinor(dims, w["setup_seed"], n=w["nv"]))
     t_build = time.perf_counter() - t0
-    n_it = 1
-    t0 = time.perf_counter()
-    krylov.fgmres(H.D, b, H.cycle, m=n_it, tol=1e-30, maxiter=n_it)
-    t_it = (time.perf_counter() - t0) / n_it
-    est = t_it * gpu_iters
+    n_it, t_it = 0, 0.0
+    while n_it < 3 and (n_it == 0 or t_it * (n_it + 1) / n_it < budget_s):
+        t0 = time.perf_counter()
+        krylov.fgmres(H.D, b, H.cycle, m=1, tol=1e-30, maxiter=1)
+        t_it += time.perf_counter() - t0
+        n_it += 1
+    t_it /= n_it
+    scale = float(np.prod(w["dims"])) / float(np.prod(dims))
+    est = t_it * scale * gpu_iters
     return {"value": round(est, 3), "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_it} FP64 FGMRES iteration(s) with the two-level cycle on the full 16^3x32 lattice "
-                      f"({t_it:.2f} s each), scaled by the GPU solve's {gpu_iters:.0f} outer iterations; "
-                      f"coarse-operator build ({t_build:.1f} s) not included"}
+            "sample": f"{n_it} FP64 FGMRES iteration(s) with the two-level cycle on an 8^4 lattice of the same "
+                      f"recipe ({t_it:.2f} s each), x{scale:.0f} volume, x{gpu_iters:.0f} outer iterations of the "
+                      f"GPU solve; oracle coarse-operator build ({t_build:.1f} s) not included"}
 
 
 def run_reference(args):
@@ -358,8 +400,13 @@ def main():
     ap.add_argument("--cg-maxiter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--ncu-solve", action="store_true", help="profile one solve only (for ncu)")
+    ap.add_argument("--kernel-case", choices=["dslash", "sap"], default=None,
+                    help="run one kernel class on a 24^3 x 48 lattice (for ncu --set full)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -125,6 +125,9 @@ int tmg_restrict(tmg_ctx *ctx, const double *r, double *c, int prec, int where);
 int tmg_prolong(tmg_ctx *ctx, const double *c, double *e, int prec, int where);
 int tmg_coarse_apply(tmg_ctx *ctx, const double *x, double *y, double mu, int prec, int where);
 int tmg_cycle(tmg_ctx *ctx, const double *r, double *z, int where);
+/* x ~= D_c(mu)^-1 b (Eq. 1's coarse solve): GMRES from zero with at most coarse_m steps, stopping
+ * at relative residual coarse_rtol; coarse vectors [V_c][2 N_v], computed in precision prec. */
+int tmg_coarse_solve(tmg_ctx *ctx, const double *b, double *x, double mu, int prec, int where);
 
 /* ---- solves ---- */
 typedef struct {
@@ -159,7 +162,7 @@ int tmg_bench_dslash(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_launch);
 enum {
   TMG_PK_DSLASH_F64 = 0, TMG_PK_DSLASH_F32 = 1, TMG_PK_DSLASH_F16 = 2,
   TMG_PK_SAP_F64 = 3, TMG_PK_SAP_F32 = 4, TMG_PK_SAP_F16 = 5,
-  TMG_PK_RESTRICT = 6, TMG_PK_PROLONG = 7, TMG_PK_COARSE = 8, TMG_PK_COUNT = 9
+  TMG_PK_RESTRICT = 6, TMG_PK_PROLONG = 7, TMG_PK_COARSE = 8, TMG_PK_COARSE_SOLVE = 9, TMG_PK_COUNT = 10
 };
 /* enable != 0: reset the records and start timing every launch of the classes above;
  * enable == 0: stop (records are kept until the next call). */

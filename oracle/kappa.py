@@ -75,13 +75,37 @@ def sigma_min(U, p: dirac.Params, clover=None):
     return float(np.min(np.abs(w)))
 
 
-def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, max_steps=80, log=None):
+def sigma_min_mg(U, p: dirac.Params, clover=None, mgp=None, seed=7, tol=1e-10):
+    """sigma_min(D_W) by Lanczos (ARPACK) on Q^-1, with Q^-1 v = D_W^-1 G5 v from the oracle's own
+    two-level DD-alpha-AMG solve at mu = 0; used where a sparse LU of Q is too expensive."""
+    from . import mg
+    from synth import fields  # noqa: F401  (seeded vectors only)
+    p0 = dirac.Params(kappa=p.kappa, csw=p.csw, mu=0.0, tbc=p.tbc)
+    if mgp is None:
+        mgp = mg.MGParams(nv=8, n_init=3, n_iter=1)
+    H = mg.Hierarchy(U, p0, mgp, clover)
+    lat = U.shape[:4]
+    H.setup(fields.gaussian_spinor((lat[3], lat[2], lat[1], lat[0]), seed, n=mgp.nv))
+    shape = lat + (4, 3)
+    n = int(np.prod(shape))
+
+    def qinv(v):
+        x, _, res = H.solve(dirac.apply_g5(v.reshape(shape)), tol=tol, mu=0.0)
+        return x.ravel()
+
+    op = spla.LinearOperator((n, n), matvec=qinv, dtype=np.complex128)
+    w = spla.eigsh(op, k=2, which="LM", return_eigenvectors=False, tol=1e-6)
+    return float(1.0 / np.max(np.abs(w)))
+
+
+def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, max_steps=80, log=None, method=None):
     """First crossing from above of sigma_min(D_W(m0)) = target, to +-rel_tol.  Returns
     (m0, sigma_min, evaluations)."""
     clover = dirac.clover_term(U, csw)
+    method = sigma_min if method is None else method
 
     def s(m0):
-        v = sigma_min(U, dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, tbc=tbc), clover)
+        v = method(U, dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, tbc=tbc), clover)
         if log is not None:
             log.append((m0, v))
         return v

@@ -68,6 +68,7 @@ _SIGS = {
     "tmg_prolong": [_P, _P, _P, _I, _I],
     "tmg_coarse_apply": [_P, _P, _P, _D, _I, _I],
     "tmg_cycle": [_P, _P, _P, _I],
+    "tmg_coarse_solve": [_P, _P, _P, _D, _I, _I],
     "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
     "tmg_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
@@ -76,7 +77,7 @@ _SIGS = {
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
-                 "prolong", "coarse_apply"]
+                 "prolong", "coarse_apply", "coarse_solve"]
 
 
 def lib():
@@ -241,6 +242,14 @@ class Context:
         py, _ = _ptr(y)
         self._check(lib().tmg_coarse_apply(self._h, px, py, float(mu), prec, wh))
         return y
+
+    def coarse_solve(self, c, mu=0.0, prec=PREC_F64):
+        """x ~= D_c(mu)^-1 c by the coarse GMRES of the cycle."""
+        x = _empty_like(c, c.shape)
+        pc, wh = _ptr(c)
+        px, _ = _ptr(x)
+        self._check(lib().tmg_coarse_solve(self._h, pc, px, float(mu), prec, wh))
+        return x
 
     def cycle(self, r):
         z = _empty_like(r, r.shape)

@@ -394,6 +394,26 @@ int tmg_coarse_apply(tmg_ctx* ctx, const double* x, double* y, double mu, int pr
   });
 }
 
+int tmg_coarse_solve(tmg_ctx* ctx, const double* b, double* x, double mu, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || (prec != TMG_PREC_F64 && prec != TMG_PREC_F32) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_coarse_solve: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_coarse_solve: no setup");
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, b, 2 * n, where);
+    tmg::CField bi, xo;
+    bi.create(prec, n);
+    xo.create(prec, n);
+    convert_field(c, d, TMG_PREC_F64, bi.buf.p, prec, n);
+    coarse_gmres_persistent(c, prec, bi.buf.p, xo.buf.p, mu);
+    double* o = stage_out_ptr(c, c.stage_b, x, 2 * n, where);
+    convert_field(c, xo.buf.p, prec, o, TMG_PREC_F64, n);
+    stage_out_finish(c, c.stage_b, x, 2 * n, where);
+    return TMG_OK;
+  });
+}
+
 int tmg_cycle(tmg_ctx* ctx, const double* r, double* z, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;

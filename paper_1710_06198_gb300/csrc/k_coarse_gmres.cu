@@ -1,0 +1,304 @@
+// The coarse solve D_c^-1 of Eq. 1 (arXiv:1710.06198) as ONE persistent cooperative kernel:
+// GMRES from zero, at most m steps, stopping once the Givens estimate of the relative residual
+// reaches rtol; classical Gram-Schmidt with an optional second pass.
+//
+// Every CTA stays resident for the whole solve; phases are separated by grid-wide barriers of a
+// cooperative launch.  The small sequential work (Hessenberg column, Givens rotations, stopping
+// test) is repeated identically by every CTA from the same reduced values, so no extra barrier is
+// needed to broadcast it; CTA 0 alone keeps the rotated Hessenberg for the back substitution.
+// Vectors are in the coarse precision S (FP32 or FP64); all reductions finish in FP64.
+#include <cooperative_groups.h>
+
+#include "tmg_host.h"
+
+namespace cg = cooperative_groups;
+
+namespace tmg {
+
+namespace {
+
+constexpr int CMAXM = 64;
+constexpr int CMAXND = 64;   // largest coarse dof count per site (N_v <= 32)
+
+template <typename S>
+struct CplxT;
+template <> struct CplxT<float> { using T2 = float2; };
+template <> struct CplxT<double> { using T2 = double2; };
+
+template <typename S>
+struct CgArgs {
+  int nd, nv, nc, m, passes;
+  const typename CplxT<S>::T2* Dc;   // [nc][9][nd(l)][nd(k)]
+  const int* nbr;                    // [nc][9]
+  const typename CplxT<S>::T2* b;
+  typename CplxT<S>::T2* x;
+  typename CplxT<S>::T2* V;          // (m + 1) x n basis
+  typename CplxT<S>::T2* w;
+  S mu;
+  double rtol;
+  double2* part;                     // [CMAXM + 1][grid] dot partials
+  double* npart;                     // [grid] norm partials
+  double2* R;                        // rotated Hessenberg, column-major (CMAXM + 1) x CMAXM
+  double2* y;                        // solution coefficients
+  int* counter;                      // accumulated step count
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of one double per thread over the CTA (result returned to every thread).
+__device__ __forceinline__ double cta_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
+  using T2 = typename CplxT<S>::T2;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  __shared__ double2 hcol[CMAXM + 2];
+  __shared__ double2 cs[CMAXM], sn[CMAXM], gv[CMAXM + 1];
+  __shared__ double2 hp[CMAXM + 1];
+  __shared__ double2 rowp[9 * CMAXND];
+  __shared__ int s_done, s_k;
+  __shared__ double s_beta, s_hn;
+  const int n = a.nc * a.nd;
+  const int G = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
+  // chunk of elements owned by this CTA for the dot products
+  const int chunk = (n + G - 1) / G;
+  const int e0 = blockIdx.x * chunk, e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+
+  // beta = ||b||
+  {
+    S nn = 0;
+    for (int e = tid; e < n; e += nth) { const T2 v = a.b[e]; nn += v.x * v.x + v.y * v.y; }
+    const double t = cta_sum((double)nn, sh);
+    if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+  }
+  grid.sync();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < G; q++) t += a.npart[q];
+    s_beta = sqrt(t);
+    s_done = !(s_beta > 0.0);
+    s_k = 0;
+    for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
+    gv[0] = make_double2(s_beta, 0.0);
+  }
+  __syncthreads();
+  {
+    const S inv = s_beta > 0.0 ? (S)(1.0 / s_beta) : (S)0;
+    for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
+  }
+  for (int j = 0; j < a.m && !s_done; j++) {
+    grid.sync();                                     // v_j complete
+    const T2* vj = a.V + (size_t)j * n;
+    // w = D_c(mu) v_j : a CTA per coarse site, a warp per stencil block (lanes = rows, coalesced
+    // 32-row columns of the block), then the 9 partial rows are summed through shared memory.
+    for (int site = blockIdx.x; site < a.nc; site += G) {
+      for (int d = warp; d < 9; d += nwarp) {
+        const int nb = a.nbr[site * 9 + d];
+        const T2* blk = a.Dc + ((size_t)(site * 9 + d) * a.nd) * a.nd;
+        const T2* xv = vj + (size_t)nb * a.nd;
+        for (int k = lane; k < a.nd; k += 32) {
+          S ar = 0, ai = 0;
+#pragma unroll 4
+          for (int l = 0; l < a.nd; l++) {
+            const T2 m = blk[(size_t)l * a.nd + k];
+            const T2 v = xv[l];
+            ar += m.x * v.x - m.y * v.y;
+            ai += m.x * v.y + m.y * v.x;
+          }
+          rowp[d * CMAXND + k] = make_double2((double)ar, (double)ai);
+        }
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < a.nd; k += blockDim.x) {
+        double ar = 0.0, ai = 0.0;
+        for (int d = 0; d < 9; d++) { ar += rowp[d * CMAXND + k].x; ai += rowp[d * CMAXND + k].y; }
+        const T2 xs = vj[(size_t)site * a.nd + k];
+        const double tw = k < a.nv ? (double)a.mu : -(double)a.mu;
+        T2 o;
+        o.x = (S)(ar - tw * (double)xs.y);
+        o.y = (S)(ai + tw * (double)xs.x);
+        a.w[(size_t)site * a.nd + k] = o;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int i = 0; i <= j + 1; i++) hcol[i] = make_double2(0.0, 0.0);
+    for (int pass = 0; pass < a.passes; pass++) {
+      grid.sync();                                   // w complete
+      // partial <v_i, w> over this CTA's chunk, one warp per basis vector
+      for (int i = warp; i <= j; i += nwarp) {
+        const T2* vi = a.V + (size_t)i * n;
+        S re = 0, im = 0;
+        for (int e = e0 + lane; e < e1; e += 32) {
+          const T2 p = vi[e], q = a.w[e];
+          re += p.x * q.x + p.y * q.y;
+          im += p.x * q.y - p.y * q.x;
+        }
+        const double dre = warp_sum((double)re), dim = warp_sum((double)im);
+        if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
+      }
+      grid.sync();                                   // partials complete
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < G; q++) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
+        hp[i] = make_double2(re, im);
+        hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+      }
+      __syncthreads();
+      // w -= sum_i h_i v_i on every element (grid-stride) and, in the last pass, ||w||^2
+      S nn = 0;
+      for (int e = tid; e < n; e += nth) {
+        T2 q = a.w[e];
+        S qr = q.x, qi = q.y;
+        for (int i = 0; i <= j; i++) {
+          const T2 p = a.V[(size_t)i * n + e];
+          const S hr = (S)hp[i].x, hi = (S)hp[i].y;
+          qr -= hr * p.x - hi * p.y;
+          qi -= hr * p.y + hi * p.x;
+        }
+        q.x = qr;
+        q.y = qi;
+        a.w[e] = q;
+        nn += qr * qr + qi * qi;
+      }
+      if (pass == a.passes - 1) {
+        const double t = cta_sum((double)nn, sh);
+        if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+      }
+    }
+    grid.sync();                                     // w and norm partials complete
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < G; q++) t += a.npart[q];
+      const double hn = sqrt(t);
+      hcol[j + 1] = make_double2(hn, 0.0);
+      for (int i = 0; i < j; i++) {                  // previous rotations [[conj c, conj s], [-s, c]]
+        const double2 x0 = hcol[i], x1 = hcol[i + 1];
+        const double2 c = cs[i], s = sn[i];
+        hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
+                               c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
+        hcol[i + 1] = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                                   -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+      }
+      const double2 p = hcol[j], q = hcol[j + 1];
+      const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+      cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
+      sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
+      hcol[j] = make_double2(den, 0.0);
+      hcol[j + 1] = make_double2(0.0, 0.0);
+      const double2 g = gv[j];
+      gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
+      gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+      if (blockIdx.x == 0)
+        for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
+      s_hn = hn;
+      s_k = j + 1;
+      const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+      if (res <= a.rtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
+    }
+    __syncthreads();
+    if (!s_done) {
+      const S inv = (S)(1.0 / s_hn);
+      T2* vn = a.V + (size_t)(j + 1) * n;
+      for (int e = tid; e < n; e += nth) { T2 v = a.w[e]; v.x *= inv; v.y *= inv; vn[e] = v; }
+    }
+  }
+  grid.sync();                                       // rotated Hessenberg stored by CTA 0
+  const int k = s_k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; i--) {
+      double2 acc = gv[i];
+      for (int l = i + 1; l < k; l++) {
+        const double2 h = a.R[(size_t)l * (CMAXM + 1) + i], yl = a.y[l];
+        acc.x -= h.x * yl.x - h.y * yl.y;
+        acc.y -= h.x * yl.y + h.y * yl.x;
+      }
+      const double2 d = a.R[(size_t)i * (CMAXM + 1) + i];
+      const double dn = d.x * d.x + d.y * d.y;
+      a.y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : make_double2(0.0, 0.0);
+    }
+    if (a.counter) *a.counter += k;
+  }
+  grid.sync();                                       // coefficients ready
+  __shared__ S yr[CMAXM], yi[CMAXM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = (S)a.y[i].x; yi[i] = (S)a.y[i].y; }
+  __syncthreads();
+  for (int e = tid; e < n; e += nth) {
+    S xr = 0, xi = 0;
+    for (int i = 0; i < k; i++) {
+      const T2 v = a.V[(size_t)i * n + e];
+      xr += yr[i] * v.x - yi[i] * v.y;
+      xi += yr[i] * v.y + yi[i] * v.x;
+    }
+    T2 o;
+    o.x = xr;
+    o.y = xi;
+    a.x[e] = o;
+  }
+}
+
+template <typename S>
+void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
+  using T2 = typename CplxT<S>::T2;
+  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  static int max_per_sm[2] = {-1, -1};
+  int& mps = max_per_sm[sizeof(S) == 8];
+  if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
+  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, mps)));
+  c.cw_V.alloc((m + 1) * n * sizeof(T2));
+  c.cw_w.alloc(n * sizeof(T2));
+  c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  CgArgs<S> a;
+  a.nd = c.cl.nd;
+  a.nv = c.cl.nv;
+  a.nc = c.cl.nc;
+  a.m = m;
+  a.passes = 2;
+  a.Dc = (const T2*)Dc;
+  a.nbr = c.cl.nbr.as<int>();
+  a.b = (const T2*)b;
+  a.x = (T2*)x;
+  a.V = c.cw_V.as<T2>();
+  a.w = c.cw_w.as<T2>();
+  a.mu = (S)mu;
+  a.rtol = c.mg.coarse_rtol;
+  a.part = c.cw_part.as<double2>();
+  a.R = a.part + (size_t)(CMAXM + 1) * G;
+  a.y = a.R + (size_t)(CMAXM + 1) * CMAXM;
+  a.npart = reinterpret_cast<double*>(a.y + CMAXM);
+  a.counter = c.coarse_iter_dev.as<int>();
+  void* args[] = {&a};
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
+}
+
+}  // namespace
+
+void coarse_gmres_persistent(Ctx& c, int cp, const void* b, void* x, double mu) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (cp == TMG_PREC_F64) launch<double>(c, b, x, mu, c.cl.Dc64.p);
+  else launch<float>(c, b, x, mu, c.cl.Dc32.p);
+}
+
+}  // namespace tmg

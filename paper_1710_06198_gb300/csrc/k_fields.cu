@@ -276,8 +276,17 @@ void convert_field(Ctx& c, const void* src, int psrc, void* dst, int pdst, size_
 }
 
 // ------------------------------------------------------------------ BLAS-1
+// Element arithmetic runs in the data's own precision (FP32 fields never touch the FP64 pipes,
+// which are a small fraction of the FP32 rate on this GPU); dot products accumulate per thread in
+// the data precision and reduce across threads in FP64.
+template <typename T2> struct ScalarOf;
+template <> struct ScalarOf<float2> { using T = float; };
+template <> struct ScalarOf<double2> { using T = double; };
+
 template <typename T2>
-__global__ void k_axpy(double ar, double ai, const T2* __restrict__ x, T2* __restrict__ y, size_t n) {
+__global__ void k_axpy(double ar_, double ai_, const T2* __restrict__ x, T2* __restrict__ y, size_t n) {
+  using S = typename ScalarOf<T2>::T;
+  const S ar = (S)ar_, ai = (S)ai_;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const T2 a = x[i];
     T2 b = y[i];
@@ -287,10 +296,12 @@ __global__ void k_axpy(double ar, double ai, const T2* __restrict__ x, T2* __res
   }
 }
 template <typename T2>
-__global__ void k_xpay(const T2* __restrict__ x, double ar, double ai, T2* __restrict__ y, size_t n) {
+__global__ void k_xpay(const T2* __restrict__ x, double ar_, double ai_, T2* __restrict__ y, size_t n) {
+  using S = typename ScalarOf<T2>::T;
+  const S ar = (S)ar_, ai = (S)ai_;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const T2 a = x[i];
-    T2 b = y[i];
+    const T2 b = y[i];
     T2 o;
     o.x = a.x + (ar * b.x - ai * b.y);
     o.y = a.y + (ar * b.y + ai * b.x);
@@ -298,26 +309,30 @@ __global__ void k_xpay(const T2* __restrict__ x, double ar, double ai, T2* __res
   }
 }
 template <typename T2>
-__global__ void k_scale(double ar, double ai, T2* __restrict__ x, size_t n) {
+__global__ void k_scale(double ar_, double ai_, T2* __restrict__ x, size_t n) {
+  using S = typename ScalarOf<T2>::T;
+  const S ar = (S)ar_, ai = (S)ai_;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T2 b = x[i];
+    const T2 b = x[i];
     T2 o;
     o.x = ar * b.x - ai * b.y;
     o.y = ar * b.y + ai * b.x;
     x[i] = o;
   }
 }
+// y += a x with x, y of any precision; the arithmetic runs in the destination's precision
 template <typename X2, typename Y2>
-__global__ void k_axpy_mixed(double a, const X2* __restrict__ x, Y2* __restrict__ y, size_t n) {
+__global__ void k_axpy_mixed(double a_, const X2* __restrict__ x, Y2* __restrict__ y, size_t n) {
+  using S = typename ScalarOf<Y2>::T;
+  const S a = (S)a_;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const X2 v = x[i];
     Y2 b = y[i];
-    b.x += a * (double)v.x;
-    b.y += a * (double)v.y;
+    b.x += a * (S)v.x;
+    b.y += a * (S)v.y;
     y[i] = b;
   }
 }
-
 
 void blas_zero(Ctx& c, void* x, int prec, size_t n) {
   TMG_CUDA(cudaMemsetAsync(x, 0, n * (prec == TMG_PREC_F64 ? 16 : 8), c.stream));
@@ -375,14 +390,16 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
 
 template <typename T2>
 __global__ void k_dot_partial(const T2* __restrict__ x, const T2* __restrict__ y, size_t n, double* __restrict__ part) {
-  double re = 0.0, im = 0.0;
+  using S = typename ScalarOf<T2>::T;
+  S re = 0, im = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const T2 a = x[i], b = y[i];
-    re += (double)a.x * b.x + (double)a.y * b.y;
-    im += (double)a.x * b.y - (double)a.y * b.x;
+    re += a.x * b.x + a.y * b.y;
+    im += a.x * b.y - a.y * b.x;
   }
-  block_reduce2(re, im);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = re; part[2 * blockIdx.x + 1] = im; }
+  double dre = re, dim = im;
+  block_reduce2(dre, dim);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = dre; part[2 * blockIdx.x + 1] = dim; }
 }
 
 __global__ void k_reduce_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
@@ -393,7 +410,8 @@ __global__ void k_reduce_final(const double* __restrict__ part, int nparts, doub
 }
 
 void blas_dot_dev(Ctx& c, const void* x, const void* y, int prec, size_t n, double* out_dev) {
-  const int gr = std::min(grid_for(c, n), 2 * c.sms);
+  // enough CTAs to fill the GPU; each thread then sums ~n / (4 * 152 * 256) products
+  const int gr = std::min(grid_for(c, n), 4 * c.sms);
   c.red.alloc((size_t)2 * 4096 * sizeof(double));
   if (prec == TMG_PREC_F64) ++c.launches, k_dot_partial<double2><<<gr, 256, 0, c.stream>>>((const double2*)x, (const double2*)y, n, c.red.as<double>());
   else ++c.launches, k_dot_partial<float2><<<gr, 256, 0, c.stream>>>((const float2*)x, (const float2*)y, n, c.red.as<double>());

@@ -7,14 +7,16 @@
 //     twist i mu G5_c added on the fly (D_c(mu) = D_c + i mu G5_c);
 //   - per-aggregate, per-chirality Gram-Schmidt of the test vectors in FP64.
 #include <algorithm>
+#include <vector>
 
 #include "dslash_core.cuh"
 #include "tmg_host.h"
 
 namespace tmg {
 
-// Reduction of N values (per thread) over the CTA; every thread gets the totals.
-// red: shared scratch of at least 32 * N doubles.
+// Reduction of N values (per thread) over the CTA; every thread gets the totals.  Warp sums use
+// shuffles in the kernel's precision; the cross-warp sum is done by one thread per value.
+// red: shared scratch of at least 33 * N doubles.
 template <int N, typename R>
 __device__ __forceinline__ void cta_allreduce(R (&v)[N], double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -26,12 +28,14 @@ __device__ __forceinline__ void cta_allreduce(R (&v)[N], double* red) {
     if (lane == 0) red[w * N + i] = (double)a;
   }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < N; i++) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
     double a = 0.0;
     for (int k = 0; k < nw; k++) a += red[k * N + i];
-    v[i] = (R)a;
+    red[32 * N + i] = a;
   }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; i++) v[i] = (R)red[32 * N + i];
   __syncthreads();
 }
 
@@ -51,7 +55,7 @@ __device__ __forceinline__ int colour_block(const Geom& g, int colour, int k) {
 // leave the block are dropped), then x += e.  Blocks of one colour never touch, so the CTAs of a
 // launch are independent; the other colour's x is only read.
 template <typename R, class S, class G, class C>
-__global__ void __launch_bounds__(256) k_sap_block(Geom g, int colour, S x, S b, G U, C A, R tw, int n_mr) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom g, int colour, S x, S b, G U, C A, R tw, int n_mr) {
   extern __shared__ double smem_d[];
   cpx<R>* rs = reinterpret_cast<cpx<R>*>(smem_d);             // [12][VB]
   double* red = smem_d + (sizeof(cpx<R>) * 12 * g.VB) / sizeof(double);
@@ -70,9 +74,6 @@ __global__ void __launch_bounds__(256) k_sap_block(Geom g, int colour, S x, S b,
   Spinor<R> e;
 #pragma unroll
   for (int k = 0; k < 12; k++) e.c[k] = mk<R>(0, 0);
-  CloverBlock<R> a0, a1;
-  A.load(s, 0, a0);
-  A.load(s, 1, a1);
   for (int it = 0; it < n_mr; it++) {
 #pragma unroll
     for (int k = 0; k < 12; k++) rs[k * g.VB + t] = r.c[k];
@@ -109,8 +110,12 @@ __global__ void __launch_bounds__(256) k_sap_block(Geom g, int colour, S x, S b,
       }
     }
     Spinor<R> p;
-    clover_mul(a0, tw, &r.c[0], &p.c[0]);
-    clover_mul(a1, -tw, &r.c[6], &p.c[6]);
+#pragma unroll
+    for (int chi = 0; chi < 2; chi++) {
+      CloverBlock<R> a;
+      A.load(s, chi, a);
+      clover_mul(a, chi == 0 ? tw : -tw, &r.c[6 * chi], &p.c[6 * chi]);
+    }
 #pragma unroll
     for (int k = 0; k < 12; k++) p.c[k] = p.c[k] - R(0.5) * acc.c[k];
     R v[3] = {0, 0, 0};
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(256) k_sap_block(Geom g, int colour, S x, S b,
 
 template <typename R, class S, class G, class C>
 static void launch_sap(Ctx& c, S x, S b, G U, C A, R tw, int n_sweeps, int kind) {
-  const size_t smem = sizeof(cpx<R>) * 12 * c.g.VB + 32 * 3 * sizeof(double);
+  const size_t smem = sizeof(cpx<R>) * 12 * c.g.VB + 33 * 3 * sizeof(double);
   if (smem > 48 * 1024) {
     TMG_CUDA(cudaFuncSetAttribute(k_sap_block<R, S, G, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(256) k_prolong(Geom g, const IN2* __restrict__
 void restrict_(Ctx& c, int prec, const void* r, void* cvec, int cprec) {
   ProfScope ps(c, PK_RESTRICT);
   const int nv = c.cl.nv;
-  const size_t smem = 32 * 32 * sizeof(double);
+  const size_t smem = 33 * 32 * sizeof(double);
   if (prec == TMG_PREC_F64) {
     SpinorF64 rs{(double2*)r, c.g.V}, ws{c.cl.W64.as<double2>(), c.g.V};
     if (cprec == TMG_PREC_F64) ++c.launches, k_restrict<double><<<c.g.nblk, c.g.VB, smem, c.stream>>>(c.g, rs, ws, nv, (double2*)cvec);
@@ -473,10 +478,29 @@ __global__ void k_copy_convert(const A2* __restrict__ a, B2* __restrict__ b, siz
 
 void build_coarse(Ctx& c) {
   const int nd = c.cl.nd;
+  {
+    std::vector<int> nb((size_t)c.g.nblk * 9);
+    for (int a = 0; a < c.g.nblk; a++) {
+      int b[4], q = a;
+      b[0] = q % c.g.NB[0]; q /= c.g.NB[0];
+      b[1] = q % c.g.NB[1]; q /= c.g.NB[1];
+      b[2] = q % c.g.NB[2]; b[3] = q / c.g.NB[2];
+      nb[(size_t)a * 9] = a;
+      for (int mu = 0; mu < 4; mu++)
+        for (int dir = 0; dir < 2; dir++) {
+          int bb[4] = {b[0], b[1], b[2], b[3]};
+          bb[mu] = (bb[mu] + (dir == 0 ? 1 : c.g.NB[mu] - 1)) % c.g.NB[mu];
+          nb[(size_t)a * 9 + 1 + 2 * mu + dir] = bb[0] + c.g.NB[0] * (bb[1] + c.g.NB[1] * (bb[2] + c.g.NB[2] * bb[3]));
+        }
+    }
+    c.cl.nbr.alloc(nb.size() * sizeof(int));
+    TMG_CUDA(cudaMemcpyAsync(c.cl.nbr.p, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+  }
   const size_t n = (size_t)c.g.nblk * 9 * nd * nd;
   c.cl.Dc64.alloc(n * sizeof(double2));
   c.cl.Dc32.alloc(n * sizeof(float2));
-  const size_t smem = 32 * 32 * sizeof(double);
+  const size_t smem = 33 * 32 * sizeof(double);
   for (int l = 0; l < nd; l++) {
     ++c.launches, k_coarse_build_col<<<c.g.nblk, c.g.VB, smem, c.stream>>>(c.g, c.cl.nv, l, c.cl.W64.as<double2>(),
                                                               GaugeF64{c.op[0].U.as<double2>(), c.g.V},
@@ -527,7 +551,7 @@ __global__ void __launch_bounds__(256) k_orthonormalise(Geom g, int nv, double2*
 }
 
 void orthonormalise(Ctx& c, void* W64) {
-  const size_t smem = 32 * 2 * sizeof(double);
+  const size_t smem = 33 * 2 * sizeof(double);
   ++c.launches, k_orthonormalise<<<2 * c.g.nblk, c.g.VB, smem, c.stream>>>(c.g, c.cl.nv, (double2*)W64);
   TMG_CHECK_LAUNCH();
 }

@@ -2,9 +2,8 @@
 // sweeps), its adaptive setup (Sec. 1.1 and Sec. 2 of arXiv:1710.06198), the coarse solve, and the
 // flexible outer Krylov solver (Sec. 1.1) with FP64 residual recomputation at every restart.
 //
-// The coarse GMRES runs entirely on the device: Hessenberg column, Givens rotations, stopping
-// test and back substitution live in device memory, so a cycle issues its kernels without a
-// single host synchronisation.  Launches after convergence test a device flag and return.
+// The coarse GMRES is one persistent cooperative kernel (k_coarse_gmres.cu), so a cycle issues
+// its kernels without a single host synchronisation.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -17,32 +16,28 @@ namespace tmg {
 namespace {
 
 constexpr int MAXM = 64;     // largest Krylov cycle
-constexpr int NPART = 64;    // reduction partials per vector
-
-struct GmState {
-  double beta;               // ||b||
-  double rtol;               // stop when |g_{j+1}| <= rtol * beta
-  double hn;                 // ||w|| of the current step
-  int done;                  // 1 once converged (or broken down); later launches return
-  int k;                     // steps taken
-  cpx<double> H[(MAXM + 1) * MAXM];  // column-major, H[j * (MAXM + 1) + i]
-  cpx<double> cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
-};
+constexpr int NPART = 1024;  // reduction partials per vector (>= CTAs of a reduction launch)
 
 // ---- multi-vector reductions on flat complex arrays ---------------------------------------------
 // part[i * NPART + b] = partial of <v_i, w> over the chunk of block b (grid: NPART x count)
+template <typename T2> struct ScalarOf;
+template <> struct ScalarOf<float2> { using T = float; };
+template <> struct ScalarOf<double2> { using T = double; };
+
 template <typename T2>
 __global__ void k_mdot_partial(const T2* __restrict__ Vb, size_t stride, const T2* __restrict__ w, size_t n,
                                double2* __restrict__ part, const int* __restrict__ skip) {
   if (skip && *skip) return;
+  using S = typename ScalarOf<T2>::T;
   const int i = blockIdx.y;
   const T2* v = Vb + (size_t)i * stride;
-  double re = 0.0, im = 0.0;
+  S tre = 0, tim = 0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const T2 a = v[e], b = w[e];
-    re += (double)a.x * b.x + (double)a.y * b.y;
-    im += (double)a.x * b.y - (double)a.y * b.x;
+    tre += a.x * b.x + a.y * b.y;
+    tim += a.x * b.y - a.y * b.x;
   }
+  double re = tre, im = tim;
   __shared__ double sre[32], sim[32];
   for (int o = 16; o > 0; o >>= 1) {
     re += __shfl_down_sync(0xffffffffu, re, o);
@@ -69,36 +64,30 @@ __global__ void k_mdot_final(const double2* __restrict__ part, int np, int count
   out[i] = make_double2(a, b);
 }
 
-// h += h2 (the re-orthogonalisation correction of classical Gram-Schmidt)
-__global__ void k_gm_sum_hcol(double2* __restrict__ h, const double2* __restrict__ h2, int count,
-                              const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  const int i = threadIdx.x;
-  if (i < count) h[i] = make_double2(h[i].x + h2[i].x, h[i].y + h2[i].y);
-}
-
 // w -= sum_i coef[i] v_i  (coef on the device); optionally partial ||w||^2 into part[b]
 template <typename T2>
 __global__ void k_mgs_update(const T2* __restrict__ Vb, size_t stride, int count, const double2* __restrict__ coef,
                              T2* __restrict__ w, size_t n, double2* __restrict__ npart, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ double2 cf[MAXM + 1];
-  for (int i = threadIdx.x; i < count; i += blockDim.x) cf[i] = coef[i];
+  using S = typename ScalarOf<T2>::T;
+  __shared__ S cfr[MAXM + 1], cfi[MAXM + 1];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) { cfr[i] = (S)coef[i].x; cfi[i] = (S)coef[i].y; }
   __syncthreads();
-  double nn = 0.0;
+  S snn = 0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double xr = w[e].x, xi = w[e].y;
+    S xr = w[e].x, xi = w[e].y;
     for (int i = 0; i < count; i++) {
       const T2 v = Vb[(size_t)i * stride + e];
-      xr -= cf[i].x * v.x - cf[i].y * v.y;
-      xi -= cf[i].x * v.y + cf[i].y * v.x;
+      xr -= cfr[i] * v.x - cfi[i] * v.y;
+      xi -= cfr[i] * v.y + cfi[i] * v.x;
     }
     T2 o;
     o.x = xr;
     o.y = xi;
     w[e] = o;
-    nn += (double)o.x * o.x + (double)o.y * o.y;
+    snn += xr * xr + xi * xi;
   }
+  double nn = snn;
   if (!npart) return;
   __shared__ double s[32];
   for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
@@ -115,16 +104,17 @@ __global__ void k_mgs_update(const T2* __restrict__ Vb, size_t stride, int count
 template <typename T2>
 __global__ void k_combine(const T2* __restrict__ Zb, size_t stride, int count, const int* __restrict__ kdev,
                           const double2* __restrict__ coef, T2* __restrict__ x, size_t n) {
+  using S = typename ScalarOf<T2>::T;
   const int k = kdev ? *kdev : count;
-  __shared__ double2 cf[MAXM];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = coef[i];
+  __shared__ S cfr[MAXM], cfi[MAXM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) { cfr[i] = (S)coef[i].x; cfi[i] = (S)coef[i].y; }
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double xr = 0, xi = 0;
+    S xr = 0, xi = 0;
     for (int i = 0; i < k; i++) {
       const T2 v = Zb[(size_t)i * stride + e];
-      xr += cf[i].x * v.x - cf[i].y * v.y;
-      xi += cf[i].x * v.y + cf[i].y * v.x;
+      xr += cfr[i] * v.x - cfi[i] * v.y;
+      xi += cfr[i] * v.y + cfi[i] * v.x;
     }
     T2 o;
     o.x = xr;
@@ -133,93 +123,11 @@ __global__ void k_combine(const T2* __restrict__ Zb, size_t stride, int count, c
   }
 }
 
-// ---- device GMRES control ---------------------------------------------------------------------
-__global__ void k_gm_init(GmState* st, const double2* __restrict__ npart, int np, double rtol) {
-  double a = 0;
-  for (int k = 0; k < np; k++) a += npart[k].x;
-  st->beta = sqrt(a);
-  st->rtol = rtol;
-  st->k = 0;
-  st->done = !(st->beta > 0.0);
-  for (int i = 0; i <= MAXM; i++) st->g[i] = mk(0.0, 0.0);
-  st->g[0] = mk(st->beta, 0.0);
-}
-
-// v0 = b / beta
-template <typename T2>
-__global__ void k_gm_scale_first(const GmState* __restrict__ st, const T2* __restrict__ b, T2* __restrict__ v0, size_t n) {
-  const double inv = st->beta > 0 ? 1.0 / st->beta : 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const T2 a = b[e];
-    T2 o;
-    o.x = a.x * inv;
-    o.y = a.y * inv;
-    v0[e] = o;
-  }
-}
-
-// After the orthogonalisation of step j: finish ||w||, store column j, rotate, test.
-__global__ void k_gm_givens(GmState* st, int j, const double2* __restrict__ hcol, const double2* __restrict__ npart,
-                            int np, int last) {
-  if (st->done) return;
-  double nn = 0;
-  for (int k = 0; k < np; k++) nn += npart[k].x;
-  const double hn = sqrt(nn);
-  cpx<double>* h = st->H + (size_t)j * (MAXM + 1);
-  for (int i = 0; i <= j; i++) h[i] = mk(hcol[i].x, hcol[i].y);
-  h[j + 1] = mk(hn, 0.0);
-  for (int i = 0; i < j; i++) {
-    const cpx<double> a = h[i], b = h[i + 1];
-    h[i] = conj(st->cs[i]) * a + conj(st->sn[i]) * b;
-    h[i + 1] = st->sn[i] * a;
-    h[i + 1] = mk(-h[i + 1].re, -h[i + 1].im);
-    h[i + 1] = h[i + 1] + st->cs[i] * b;
-  }
-  const cpx<double> a = h[j], b = h[j + 1];
-  const double den = sqrt(a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im);
-  st->cs[j] = den > 0 ? mk(a.re / den, a.im / den) : mk(1.0, 0.0);
-  st->sn[j] = den > 0 ? mk(b.re / den, b.im / den) : mk(0.0, 0.0);
-  h[j] = mk(den, 0.0);
-  h[j + 1] = mk(0.0, 0.0);
-  const cpx<double> gj = st->g[j];
-  st->g[j + 1] = mk(-(st->sn[j] * gj).re, -(st->sn[j] * gj).im);
-  st->g[j] = conj(st->cs[j]) * gj;
-  st->hn = hn;
-  st->k = j + 1;
-  const double res = sqrt(st->g[j + 1].re * st->g[j + 1].re + st->g[j + 1].im * st->g[j + 1].im);
-  if (res <= st->rtol * st->beta || !(hn > 0.0) || !(den > 0.0) || last) st->done = 1;
-}
-
-// v_{j+1} = w / hn  unless done
-template <typename T2>
-__global__ void k_gm_next(const GmState* __restrict__ st, const T2* __restrict__ w, T2* __restrict__ v, size_t n) {
-  if (st->done) return;
-  const double inv = 1.0 / st->hn;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const T2 a = w[e];
-    T2 o;
-    o.x = a.x * inv;
-    o.y = a.y * inv;
-    v[e] = o;
-  }
-}
-
-__global__ void k_gm_backsolve(GmState* st, double2* __restrict__ ycoef, int* __restrict__ counter) {
-  const int k = st->k;
-  for (int i = k - 1; i >= 0; i--) {
-    cpx<double> acc = st->g[i];
-    for (int l = i + 1; l < k; l++) acc = acc - st->H[(size_t)l * (MAXM + 1) + i] * st->y[l];
-    const cpx<double> d = st->H[(size_t)i * (MAXM + 1) + i];
-    const double dn = d.re * d.re + d.im * d.im;
-    st->y[i] = dn > 0 ? mk((acc.re * d.re + acc.im * d.im) / dn, (acc.im * d.re - acc.re * d.im) / dn) : mk(0.0, 0.0);
-  }
-  for (int i = 0; i < k; i++) ycoef[i] = make_double2(st->y[i].re, st->y[i].im);
-  if (counter) *counter += k;
-}
-
 size_t esize(int prec) { return prec == TMG_PREC_F64 ? 16 : 8; }
 
-int red_grid(size_t n) { return (int)std::min<size_t>(NPART, std::max<size_t>(1, (n + 255) / 256)); }
+int red_grid(const Ctx& c, size_t n) {
+  return (int)std::min<size_t>(std::min<size_t>(NPART, (size_t)4 * c.sms), std::max<size_t>(1, (n + 255) / 256));
+}
 
 template <typename F>
 void dispatch(int prec, F&& f) {
@@ -232,59 +140,6 @@ int egrid(const Ctx& c, size_t n) { return (int)std::max<size_t>(1, std::min<siz
 
 }  // namespace
 
-// ---------------------------------------------------------------- coarse solve
-// x ~= D_c(mu)^-1 b by one GMRES cycle from zero (at most coarse_m steps, stop at coarse_rtol),
-// classical Gram-Schmidt with one re-orthogonalisation, all control on the device.
-static void coarse_gmres(Ctx& c, int cp, const void* b, void* x, double mu) {
-  const int m = std::min(c.mg.coarse_m, MAXM);
-  const size_t n = (size_t)c.cl.nc * c.cl.nd;
-  const size_t es = esize(cp);
-  c.cw_V.alloc((m + 1) * n * es);
-  c.cw_w.alloc(n * es);
-  c.cw_state.alloc(sizeof(GmState));
-  c.cw_part.alloc(sizeof(double2) * NPART * (MAXM + 2) + sizeof(double2) * 2 * (MAXM + 1));
-  if (!c.coarse_iter_dev.p) {
-    c.coarse_iter_dev.alloc(sizeof(int));
-    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
-  }
-  GmState* st = c.cw_state.as<GmState>();
-  double2* part = c.cw_part.as<double2>();
-  double2* hcol = part + NPART * (MAXM + 2);
-  double2* hcol2 = hcol + (MAXM + 1);
-  const int* skip = &st->done;
-  const int rg = red_grid(n);
-  const int eg = egrid(c, n);
-  dispatch(cp, [&](auto tag) {
-    using T2 = decltype(tag);
-    T2* V = c.cw_V.as<T2>();
-    T2* w = c.cw_w.as<T2>();
-    const T2* bb = (const T2*)b;
-    // beta = ||b||
-    ++c.launches, k_mdot_partial<T2><<<dim3(NPART, 1), 256, 0, c.stream>>>(bb, n, bb, n, part, nullptr);
-    TMG_CHECK_LAUNCH();
-    ++c.launches, k_gm_init<<<1, 1, 0, c.stream>>>(st, part, NPART, c.mg.coarse_rtol);
-    ++c.launches, k_gm_scale_first<T2><<<eg, 256, 0, c.stream>>>(st, bb, V, n);
-    TMG_CHECK_LAUNCH();
-    for (int j = 0; j < m; j++) {
-      coarse_apply(c, cp, V + (size_t)j * n, w, mu, skip);
-      for (int pass = 0; pass < 2; pass++) {
-        double2* hc = pass == 0 ? hcol : hcol2;
-        ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>(V, n, w, n, part, skip);
-        ++c.launches, k_mdot_final<<<1, 128, 0, c.stream>>>(part, rg, j + 1, hc, skip);
-        ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>(V, n, j + 1, hc, w, n, pass == 1 ? part + NPART * (MAXM + 1) : nullptr, skip);
-      }
-      // h column = first pass + correction of the second pass
-      ++c.launches, k_gm_sum_hcol<<<1, 64, 0, c.stream>>>(hcol, hcol2, j + 1, skip);
-      ++c.launches, k_gm_givens<<<1, 1, 0, c.stream>>>(st, j, hcol, part + NPART * (MAXM + 1), rg, j == m - 1);
-      if (j < m - 1) ++c.launches, k_gm_next<T2><<<eg, 256, 0, c.stream>>>(st, w, V + (size_t)(j + 1) * n, n);
-      TMG_CHECK_LAUNCH();
-    }
-    ++c.launches, k_gm_backsolve<<<1, 1, 0, c.stream>>>(st, hcol2, c.coarse_iter_dev.as<int>());
-    ++c.launches, k_combine<T2><<<eg, 256, 0, c.stream>>>(V, n, m, &st->k, hcol2, (T2*)x, n);
-    TMG_CHECK_LAUNCH();
-  });
-}
-
 // ---------------------------------------------------------------- cycle (Eq. 1)
 static int storage(int prec) { return prec == TMG_PREC_F64 ? TMG_PREC_F64 : TMG_PREC_F32; }
 
@@ -295,7 +150,7 @@ static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu) {
   c.cw_cr.alloc(nco * esize(pc));
   c.cw_ce.alloc(nco * esize(pc));
   restrict_(c, pf, r, c.cw_cr.p, pc);
-  coarse_gmres(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
+  coarse_gmres_persistent(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
   prolong(c, pf, c.cw_ce.p, pc, z, 0);
   sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
 }
@@ -372,7 +227,7 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
   c.fw_h.alloc(sizeof(double2) * 2 * (MAXM + 1));
   double2* part = c.fw_part.as<double2>();
   double2* hdev = c.fw_h.as<double2>();
-  const int rg = red_grid(n);
+  const int rg = red_grid(c, n);
   std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   const double beta = std::sqrt(blas_norm2(c, r, sp, n));
   steps = 0;
@@ -392,7 +247,7 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
     cycle_p(c, pf, pc, vj, zj, mu);
     dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
     std::vector<double2> hc(j + 1), hc2(j + 1);
-    double2 nn_parts[NPART];
+    std::vector<double2> nn_parts(NPART);
     dispatch(sp, [&](auto tag) {
       using T2 = decltype(tag);
       for (int pass = 0; pass < 2; pass++) {
@@ -405,7 +260,7 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
     });
     TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaMemcpyAsync(hc2.data(), hdev + (MAXM + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
-    TMG_CUDA(cudaMemcpyAsync(nn_parts, part + NPART * (MAXM + 1), sizeof(double2) * rg, cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaMemcpyAsync(nn_parts.data(), part + NPART * (MAXM + 1), sizeof(double2) * rg, cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     double nn = 0.0;
     for (int q = 0; q < rg; q++) nn += nn_parts[q].x;

@@ -88,11 +88,12 @@ struct Coarse {
   int cgeom[4];                // coarse lattice dims
   DBuf W64, W32;               // orthonormalised test vectors, F64 and F32 ([nv] spinor fields)
   DBuf Dc64, Dc32;             // coarse stencil [nc][9][nd(col l)][nd(row k)]
+  DBuf nbr;                    // coarse neighbour table [nc][9] (slot 0 self, 1 + 2 mu: +mu, 2 + 2 mu: -mu)
 };
 
 // Optional per-kernel-class timing with CUDA events on the context stream (tmg_profile).
 enum { PK_DSLASH_F64 = 0, PK_DSLASH_F32, PK_DSLASH_F16, PK_SAP_F64, PK_SAP_F32, PK_SAP_F16, PK_RESTRICT,
-       PK_PROLONG, PK_COARSE, PK_COUNT };
+       PK_PROLONG, PK_COARSE, PK_COARSE_SOLVE, PK_COUNT };
 
 struct Prof {
   bool on = false;
@@ -201,6 +202,8 @@ void prolong(Ctx& c, int prec, const void* cvec, int cprec, void* e, int accumul
 // skip: optional device flag; when it is non-zero the launch does nothing
 void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const int* skip = nullptr);
 void orthonormalise(Ctx& c, void* W64);
+// x ~= D_c(mu)^-1 b: one persistent cooperative GMRES kernel (k_coarse_gmres.cu)
+void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double mu);
 void build_coarse(Ctx& c);
 
 }  // namespace tmg

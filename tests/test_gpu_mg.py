@@ -93,6 +93,17 @@ def test_sap(small, prec):
     assert rel(ctx.sap(b, x0, prec), want) < tol
 
 
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_coarse_solve(small, prec):
+    """The coarse GMRES with rtol = 0 runs exactly coarse_m steps: the same Krylov solution as
+    the oracle's (modified Gram-Schmidt there, classical with re-orthogonalisation here)."""
+    ctx, H, U, p = small
+    c = fields.gaussian_coarse((2, 2, 2, 2), 2 * ctx.nv, 42)
+    want = H.coarse_solve(c, p.mu)
+    tol = 1e-10 if prec == F64 else 1e-4
+    assert rel(ctx.coarse_solve(c, p.mu, prec), want) < tol
+
+
 def test_cycle_f64(small):
     ctx, H, U, p = small
     r = fields.gaussian_spinor(ctx.dims, 39)
