@@ -9,11 +9,6 @@
 
 using namespace tmg;
 
-struct tmg_ctx {
-  Ctx c;
-  tmg::Field fin, fout;   // per-call conversion buffers
-};
-
 namespace {
 
 int fail(tmg_ctx* ctx, int code, const std::string& msg) {

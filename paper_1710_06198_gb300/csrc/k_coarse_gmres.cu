@@ -87,10 +87,14 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
     if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
   }
   grid.sync();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     double t = 0.0;
-    for (int q = 0; q < G; q++) t += a.npart[q];
-    s_beta = sqrt(t);
+    for (int q = lane; q < G; q += 32) t += a.npart[q];
+    t = warp_sum(t);
+    if (lane == 0) s_beta = sqrt(t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     s_done = !(s_beta > 0.0);
     s_k = 0;
     for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
@@ -153,11 +157,16 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
         if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
       }
       grid.sync();                                   // partials complete
-      for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      // h_i = sum of the G partials: one warp per basis vector, lanes stride over the partials
+      for (int i = warp; i <= j; i += nwarp) {
         double re = 0.0, im = 0.0;
-        for (int q = 0; q < G; q++) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
-        hp[i] = make_double2(re, im);
-        hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+        for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) {
+          hp[i] = make_double2(re, im);
+          hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+        }
       }
       __syncthreads();
       // w -= sum_i h_i v_i on every element (grid-stride) and, in the last pass, ||w||^2
@@ -182,10 +191,15 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
       }
     }
     grid.sync();                                     // w and norm partials complete
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       double t = 0.0;
-      for (int q = 0; q < G; q++) t += a.npart[q];
-      const double hn = sqrt(t);
+      for (int q = lane; q < G; q += 32) t += a.npart[q];
+      t = warp_sum(t);
+      if (lane == 0) s_hn = sqrt(t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double hn = s_hn;
       hcol[j + 1] = make_double2(hn, 0.0);
       for (int i = 0; i < j; i++) {                  // previous rotations [[conj c, conj s], [-s, c]]
         const double2 x0 = hcol[i], x1 = hcol[i + 1];
@@ -206,7 +220,6 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
       gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
       if (blockIdx.x == 0)
         for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
-      s_hn = hn;
       s_k = j + 1;
       const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
       if (res <= a.rtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
@@ -261,7 +274,7 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   static int max_per_sm[2] = {-1, -1};
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
-  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, mps)));
+  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, 2))));
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
   c.cw_w.alloc(n * sizeof(T2));
   c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);

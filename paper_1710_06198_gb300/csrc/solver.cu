@@ -53,15 +53,25 @@ __global__ void k_mdot_partial(const T2* __restrict__ Vb, size_t stride, const T
   }
 }
 
-// out[i] = sum_b part[i * NPART + b]
+// out[i] = sum_b part[i * NPART + b], one CTA per i (grid: count)
 __global__ void k_mdot_final(const double2* __restrict__ part, int np, int count, double2* __restrict__ out,
                              const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  const int i = blockIdx.x;
   double a = 0, b = 0;
-  for (int k = 0; k < np; k++) { const double2 v = part[(size_t)i * NPART + k]; a += v.x; b += v.y; }
-  out[i] = make_double2(a, b);
+  for (int k = threadIdx.x; k < np; k += blockDim.x) { const double2 v = part[(size_t)i * NPART + k]; a += v.x; b += v.y; }
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0, tb = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { ta += sa[k]; tb += sb[k]; }
+    out[i] = make_double2(ta, tb);
+  }
 }
 
 // w -= sum_i coef[i] v_i  (coef on the device); optionally partial ||w||^2 into part[b]
@@ -252,7 +262,7 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
       using T2 = decltype(tag);
       for (int pass = 0; pass < 2; pass++) {
         ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
-        ++c.launches, k_mdot_final<<<1, 128, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
+        ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
         ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + pass * (MAXM + 1), (T2*)c.fw_w.p, n,
                                                    pass == 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
         TMG_CHECK_LAUNCH();

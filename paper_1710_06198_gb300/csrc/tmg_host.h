@@ -207,3 +207,9 @@ void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double m
 void build_coarse(Ctx& c);
 
 }  // namespace tmg
+
+// The opaque handle of the C ABI.
+struct tmg_ctx {
+  tmg::Ctx c;
+  tmg::Field fin, fout;   // per-call conversion buffers
+};
