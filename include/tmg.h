@@ -157,6 +157,18 @@ int tmg_solve(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double 
  * does not depend on values). */
 int tmg_bench_dslash(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_launch);
 
+/* Coarse solve that allocates nothing, for callers that cannot call cudaMalloc: code running
+ * under CUDA stream capture, hosts whose memory manager forbids allocation on the call path, and
+ * latency-critical loops.  (No counterpart in the paper: an interface addition.)  Same result as
+ * tmg_coarse_solve, but b and x are DEVICE pointers to FP64 coarse vectors ([V_c][2 N_v] complex,
+ * caller-owned) and all scratch comes from one fixed 32 MiB device array inside the library that
+ * every GPU loading the library keeps until the process exits.  A coarse problem whose scratch
+ * ((coarse_m + 3) x V_c x 2 N_v complex values plus partial sums) does not fit returns
+ * TMG_ERR_ARG.  The first call on a device looks up the array's device address, so make it before
+ * any stream capture.  Calls share the array: calls that overlap on the GPU race.  Stream-ordered
+ * on the context stream; no host synchronisation. */
+int tmg_coarse_solve_noalloc(tmg_ctx *ctx, const double *b, double *x, double mu, int prec);
+
 /* Kernel classes timed by tmg_profile (CUDA events around every launch of the class, on the
  * context stream).  Not a paper quantity: measurement support. */
 enum {

@@ -69,6 +69,7 @@ _SIGS = {
     "tmg_coarse_apply": [_P, _P, _P, _D, _I, _I],
     "tmg_cycle": [_P, _P, _P, _I],
     "tmg_coarse_solve": [_P, _P, _P, _D, _I, _I],
+    "tmg_coarse_solve_noalloc": [_P, _P, _P, _D, _I],
     "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
     "tmg_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],

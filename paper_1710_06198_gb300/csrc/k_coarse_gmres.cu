@@ -306,7 +306,75 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
 }
 
+template <typename S>
+int grid_size(Ctx& c) {
+  int mps = 0;
+  TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
+  return std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, 2))));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Scratch layout used by coarse_gmres_on_scratch: basis V, w, dot partials, R, y, norm partials,
+// step counter, each 256-byte aligned.
+template <typename S>
+size_t scratch_layout(const Ctx& c, int G, size_t off[8]) {
+  using T2 = typename CplxT<S>::T2;
+  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  const size_t sz[7] = {(m + 1) * n * sizeof(T2), n * sizeof(T2), sizeof(double2) * (CMAXM + 1) * G,
+                        sizeof(double2) * (CMAXM + 1) * CMAXM, sizeof(double2) * CMAXM, sizeof(double) * G, sizeof(int)};
+  size_t o = 0;
+  for (int i = 0; i < 7; i++) {
+    off[i] = o;
+    o = align256(o + sz[i]);
+  }
+  off[7] = o;
+  return o;
+}
+
+template <typename S>
+void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* scratch, int G) {
+  using T2 = typename CplxT<S>::T2;
+  size_t off[8];
+  scratch_layout<S>(c, G, off);
+  CgArgs<S> a;
+  a.nd = c.cl.nd;
+  a.nv = c.cl.nv;
+  a.nc = c.cl.nc;
+  a.m = std::min(c.mg.coarse_m, CMAXM);
+  a.passes = 2;
+  a.Dc = (const T2*)Dc;
+  a.nbr = c.cl.nbr.as<int>();
+  a.b = (const T2*)b;
+  a.x = (T2*)x;
+  a.V = (T2*)(scratch + off[0]);
+  a.w = (T2*)(scratch + off[1]);
+  a.part = (double2*)(scratch + off[2]);
+  a.R = (double2*)(scratch + off[3]);
+  a.y = (double2*)(scratch + off[4]);
+  a.npart = (double*)(scratch + off[5]);
+  a.counter = (int*)(scratch + off[6]);
+  a.mu = (S)mu;
+  a.rtol = c.mg.coarse_rtol;
+  TMG_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), c.stream));   // the shared scratch keeps old contents
+  void* args[] = {&a};
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
+}
+
 }  // namespace
+
+size_t coarse_gmres_scratch_bytes(Ctx& c, int cp) {
+  size_t off[8];
+  if (cp == TMG_PREC_F64) return scratch_layout<double>(c, grid_size<double>(c), off);
+  return scratch_layout<float>(c, grid_size<float>(c), off);
+}
+
+void coarse_gmres_on_scratch(Ctx& c, int cp, const void* b, void* x, double mu, void* scratch) {
+  if (cp == TMG_PREC_F64) launch_on<double>(c, b, x, mu, c.cl.Dc64.p, (char*)scratch, grid_size<double>(c));
+  else launch_on<float>(c, b, x, mu, c.cl.Dc32.p, (char*)scratch, grid_size<float>(c));
+}
 
 void coarse_gmres_persistent(Ctx& c, int cp, const void* b, void* x, double mu) {
   ProfScope ps(c, PK_COARSE_SOLVE);

@@ -204,6 +204,9 @@ void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const in
 void orthonormalise(Ctx& c, void* W64);
 // x ~= D_c(mu)^-1 b: one persistent cooperative GMRES kernel (k_coarse_gmres.cu)
 void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double mu);
+// The same solve on caller-provided device scratch (no allocation): bytes needed, and the launch.
+size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
+void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);
 void build_coarse(Ctx& c);
 
 }  // namespace tmg
