@@ -177,6 +177,9 @@ def run_ours(args):
     ctx = tmg.Context(w["dims"], w["block"], device=local)
     ctx.set_params(kappa, w["csw"], w["mu"])
     ctx.load_gauge(U, -1)
+    for kv in args.tune:
+        k, v = kv.split("=")
+        ctx.tune(k, float(v))
     prm = tmg.Context.mg_defaults()
     prm.nv = w["nv"]
     prm.prec_fine = tmg.PREC_F16 if args.fine == "f16" else tmg.PREC_F32
@@ -307,7 +310,7 @@ def run_ours(args):
         "config": {"workload": w["name"], "lattice": list(w["dims"]), "kappa": kappa,
                    "kappa_source": kinfo.get("source"), "csw": w["csw"], "mu": w["mu"], "levels": 2,
                    "sap_block": list(w["block"]), "aggregate": list(w["block"]), "nv": w["nv"],
-                   "fine_precision": args.fine, "tol": w["tol"], "rhs": 1, "l2": "flushed (512 MB write) between steps",
+                   "fine_precision": args.fine, "tol": w["tol"], "rhs": 1, "tune": args.tune, "l2": "flushed (512 MB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": iters[-1], "refinements": stats["refinements"], "coarse_iterations": stats["coarse_iterations"],
         "true_residual": true_res, "setup_s": round(setup_s, 3),
@@ -401,6 +404,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--ncu-solve", action="store_true", help="profile one solve only (for ncu)")
+    ap.add_argument("--tune", action="append", default=[], help="launch-shape knob key=value (tmg_tune)")
     ap.add_argument("--kernel-case", choices=["dslash", "sap"], default=None,
                     help="run one kernel class on a 24^3 x 48 lattice (for ncu --set full)")
     args = ap.parse_args()

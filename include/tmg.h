@@ -151,6 +151,16 @@ enum {
 int tmg_solve(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double *mu_per_col,
               double tol, int method, int maxiter, tmg_stats *stats, int where);
 
+/* ---- force (the HMC force terms of Sec. 2 and 3, solves in the two-step form of Sec. 1.1) ----
+ * S = phi^dag (D D^dag)^-1 phi = ||D(mu)^-1 phi||^2.  F[V][4][3][3] (complex, lexicographic sites,
+ * direction, row, column) is the traceless Hermitian field with dS/dt = sum_{x,mu} tr(H F) under
+ * U_mu(x) -> exp(i t H_mu(x)) U_mu(x).
+ *   tmg_force_xy: F from X = D^-dag Y and Y = D^-1 phi given by the caller (FP64 fine spinors);
+ *   tmg_force:    solves Y = D(mu)^-1 phi and X = g5 D(-mu)^-1 g5 Y with the mixed-precision
+ *                 multigrid (tolerance tol, needs tmg_setup), returns S in *action (may be NULL). */
+int tmg_force_xy(tmg_ctx *ctx, const double *X, const double *Y, double *F, int where);
+int tmg_force(tmg_ctx *ctx, const double *phi, double *F, double tol, double *action, tmg_stats *stats, int where);
+
 /* Time `n_iter` back-to-back launches of the dslash kernel (y = D x, one column, storage
  * precision prec) on the context stream with CUDA events; writes the mean milliseconds per
  * launch.  Inputs are the library's internal fields (random data is not needed: the timing
@@ -163,7 +173,7 @@ int tmg_bench_dslash(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_launch);
  * tmg_coarse_solve, but b and x are DEVICE pointers to FP64 coarse vectors ([V_c][2 N_v] complex,
  * caller-owned) and all scratch comes from one fixed 32 MiB device array inside the library that
  * every GPU loading the library keeps until the process exits.  A coarse problem whose scratch
- * ((coarse_m + 3) x V_c x 2 N_v complex values plus partial sums) does not fit returns
+ * ((coarse_m + 13) x V_c x 2 N_v complex values plus partial sums) does not fit returns
  * TMG_ERR_ARG.  The first call on a device looks up the array's device address, so make it before
  * any stream capture.  Calls share the array: calls that overlap on the GPU race.  Stream-ordered
  * on the context stream; no host synchronisation. */
@@ -181,6 +191,11 @@ enum {
 int tmg_profile(tmg_ctx *ctx, int enable);
 /* Launches recorded for class `kind` and their summed device time in milliseconds. */
 int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total);
+
+/* Launch-shape knobs (not paper quantities): "coarse_ctas_per_sm" (1..8, CTAs per SM of the
+ * persistent coarse GMRES, capped by occupancy) and "coarse_gs_passes" (1 or 2 classical
+ * Gram-Schmidt passes in the coarse GMRES; 0 = 1 in FP32, 2 in FP64).  TMG_ERR_ARG for an unknown key or value. */
+int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 
 /* Number of CUDA kernels this context has launched so far (every launcher counts its launches;
  * lets a caller count the kernels inside a timed region).  Not a paper quantity. */

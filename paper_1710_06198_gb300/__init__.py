@@ -74,6 +74,9 @@ _SIGS = {
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
     "tmg_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "tmg_profile": [_P, _I],
+    "tmg_tune": [_P, ctypes.c_char_p, _D],
+    "tmg_force_xy": [_P, _P, _P, _P, _I],
+    "tmg_force": [_P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(Stats), _I],
     "tmg_profile_read": [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)],
 }
 
@@ -274,6 +277,28 @@ class Context:
         if check:
             self._check(rc)
         return x, st.as_dict()
+
+    def force_xy(self, X, Y):
+        """F[T, Z, Y, X, mu, 3, 3] of S = ||D^-1 phi||^2 from X = D^-dag Y, Y = D^-1 phi."""
+        F = _empty_like(X, self.lat + (4, 3, 3))
+        px, wh = _ptr(X)
+        py, _ = _ptr(Y)
+        pf, _ = _ptr(F)
+        self._check(lib().tmg_force_xy(self._h, px, py, pf, wh))
+        return F
+
+    def force(self, phi, tol=1e-10):
+        """(S, F, stats): action and force with both solves done by the multigrid."""
+        F = _empty_like(phi, self.lat + (4, 3, 3))
+        pp, wh = _ptr(phi)
+        pf, _ = _ptr(F)
+        S = ctypes.c_double()
+        st = Stats()
+        self._check(lib().tmg_force(self._h, pp, pf, float(tol), ctypes.byref(S), ctypes.byref(st), wh))
+        return S.value, F, st.as_dict()
+
+    def tune(self, key, value):
+        self._check(lib().tmg_tune(self._h, key.encode(), float(value)))
 
     def bench_dslash(self, prec=PREC_F32, n_iter=100):
         ms = ctypes.c_double()

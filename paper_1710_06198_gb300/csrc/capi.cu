@@ -6,6 +6,7 @@
 
 #include "tmg_host.h"
 #include "solver.h"
+#include <algorithm>
 
 using namespace tmg;
 
@@ -245,6 +246,84 @@ int tmg_profile_read(tmg_ctx* ctx, int kind, long long* count, double* ms_total)
     }
     *count = (long long)ctx->c.prof.recs[kind].size();
     *ms_total = t;
+    return TMG_OK;
+  });
+}
+
+int tmg_force_xy(tmg_ctx* ctx, const double* X, const double* Y, double* F, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!X || !Y || !F || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_force_xy: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_force_xy: no gauge field loaded");
+    const size_t col = (size_t)24 * c.g.V;
+    tmg::Field xf, yf;
+    xf.create(c.g, TMG_PREC_F64, 1);
+    yf.create(c.g, TMG_PREC_F64, 1);
+    spinor_from_lex(c, stage_in(c, c.stage_a, X, col, where), xf.buf.p, TMG_PREC_F64);
+    spinor_from_lex(c, stage_in(c, c.stage_b, Y, col, where), yf.buf.p, TMG_PREC_F64);
+    const size_t nf = (size_t)c.g.V * 4 * 9 * 2;
+    DBuf fo;
+    double* fd = where == TMG_DEVICE ? F : (fo.alloc(nf * sizeof(double)), fo.as<double>());
+    force_from_xy(c, xf.buf.p, yf.buf.p, fd);
+    if (where == TMG_HOST) {
+      TMG_CUDA(cudaMemcpyAsync(F, fd, nf * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    }
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    return TMG_OK;
+  });
+}
+
+int tmg_force(tmg_ctx* ctx, const double* phi, double* F, double tol, double* action, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!phi || !F || !(tol > 0.0) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_force: bad argument");
+    if (!c.gauge_loaded || !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_force: needs a gauge field and a setup");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    const size_t n = (size_t)12 * c.g.V;
+    tmg::Field pf, yf, xf, tf;
+    pf.create(c.g, TMG_PREC_F64, 1);
+    yf.create(c.g, TMG_PREC_F64, 1);
+    xf.create(c.g, TMG_PREC_F64, 1);
+    tf.create(c.g, TMG_PREC_F64, 1);
+    spinor_from_lex(c, stage_in(c, c.stage_a, phi, col, where), pf.buf.p, TMG_PREC_F64);
+    SolveStats s1{}, s2{};
+    // Y = D(mu)^-1 phi ; X = D(mu)^-dag Y = g5 D(-mu)^-1 g5 Y (the same P serves both signs of mu)
+    int rc = solve_one(c, TMG_SOLVE_MG_MIXED, pf.buf.p, yf.buf.p, c.mu, tol, 100000, s1);
+    if (rc != TMG_OK) return fail(ctx, rc, "tmg_force: solve for Y failed");
+    blas_copy(c, yf.buf.p, tf.buf.p, TMG_PREC_F64, n);
+    gamma5_inplace(c, tf.buf.p, TMG_PREC_F64);
+    rc = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, xf.buf.p, -c.mu, tol, 100000, s2);
+    if (rc != TMG_OK) return fail(ctx, rc, "tmg_force: solve for X failed");
+    gamma5_inplace(c, xf.buf.p, TMG_PREC_F64);
+    if (action) *action = blas_norm2(c, yf.buf.p, TMG_PREC_F64, n);
+    const size_t nf = (size_t)c.g.V * 4 * 9 * 2;
+    DBuf fo;
+    double* fd = where == TMG_DEVICE ? F : (fo.alloc(nf * sizeof(double)), fo.as<double>());
+    force_from_xy(c, xf.buf.p, yf.buf.p, fd);
+    if (where == TMG_HOST) {
+      TMG_CUDA(cudaMemcpyAsync(F, fd, nf * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    }
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (stats) {
+      stats->iterations = s1.iterations + s2.iterations;
+      stats->refinements = s1.refinements + s2.refinements;
+      stats->coarse_iterations = s1.coarse_iterations + s2.coarse_iterations;
+      stats->true_residual = std::max(s1.true_residual, s2.true_residual);
+      stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return TMG_OK;
+  });
+}
+
+int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
+  return guarded(ctx, [&]() -> int {
+    if (!key) return fail(ctx, TMG_ERR_ARG, "tmg_tune: null key");
+    const std::string k(key);
+    const int v = (int)value;
+    if (k == "coarse_ctas_per_sm" && v >= 1 && v <= 8) ctx->c.coarse_ctas_per_sm = v;
+    else if (k == "coarse_gs_passes" && (v >= 0 && v <= 2)) ctx->c.coarse_gs_passes = v;
+    else return fail(ctx, TMG_ERR_ARG, "tmg_tune: unknown key or value out of range: " + k);
     return TMG_OK;
   });
 }

@@ -34,6 +34,7 @@ struct CgArgs {
   typename CplxT<S>::T2* x;
   typename CplxT<S>::T2* V;          // (m + 1) x n basis
   typename CplxT<S>::T2* w;
+  typename CplxT<S>::T2* rows;       // [nc][9][nd] partial stencil rows
   S mu;
   double rtol;
   double2* part;                     // [CMAXM + 1][grid] dot partials
@@ -68,16 +69,17 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
   __shared__ double2 hcol[CMAXM + 2];
   __shared__ double2 cs[CMAXM], sn[CMAXM], gv[CMAXM + 1];
   __shared__ double2 hp[CMAXM + 1];
-  __shared__ double2 rowp[9 * CMAXND];
   __shared__ int s_done, s_k;
   __shared__ double s_beta, s_hn;
   const int n = a.nc * a.nd;
   const int G = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
-  // chunk of elements owned by this CTA for the dot products
+  // contiguous chunk of the vector owned by this CTA (the CTA that writes an element is the only
+  // one that reads it until the next grid barrier)
   const int chunk = (n + G - 1) / G;
-  const int e0 = blockIdx.x * chunk, e1 = min(n, e0 + chunk);
+  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int gwarp = blockIdx.x * nwarp + warp, nwarps_total = G * nwarp;
 
   // beta = ||b||
   {
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
   if (threadIdx.x == 0) {
     s_done = !(s_beta > 0.0);
     s_k = 0;
+    s_hn = 1.0;
     for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
     gv[0] = make_double2(s_beta, 0.0);
   }
@@ -105,46 +108,56 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
     const S inv = s_beta > 0.0 ? (S)(1.0 / s_beta) : (S)0;
     for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
   }
+  grid.sync();                                       // v_0 complete
   for (int j = 0; j < a.m && !s_done; j++) {
-    grid.sync();                                     // v_j complete
-    const T2* vj = a.V + (size_t)j * n;
-    // w = D_c(mu) v_j : a CTA per coarse site, a warp per stencil block (lanes = rows, coalesced
-    // 32-row columns of the block), then the 9 partial rows are summed through shared memory.
-    for (int site = blockIdx.x; site < a.nc; site += G) {
-      for (int d = warp; d < 9; d += nwarp) {
-        const int nb = a.nbr[site * 9 + d];
-        const T2* blk = a.Dc + ((size_t)(site * 9 + d) * a.nd) * a.nd;
-        const T2* xv = vj + (size_t)nb * a.nd;
-        for (int k = lane; k < a.nd; k += 32) {
-          S ar = 0, ai = 0;
-#pragma unroll 4
-          for (int l = 0; l < a.nd; l++) {
-            const T2 m = blk[(size_t)l * a.nd + k];
-            const T2 v = xv[l];
-            ar += m.x * v.x - m.y * v.y;
-            ai += m.x * v.y + m.y * v.x;
-          }
-          rowp[d * CMAXND + k] = make_double2((double)ar, (double)ai);
+    // v_j = v_0, or the previous step's orthogonalised w scaled by 1 / h_{j,j-1}.
+    const T2* src = j == 0 ? a.V : a.w;
+    const S scale = j == 0 ? (S)1 : (S)(1.0 / s_hn);
+    T2* vj = a.V + (size_t)j * n;
+    // (1) stencil products, one warp per (coarse site, stencil block) spread over the whole grid:
+    //     lanes are rows, so every column of a block is one coalesced 32-row read.
+    for (int task = gwarp; task < a.nc * 9; task += nwarps_total) {
+      const int site = task / 9;
+      const int nb = a.nbr[task];
+      const T2* blk = a.Dc + (size_t)task * a.nd * a.nd;
+      const T2* xv = src + (size_t)nb * a.nd;
+      for (int k = lane; k < a.nd; k += 32) {
+        S ar = 0, ai = 0;
+#pragma unroll 8
+        for (int l = 0; l < a.nd; l++) {
+          const T2 m = blk[(size_t)l * a.nd + k];
+          const T2 v = xv[l];
+          ar += m.x * v.x - m.y * v.y;
+          ai += m.x * v.y + m.y * v.x;
         }
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < a.nd; k += blockDim.x) {
-        double ar = 0.0, ai = 0.0;
-        for (int d = 0; d < 9; d++) { ar += rowp[d * CMAXND + k].x; ai += rowp[d * CMAXND + k].y; }
-        const T2 xs = vj[(size_t)site * a.nd + k];
-        const double tw = k < a.nv ? (double)a.mu : -(double)a.mu;
         T2 o;
-        o.x = (S)(ar - tw * (double)xs.y);
-        o.y = (S)(ai + tw * (double)xs.x);
-        a.w[(size_t)site * a.nd + k] = o;
+        o.x = ar * scale;
+        o.y = ai * scale;
+        a.rows[(size_t)task * a.nd + k] = o;
+        (void)site;
       }
-      __syncthreads();
+    }
+    grid.sync();                                     // partial rows complete
+    // (2) own chunk: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int site = e / a.nd, k = e - site * a.nd;
+      T2 xs = src[e];
+      xs.x *= scale;
+      xs.y *= scale;
+      if (j > 0) vj[e] = xs;
+      S ar = 0, ai = 0;
+      for (int d = 0; d < 9; d++) { const T2 r = a.rows[((size_t)site * 9 + d) * a.nd + k]; ar += r.x; ai += r.y; }
+      const S tw = k < a.nv ? a.mu : -a.mu;
+      T2 o;
+      o.x = ar - tw * xs.y;
+      o.y = ai + tw * xs.x;
+      a.w[e] = o;
     }
     if (threadIdx.x == 0)
       for (int i = 0; i <= j + 1; i++) hcol[i] = make_double2(0.0, 0.0);
+    __syncthreads();
     for (int pass = 0; pass < a.passes; pass++) {
-      grid.sync();                                   // w complete
-      // partial <v_i, w> over this CTA's chunk, one warp per basis vector
+      // partial <v_i, w> over the own chunk, one warp per basis vector
       for (int i = warp; i <= j; i += nwarp) {
         const T2* vi = a.V + (size_t)i * n;
         S re = 0, im = 0;
@@ -157,7 +170,6 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
         if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
       }
       grid.sync();                                   // partials complete
-      // h_i = sum of the G partials: one warp per basis vector, lanes stride over the partials
       for (int i = warp; i <= j; i += nwarp) {
         double re = 0.0, im = 0.0;
         for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
@@ -169,9 +181,9 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
         }
       }
       __syncthreads();
-      // w -= sum_i h_i v_i on every element (grid-stride) and, in the last pass, ||w||^2
+      // w -= sum_i h_i v_i on the own chunk and, in the last pass, ||w||^2
       S nn = 0;
-      for (int e = tid; e < n; e += nth) {
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         T2 q = a.w[e];
         S qr = q.x, qi = q.y;
         for (int i = 0; i <= j; i++) {
@@ -188,6 +200,8 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
       if (pass == a.passes - 1) {
         const double t = cta_sum((double)nn, sh);
         if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+      } else {
+        __syncthreads();
       }
     }
     grid.sync();                                     // w and norm partials complete
@@ -225,11 +239,6 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
       if (res <= a.rtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
     }
     __syncthreads();
-    if (!s_done) {
-      const S inv = (S)(1.0 / s_hn);
-      T2* vn = a.V + (size_t)(j + 1) * n;
-      for (int e = tid; e < n; e += nth) { T2 v = a.w[e]; v.x *= inv; v.y *= inv; vn[e] = v; }
-    }
   }
   grid.sync();                                       // rotated Hessenberg stored by CTA 0
   const int k = s_k;
@@ -274,9 +283,9 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   static int max_per_sm[2] = {-1, -1};
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
-  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, 2))));
+  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
-  c.cw_w.alloc(n * sizeof(T2));
+  c.cw_w.alloc(10 * n * sizeof(T2));
   c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
   if (!c.coarse_iter_dev.p) {
     c.coarse_iter_dev.alloc(sizeof(int));
@@ -287,13 +296,14 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   a.nv = c.cl.nv;
   a.nc = c.cl.nc;
   a.m = m;
-  a.passes = 2;
+  a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
   a.b = (const T2*)b;
   a.x = (T2*)x;
   a.V = c.cw_V.as<T2>();
   a.w = c.cw_w.as<T2>();
+  a.rows = a.w + n;
   a.mu = (S)mu;
   a.rtol = c.mg.coarse_rtol;
   a.part = c.cw_part.as<double2>();
@@ -315,14 +325,14 @@ int grid_size(Ctx& c) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Scratch layout used by coarse_gmres_on_scratch: basis V, w, dot partials, R, y, norm partials,
+// Scratch layout used by coarse_gmres_on_scratch: basis V, w and the 9 partial stencil rows, dot partials, R, y, norm partials,
 // step counter, each 256-byte aligned.
 template <typename S>
 size_t scratch_layout(const Ctx& c, int G, size_t off[8]) {
   using T2 = typename CplxT<S>::T2;
   const int m = std::min(c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)c.cl.nc * c.cl.nd;
-  const size_t sz[7] = {(m + 1) * n * sizeof(T2), n * sizeof(T2), sizeof(double2) * (CMAXM + 1) * G,
+  const size_t sz[7] = {(m + 1) * n * sizeof(T2), 10 * n * sizeof(T2), sizeof(double2) * (CMAXM + 1) * G,
                         sizeof(double2) * (CMAXM + 1) * CMAXM, sizeof(double2) * CMAXM, sizeof(double) * G, sizeof(int)};
   size_t o = 0;
   for (int i = 0; i < 7; i++) {
@@ -343,13 +353,14 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.nv = c.cl.nv;
   a.nc = c.cl.nc;
   a.m = std::min(c.mg.coarse_m, CMAXM);
-  a.passes = 2;
+  a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
   a.b = (const T2*)b;
   a.x = (T2*)x;
   a.V = (T2*)(scratch + off[0]);
   a.w = (T2*)(scratch + off[1]);
+  a.rows = a.w + (size_t)c.cl.nc * c.cl.nd;
   a.part = (double2*)(scratch + off[2]);
   a.R = (double2*)(scratch + off[3]);
   a.y = (double2*)(scratch + off[4]);

@@ -358,6 +358,13 @@ void blas_scale(Ctx& c, double ar, double ai, void* x, int prec, size_t n) {
   else ++c.launches, k_scale<float2><<<gr, 256, 0, c.stream>>>(ar, ai, (float2*)x, n);
   TMG_CHECK_LAUNCH();
 }
+// g5 = diag(1, 1, -1, -1): spins 2, 3 are the complex components 6..11, i.e. component pairs 3..5,
+// which form the contiguous second half [6 V, 12 V) of a field's flat complex array.
+void gamma5_inplace(Ctx& c, void* x, int prec) {
+  const size_t half = (size_t)6 * c.g.V;
+  blas_scale(c, -1.0, 0.0, (char*)x + half * (prec == TMG_PREC_F64 ? 16 : 8), prec, half);
+}
+
 void blas_axpy_mixed(Ctx& c, double a, const void* x, int px, void* y, int py, size_t n) {
   const int gr = grid_for(c, n);
   if (px == TMG_PREC_F32 && py == TMG_PREC_F64) ++c.launches, k_axpy_mixed<<<gr, 256, 0, c.stream>>>(a, (const float2*)x, (double2*)y, n);

@@ -141,6 +141,9 @@ struct Ctx {
   std::string err;
   int sms = 152;
   long long launches = 0;  // kernels launched by this context (all launchers count)
+  // launch-shape tuning knobs (tmg_tune)
+  int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
+  int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
   Prof prof;
 };
 
@@ -182,6 +185,8 @@ void blas_axpy(Ctx& c, double are, double aim, const void* x, void* y, int prec,
 void blas_xpay(Ctx& c, const void* x, double are, double aim, void* y, int prec, size_t n);
 // x = a x
 void blas_scale(Ctx& c, double are, double aim, void* x, int prec, size_t n);
+// x = g5 x on a fine field
+void gamma5_inplace(Ctx& c, void* x, int prec);
 // y_prec_dst += a * x_prec_src (mixed precision accumulate, F32 -> F64 typical)
 void blas_axpy_mixed(Ctx& c, double a, const void* x, int px, void* y, int py, size_t n);
 // result[0] = re <x, y>, result[1] = im <x, y> into device doubles (FP64 accumulation)
@@ -194,6 +199,11 @@ void blas_dot(Ctx& c, const void* x, const void* y, int prec, size_t n, double* 
 void dslash(Ctx& c, int prec, void* y, const void* x, const void* b, double mu, int mode, int dagger);
 // non-degenerate doublet (Eq. 2) on F64 / F32 fields with 2 flavour columns
 void dslash_nd(Ctx& c, int prec, void* y, const void* x);
+
+// ---------------------------------------------------------------- force (k_force.cu)
+// F (lexicographic [V][4][3][3] complex, device) of S = ||D^-1 phi||^2 from internal F64 fields
+// X = D^-dag D^-1 phi and Y = D^-1 phi
+void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex);
 
 // ---------------------------------------------------------------- multigrid (k_mg.cu)
 void sap_sweeps(Ctx& c, int prec, void* x, const void* b, void* r_scratch, double mu, int n_sweeps);
