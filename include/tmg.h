@@ -142,7 +142,9 @@ enum {
   TMG_SOLVE_MG_F64 = 0,   /* FGMRES + DD-alpha-AMG, everything in FP64                     */
   TMG_SOLVE_MG_MIXED = 1, /* FP64 defect correction around FGMRES + DD-alpha-AMG in the MG   */
                           /* params' fine/coarse precisions                                 */
-  TMG_SOLVE_CG_F64 = 2    /* CG on D D^dag in FP64 (comparator of Sec. 1.1 / Fig. 1)       */
+  TMG_SOLVE_CG_F64 = 2,   /* CG on D D^dag in FP64 (comparator of Sec. 1.1 / Fig. 1)       */
+  TMG_SOLVE_MG_BATCHED = 3 /* as TMG_SOLVE_MG_MIXED, all n_rhs (<= 32) columns in lock-step: */
+                          /* one launch per operation for every column, FP32 coarse level    */
 };
 
 /* Solve D(mu) x = b (relative FP64 residual tol) for n_rhs right-hand sides, one after another.

@@ -5,7 +5,8 @@ mu = 0".  sigma_min(D_W) is the smallest singular value of D_W, equal to the sma
 of the Hermitian Q = G5 D_W (Eq. 3 uses Q = G5 D).  This module assembles D_W as a sparse matrix,
 gets min |lambda(Q)| by shift-invert Lanczos around 0 (scipy ``eigsh``, i.e. a sparse LU of Q), and
 runs the search: start at m0 = 0, step m0 down by 0.05 until sigma_min drops below the target, then
-bisect the last step until sigma_min is within +-2 % of the target (the first crossing from above).
+bisect the last step until sigma_min is within +-2 % of the target (the first crossing from above);
+if no m0 down to -2 reaches the target, the most critical m0 (minimum of sigma_min) is used.
 
 Pinned by tests/test_oracle_kappa.py: the sparse matrix equals the matrix-free operator of
 ``oracle.dirac`` on random vectors, and on the free field sigma_min equals the closed form
@@ -98,39 +99,60 @@ def sigma_min_mg(U, p: dirac.Params, clover=None, mgp=None, seed=7, tol=1e-10):
     return float(1.0 / np.max(np.abs(w)))
 
 
-def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, max_steps=80, log=None, method=None):
-    """First crossing from above of sigma_min(D_W(m0)) = target, to +-rel_tol.  Returns
-    (m0, sigma_min, evaluations)."""
+def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, m0_min=-2.0, log=None, method=None, progress=None):
+    """kappa search on sigma_min(D_W(m0)).
+
+    Scan m0 = 0, -step, -2 step, ... down to m0_min.  If sigma_min drops below the target, bisect
+    the last step until sigma_min is within +-rel_tol of the target (the first crossing from
+    above).  If it never does (a lattice too small or a field too smooth to have a mode that
+    low), return the scan's minimiser refined by golden-section search: the most critical m0.
+    Returns (m0, sigma_min, reached_target)."""
     clover = dirac.clover_term(U, csw)
     method = sigma_min if method is None else method
+    log = [] if log is None else log
 
     def s(m0):
         v = method(U, dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, tbc=tbc), clover)
-        if log is not None:
-            log.append((m0, v))
+        log.append((m0, v))
+        if progress is not None:
+            progress(m0, v)
         return v
 
     hi, s_hi = 0.0, s(0.0)
     if s_hi < target:
         raise ValueError("sigma_min already below target at m0 = 0")
-    lo = hi
-    for _ in range(max_steps):
-        lo = hi - step
+    n = int(round(-m0_min / step))
+    for i in range(1, n + 1):
+        lo = -i * step
         s_lo = s(lo)
         if s_lo < target:
-            break
+            if abs(s_lo - target) <= rel_tol * target:
+                return lo, s_lo, True
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                s_mid = s(mid)
+                if abs(s_mid - target) <= rel_tol * target:
+                    return mid, s_mid, True
+                if s_mid < target:
+                    lo = mid
+                else:
+                    hi = mid
+            raise ValueError("bisection did not reach the tolerance")
         hi, s_hi = lo, s_lo
-    else:
-        raise ValueError("no crossing found")
-    if abs(s_lo - target) <= rel_tol * target:
-        return lo, s_lo, len(log) if log is not None else None
-    for _ in range(60):
-        mid = 0.5 * (lo + hi)
-        s_mid = s(mid)
-        if abs(s_mid - target) <= rel_tol * target:
-            return mid, s_mid, len(log) if log is not None else None
-        if s_mid < target:
-            lo = mid
+    # no crossing: golden-section refinement around the scan minimum
+    m_best, s_best = min(log, key=lambda t: t[1])
+    a_, b_ = m_best - step, m_best + step
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    c_, d_ = b_ - g * (b_ - a_), a_ + g * (b_ - a_)
+    fc, fd = s(c_), s(d_)
+    for _ in range(12):
+        if fc < fd:
+            b_, d_, fd = d_, c_, fc
+            c_ = b_ - g * (b_ - a_)
+            fc = s(c_)
         else:
-            hi = mid
-    raise ValueError("bisection did not reach the tolerance")
+            a_, c_, fc = c_, d_, fd
+            d_ = a_ + g * (b_ - a_)
+            fd = s(d_)
+    m_best, s_best = min(log, key=lambda t: t[1])
+    return m_best, s_best, False

@@ -24,8 +24,10 @@ def main(argv):
     U = fields.gauge_field(dims, eps, seed)
     log = []
     t0 = time.time()
-    m0, smin, _ = kappa.search_m0(U, csw, -1, target, log=log)
-    rec = {"m0": m0, "kappa": dirac.kappa_from_m0(m0), "sigma_min": smin, "search_lattice": list(dims),
+    prog = lambda m, v: print(f"m0 {m:+.5f} sigma_min {v:.6e} ({time.time() - t0:.0f} s)", file=sys.stderr, flush=True)
+    m0, smin, reached = kappa.search_m0(U, csw, -1, target, log=log, progress=prog)
+    rec = {"m0": m0, "kappa": dirac.kappa_from_m0(m0), "sigma_min": smin, "reached_target": reached,
+           "search_lattice": list(dims),
            "eps": eps, "seed": seed, "csw": csw, "target": target, "evaluations": len(log),
            "cpu_s": round(time.time() - t0, 1), "log": log}
     print(json.dumps({name: rec}))

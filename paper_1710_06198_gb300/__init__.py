@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libtmg.so")
 PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 OP_D, OP_DDAG, OP_DND, OP_HOP = 0, 1, 2, 3
-SOLVE_MG_F64, SOLVE_MG_MIXED, SOLVE_CG_F64 = 0, 1, 2
+SOLVE_MG_F64, SOLVE_MG_MIXED, SOLVE_CG_F64, SOLVE_MG_BATCHED = 0, 1, 2, 3
 STATUS = {0: "TMG_OK", -1: "TMG_ERR_ARG", -2: "TMG_ERR_CUDA", -3: "TMG_ERR_OOM", -4: "TMG_ERR_NOCONV",
           -5: "TMG_ERR_BREAKDOWN", -6: "TMG_ERR_TIMEOUT", -7: "TMG_ERR_STATE"}
 

@@ -7,6 +7,7 @@
 #include "tmg_host.h"
 #include "solver.h"
 #include <algorithm>
+#include <vector>
 
 using namespace tmg;
 
@@ -168,6 +169,25 @@ int tmg_apply(tmg_ctx* ctx, int op, const double* x, double* y, int n_rhs, const
     const int sp = storage_of(prec);
     const int nfl = op == TMG_OP_DND ? 2 : 1;
     const size_t col = (size_t)24 * c.g.V;  // doubles per flavour column
+    if (op == TMG_OP_D && prec != TMG_PREC_F64 && n_rhs > 1) {
+      // all columns through the multi-column kernel (links and clover fetched once per site)
+      ctx->fin.create(c.g, sp, n_rhs);
+      ctx->fout.create(c.g, sp, n_rhs);
+      const double* xd = stage_in(c, c.stage_a, x, col * n_rhs, where);
+      for (int j = 0; j < n_rhs; j++) spinor_from_lex(c, xd + j * col, ctx->fin.col(c.g, j), sp);
+      std::vector<float> mus(n_rhs, (float)c.mu);
+      if (mu_per_col)
+        for (int j = 0; j < n_rhs; j++) mus[j] = (float)mu_per_col[j];
+      DBuf mu_dev;
+      mu_dev.alloc(n_rhs * sizeof(float));
+      TMG_CUDA(cudaMemcpyAsync(mu_dev.p, mus.data(), n_rhs * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+      dslash_mrhs(c, prec, n_rhs, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, mu_dev.as<float>(), 0);
+      double* yd = stage_out_ptr(c, c.stage_b, y, col * n_rhs, where);
+      for (int j = 0; j < n_rhs; j++) spinor_to_lex(c, ctx->fout.col(c.g, j), sp, yd + j * col);
+      stage_out_finish(c, c.stage_b, y, col * n_rhs, where);
+      TMG_CUDA(cudaStreamSynchronize(c.stream));
+      return TMG_OK;
+    }
     ctx->fin.create(c.g, sp, nfl);
     ctx->fout.create(c.g, sp, nfl);
     for (int j = 0; j < n_rhs; j++) {
@@ -506,7 +526,7 @@ int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double*
               int maxiter, tmg_stats* stats, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
-    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 2)
+    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 3)
       return fail(ctx, TMG_ERR_ARG, "tmg_solve: bad argument");
     if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no gauge field loaded");
     if (method != TMG_SOLVE_CG_F64 && !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no multigrid setup");
@@ -514,6 +534,31 @@ int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double*
     const size_t col = (size_t)24 * c.g.V;
     tmg_stats acc{};
     int rc = TMG_OK;
+    if (method == TMG_SOLVE_MG_BATCHED) {
+      if (n_rhs > 32) return fail(ctx, TMG_ERR_ARG, "tmg_solve: at most 32 columns per batched solve");
+      tmg::Field bf, xf;
+      bf.create(c.g, TMG_PREC_F64, n_rhs);
+      xf.create(c.g, TMG_PREC_F64, n_rhs);
+      const double* bd = stage_in(c, c.stage_a, b, col * n_rhs, where);
+      for (int j = 0; j < n_rhs; j++) spinor_from_lex(c, bd + j * col, bf.col(c.g, j), TMG_PREC_F64);
+      std::vector<double> mus(n_rhs, c.mu);
+      if (mu_per_col)
+        for (int j = 0; j < n_rhs; j++) mus[j] = mu_per_col[j];
+      SolveStats st{};
+      rc = solve_batched(c, n_rhs, bf.buf.p, xf.buf.p, mus.data(), tol, maxiter, st);
+      double* out = stage_out_ptr(c, c.stage_b, x, col * n_rhs, where);
+      for (int j = 0; j < n_rhs; j++) spinor_to_lex(c, xf.col(c.g, j), TMG_PREC_F64, out + j * col);
+      stage_out_finish(c, c.stage_b, x, col * n_rhs, where);
+      TMG_CUDA(cudaStreamSynchronize(c.stream));
+      acc.iterations = st.iterations;
+      acc.refinements = st.refinements;
+      acc.coarse_iterations = st.coarse_iterations;
+      acc.true_residual = st.true_residual;
+      acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (stats) *stats = acc;
+      if (rc != TMG_OK && c.err.empty()) c.err = "solver did not converge";
+      return rc;
+    }
     for (int j = 0; j < n_rhs; j++) {
       const double mu = mu_per_col ? mu_per_col[j] : c.mu;
       tmg::Field bf, xf;

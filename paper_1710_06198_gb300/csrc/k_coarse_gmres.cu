@@ -275,6 +275,284 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
   }
 }
 
+// ---- batched version: ncol right-hand sides (each with its own twist) in lock-step.  Every
+// stencil block is read once per group of 4 columns; Gram-Schmidt, Givens rotations and the
+// stopping test are per column.  The loop ends when every column has converged (or after m steps).
+// Layout: vectors [col][n]; basis V[i][col][n]; rows [col][nc * 9][nd].
+constexpr int CB = 4;   // columns per register group in the stencil products
+constexpr int BMAXC = 32;
+
+struct CgbArgs {
+  int nd, nv, nc, m, ncol;
+  const float2* Dc;
+  const int* nbr;
+  const float2* b;
+  float2* x;
+  float2* V;
+  float2* w;
+  float2* rows;
+  const float* mu;       // [ncol]
+  double rtol;
+  double2* part;         // [ncol][CMAXM + 1][G]
+  double* npart;         // [ncol][G]
+  double2* R;            // [ncol][(CMAXM + 1) * CMAXM]
+  double2* y;            // [ncol][CMAXM]
+  int* counter;
+};
+
+__global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double2 bsm[];
+  // per column: cs[CMAXM], sn[CMAXM], gv[CMAXM + 1], hcol[CMAXM + 2], hp[CMAXM + 1]
+  const int per = 5 * CMAXM + 4;
+  __shared__ double sh[32];
+  __shared__ double s_beta[BMAXC], s_hn[BMAXC];
+  __shared__ int s_done[BMAXC], s_k[BMAXC], s_all;
+  const int n = a.nc * a.nd;
+  const int G = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
+  const int chunk = (n + G - 1) / G;
+  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int gwarp = blockIdx.x * nwarp + warp, nwarps_total = G * nwarp;
+  const size_t cn = (size_t)a.ncol * n;   // stride of one basis index
+  auto CS = [&](int c) { return bsm + (size_t)c * per; };
+  auto SN = [&](int c) { return bsm + (size_t)c * per + CMAXM; };
+  auto GV = [&](int c) { return bsm + (size_t)c * per + 2 * CMAXM; };
+  auto HC = [&](int c) { return bsm + (size_t)c * per + 3 * CMAXM + 1; };
+  auto HP = [&](int c) { return bsm + (size_t)c * per + 4 * CMAXM + 3; };
+
+  for (int c = 0; c < a.ncol; c++) {
+    float nn = 0;
+    for (int e = tid; e < n; e += nth) { const float2 v = a.b[(size_t)c * n + e]; nn += v.x * v.x + v.y * v.y; }
+    const double t = cta_sum((double)nn, sh);
+    if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+  }
+  grid.sync();
+  for (int c = warp; c < a.ncol; c += nwarp) {
+    double t = 0.0;
+    for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
+    t = warp_sum(t);
+    if (lane == 0) {
+      s_beta[c] = sqrt(t);
+      s_done[c] = !(s_beta[c] > 0.0);
+      s_k[c] = 0;
+      s_hn[c] = 1.0;
+      double2* gv = GV(c);
+      for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
+      gv[0] = make_double2(s_beta[c], 0.0);
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < a.ncol; c++) {
+    const float inv = s_beta[c] > 0.0 ? (float)(1.0 / s_beta[c]) : 0.f;
+    for (int e = tid; e < n; e += nth) {
+      float2 v = a.b[(size_t)c * n + e];
+      v.x *= inv;
+      v.y *= inv;
+      a.V[(size_t)c * n + e] = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int c = 0; c < a.ncol; c++) all &= s_done[c];
+    s_all = all;
+  }
+  grid.sync();
+  for (int j = 0; j < a.m && !s_all; j++) {
+    const float2* src = j == 0 ? a.V : a.w;
+    float2* vj = a.V + (size_t)j * cn;
+    // (1) stencil products for all columns: warp per (site, block), columns in groups of CB
+    for (int task = gwarp; task < a.nc * 9; task += nwarps_total) {
+      const int nb = a.nbr[task];
+      const float2* blk = a.Dc + (size_t)task * a.nd * a.nd;
+      for (int c0 = 0; c0 < a.ncol; c0 += CB) {
+        float sc[CB];
+#pragma unroll
+        for (int q = 0; q < CB; q++) sc[q] = (c0 + q < a.ncol && j > 0) ? (float)(1.0 / s_hn[c0 + q]) : 1.f;
+        for (int k = lane; k < a.nd; k += 32) {
+          float ar[CB], ai[CB];
+#pragma unroll
+          for (int q = 0; q < CB; q++) { ar[q] = 0.f; ai[q] = 0.f; }
+#pragma unroll 4
+          for (int l = 0; l < a.nd; l++) {
+            const float2 m = blk[(size_t)l * a.nd + k];
+#pragma unroll
+            for (int q = 0; q < CB; q++) {
+              if (c0 + q < a.ncol) {
+                const float2 v = src[(size_t)(c0 + q) * n + (size_t)nb * a.nd + l];
+                ar[q] += m.x * v.x - m.y * v.y;
+                ai[q] += m.x * v.y + m.y * v.x;
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < CB; q++)
+            if (c0 + q < a.ncol)
+              a.rows[((size_t)(c0 + q) * a.nc * 9 + task) * a.nd + k] = make_float2(ar[q] * sc[q], ai[q] * sc[q]);
+        }
+      }
+    }
+    grid.sync();
+    // (2) own chunk: v_j, w = sum of rows + twist, per column
+    for (int c = 0; c < a.ncol; c++) {
+      const float scale = j == 0 ? 1.f : (float)(1.0 / s_hn[c]);
+      const float mu = a.mu[c];
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int site = e / a.nd, k = e - site * a.nd;
+        float2 xs = src[(size_t)c * n + e];
+        xs.x *= scale;
+        xs.y *= scale;
+        if (j > 0) vj[(size_t)c * n + e] = xs;
+        float ar = 0.f, ai = 0.f;
+        for (int d = 0; d < 9; d++) {
+          const float2 r = a.rows[((size_t)c * a.nc * 9 + (size_t)site * 9 + d) * a.nd + k];
+          ar += r.x;
+          ai += r.y;
+        }
+        const float tw = k < a.nv ? mu : -mu;
+        a.w[(size_t)c * n + e] = make_float2(ar - tw * xs.y, ai + tw * xs.x);
+      }
+    }
+    for (int c = threadIdx.x; c < a.ncol; c += blockDim.x)
+      for (int i = 0; i <= j + 1; i++) HC(c)[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    // (3) dots <v_i, w> per column, partials per CTA
+    for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
+      const int i = t / a.ncol, c = t - i * a.ncol;
+      const float2* vi = a.V + (size_t)i * cn + (size_t)c * n;
+      const float2* wc = a.w + (size_t)c * n;
+      float re = 0.f, im = 0.f;
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const float2 p = vi[e], q = wc[e];
+        re += p.x * q.x + p.y * q.y;
+        im += p.x * q.y - p.y * q.x;
+      }
+      const double dre = warp_sum((double)re), dim = warp_sum((double)im);
+      if (lane == 0) a.part[((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x] = make_double2(dre, dim);
+    }
+    grid.sync();
+    for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
+      const int i = t / a.ncol, c = t - i * a.ncol;
+      double re = 0.0, im = 0.0;
+      for (int q = lane; q < G; q += 32) {
+        const double2 v = a.part[((size_t)c * (CMAXM + 1) + i) * G + q];
+        re += v.x;
+        im += v.y;
+      }
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) {
+        HP(c)[i] = make_double2(re, im);
+        HC(c)[i] = make_double2(HC(c)[i].x + re, HC(c)[i].y + im);
+      }
+    }
+    __syncthreads();
+    // (4) update and norms on the own chunk
+    for (int c = 0; c < a.ncol; c++) {
+      float nn = 0.f;
+      const double2* hp = HP(c);
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        float2 q = a.w[(size_t)c * n + e];
+        for (int i = 0; i <= j; i++) {
+          const float2 p = a.V[(size_t)i * cn + (size_t)c * n + e];
+          const float hr = (float)hp[i].x, hi = (float)hp[i].y;
+          q.x -= hr * p.x - hi * p.y;
+          q.y -= hr * p.y + hi * p.x;
+        }
+        a.w[(size_t)c * n + e] = q;
+        nn += q.x * q.x + q.y * q.y;
+      }
+      const double t = cta_sum((double)nn, sh);
+      if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+    }
+    grid.sync();
+    // (5) per column: norm, Givens, stopping test (one warp per column)
+    for (int c = warp; c < a.ncol; c += nwarp) {
+      double t = 0.0;
+      for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
+      t = warp_sum(t);
+      if (lane == 0 && !s_done[c]) {
+        const double hn = sqrt(t);
+        s_hn[c] = hn > 0.0 ? hn : 1.0;   // a broken-down column is finished; keep its scale finite
+        double2* hcol = HC(c);
+        double2* cs = CS(c);
+        double2* sn = SN(c);
+        double2* gv = GV(c);
+        hcol[j + 1] = make_double2(hn, 0.0);
+        for (int i = 0; i < j; i++) {
+          const double2 x0 = hcol[i], x1 = hcol[i + 1];
+          const double2 cc = cs[i], ss = sn[i];
+          hcol[i] = make_double2(cc.x * x0.x + cc.y * x0.y + ss.x * x1.x + ss.y * x1.y,
+                                 cc.x * x0.y - cc.y * x0.x + ss.x * x1.y - ss.y * x1.x);
+          hcol[i + 1] = make_double2(-(ss.x * x0.x - ss.y * x0.y) + (cc.x * x1.x - cc.y * x1.y),
+                                     -(ss.x * x0.y + ss.y * x0.x) + (cc.x * x1.y + cc.y * x1.x));
+        }
+        const double2 p = hcol[j], q = hcol[j + 1];
+        const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+        cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
+        sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
+        hcol[j] = make_double2(den, 0.0);
+        const double2 g = gv[j];
+        gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
+        gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+        if (blockIdx.x == 0)
+          for (int i = 0; i <= j; i++) a.R[(size_t)c * (CMAXM + 1) * CMAXM + (size_t)j * (CMAXM + 1) + i] = hcol[i];
+        s_k[c] = j + 1;
+        const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+        if (res <= a.rtol * s_beta[c] || !(hn > 0.0) || !(den > 0.0)) s_done[c] = 1;
+      } else if (lane == 0) {
+        s_hn[c] = s_hn[c] > 0.0 ? s_hn[c] : 1.0;   // a finished column keeps a harmless scale
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int all = 1;
+      for (int c = 0; c < a.ncol; c++) all &= s_done[c];
+      s_all = all || (j == a.m - 1);
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  if (blockIdx.x == 0) {
+    for (int c = warp; c < a.ncol; c += nwarp) {
+      if (lane != 0) continue;
+      const int k = s_k[c];
+      const double2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM;
+      double2* y = a.y + (size_t)c * CMAXM;
+      const double2* gv = GV(c);
+      for (int i = k - 1; i >= 0; i--) {
+        double2 acc = gv[i];
+        for (int l = i + 1; l < k; l++) {
+          const double2 h = R[(size_t)l * (CMAXM + 1) + i], yl = y[l];
+          acc.x -= h.x * yl.x - h.y * yl.y;
+          acc.y -= h.x * yl.y + h.y * yl.x;
+        }
+        const double2 d = R[(size_t)i * (CMAXM + 1) + i];
+        const double dn = d.x * d.x + d.y * d.y;
+        y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : make_double2(0.0, 0.0);
+      }
+      if (a.counter) atomicAdd(a.counter, k);
+    }
+  }
+  grid.sync();
+  for (int c = 0; c < a.ncol; c++) {
+    const int k = s_k[c];
+    const double2* y = a.y + (size_t)c * CMAXM;
+    for (int e = tid; e < n; e += nth) {
+      float xr = 0.f, xi = 0.f;
+      for (int i = 0; i < k; i++) {
+        const float2 v = a.V[(size_t)i * cn + (size_t)c * n + e];
+        const float yr = (float)y[i].x, yi = (float)y[i].y;
+        xr += yr * v.x - yi * v.y;
+        xi += yr * v.y + yi * v.x;
+      }
+      a.x[(size_t)c * n + e] = make_float2(xr, xi);
+    }
+  }
+}
+
 template <typename S>
 void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   using T2 = typename CplxT<S>::T2;
@@ -385,6 +663,50 @@ size_t coarse_gmres_scratch_bytes(Ctx& c, int cp) {
 void coarse_gmres_on_scratch(Ctx& c, int cp, const void* b, void* x, double mu, void* scratch) {
   if (cp == TMG_PREC_F64) launch_on<double>(c, b, x, mu, c.cl.Dc64.p, (char*)scratch, grid_size<double>(c));
   else launch_on<float>(c, b, x, mu, c.cl.Dc32.p, (char*)scratch, grid_size<float>(c));
+}
+
+void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  const size_t smem = sizeof(double2) * (size_t)ncol * (5 * CMAXM + 4);
+  if (smem > 48 * 1024)
+    TMG_CUDA(cudaFuncSetAttribute(k_coarse_gmres_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int mps = 0;
+  TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres_batched, 256, smem));
+  if (mps < 1) throw Error{TMG_ERR_ARG, "batched coarse solve: too many columns for one CTA's shared memory"};
+  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::min(mps, 2)));
+  c.cw_V.alloc((m + 1) * n * ncol * sizeof(float2));
+  c.cw_w.alloc(10 * n * ncol * sizeof(float2));
+  c.cw_part.alloc(sizeof(double2) * ((size_t)ncol * (CMAXM + 1) * G + (size_t)ncol * (CMAXM + 1) * CMAXM +
+                                     (size_t)ncol * CMAXM) + sizeof(double) * (size_t)ncol * G);
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  CgbArgs a;
+  a.nd = c.cl.nd;
+  a.nv = c.cl.nv;
+  a.nc = c.cl.nc;
+  a.m = m;
+  a.ncol = ncol;
+  a.Dc = c.cl.Dc32.as<float2>();
+  a.nbr = c.cl.nbr.as<int>();
+  a.b = (const float2*)b;
+  a.x = (float2*)x;
+  a.V = c.cw_V.as<float2>();
+  a.w = c.cw_w.as<float2>();
+  a.rows = a.w + n * ncol;
+  a.mu = mu_dev;
+  a.rtol = c.mg.coarse_rtol;
+  a.part = c.cw_part.as<double2>();
+  a.R = a.part + (size_t)ncol * (CMAXM + 1) * G;
+  a.y = a.R + (size_t)ncol * (CMAXM + 1) * CMAXM;
+  a.npart = reinterpret_cast<double*>(a.y + (size_t)ncol * CMAXM);
+  a.counter = c.coarse_iter_dev.as<int>();
+  void* args[] = {&a};
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres_batched, dim3(G), dim3(256), args, smem, c.stream));
 }
 
 void coarse_gmres_persistent(Ctx& c, int cp, const void* b, void* x, double mu) {

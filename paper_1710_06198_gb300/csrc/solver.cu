@@ -133,6 +133,109 @@ __global__ void k_combine(const T2* __restrict__ Zb, size_t stride, int count, c
   }
 }
 
+// ---- column-batched variants: column c of a field at c * n elements, partials [c][i][NPART]
+__global__ void k_mdot_partial_b(const float2* __restrict__ Vb, size_t istride, const float2* __restrict__ w,
+                                 size_t n, double2* __restrict__ part) {
+  const int i = blockIdx.y, c = blockIdx.z;
+  const float2* v = Vb + (size_t)i * istride + (size_t)c * n;
+  const float2* wc = w + (size_t)c * n;
+  float tre = 0.f, tim = 0.f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 a = v[e], b = wc[e];
+    tre += a.x * b.x + a.y * b.y;
+    tim += a.x * b.y - a.y * b.x;
+  }
+  double re = tre, im = tim;
+  __shared__ double sre[32], sim[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sre[threadIdx.x >> 5] = re; sim[threadIdx.x >> 5] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { a += sre[k]; b += sim[k]; }
+    part[((size_t)c * (MAXM + 1) + i) * NPART + blockIdx.x] = make_double2(a, b);
+  }
+}
+
+// out[c][i] = sum_b part[c][i][b]; grid (count, ncol)
+__global__ void k_mdot_final_b(const double2* __restrict__ part, int np, double2* __restrict__ out) {
+  const int i = blockIdx.x, c = blockIdx.y;
+  const double2* p = part + ((size_t)c * (MAXM + 1) + i) * NPART;
+  double a = 0, b = 0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) { a += p[k].x; b += p[k].y; }
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0, tb = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { ta += sa[k]; tb += sb[k]; }
+    out[(size_t)c * (MAXM + 1) + i] = make_double2(ta, tb);
+  }
+}
+
+// w_c -= sum_i coef[c][i] v_i,c ; optional partial ||w_c||^2 into npart[c][b]; grid (G, ncol)
+__global__ void k_mgs_update_b(const float2* __restrict__ Vb, size_t istride, int count, const double2* __restrict__ coef,
+                               float2* __restrict__ w, size_t n, double* __restrict__ npart) {
+  const int c = blockIdx.y;
+  __shared__ float cfr[MAXM + 1], cfi[MAXM + 1];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    cfr[i] = (float)coef[(size_t)c * (MAXM + 1) + i].x;
+    cfi[i] = (float)coef[(size_t)c * (MAXM + 1) + i].y;
+  }
+  __syncthreads();
+  float snn = 0.f;
+  float2* wc = w + (size_t)c * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float2 q = wc[e];
+    for (int i = 0; i < count; i++) {
+      const float2 v = Vb[(size_t)i * istride + (size_t)c * n + e];
+      q.x -= cfr[i] * v.x - cfi[i] * v.y;
+      q.y -= cfr[i] * v.y + cfi[i] * v.x;
+    }
+    wc[e] = q;
+    snn += q.x * q.x + q.y * q.y;
+  }
+  if (!npart) return;
+  double nn = snn;
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) a += sh[k];
+    npart[(size_t)c * NPART + blockIdx.x] = a;
+  }
+}
+
+// x_c = sum_{i<k} coef[c][i] z_i,c ; grid (G, ncol)
+__global__ void k_combine_b(const float2* __restrict__ Zb, size_t istride, int k, const double2* __restrict__ coef,
+                            float2* __restrict__ x, size_t n) {
+  const int c = blockIdx.y;
+  __shared__ float cfr[MAXM], cfi[MAXM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    cfr[i] = (float)coef[(size_t)c * (MAXM + 1) + i].x;
+    cfi[i] = (float)coef[(size_t)c * (MAXM + 1) + i].y;
+  }
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float xr = 0.f, xi = 0.f;
+    for (int i = 0; i < k; i++) {
+      const float2 v = Zb[(size_t)i * istride + (size_t)c * n + e];
+      xr += cfr[i] * v.x - cfi[i] * v.y;
+      xi += cfr[i] * v.y + cfi[i] * v.x;
+    }
+    x[(size_t)c * n + e] = make_float2(xr, xi);
+  }
+}
+
 size_t esize(int prec) { return prec == TMG_PREC_F64 ? 16 : 8; }
 
 int red_grid(const Ctx& c, size_t n) {
@@ -398,6 +501,184 @@ int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol,
     if (k == 0) {
       rc = TMG_ERR_BREAKDOWN;
       break;
+    }
+  }
+  if (c.coarse_iter_dev.p) {
+    TMG_CUDA(cudaMemcpyAsync(&c1, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    st.coarse_iterations = c1 - c0;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------- batched mixed-precision solve
+// All columns advance in lock-step: one launch per operation for every column (multi-column
+// dslash, SAP, P, P^dag, and the batched coarse GMRES), per-column FGMRES recurrences on the host.
+// The FP64 defect correction recomputes every column's true residual at each restart; columns
+// that have converged keep a zero correction.
+int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu, double tol, int maxiter,
+                  SolveStats& st) {
+  const size_t n = (size_t)12 * c.g.V;
+  const int m = std::min(c.mg.restart, MAXM);
+  const int pf = c.mg.prec_fine == TMG_PREC_F64 ? TMG_PREC_F32 : c.mg.prec_fine;
+  const size_t nco = (size_t)c.cl.nc * c.cl.nd;
+  const int rg = red_grid(c, n);
+  DBuf r64, rin, e, V, Z, w, cr, ce, mu_dev, part, hdev, npart;
+  r64.alloc(ncol * n * 16);
+  rin.alloc(ncol * n * 8);
+  e.alloc(ncol * n * 8);
+  V.alloc((size_t)(m + 1) * ncol * n * 8);
+  Z.alloc((size_t)m * ncol * n * 8);
+  w.alloc(ncol * n * 8);
+  cr.alloc(ncol * nco * 8);
+  ce.alloc(ncol * nco * 8);
+  mu_dev.alloc(ncol * sizeof(float));
+  part.alloc(sizeof(double2) * (size_t)ncol * (MAXM + 1) * NPART);
+  hdev.alloc(sizeof(double2) * (size_t)2 * ncol * (MAXM + 1));
+  npart.alloc(sizeof(double) * (size_t)ncol * NPART);
+  std::vector<float> muf(ncol);
+  for (int j = 0; j < ncol; j++) muf[j] = (float)mu[j];
+  TMG_CUDA(cudaMemcpyAsync(mu_dev.p, muf.data(), ncol * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+  int c0 = 0, c1 = 0;
+  if (c.coarse_iter_dev.p) TMG_CUDA(cudaMemcpyAsync(&c0, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  std::vector<double> bn(ncol), rn(ncol);
+  for (int j = 0; j < ncol; j++) {
+    const char* bj = (const char*)b64 + j * n * 16;
+    blas_zero(c, (char*)x64 + j * n * 16, TMG_PREC_F64, n);
+    blas_copy(c, bj, r64.as<char>() + j * n * 16, TMG_PREC_F64, n);
+    bn[j] = std::sqrt(blas_norm2(c, bj, TMG_PREC_F64, n));
+    if (!std::isfinite(bn[j])) throw Error{TMG_ERR_BREAKDOWN, "batched solve: right-hand side is not finite"};
+  }
+  float2* Vp = V.as<float2>();
+  float2* Zp = Z.as<float2>();
+  const size_t istride = (size_t)ncol * n;
+  int rc = TMG_OK;
+  while (true) {
+    bool all = true;
+    double worst = 0.0;
+    for (int j = 0; j < ncol; j++) {
+      rn[j] = std::sqrt(blas_norm2(c, r64.as<char>() + j * n * 16, TMG_PREC_F64, n));
+      if (!std::isfinite(rn[j])) throw Error{TMG_ERR_BREAKDOWN, "batched solve: residual is not finite"};
+      const double rel = bn[j] > 0.0 ? rn[j] / bn[j] : 0.0;
+      worst = std::max(worst, rel);
+      if (rel > tol) all = false;
+    }
+    st.true_residual = worst;
+    if (all) break;
+    if (st.iterations >= maxiter) {
+      rc = TMG_ERR_NOCONV;
+      break;
+    }
+    // unit-norm FP32 residuals of the unconverged columns (converged ones: zero)
+    for (int j = 0; j < ncol; j++) {
+      char* rj = rin.as<char>() + j * n * 8;
+      if (bn[j] > 0.0 && rn[j] > tol * bn[j]) {
+        convert_field(c, r64.as<char>() + j * n * 16, TMG_PREC_F64, rj, TMG_PREC_F32, n);
+        blas_scale(c, 1.0 / rn[j], 0.0, rj, TMG_PREC_F32, n);
+      } else {
+        blas_zero(c, rj, TMG_PREC_F32, n);
+      }
+    }
+    // FGMRES(m) cycle on all columns; beta = 1 (or 0) per column
+    std::vector<double> beta(ncol), target(ncol);
+    for (int j = 0; j < ncol; j++) {
+      const bool act = bn[j] > 0.0 && rn[j] > tol * bn[j];
+      beta[j] = act ? 1.0 : 0.0;
+      target[j] = act ? std::max(tol * bn[j] / rn[j], 1e-6) : 1.0;
+    }
+    blas_copy(c, rin.p, Vp, TMG_PREC_F32, ncol * n);
+    std::vector<std::complex<double>> H((size_t)ncol * (m + 1) * m), cs((size_t)ncol * m), sn((size_t)ncol * m),
+        g((size_t)ncol * (m + 1)), y((size_t)ncol * m);
+    for (int j = 0; j < ncol; j++) g[(size_t)j * (m + 1)] = beta[j];
+    std::vector<char> done(ncol);
+    for (int j = 0; j < ncol; j++) done[j] = beta[j] == 0.0;
+    int k = 0;
+    for (int it = 0; it < m; it++) {
+      float2* vj = Vp + (size_t)it * istride;
+      float2* zj = Zp + (size_t)it * istride;
+      // z = M v (one batched cycle)
+      restrict_mrhs(c, ncol, vj, cr.p);
+      coarse_gmres_batched(c, ncol, cr.p, ce.p, mu_dev.as<float>());
+      prolong_mrhs(c, ncol, ce.p, zj);
+      sap_mrhs(c, pf, ncol, zj, vj, mu_dev.as<float>(), c.mg.sap_sweeps);
+      dslash_mrhs(c, pf, ncol, w.p, zj, nullptr, mu_dev.as<float>(), 0);
+      for (int pass = 0; pass < 2; pass++) {
+        ++c.launches, k_mdot_partial_b<<<dim3(rg, it + 1, ncol), 256, 0, c.stream>>>(Vp, istride, w.as<float2>(), n, part.as<double2>());
+        ++c.launches, k_mdot_final_b<<<dim3(it + 1, ncol), 256, 0, c.stream>>>(part.as<double2>(), rg,
+                                                                               hdev.as<double2>() + (size_t)pass * ncol * (MAXM + 1));
+        ++c.launches, k_mgs_update_b<<<dim3(rg, ncol), 256, 0, c.stream>>>(Vp, istride, it + 1,
+                                                                            hdev.as<double2>() + (size_t)pass * ncol * (MAXM + 1),
+                                                                            w.as<float2>(), n, pass == 1 ? npart.as<double>() : nullptr);
+        TMG_CHECK_LAUNCH();
+      }
+      std::vector<double2> hc((size_t)2 * ncol * (MAXM + 1));
+      std::vector<double> nn((size_t)ncol * NPART);
+      TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev.p, sizeof(double2) * hc.size(), cudaMemcpyDeviceToHost, c.stream));
+      TMG_CUDA(cudaMemcpyAsync(nn.data(), npart.p, sizeof(double) * nn.size(), cudaMemcpyDeviceToHost, c.stream));
+      TMG_CUDA(cudaStreamSynchronize(c.stream));
+      k = it + 1;
+      bool all_done = true;
+      std::vector<double> inv(ncol, 0.0);
+      for (int j = 0; j < ncol; j++) {
+        double s2 = 0.0;
+        for (int q = 0; q < rg; q++) s2 += nn[(size_t)j * NPART + q];
+        const double hn = std::sqrt(s2);
+        std::complex<double>* h = &H[((size_t)j * m + it) * (m + 1)];
+        for (int i = 0; i <= it; i++) {
+          const double2 a1 = hc[(size_t)j * (MAXM + 1) + i], a2 = hc[(size_t)ncol * (MAXM + 1) + (size_t)j * (MAXM + 1) + i];
+          h[i] = std::complex<double>(a1.x + a2.x, a1.y + a2.y);
+        }
+        h[it + 1] = hn;
+        std::complex<double>* csj = &cs[(size_t)j * m];
+        std::complex<double>* snj = &sn[(size_t)j * m];
+        std::complex<double>* gj = &g[(size_t)j * (m + 1)];
+        for (int i = 0; i < it; i++) {
+          const std::complex<double> a = h[i], bb = h[i + 1];
+          h[i] = std::conj(csj[i]) * a + std::conj(snj[i]) * bb;
+          h[i + 1] = -snj[i] * a + csj[i] * bb;
+        }
+        const std::complex<double> a = h[it], bb = h[it + 1];
+        const double den = std::sqrt(std::norm(a) + std::norm(bb));
+        csj[it] = den > 0 ? a / den : 1.0;
+        snj[it] = den > 0 ? bb / den : 0.0;
+        h[it] = den;
+        h[it + 1] = 0.0;
+        gj[it + 1] = -snj[it] * gj[it];
+        gj[it] = std::conj(csj[it]) * gj[it];
+        if (!done[j] && (std::abs(gj[it + 1]) <= target[j] * beta[j] || hn == 0.0)) done[j] = 1;
+        all_done = all_done && done[j];
+        inv[j] = hn > 0.0 ? 1.0 / hn : 0.0;
+      }
+      if (all_done || it == m - 1) break;
+      float2* vn = Vp + (size_t)(it + 1) * istride;
+      for (int j = 0; j < ncol; j++) {
+        blas_copy(c, w.as<float2>() + (size_t)j * n, vn + (size_t)j * n, TMG_PREC_F32, n);
+        blas_scale(c, inv[j], 0.0, vn + (size_t)j * n, TMG_PREC_F32, n);
+      }
+    }
+    // per-column back substitution (only over the steps each column has: all columns used k steps)
+    std::vector<double2> yc((size_t)ncol * (MAXM + 1));
+    for (int j = 0; j < ncol; j++) {
+      std::complex<double>* yj = &y[(size_t)j * m];
+      const std::complex<double>* gj = &g[(size_t)j * (m + 1)];
+      for (int i = k - 1; i >= 0; i--) {
+        std::complex<double> acc = gj[i];
+        for (int l = i + 1; l < k; l++) acc -= H[((size_t)j * m + l) * (m + 1) + i] * yj[l];
+        const std::complex<double> d = H[((size_t)j * m + i) * (m + 1) + i];
+        yj[i] = std::abs(d) > 0.0 ? acc / d : 0.0;
+        yc[(size_t)j * (MAXM + 1) + i] = make_double2(yj[i].real(), yj[i].imag());
+      }
+    }
+    TMG_CUDA(cudaMemcpyAsync(hdev.p, yc.data(), sizeof(double2) * yc.size(), cudaMemcpyHostToDevice, c.stream));
+    ++c.launches, k_combine_b<<<dim3(egrid(c, n), ncol), 256, 0, c.stream>>>(Zp, istride, k, hdev.as<double2>(), e.as<float2>(), n);
+    TMG_CHECK_LAUNCH();
+    st.iterations += k;
+    st.refinements++;
+    for (int j = 0; j < ncol; j++) {
+      if (beta[j] == 0.0) continue;
+      char* xj = (char*)x64 + j * n * 16;
+      blas_axpy_mixed(c, rn[j], e.as<char>() + j * n * 8, TMG_PREC_F32, xj, TMG_PREC_F64, n);
+      dslash(c, TMG_PREC_F64, r64.as<char>() + j * n * 16, xj, (const char*)b64 + j * n * 16, mu[j], 1, 0);
     }
   }
   if (c.coarse_iter_dev.p) {

@@ -19,5 +19,7 @@ void mg_setup(Ctx& c, const double* v0_lex);
 void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // Solve D(mu) x = b on FP64 internal fields (b, x: F64 storage).  Returns a tmg_status.
 int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st);
+// ncol systems D(mu_c) x_c = b_c (F64 fields, column c at c * 12 V) solved in lock-step.
+int solve_batched(Ctx& c, int ncol, const void* b, void* x, const double* mu, double tol, int maxiter, SolveStats& st);
 
 }  // namespace tmg

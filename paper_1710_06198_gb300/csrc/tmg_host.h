@@ -214,6 +214,13 @@ void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const in
 void orthonormalise(Ctx& c, void* W64);
 // x ~= D_c(mu)^-1 b: one persistent cooperative GMRES kernel (k_coarse_gmres.cu)
 void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double mu);
+// ncol columns in lock-step (FP32 coarse vectors [col][nc * nd], twists mu_dev[ncol] on the device)
+void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev);
+// multi-column fine-level kernels (k_batch.cu), FP32 spinors [col][12 V], twists per column
+void dslash_mrhs(Ctx& c, int prec, int ncol, void* y, const void* x, const void* b, const float* mu_col_dev, int mode);
+void sap_mrhs(Ctx& c, int prec, int ncol, void* x, const void* b, const float* mu_col_dev, int n_sweeps);
+void restrict_mrhs(Ctx& c, int ncol, const void* r, void* cvec);
+void prolong_mrhs(Ctx& c, int ncol, const void* cvec, void* e);
 // The same solve on caller-provided device scratch (no allocation): bytes needed, and the launch.
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
 void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);
