@@ -125,6 +125,10 @@ int tmg_restrict(tmg_ctx *ctx, const double *r, double *c, int prec, int where);
 int tmg_prolong(tmg_ctx *ctx, const double *c, double *e, int prec, int where);
 int tmg_coarse_apply(tmg_ctx *ctx, const double *x, double *y, double mu, int prec, int where);
 int tmg_cycle(tmg_ctx *ctx, const double *r, double *z, int where);
+/* Multi-RHS coarse operator Y = D_c(mu_n) X (Eq. 1's D_c, twist per column, Sec. 1.1) for
+ * n_rhs (1..32) coarse vectors ([n_rhs][V_c][2 N_v]) on the tensor cores (tcgen05, split TF32,
+ * FP32-level accuracy), N_v <= 32.  TMG_ERR_TIMEOUT if a bounded device-side wait gave up. */
+int tmg_coarse_apply_multi(tmg_ctx *ctx, const double *x, double *y, int n_rhs, const double *mu_per_col, int where);
 /* x ~= D_c(mu)^-1 b (Eq. 1's coarse solve): GMRES from zero with at most coarse_m steps, stopping
  * at relative residual coarse_rtol; coarse vectors [V_c][2 N_v], computed in precision prec. */
 int tmg_coarse_solve(tmg_ctx *ctx, const double *b, double *x, double mu, int prec, int where);

@@ -69,6 +69,7 @@ _SIGS = {
     "tmg_coarse_apply": [_P, _P, _P, _D, _I, _I],
     "tmg_cycle": [_P, _P, _P, _I],
     "tmg_coarse_solve": [_P, _P, _P, _D, _I, _I],
+    "tmg_coarse_apply_multi": [_P, _P, _P, _I, _P, _I],
     "tmg_coarse_solve_noalloc": [_P, _P, _P, _D, _I],
     "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
@@ -245,6 +246,19 @@ class Context:
         px, wh = _ptr(x)
         py, _ = _ptr(y)
         self._check(lib().tmg_coarse_apply(self._h, px, py, float(mu), prec, wh))
+        return y
+
+    def coarse_apply_multi(self, x, mu_per_col=None):
+        """Y[n] = D_c(mu_n) X[n] for x[n_rhs, ..., 2 Nv] on the tensor cores."""
+        n = x.shape[0]
+        y = _empty_like(x, x.shape)
+        px, wh = _ptr(x)
+        py, _ = _ptr(y)
+        mp = None
+        if mu_per_col is not None:
+            mu_arr = np.ascontiguousarray(np.asarray(mu_per_col, dtype=np.float64).reshape(n))
+            mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
+        self._check(lib().tmg_coarse_apply_multi(self._h, px, py, n, mp, wh))
         return y
 
     def coarse_solve(self, c, mu=0.0, prec=PREC_F64):

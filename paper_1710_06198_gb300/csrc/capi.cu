@@ -488,6 +488,39 @@ int tmg_coarse_apply(tmg_ctx* ctx, const double* x, double* y, double mu, int pr
   });
 }
 
+int tmg_coarse_apply_multi(tmg_ctx* ctx, const double* x, double* y, int n_rhs, const double* mu_per_col, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!x || !y || n_rhs < 1 || n_rhs > 32 || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_coarse_apply_multi: bad argument (1..32 columns)");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_coarse_apply_multi: no setup");
+    if (2 * c.cl.nd > 128) return fail(ctx, TMG_ERR_ARG, "tmg_coarse_apply_multi: N_v > 32");
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, x, 2 * n * n_rhs, where);
+    tmg::CField xi, yo;
+    xi.create(TMG_PREC_F32, n * n_rhs);
+    yo.create(TMG_PREC_F32, n * n_rhs);
+    convert_field(c, d, TMG_PREC_F64, xi.buf.p, TMG_PREC_F32, n * n_rhs);
+    std::vector<float> mus(n_rhs, (float)c.mu);
+    if (mu_per_col)
+      for (int j = 0; j < n_rhs; j++) mus[j] = (float)mu_per_col[j];
+    DBuf aux;
+    aux.alloc(sizeof(float) * 32 + sizeof(int));
+    TMG_CUDA(cudaMemcpyAsync(aux.p, mus.data(), n_rhs * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    int* err = reinterpret_cast<int*>(aux.as<float>() + 32);
+    TMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c.stream));
+    coarse_apply_tc(c, n_rhs, xi.buf.p, yo.buf.p, aux.as<float>(), err);
+    int herr = 0;
+    TMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    double* o = stage_out_ptr(c, c.stage_b, y, 2 * n * n_rhs, where);
+    convert_field(c, yo.buf.p, TMG_PREC_F32, o, TMG_PREC_F64, n * n_rhs);
+    stage_out_finish(c, c.stage_b, y, 2 * n * n_rhs, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (herr) return fail(ctx, TMG_ERR_TIMEOUT, "tmg_coarse_apply_multi: a tensor-core completion wait gave up");
+    return TMG_OK;
+  });
+}
+
 int tmg_coarse_solve(tmg_ctx* ctx, const double* b, double* x, double mu, int prec, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;

@@ -1,0 +1,263 @@
+// Multi-right-hand-side coarse operator Y = D_c(mu_n) X on the 5th-generation tensor cores
+// (tcgen05, accumulators in tensor memory), the one dense block contraction of the DD-alpha-AMG
+// hot path (Eq. 1: D_c = P^dag D P is a 9-point stencil of dense (2 N_v)^2 complex blocks).
+//
+// One CTA (4 warps) per coarse site.  For each of the 9 stencil blocks the CTA stages, in shared
+// memory and in the canonical K-major no-swizzle core-matrix layout,
+//   A = real embedding of the complex block, [[Re A, -Im A], [Im A, Re A]] (2 nd x 2 nd, rows
+//       zero-padded to M = 128),
+//   B = real embedding of the neighbour's column vectors [Re x; Im x] (N columns, padded to 16/32),
+// and one elected thread issues tcgen05.mma kind::tf32.  FP32 accuracy comes from split TF32:
+// v = hi + lo with hi = tf32(v), lo = tf32(v - hi), and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (the dropped A_lo B_lo term is below FP32 rounding).  Each K = 8 step accumulates its three
+// products in its own TMEM column range, and the partial results are summed in FP32 registers
+// after tcgen05.ld: the tensor core never adds more than 24 products into one accumulator, which
+// keeps its accumulation rounding below the FP32 tolerance for any N_v.  The twist i mu_n G5_c
+// is added in the epilogue.
+//
+// Every wait on the MMA-completion mbarrier is bounded; a wait that gives up sets *err and the
+// CTA still frees its tensor memory before returning.
+#include "tmg_host.h"
+
+namespace tmg {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr unsigned kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_round(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// float offset of element (row r, k) in a K-major core-matrix tile with KP columns:
+// core matrix = 8 rows x 4 floats (128 bytes, rows 16 bytes apart); core matrices adjacent in K
+// are 128 bytes apart (leading byte offset), adjacent in rows KP/4 * 128 bytes apart (stride).
+__device__ __forceinline__ int core_off(int r, int k, int KP) {
+  return ((r >> 3) * (KP >> 2) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// shared-memory matrix descriptor: start address, leading / stride byte offsets (>> 4), version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::tf32: D F32, A and B TF32, both K-major, shape M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned it = 0; it < kSpinLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int NPAD>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[NPAD]);
+
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
+  float a[16], b[16];
+  tmem_load<16>(taddr, a);
+  tmem_load<16>(taddr + 16, b);
+#pragma unroll
+  for (int i = 0; i < 16; i++) { v[i] = a[i]; v[16 + i] = b[i]; }
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv, int ncol, const float2* __restrict__ Dc,
+                                                         const int* __restrict__ nbr, const float2* __restrict__ X,
+                                                         float2* __restrict__ Y, const float* __restrict__ mu,
+                                                         int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int KP = ((2 * nd + 7) / 8) * 8;                 // K padded to the MMA step
+  float* Ahi = reinterpret_cast<float*>(sm);
+  float* Alo = Ahi + TC_M * KP;
+  float* Bhi = Alo + TC_M * KP;
+  float* Blo = Bhi + NPAD * KP;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + NPAD * KP);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  volatile int* s_ok = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int site = blockIdx.x;
+  const size_t n = (size_t)nc * nd;
+  const int nsteps = KP / 8;                                // K = 8 MMA steps per stencil block
+  uint32_t kCols = 32;
+  while (kCols < (uint32_t)(nsteps * NPAD)) kCols <<= 1;    // TMEM columns: one range per step
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // rows >= 2 nd of A stay zero for the whole kernel; zero everything once
+  for (int i = tid; i < 2 * TC_M * KP; i += blockDim.x) Ahi[i] = 0.f;
+  for (int i = tid; i < 2 * NPAD * KP; i += blockDim.x) Bhi[i] = 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_tf32(TC_M, NPAD);
+  const uint32_t lbo = 128, sboA = (uint32_t)(KP / 4) * 128, sboB = sboA;
+  bool ok = true;
+  float acc[NPAD];
+#pragma unroll
+  for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
+
+  for (int d = 0; d < 9 && ok; d++) {
+    const float2* blk = Dc + (size_t)(site * 9 + d) * nd * nd;   // [l][k]: element (row k, col l)
+    // A real embedding: row r < nd -> (Re, -Im); row nd + r -> (Im, Re)
+    for (int i = tid; i < nd * nd; i += blockDim.x) {
+      const int l = i / nd, k = i - l * nd;
+      const float2 z = blk[i];
+      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+      const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
+      Ahi[core_off(k, l, KP)] = re_h;
+      Ahi[core_off(k, nd + l, KP)] = -im_h;
+      Ahi[core_off(nd + k, l, KP)] = im_h;
+      Ahi[core_off(nd + k, nd + l, KP)] = re_h;
+      Alo[core_off(k, l, KP)] = re_l;
+      Alo[core_off(k, nd + l, KP)] = -im_l;
+      Alo[core_off(nd + k, l, KP)] = im_l;
+      Alo[core_off(nd + k, nd + l, KP)] = re_l;
+    }
+    // B: column vectors of the neighbour (N rows of K-major data)
+    const int nb = nbr[site * 9 + d];
+    for (int i = tid; i < ncol * nd; i += blockDim.x) {
+      const int col = i / nd, l = i - col * nd;
+      const float2 z = X[(size_t)col * n + (size_t)nb * nd + l];
+      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+      Bhi[core_off(col, l, KP)] = re_h;
+      Bhi[core_off(col, nd + l, KP)] = im_h;
+      Blo[core_off(col, l, KP)] = tf32_round(z.x - re_h);
+      Blo[core_off(col, nd + l, KP)] = tf32_round(z.y - im_h);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t aH = smem_u32(Ahi), aL = smem_u32(Alo), bH = smem_u32(Bhi), bL = smem_u32(Blo);
+      for (int s = 0; s < nsteps; s++) {
+        const uint32_t koff = (uint32_t)s * 2 * 128;     // two core matrices per K = 8 step
+        const uint32_t dcol = tmem + (uint32_t)(s * NPAD);
+        const uint64_t dAh = smem_desc(aH + koff, lbo, sboA), dAl = smem_desc(aL + koff, lbo, sboA);
+        const uint64_t dBh = smem_desc(bH + koff, lbo, sboB), dBl = smem_desc(bL + koff, lbo, sboB);
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(dcol), "l"(dAh), "l"(dBh), "r"(idesc), "r"(0u));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(dcol), "l"(dAh), "l"(dBl), "r"(idesc), "r"(1u));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(dcol), "l"(dAl), "l"(dBh), "r"(idesc), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                   : "memory");
+    }
+    // the MMAs read shared memory asynchronously: thread 0 waits (bounded) for their completion,
+    // then the whole CTA learns the outcome at one barrier, so every thread leaves the loop together
+    if (tid == 0) {
+      const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(d & 1));
+      *s_ok = done ? 1 : 0;
+      if (!done) atomicExch(err, 1);
+    }
+    __syncthreads();
+    ok = *s_ok != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      // warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the real-embedded result), one column
+      // range per K step, and sums them in FP32
+      for (int s2 = 0; s2 < nsteps; s2++) {
+        float part[NPAD];
+        tmem_load<NPAD>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s2 * NPAD), part);
+#pragma unroll
+        for (int i = 0; i < NPAD; i++) acc[i] += part[i];
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // TMEM reads done before the next block's MMAs overwrite the ranges
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (ok) {
+    const int r = warp * 32 + lane;
+    if (r < 2 * nd) {
+      const bool imag = r >= nd;
+      const int k = imag ? r - nd : r;
+      for (int col = 0; col < ncol; col++) {
+        const float2 xs = X[(size_t)col * n + (size_t)site * nd + k];
+        const float tw = k < nv ? mu[col] : -mu[col];
+        float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * nd + k);
+        if (!imag) yp[0] = acc[col] - tw * xs.y;
+        else yp[1] = acc[col] + tw * xs.x;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+}  // namespace
+
+// Y = D_c(mu_col) X for ncol FP32 coarse vectors ([col][nc * nd] complex) on the tensor cores.
+void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+  ProfScope ps(c, PK_COARSE);
+  const int nd = c.cl.nd;
+  if (ncol < 1 || ncol > 32 || 2 * nd > TC_M) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns, N_v <= 64"};
+  const int KP = ((2 * nd + 7) / 8) * 8;
+  const int npad = ncol <= 16 ? 16 : 32;
+  const size_t smem = sizeof(float) * (size_t)(2 * TC_M * KP + 2 * npad * KP) + 32;
+  if (npad == 16) {
+    TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ++c.launches, k_coarse_apply_tc<16><<<c.cl.nc, 128, smem, c.stream>>>(c.cl.nc, nd, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
+                                                                          c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
+                                                                          mu_dev, err_dev);
+  } else {
+    TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ++c.launches, k_coarse_apply_tc<32><<<c.cl.nc, 128, smem, c.stream>>>(c.cl.nc, nd, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
+                                                                          c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
+                                                                          mu_dev, err_dev);
+  }
+  TMG_CHECK_LAUNCH();
+}
+
+}  // namespace tmg

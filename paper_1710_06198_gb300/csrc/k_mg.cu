@@ -56,13 +56,26 @@ __device__ __forceinline__ int colour_block(const Geom& g, int colour, int k) {
 // launch are independent; the other colour's x is only read.
 template <typename R, class S, class G, class C>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom g, int colour, S x, S b, G U, C A, R tw, int n_mr) {
+  // shared memory: r [12][VB] complex; for FP32 arithmetic also the block's links, reconstructed
+  // once to 18 reals, [4][9][VB] complex (the MR steps then never touch global memory for links)
   extern __shared__ double smem_d[];
-  cpx<R>* rs = reinterpret_cast<cpx<R>*>(smem_d);             // [12][VB]
-  double* red = smem_d + (sizeof(cpx<R>) * 12 * g.VB) / sizeof(double);
+  cpx<R>* rs = reinterpret_cast<cpx<R>*>(smem_d);
+  constexpr bool kCacheLinks = sizeof(R) == 4;
+  cpx<R>* ls = rs + 12 * g.VB;
+  double* red = smem_d + (sizeof(cpx<R>) * (kCacheLinks ? 48 : 12) * g.VB) / sizeof(double);
   const int blk = colour_block(g, colour, blockIdx.x);
   const int t = threadIdx.x;
   const int s = blk * g.VB + t;
   const SiteCoord sc = decode_site(g, s);
+  if (kCacheLinks) {
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      Link<R> u;
+      U.load(s, mu, u);
+#pragma unroll
+      for (int k = 0; k < 9; k++) ls[(mu * 9 + k) * g.VB + t] = u.m[k];
+    }
+  }
   Spinor<R> r;
   {
     Spinor<R> dx, bs;
@@ -92,7 +105,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
         cpx<R> h[6], uh[6];
         spin_project(mu, +1, p, h);
         Link<R> u;
-        U.load(s, mu, u);
+        if (kCacheLinks) {
+#pragma unroll
+          for (int k = 0; k < 9; k++) u.m[k] = ls[(mu * 9 + k) * g.VB + t];
+        } else {
+          U.load(s, mu, u);
+        }
         su3_mul_half(u, false, h, uh);
         spin_reconstruct_add(mu, +1, uh, acc);
       }
@@ -104,7 +122,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
         cpx<R> h[6], uh[6];
         spin_project(mu, -1, p, h);
         Link<R> u;
-        U.load(s - g.ls[mu], mu, u);
+        if (kCacheLinks) {
+#pragma unroll
+          for (int k = 0; k < 9; k++) u.m[k] = ls[(mu * 9 + k) * g.VB + tb];
+        } else {
+          U.load(s - g.ls[mu], mu, u);
+        }
         su3_mul_half(u, true, h, uh);
         spin_reconstruct_add(mu, -1, uh, acc);
       }
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
 
 template <typename R, class S, class G, class C>
 static void launch_sap(Ctx& c, S x, S b, G U, C A, R tw, int n_sweeps, int kind) {
-  const size_t smem = sizeof(cpx<R>) * 12 * c.g.VB + 33 * 3 * sizeof(double);
+  const size_t smem = sizeof(cpx<R>) * (sizeof(R) == 4 ? 48 : 12) * c.g.VB + 33 * 3 * sizeof(double);
   if (smem > 48 * 1024) {
     TMG_CUDA(cudaFuncSetAttribute(k_sap_block<R, S, G, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }

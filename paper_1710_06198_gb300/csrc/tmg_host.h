@@ -221,6 +221,9 @@ void dslash_mrhs(Ctx& c, int prec, int ncol, void* y, const void* x, const void*
 void sap_mrhs(Ctx& c, int prec, int ncol, void* x, const void* b, const float* mu_col_dev, int n_sweeps);
 void restrict_mrhs(Ctx& c, int ncol, const void* r, void* cvec);
 void prolong_mrhs(Ctx& c, int ncol, const void* cvec, void* e);
+// Y = D_c(mu_col) X for ncol <= 32 FP32 coarse vectors on the tensor cores (k_coarse_tc.cu);
+// err_dev (device int) is set to 1 if a bounded wait gave up
+void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev);
 // The same solve on caller-provided device scratch (no allocation): bytes needed, and the launch.
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
 void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);
