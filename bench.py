@@ -163,6 +163,15 @@ def run_kernel_case(args):
     if args.kernel_case == "dslash":
         ms = ctx.bench_dslash(tmg.PREC_F32, 3)
         print(json.dumps({"kernel_case": "dslash", "ms": ms}))
+    elif args.kernel_case == "coarse_tc":
+        prm = tmg.Context.mg_defaults()
+        prm.nv, prm.n_init, prm.n_iter = 16, 0, 0
+        ctx.setup(fields.gaussian_spinor(dims, 5, n=16), prm)
+        clat = ctx.coarse_lat
+        xc = torch.from_numpy(fields.gaussian_coarse((clat[3], clat[2], clat[1], clat[0]), 32, 7, n=20)).cuda()
+        yc = ctx.coarse_apply_multi(xc, np.linspace(0.001, 0.01, 20))
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": "coarse_tc", "norm": float(torch.linalg.vector_norm(yc))}))
     elif args.kernel_case == "sap":
         prm = tmg.Context.mg_defaults()
         prm.nv, prm.n_init, prm.n_iter, prm.sap_sweeps = 2, 0, 0, 1
@@ -479,7 +488,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--ncu-solve", action="store_true", help="profile one solve only (for ncu)")
     ap.add_argument("--tune", action="append", default=[], help="launch-shape knob key=value (tmg_tune)")
-    ap.add_argument("--kernel-case", choices=["dslash", "sap"], default=None,
+    ap.add_argument("--kernel-case", choices=["dslash", "sap", "coarse_tc"], default=None,
                     help="run one kernel class on a 24^3 x 48 lattice (for ncu --set full)")
     args = ap.parse_args()
     if args.kernel_case:

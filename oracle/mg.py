@@ -375,3 +375,196 @@ class Hierarchy:
     def solve(self, b, tol=1e-10, maxiter=2000, mu=None):
         return krylov.fgmres(lambda x: self.D(x, mu), b, lambda r: self.cycle(r, mu),
                              m=self.mg.restart, tol=tol, maxiter=maxiter)
+
+
+# ---------------------------------------------------------------- third level (coarse aggregation)
+# Readings for three levels (the paper runs three levels, Sec. 1.2, without further detail): the
+# level-1 operator D_c is coarsened again by aggregating blocks of level-1 sites with N_v2 level-1
+# test vectors, split by the level-1 chirality (G5_c), orthonormalised like the fine level; the
+# level-1 system is solved by FGMRES (a K-cycle) preconditioned by a level-1 cycle made of the
+# level-2 coarse-grid correction followed by a few GMRES steps on D_c (SAP needs an even number of
+# blocks, which the level-1 lattices of the workloads do not have).
+
+
+def to_blocks_c(f, bdims):
+    return to_blocks(f, bdims, 1)
+
+
+def orthonormalise_c(vectors, adims, nv1):
+    """vectors[Nv2, nT, nZ, nY, nX, 2 nv1] -> W2 orthonormalised per (level-2 aggregate, level-1
+    chirality) by modified Gram-Schmidt applied twice, j = 0..Nv2-1."""
+    nv2 = vectors.shape[0]
+    b = to_blocks_c(vectors, adims)                      # [Nv2, agg4, bt,bz,by,bx, 2 nv1]
+    shp = b.shape
+    b = b.reshape(shp[:5] + (-1, 2, nv1))                # [..., sites, chi, nv1]
+    b = np.moveaxis(b, -2, 5)                            # [Nv2, agg4, chi, sites, nv1]
+    w = b.reshape(shp[:5] + (2, -1)).copy()
+    for _ in range(2):
+        for j in range(nv2):
+            for i in range(j):
+                ov = np.sum(np.conj(w[i]) * w[j], axis=-1, keepdims=True)
+                w[j] = w[j] - ov * w[i]
+            w[j] = w[j] / np.sqrt(np.sum(np.abs(w[j]) ** 2, axis=-1, keepdims=True))
+    w = w.reshape(b.shape)
+    w = np.moveaxis(w, 5, -2).reshape(shp)
+    return from_blocks(w, 1)
+
+
+@dataclass
+class Prolongator2:
+    W: np.ndarray          # [Nv2, nT, nZ, nY, nX, 2 nv1]
+    adims: tuple
+    nv1: int
+
+    @property
+    def nv(self):
+        return self.W.shape[0]
+
+    @property
+    def coarse_lat(self):
+        T, Z, Y, X = self.W.shape[1:5]
+        ax, ay, az, at = self.adims
+        return (T // at, Z // az, Y // ay, X // ax)
+
+
+def prolong_c(P: Prolongator2, c):
+    """level-1 vector e(a)_chi = sum_j W2_j(a)_chi c[a2(a), chi, j]."""
+    nv, nv1 = P.nv, P.nv1
+    ax, ay, az, at = P.adims
+    cf = np.repeat(np.repeat(np.repeat(np.repeat(c, at, axis=-5), az, axis=-4), ay, axis=-3), ax, axis=-2)
+    e = np.zeros(c.shape[:-5] + P.W.shape[1:], dtype=np.complex128)
+    e[..., :nv1] = np.einsum("j...k,...j->...k", P.W[..., :nv1], cf[..., :nv])
+    e[..., nv1:] = np.einsum("j...k,...j->...k", P.W[..., nv1:], cf[..., nv:])
+    return e
+
+
+def restrict_c(P: Prolongator2, r):
+    """c[a2, chi, j] = sum_{a in a2} W2_j(a)_chi^dag r(a)_chi."""
+    nv1 = P.nv1
+    sp = np.einsum("j...k,...k->...j", np.conj(P.W[..., :nv1]), r[..., :nv1])
+    sm = np.einsum("j...k,...k->...j", np.conj(P.W[..., nv1:]), r[..., nv1:])
+    s = np.concatenate([sp, sm], axis=-1)
+    return to_blocks_c(s, P.adims).sum(axis=(-5, -4, -3, -2))
+
+
+def coarse_inner_masks(clat, adims):
+    c = coords(clat)
+    fwd = [(c[mu] % adims[mu]) != adims[mu] - 1 for mu in range(4)]
+    bwd = [(c[mu] % adims[mu]) != 0 for mu in range(4)]
+    return fwd, bwd
+
+
+def build_coarse_c(Dc: CoarseOp, P: Prolongator2):
+    """Stencil blocks of P2^dag D_c P2 (twist excluded), column by column like build_coarse."""
+    nv2 = P.nv
+    nd2 = 2 * nv2
+    nv1 = P.nv1
+    clat = Dc.self_blk.shape[:4]
+    c2 = P.coarse_lat
+    c = coords(clat)
+    fm, bm = coarse_inner_masks(clat, P.adims)
+    self_blk = np.zeros(c2 + (nd2, nd2), dtype=np.complex128)
+    fwd = np.zeros((4,) + c2 + (nd2, nd2), dtype=np.complex128)
+    bwd = np.zeros((4,) + c2 + (nd2, nd2), dtype=np.complex128)
+    mv = lambda A, v: np.einsum("...kl,...l->...k", A, v)
+    for l in range(nd2):
+        chi, j = divmod(l, nv2)
+        w = np.zeros(clat + (2 * nv1,), dtype=np.complex128)
+        sl = slice(0, nv1) if chi == 0 else slice(nv1, 2 * nv1)
+        w[..., sl] = P.W[j][..., sl]
+        s = mv(Dc.self_blk, w)
+        for mu in range(4):
+            s = s + fm[mu][..., None] * mv(Dc.fwd[mu], _cshift(w, mu, +1))
+            s = s + bm[mu][..., None] * mv(Dc.bwd[mu], _cshift(w, mu, -1))
+        self_blk[..., :, l] = restrict_c(P, s)
+        for mu in range(4):
+            face_f = (c[mu] % P.adims[mu]) == P.adims[mu] - 1
+            face_b = (c[mu] % P.adims[mu]) == 0
+            hf = mv(Dc.fwd[mu], _cshift(w, mu, +1)) * face_f[..., None]
+            hb = mv(Dc.bwd[mu], _cshift(w, mu, -1)) * face_b[..., None]
+            fwd[mu][..., :, l] = restrict_c(P, hf)
+            bwd[mu][..., :, l] = restrict_c(P, hb)
+    return CoarseOp(self_blk, fwd, bwd, nv2)
+
+
+@dataclass
+class MGParams3:
+    agg2: tuple = (2, 2, 2, 2)     # level-2 aggregate in level-1 sites (x, y, z, t)
+    nv2: int = 8
+    smooth_m: int = 3              # GMRES steps of the level-1 smoother
+    k_restart: int = 10            # level-1 FGMRES (K-cycle) restart
+    k_rtol: float = 1e-1
+    k_maxiter: int = 10
+    coarse_m: int = 30             # level-2 GMRES
+    coarse_rtol: float = 5e-2
+    n_init: int = 5
+    n_iter: int = 3
+
+
+class Level1:
+    """The level-1 operator D_c with its own aggregation: cycle and K-cycle solve."""
+
+    def __init__(self, Dc: CoarseOp, prm: MGParams3):
+        self.Dc, self.prm = Dc, prm
+        self.P2 = None
+        self.Dcc = None
+
+    def A(self, x, mu):
+        return coarse_apply(self.Dc, x, mu)
+
+    def set_vectors(self, v):
+        self.P2 = Prolongator2(orthonormalise_c(v, self.prm.agg2, self.Dc.nv), tuple(self.prm.agg2), self.Dc.nv)
+        self.Dcc = build_coarse_c(self.Dc, self.P2)
+
+    def smooth(self, b, x, mu):
+        """x + (at most smooth_m GMRES steps on D_c(mu) e = b - D_c x, from zero)."""
+        r = b - self.A(x, mu)
+        e, _ = krylov.gmres_fixed(lambda v: self.A(v, mu), r, self.prm.smooth_m, 0.0)
+        return x + e
+
+    def cycle(self, r, mu):
+        c = restrict_c(self.P2, r)
+        e2, _ = krylov.gmres_fixed(lambda v: coarse_apply(self.Dcc, v, mu), c, self.prm.coarse_m,
+                                   self.prm.coarse_rtol)
+        z = prolong_c(self.P2, e2)
+        return self.smooth(r, z, mu)
+
+    def solve(self, b, mu):
+        """The level-1 K-cycle: FGMRES on D_c preconditioned by the level-1 cycle, from zero."""
+        x, _, _ = krylov.fgmres(lambda v: self.A(v, mu), b, lambda r: self.cycle(r, mu),
+                                m=self.prm.k_restart, tol=self.prm.k_rtol, maxiter=self.prm.k_maxiter)
+        return x
+
+    def setup(self, v0, mu):
+        v = np.array(v0, dtype=np.complex128, copy=True)
+        for _ in range(self.prm.n_init):
+            for j in range(v.shape[0]):
+                x = self.smooth(v[j], np.zeros_like(v[j]), mu)
+                v[j] = x / np.sqrt(np.real(np.vdot(x.ravel(), x.ravel())))
+        self.set_vectors(v)
+        for _ in range(self.prm.n_iter):
+            for j in range(v.shape[0]):
+                x = self.cycle(v[j], mu)
+                v[j] = x / np.sqrt(np.real(np.vdot(x.ravel(), x.ravel())))
+            self.set_vectors(v)
+        return v
+
+
+class Hierarchy3(Hierarchy):
+    """Three-level DD-alpha-AMG: the coarse solve of Eq. 1 becomes the level-1 K-cycle."""
+
+    def __init__(self, U, p, mg: MGParams, prm3: MGParams3, clover=None):
+        super().__init__(U, p, mg, clover)
+        self.prm3 = prm3
+        self.L1 = None
+
+    def setup3(self, v0, v1):
+        self.setup(v0)
+        self.L1 = Level1(self.Dc, self.prm3)
+        self.L1.setup(v1, self.p.mu)
+
+    def coarse_solve(self, c, mu=None):
+        mu = self.p.mu if mu is None else mu
+        if self.L1 is None:
+            return super().coarse_solve(c, mu)
+        return self.L1.solve(c, mu)
