@@ -89,7 +89,7 @@ int tmg_apply(tmg_ctx *ctx, int op, const double *x, double *y, int n_rhs,
               const double *mu_per_col, int prec, int where);
 
 /* ---- multigrid (Eq. 1) ---- */
-typedef struct {
+typedef struct tmg_mg_params {
   int nv;              /* test vectors N_v (coarse dofs per site = 2 N_v); 2..32 */
   int sap_sweeps;      /* k of Eq. 1 */
   int sap_mr;          /* MR steps per SAP block solve */
@@ -132,6 +132,53 @@ int tmg_coarse_apply_multi(tmg_ctx *ctx, const double *x, double *y, int n_rhs, 
 /* x ~= D_c(mu)^-1 b (Eq. 1's coarse solve): GMRES from zero with at most coarse_m steps, stopping
  * at relative residual coarse_rtol; coarse vectors [V_c][2 N_v], computed in precision prec. */
 int tmg_coarse_solve(tmg_ctx *ctx, const double *b, double *x, double mu, int prec, int where);
+
+/* ---- third level (Sec. 1.2 runs the method with three levels) ----
+ * The level-1 operator D_c is aggregated again: level-2 aggregates are agg[0..3] blocks of
+ * level-1 sites (x, y, z, t; each must divide the level-1 lattice), the level-2 basis P2 holds nv
+ * level-1 vectors split by level-1 chirality (G5_c-compatible like P, so the twist stays
+ * i mu G5 on level 2), orthonormalised per (aggregate, chirality) by modified Gram-Schmidt twice
+ * in FP64.  D_cc = P2^dag D_c P2 is a 9-point stencil of [2 nv]^2 blocks (twist excluded).
+ * Once built, the coarse solve of every cycle (tmg_cycle, tmg_solve, tmg_force) becomes the
+ * level-1 K-cycle: FGMRES on D_c (at most k_restart steps, stop at k_rtol) preconditioned by the
+ * level-1 cycle z = P2 D_cc^-1 P2^dag r (level-2 GMRES, coarse_m / coarse_rtol) followed by
+ * smooth_m GMRES steps on D_c(mu) e = r - D_c z.  The whole K-cycle runs as one persistent kernel
+ * in the multigrid's coarse precision. */
+typedef struct {
+  int agg[4];          /* level-2 aggregate in level-1 sites */
+  int nv;              /* level-2 test vectors per chirality (2 nv <= 64, nv <= agg volume x N_v) */
+  int smooth_m;        /* GMRES steps of the level-1 smoother (1..64) */
+  int k_restart;       /* maximum FGMRES steps of the K-cycle (1..16) */
+  double k_rtol;       /* relative residual target of the K-cycle */
+  int coarse_m;        /* maximum level-2 GMRES steps (1..64) */
+  double coarse_rtol;  /* relative residual target of the level-2 GMRES */
+  int n_init;          /* initial smoother passes of the level-2 setup */
+  int n_iter;          /* level-1 cycle-based setup iterations */
+} tmg_level2_params;
+
+/* Defaults: agg 2^4, nv 8, smoother 3 steps, K-cycle 10 steps / 0.1, level-2 GMRES 30 / 5e-2,
+ * setup 5 + 3. */
+int tmg_level2_defaults(tmg_level2_params *p);
+
+/* Level-2 setup after tmg_setup, applied to D_c exactly like the fine setup is applied to D: from
+ * the caller's nv level-1 vectors v1 ([nv][V_c][2 N_v] complex FP64, host or device), n_init
+ * passes of v <- smoother(v) with normalisation, build P2 and D_cc, then n_iter passes of
+ * v <- level-1 cycle(v) with normalisation and a rebuild.  A later tmg_setup drops level 2. */
+int tmg_setup_level2(tmg_ctx *ctx, const tmg_level2_params *p, const double *v1, int where);
+
+/* Copy out the orthonormalised level-2 basis ([nv][V_c][2 N_v] FP64). */
+int tmg_get_vectors2(tmg_ctx *ctx, double *W2, int where);
+
+/* Level-2 pieces in precision prec (F64 / F32): c2 = P2^dag c ([V_c2][2 nv] from [V_c][2 N_v]),
+ * e = P2 c2, y = D_cc(mu) x. */
+int tmg_restrict2(tmg_ctx *ctx, const double *c, double *c2, int prec, int where);
+int tmg_prolong2(tmg_ctx *ctx, const double *c2, double *e, int prec, int where);
+int tmg_coarse_apply2(tmg_ctx *ctx, const double *x, double *y, double mu, int prec, int where);
+
+/* The level-1 K-cycle kernel on a level-1 vector b ([V_c][2 N_v]) in precision prec:
+ * mode 0: x ~= D_c(mu)^-1 b (the three-level coarse solve); mode 1: x = level-1 cycle of b;
+ * mode 2: x = smoother of b from zero (smooth_m GMRES steps). */
+int tmg_kcycle(tmg_ctx *ctx, const double *b, double *x, double mu, int mode, int prec, int where);
 
 /* ---- solves ---- */
 typedef struct {
@@ -200,7 +247,8 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
 
 /* Launch-shape knobs (not paper quantities): "coarse_ctas_per_sm" (1..8, CTAs per SM of the
  * persistent coarse GMRES, capped by occupancy) and "coarse_gs_passes" (1 or 2 classical
- * Gram-Schmidt passes in the coarse GMRES; 0 = 1 in FP32, 2 in FP64).  TMG_ERR_ARG for an unknown key or value. */
+ * Gram-Schmidt passes in the coarse GMRES; 0 = 1 in FP32, 2 in FP64), "kcycle_ctas_per_sm" (1..4,
+ * CTAs per SM of the persistent level-1 K-cycle).  TMG_ERR_ARG for an unknown key or value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 
 /* Number of CUDA kernels this context has launched so far (every launcher counts its launches;

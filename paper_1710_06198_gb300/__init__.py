@@ -43,6 +43,12 @@ class MGParams(ctypes.Structure):
                 ("prec_coarse", ctypes.c_int)]
 
 
+class Level2Params(ctypes.Structure):
+    _fields_ = [("agg", ctypes.c_int * 4), ("nv", ctypes.c_int), ("smooth_m", ctypes.c_int),
+                ("k_restart", ctypes.c_int), ("k_rtol", ctypes.c_double), ("coarse_m", ctypes.c_int),
+                ("coarse_rtol", ctypes.c_double), ("n_init", ctypes.c_int), ("n_iter", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("coarse_iterations", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
@@ -79,6 +85,13 @@ _SIGS = {
     "tmg_force_xy": [_P, _P, _P, _P, _I],
     "tmg_force": [_P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(Stats), _I],
     "tmg_profile_read": [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)],
+    "tmg_level2_defaults": [ctypes.POINTER(Level2Params)],
+    "tmg_setup_level2": [_P, ctypes.POINTER(Level2Params), _P, _I],
+    "tmg_get_vectors2": [_P, _P, _I],
+    "tmg_restrict2": [_P, _P, _P, _I, _I],
+    "tmg_prolong2": [_P, _P, _P, _I, _I],
+    "tmg_coarse_apply2": [_P, _P, _P, _D, _I, _I],
+    "tmg_kcycle": [_P, _P, _P, _D, _I, _I, _I],
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
@@ -267,6 +280,64 @@ class Context:
         pc, wh = _ptr(c)
         px, _ = _ptr(x)
         self._check(lib().tmg_coarse_solve(self._h, pc, px, float(mu), prec, wh))
+        return x
+
+    # ---- third level
+    @staticmethod
+    def level2_defaults():
+        p = Level2Params()
+        lib().tmg_level2_defaults(ctypes.byref(p))
+        return p
+
+    def setup_level2(self, v1, params: Level2Params):
+        """Level-2 setup on D_c from nv level-1 vectors v1[nv, ..., 2 Nv]."""
+        _same_where(v1)
+        p, wh = _ptr(v1)
+        self._check(lib().tmg_setup_level2(self._h, ctypes.byref(params), p, wh))
+        self.nv2 = params.nv
+        self.agg2 = tuple(params.agg)
+
+    @property
+    def coarse2_lat(self):
+        """Level-2 lattice as (T, Z, Y, X)."""
+        c = self.coarse_lat
+        a = self.agg2
+        return (c[0] // a[3], c[1] // a[2], c[2] // a[1], c[3] // a[0])
+
+    def get_vectors2(self, like=None):
+        shape = (self.nv2,) + self.coarse_lat + (2 * self.nv,)
+        W = _empty_like(like, shape) if like is not None else np.empty(shape, np.complex128)
+        p, wh = _ptr(W)
+        self._check(lib().tmg_get_vectors2(self._h, p, wh))
+        return W
+
+    def restrict2(self, c, prec=PREC_F64):
+        c2 = _empty_like(c, self.coarse2_lat + (2 * self.nv2,))
+        pc, wh = _ptr(c)
+        p2, _ = _ptr(c2)
+        self._check(lib().tmg_restrict2(self._h, pc, p2, prec, wh))
+        return c2
+
+    def prolong2(self, c2, prec=PREC_F64):
+        e = _empty_like(c2, self.coarse_lat + (2 * self.nv,))
+        p2, wh = _ptr(c2)
+        pe, _ = _ptr(e)
+        self._check(lib().tmg_prolong2(self._h, p2, pe, prec, wh))
+        return e
+
+    def coarse_apply2(self, x, mu=0.0, prec=PREC_F64):
+        y = _empty_like(x, x.shape)
+        px, wh = _ptr(x)
+        py, _ = _ptr(y)
+        self._check(lib().tmg_coarse_apply2(self._h, px, py, float(mu), prec, wh))
+        return y
+
+    def kcycle(self, b, mu=0.0, mode=0, prec=PREC_F64):
+        """Level-1 K-cycle kernel: mode 0 solve, 1 level-1 cycle, 2 smoother from zero."""
+        x = _empty_like(b, b.shape)
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        self._check(lib().tmg_kcycle(self._h, pb, px, float(mu), int(mode), prec, wh))
         return x
 
     def cycle(self, r):

@@ -58,6 +58,29 @@ void stage_out_finish(Ctx& c, DBuf& stage, double* p, size_t n_doubles, int wher
 
 int storage_of(int prec) { return prec == TMG_PREC_F64 ? TMG_PREC_F64 : TMG_PREC_F32; }
 
+// in (n_in complex, FP64) -> op in precision prec -> out (n_out complex, FP64)
+template <typename F>
+int level2_op(tmg_ctx* ctx, const char* name, const double* in, double* out, size_t n_in, size_t n_out, int prec,
+                     int where, F&& op) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!in || !out || (prec != TMG_PREC_F64 && prec != TMG_PREC_F32) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, std::string(name) + ": bad argument");
+    if (!c.l2_ready) return fail(ctx, TMG_ERR_STATE, std::string(name) + ": no level-2 setup");
+    const double* d = stage_in(c, c.stage_a, in, 2 * n_in, where);
+    tmg::CField xi, yo;
+    xi.create(prec, n_in);
+    yo.create(prec, n_out);
+    convert_field(c, d, TMG_PREC_F64, xi.buf.p, prec, n_in);
+    op(xi.buf.p, yo.buf.p);
+    double* o = stage_out_ptr(c, c.stage_b, out, 2 * n_out, where);
+    convert_field(c, yo.buf.p, prec, o, TMG_PREC_F64, n_out);
+    stage_out_finish(c, c.stage_b, out, 2 * n_out, where);
+    return TMG_OK;
+  });
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -343,6 +366,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     const int v = (int)value;
     if (k == "coarse_ctas_per_sm" && v >= 1 && v <= 8) ctx->c.coarse_ctas_per_sm = v;
     else if (k == "coarse_gs_passes" && (v >= 0 && v <= 2)) ctx->c.coarse_gs_passes = v;
+    else if (k == "kcycle_ctas_per_sm" && v >= 1 && v <= 4) ctx->c.kcycle_ctas_per_sm = v;
     else return fail(ctx, TMG_ERR_ARG, "tmg_tune: unknown key or value out of range: " + k);
     return TMG_OK;
   });
@@ -539,6 +563,89 @@ int tmg_coarse_solve(tmg_ctx* ctx, const double* b, double* x, double mu, int pr
     stage_out_finish(c, c.stage_b, x, 2 * n, where);
     return TMG_OK;
   });
+}
+
+// ---------------------------------------------------------------- third level
+int tmg_level2_defaults(tmg_level2_params* p) {
+  if (!p) return TMG_ERR_ARG;
+  for (int mu = 0; mu < 4; mu++) p->agg[mu] = 2;
+  p->nv = 8;
+  p->smooth_m = 3;
+  p->k_restart = 10;
+  p->k_rtol = 1e-1;
+  p->coarse_m = 30;
+  p->coarse_rtol = 5e-2;
+  p->n_init = 5;
+  p->n_iter = 3;
+  return TMG_OK;
+}
+
+int tmg_setup_level2(tmg_ctx* ctx, const tmg_level2_params* p, const double* v1, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!p || !v1 || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_setup_level2: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_setup_level2: no fine setup");
+    int avol = 1;
+    for (int mu = 0; mu < 4; mu++) {
+      if (p->agg[mu] < 1 || c.g.NB[mu] % p->agg[mu]) return fail(ctx, TMG_ERR_ARG, "tmg_setup_level2: aggregate does not tile the level-1 lattice");
+      avol *= p->agg[mu];
+    }
+    if (p->nv < 1 || 2 * p->nv > 64 || p->nv > avol * c.cl.nv || p->smooth_m < 1 || p->smooth_m > 64 || p->k_restart < 1 ||
+        p->k_restart > 16 || p->coarse_m < 1 || p->coarse_m > 64 || !(p->k_rtol >= 0.0) || !(p->coarse_rtol >= 0.0) ||
+        p->n_init < 0 || p->n_iter < 0)
+      return fail(ctx, TMG_ERR_ARG, "tmg_setup_level2: invalid level-2 parameters");
+    c.l2p = *p;
+    const size_t n = (size_t)p->nv * 2 * c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, v1, n, where);
+    mg_setup2(c, d);
+    if (where == TMG_HOST) c.stage_a.release();
+    return TMG_OK;
+  });
+}
+
+int tmg_get_vectors2(tmg_ctx* ctx, double* W2, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!W2 || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_get_vectors2: bad argument");
+    if (!c.l2_ready) return fail(ctx, TMG_ERR_STATE, "tmg_get_vectors2: no level-2 setup");
+    const size_t n = (size_t)c.cl2.nv * 2 * c.cl.nc * c.cl.nd;
+    double* d = stage_out_ptr(c, c.stage_b, W2, n, where);
+    TMG_CUDA(cudaMemcpyAsync(d, c.cl2.W64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    stage_out_finish(c, c.stage_b, W2, n, where);
+    if (where == TMG_DEVICE) TMG_CUDA(cudaStreamSynchronize(c.stream));
+    return TMG_OK;
+  });
+}
+
+int tmg_restrict2(tmg_ctx* ctx, const double* cv, double* c2, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  return level2_op(ctx, "tmg_restrict2", cv, c2, (size_t)c.cl.nc * c.cl.nd, (size_t)c.cl2.nc * c.cl2.nd, prec, where,
+                   [&](const void* x, void* y) { restrict_c(c, prec, x, y); });
+}
+
+int tmg_prolong2(tmg_ctx* ctx, const double* c2, double* e, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  return level2_op(ctx, "tmg_prolong2", c2, e, (size_t)c.cl2.nc * c.cl2.nd, (size_t)c.cl.nc * c.cl.nd, prec, where,
+                   [&](const void* x, void* y) { prolong_c(c, prec, x, y); });
+}
+
+int tmg_coarse_apply2(tmg_ctx* ctx, const double* x, double* y, double mu, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  const size_t n2 = (size_t)c.cl2.nc * c.cl2.nd;
+  return level2_op(ctx, "tmg_coarse_apply2", x, y, n2, n2, prec, where,
+                   [&](const void* a, void* b) { coarse_apply_c(c, prec, a, b, mu); });
+}
+
+int tmg_kcycle(tmg_ctx* ctx, const double* b, double* x, double mu, int mode, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (mode < 0 || mode > 2) return fail(ctx, TMG_ERR_ARG, "tmg_kcycle: mode must be 0, 1 or 2");
+  const size_t n1 = (size_t)c.cl.nc * c.cl.nd;
+  return level2_op(ctx, "tmg_kcycle", b, x, n1, n1, prec, where,
+                   [&](const void* bb, void* xx) { kcycle(c, prec, bb, xx, mu, mode); });
 }
 
 int tmg_cycle(tmg_ctx* ctx, const double* r, double* z, int where) {

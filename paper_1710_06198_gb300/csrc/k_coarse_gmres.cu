@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 
 #include "tmg_host.h"
+#include "level2.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -61,8 +62,10 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   return t;
 }
 
+// GMRES from zero on the operator of a (any level): grid-wide phases, the caller's grid must be a
+// cooperative launch; a.x is complete after the caller's next grid barrier.
 template <typename S>
-__global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
+__device__ void gmres_dev(const CgArgs<S>& a) {
   using T2 = typename CplxT<S>::T2;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[32];
@@ -265,6 +268,349 @@ __global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
     S xr = 0, xi = 0;
     for (int i = 0; i < k; i++) {
       const T2 v = a.V[(size_t)i * n + e];
+      xr += yr[i] * v.x - yi[i] * v.y;
+      xi += yr[i] * v.y + yi[i] * v.x;
+    }
+    T2 o;
+    o.x = xr;
+    o.y = xi;
+    a.x[e] = o;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
+  gmres_dev(a);
+}
+
+// ---- third level: the level-1 K-cycle as one persistent cooperative kernel.
+// FGMRES on D_c (right-preconditioned, flexible, from zero, at most kr steps) whose preconditioner
+// is the level-1 cycle: z = P2 gmres_L2(P2^dag v), then z += gmres_sm(v - D_c z) (smooth_m steps).
+constexpr int KMAXR = 16;
+
+template <typename S>
+struct KcArgs {
+  using T2 = typename CplxT<S>::T2;
+  L2Geom q;
+  CgArgs<S> sm;        // level-1 operator; smoother GMRES (b = r, x = es unless mode 2)
+  CgArgs<S> l2;        // level-2 operator; level-2 GMRES (b = c2, x = e2)
+  const T2* W2;        // level-2 basis [nv2][nc1 nd1]
+  const T2* b;
+  T2* x;
+  T2* V;               // FGMRES basis (kr + 1) x n1
+  T2* Z;               // preconditioned vectors kr x n1
+  T2* t;               // D_c z work vector
+  int kr, passes, mode;
+  double krtol;
+  double2* part;       // [KMAXR + 1][G]
+  double* npart;       // [G]
+  double2* R;          // (KMAXR + 1) x KMAXR rotated Hessenberg (CTA 0)
+  double2* y;          // [KMAXR]
+  int* counter;        // FGMRES steps
+};
+
+// dst = D(mu) src (sub == nullptr) or dst = sub - D(mu) src on the operator of op; grid-wide, dst
+// complete after the caller's next grid barrier.
+template <typename S>
+__device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* src, typename CplxT<S>::T2* dst,
+                            const typename CplxT<S>::T2* sub) {
+  using T2 = typename CplxT<S>::T2;
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int gwarp = blockIdx.x * nwarp + (threadIdx.x >> 5), nwarps_total = gridDim.x * nwarp;
+  for (int task = gwarp; task < op.nc * 9; task += nwarps_total) {
+    const T2* blk = op.Dc + (size_t)task * op.nd * op.nd;
+    const T2* xv = src + (size_t)op.nbr[task] * op.nd;
+    for (int k = lane; k < op.nd; k += 32) {
+      S ar = 0, ai = 0;
+#pragma unroll 8
+      for (int l = 0; l < op.nd; l++) {
+        const T2 m = blk[(size_t)l * op.nd + k];
+        const T2 v = xv[l];
+        ar += m.x * v.x - m.y * v.y;
+        ai += m.x * v.y + m.y * v.x;
+      }
+      T2 o;
+      o.x = ar;
+      o.y = ai;
+      op.rows[(size_t)task * op.nd + k] = o;
+    }
+  }
+  grid.sync();
+  const int n = op.nc * op.nd;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int site = e / op.nd, k = e - site * op.nd;
+    S ar = 0, ai = 0;
+    for (int d = 0; d < 9; d++) { const T2 r = op.rows[((size_t)site * 9 + d) * op.nd + k]; ar += r.x; ai += r.y; }
+    const T2 xs = src[e];
+    const S tw = k < op.nv ? op.mu : -op.mu;
+    ar -= tw * xs.y;
+    ai += tw * xs.x;
+    T2 o;
+    if (sub) {
+      const T2 s0 = sub[e];
+      o.x = s0.x - ar;
+      o.y = s0.y - ai;
+    } else {
+      o.x = ar;
+      o.y = ai;
+    }
+    dst[e] = o;
+  }
+}
+
+// c2 = P2^dag v (grid-wide, one thread per level-2 dof)
+template <typename S>
+__device__ void restrict2_dev(const L2Geom& q, const typename CplxT<S>::T2* W, const typename CplxT<S>::T2* v,
+                              typename CplxT<S>::T2* c2) {
+  using T2 = typename CplxT<S>::T2;
+  const size_t n1 = (size_t)q.nc1 * q.nd1;
+  const int nd2 = 2 * q.nv2;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < q.nc2 * nd2; o += gridDim.x * blockDim.x) {
+    const int a2 = o / nd2, r = o - a2 * nd2, chi = r / q.nv2, j = r - chi * q.nv2;
+    S re = 0, im = 0;
+    for (int t = 0; t < q.avol; t++) {
+      const size_t base = (size_t)l2_member(q, a2, t) * q.nd1 + chi * q.nv1;
+      for (int k = 0; k < q.nv1; k++) {
+        const T2 w = W[(size_t)j * n1 + base + k];
+        const T2 x = v[base + k];
+        re += w.x * x.x + w.y * x.y;
+        im += w.x * x.y - w.y * x.x;
+      }
+    }
+    T2 out;
+    out.x = re;
+    out.y = im;
+    c2[o] = out;
+  }
+}
+
+// z = P2 c2 (grid-wide, one thread per level-1 dof)
+template <typename S>
+__device__ void prolong2_dev(const L2Geom& q, const typename CplxT<S>::T2* W, const typename CplxT<S>::T2* c2,
+                             typename CplxT<S>::T2* z) {
+  using T2 = typename CplxT<S>::T2;
+  const int n1 = q.nc1 * q.nd1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1; e += gridDim.x * blockDim.x) {
+    const int a1 = e / q.nd1, k = e - a1 * q.nd1;
+    int c[4];
+    l1_coords(q, a1, c);
+    const T2* cv = c2 + (size_t)l2_agg_of(q, c) * 2 * q.nv2 + (k < q.nv1 ? 0 : q.nv2);
+    S re = 0, im = 0;
+    for (int j = 0; j < q.nv2; j++) {
+      const T2 w = W[(size_t)j * n1 + e];
+      const T2 v = cv[j];
+      re += w.x * v.x - w.y * v.y;
+      im += w.x * v.y + w.y * v.x;
+    }
+    T2 out;
+    out.x = re;
+    out.y = im;
+    z[e] = out;
+  }
+}
+
+// z = level-1 cycle of v (grid-wide; z complete on return)
+template <typename S>
+__device__ void l1_cycle_dev(const KcArgs<S>& a, const typename CplxT<S>::T2* v, typename CplxT<S>::T2* z) {
+  using T2 = typename CplxT<S>::T2;
+  cg::grid_group grid = cg::this_grid();
+  restrict2_dev<S>(a.q, a.W2, v, const_cast<T2*>(a.l2.b));
+  grid.sync();
+  gmres_dev(a.l2);
+  grid.sync();
+  prolong2_dev<S>(a.q, a.W2, a.l2.x, z);
+  grid.sync();
+  stencil_dev(a.sm, z, const_cast<T2*>(a.sm.b), v);
+  grid.sync();
+  gmres_dev(a.sm);
+  grid.sync();
+  const int n1 = a.q.nc1 * a.q.nd1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1; e += gridDim.x * blockDim.x) {
+    T2 o = z[e];
+    const T2 d = a.sm.x[e];
+    o.x += d.x;
+    o.y += d.y;
+    z[e] = o;
+  }
+  grid.sync();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
+  using T2 = typename CplxT<S>::T2;
+  cg::grid_group grid = cg::this_grid();
+  if (a.mode == 2) {              // smoother from zero
+    gmres_dev(a.sm);
+    return;
+  }
+  if (a.mode == 1) {              // one level-1 cycle
+    l1_cycle_dev(a, a.b, a.x);
+    return;
+  }
+  __shared__ double sh[32];
+  __shared__ double2 hcol[KMAXR + 2], hp[KMAXR + 1];
+  __shared__ double2 cs[KMAXR], sn[KMAXR], gv[KMAXR + 1];
+  __shared__ int s_done, s_k;
+  __shared__ double s_beta, s_hn;
+  const int n = a.q.nc1 * a.q.nd1;
+  const int G = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
+  const int chunk = (n + G - 1) / G;
+  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  {
+    S nn = 0;
+    for (int e = tid; e < n; e += nth) { const T2 v = a.b[e]; nn += v.x * v.x + v.y * v.y; }
+    const double t = cta_sum((double)nn, sh);
+    if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+  }
+  grid.sync();
+  if (warp == 0) {
+    double t = 0.0;
+    for (int q = lane; q < G; q += 32) t += a.npart[q];
+    t = warp_sum(t);
+    if (lane == 0) s_beta = sqrt(t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_done = !(s_beta > 0.0);
+    s_k = 0;
+    for (int i = 0; i <= KMAXR; i++) gv[i] = make_double2(0.0, 0.0);
+    gv[0] = make_double2(s_beta, 0.0);
+  }
+  __syncthreads();
+  {
+    const S inv = s_beta > 0.0 ? (S)(1.0 / s_beta) : (S)0;
+    for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
+  }
+  grid.sync();
+  for (int j = 0; j < a.kr && !s_done; j++) {
+    T2* vj = a.V + (size_t)j * n;
+    T2* zj = a.Z + (size_t)j * n;
+    l1_cycle_dev(a, vj, zj);                         // z_j = M v_j (ends with a grid barrier)
+    stencil_dev(a.sm, zj, a.t, (const T2*)nullptr);  // w = D_c z_j
+    grid.sync();
+    if (threadIdx.x == 0)
+      for (int i = 0; i <= j + 1; i++) hcol[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int pass = 0; pass < a.passes; pass++) {
+      for (int i = warp; i <= j; i += nwarp) {
+        const T2* vi = a.V + (size_t)i * n;
+        S re = 0, im = 0;
+        for (int e = e0 + lane; e < e1; e += 32) {
+          const T2 p = vi[e], q = a.t[e];
+          re += p.x * q.x + p.y * q.y;
+          im += p.x * q.y - p.y * q.x;
+        }
+        const double dre = warp_sum((double)re), dim = warp_sum((double)im);
+        if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
+      }
+      grid.sync();
+      for (int i = warp; i <= j; i += nwarp) {
+        double re = 0.0, im = 0.0;
+        for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) {
+          hp[i] = make_double2(re, im);
+          hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+        }
+      }
+      __syncthreads();
+      S nn = 0;
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        T2 q = a.t[e];
+        S qr = q.x, qi = q.y;
+        for (int i = 0; i <= j; i++) {
+          const T2 p = a.V[(size_t)i * n + e];
+          const S hr = (S)hp[i].x, hi = (S)hp[i].y;
+          qr -= hr * p.x - hi * p.y;
+          qi -= hr * p.y + hi * p.x;
+        }
+        q.x = qr;
+        q.y = qi;
+        a.t[e] = q;
+        nn += qr * qr + qi * qi;
+      }
+      if (pass == a.passes - 1) {
+        const double t = cta_sum((double)nn, sh);
+        if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+      } else {
+        __syncthreads();
+      }
+    }
+    grid.sync();
+    if (warp == 0) {
+      double t = 0.0;
+      for (int q = lane; q < G; q += 32) t += a.npart[q];
+      t = warp_sum(t);
+      if (lane == 0) s_hn = sqrt(t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double hn = s_hn;
+      hcol[j + 1] = make_double2(hn, 0.0);
+      for (int i = 0; i < j; i++) {
+        const double2 x0 = hcol[i], x1 = hcol[i + 1];
+        const double2 c = cs[i], s = sn[i];
+        hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
+                               c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
+        hcol[i + 1] = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                                   -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+      }
+      const double2 p = hcol[j], q = hcol[j + 1];
+      const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+      cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
+      sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
+      hcol[j] = make_double2(den, 0.0);
+      hcol[j + 1] = make_double2(0.0, 0.0);
+      const double2 g = gv[j];
+      gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
+      gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+      if (blockIdx.x == 0)
+        for (int i = 0; i <= j; i++) a.R[(size_t)j * (KMAXR + 1) + i] = hcol[i];
+      s_k = j + 1;
+      const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+      if (res <= a.krtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.kr - 1) s_done = 1;
+    }
+    __syncthreads();
+    if (!s_done) {                                   // v_{j+1} = w / h_{j+1,j} on the own chunk
+      const S inv = (S)(1.0 / s_hn);
+      T2* vn = a.V + (size_t)(j + 1) * n;
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        T2 q = a.t[e];
+        q.x *= inv;
+        q.y *= inv;
+        vn[e] = q;
+      }
+    }
+    grid.sync();
+  }
+  const int k = s_k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; i--) {
+      double2 acc = gv[i];
+      for (int l = i + 1; l < k; l++) {
+        const double2 h = a.R[(size_t)l * (KMAXR + 1) + i], yl = a.y[l];
+        acc.x -= h.x * yl.x - h.y * yl.y;
+        acc.y -= h.x * yl.y + h.y * yl.x;
+      }
+      const double2 d = a.R[(size_t)i * (KMAXR + 1) + i];
+      const double dn = d.x * d.x + d.y * d.y;
+      a.y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : make_double2(0.0, 0.0);
+    }
+    if (a.counter) *a.counter += k;
+  }
+  grid.sync();
+  __shared__ S yr[KMAXR], yi[KMAXR];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = (S)a.y[i].x; yi[i] = (S)a.y[i].y; }
+  __syncthreads();
+  for (int e = tid; e < n; e += nth) {
+    S xr = 0, xi = 0;
+    for (int i = 0; i < k; i++) {
+      const T2 v = a.Z[(size_t)i * n + e];
       xr += yr[i] * v.x - yi[i] * v.y;
       xi += yr[i] * v.y + yi[i] * v.x;
     }
@@ -713,6 +1059,122 @@ void coarse_gmres_persistent(Ctx& c, int cp, const void* b, void* x, double mu) 
   ProfScope ps(c, PK_COARSE_SOLVE);
   if (cp == TMG_PREC_F64) launch<double>(c, b, x, mu, c.cl.Dc64.p);
   else launch<float>(c, b, x, mu, c.cl.Dc32.p);
+}
+
+}  // namespace tmg
+
+namespace tmg {
+
+namespace {
+
+template <typename S>
+void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode) {
+  using T2 = typename CplxT<S>::T2;
+  const tmg_level2_params& p = c.l2p;
+  const size_t n1 = (size_t)c.cl.nc * c.cl.nd, n2 = (size_t)c.cl2.nc * c.cl2.nd;
+  static int max_per_sm[2] = {-1, -1};
+  int& mps = max_per_sm[sizeof(S) == 8];
+  if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_kcycle<S>, 256, 0));
+  if (mps < 1) throw Error{TMG_ERR_CUDA, "K-cycle kernel cannot be resident"};
+  const int G = c.sms * std::max(1, std::min(mps, c.kcycle_ctas_per_sm));
+  const int sm_m = std::min(p.smooth_m, CMAXM), cm = std::min(p.coarse_m, CMAXM), kr = std::min(p.k_restart, KMAXR);
+  // one scratch allocation, carved 256-byte aligned
+  const size_t vec_elems[] = {(kr + 1) * n1, kr * n1, n1, n1, n1, (sm_m + 1) * n1, 10 * n1, n2, n2, (cm + 1) * n2, 10 * n2};
+  const size_t nvec = sizeof(vec_elems) / sizeof(vec_elems[0]);
+  const size_t d2_elems[] = {(size_t)(KMAXR + 1) * G, (size_t)(KMAXR + 1) * KMAXR, KMAXR,
+                             (size_t)(CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM,
+                             (size_t)(CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM};
+  const size_t nd2 = sizeof(d2_elems) / sizeof(d2_elems[0]);
+  size_t off[32], o = 0;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  for (size_t i = 0; i < nvec; i++) { off[i] = o; o = al(o + vec_elems[i] * sizeof(T2)); }
+  for (size_t i = 0; i < nd2; i++) { off[nvec + i] = o; o = al(o + d2_elems[i] * sizeof(double2)); }
+  off[nvec + nd2] = o;
+  o = al(o + 3 * (size_t)G * sizeof(double));
+  c.kw.alloc(o);
+  if (!c.l2_iter_dev.p) {
+    c.l2_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.l2_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  char* base = (char*)c.kw.p;
+  auto vec = [&](int i) { return (T2*)(base + off[i]); };
+  auto d2 = [&](int i) { return (double2*)(base + off[nvec + i]); };
+  double* npart = (double*)(base + off[nvec + nd2]);
+  const int passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
+
+  KcArgs<S> a;
+  a.q = l2geom(c);
+  CgArgs<S>& s = a.sm;
+  s.nd = c.cl.nd;
+  s.nv = c.cl.nv;
+  s.nc = c.cl.nc;
+  s.m = sm_m;
+  s.passes = passes;
+  s.Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
+  s.nbr = c.cl.nbr.as<int>();
+  s.b = mode == 2 ? (const T2*)b : vec(3);
+  s.x = mode == 2 ? (T2*)x : vec(4);
+  s.V = vec(5);
+  s.w = vec(6);
+  s.rows = s.w + n1;
+  s.mu = (S)mu;
+  s.rtol = 0.0;
+  s.part = d2(3);
+  s.R = d2(4);
+  s.y = d2(5);
+  s.npart = npart + G;
+  s.counter = nullptr;
+  CgArgs<S>& l = a.l2;
+  l.nd = c.cl2.nd;
+  l.nv = c.cl2.nv;
+  l.nc = c.cl2.nc;
+  l.m = cm;
+  l.passes = passes;
+  l.Dc = (const T2*)(sizeof(S) == 8 ? c.cl2.Dc64.p : c.cl2.Dc32.p);
+  l.nbr = c.cl2.nbr.as<int>();
+  l.b = vec(7);
+  l.x = vec(8);
+  l.V = vec(9);
+  l.w = vec(10);
+  l.rows = l.w + n2;
+  l.mu = (S)mu;
+  l.rtol = p.coarse_rtol;
+  l.part = d2(6);
+  l.R = d2(7);
+  l.y = d2(8);
+  l.npart = npart + 2 * G;
+  l.counter = c.l2_iter_dev.as<int>();
+  a.W2 = (const T2*)(sizeof(S) == 8 ? c.cl2.W64.p : c.cl2.W32.p);
+  a.b = (const T2*)b;
+  a.x = (T2*)x;
+  a.V = vec(0);
+  a.Z = vec(1);
+  a.t = vec(2);
+  a.kr = kr;
+  a.passes = passes;
+  a.mode = mode;
+  a.krtol = p.k_rtol;
+  a.part = d2(0);
+  a.R = d2(1);
+  a.y = d2(2);
+  a.npart = npart;
+  a.counter = c.coarse_iter_dev.as<int>();
+  void* args[] = {&a};
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_kcycle<S>, dim3(G), dim3(256), args, 0, c.stream));
+}
+
+}  // namespace
+
+void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (!c.l2_ready && mode != 2) throw Error{TMG_ERR_STATE, "K-cycle: level 2 not built"};
+  if (prec == TMG_PREC_F64) kcycle_launch<double>(c, b, x, mu, mode);
+  else kcycle_launch<float>(c, b, x, mu, mode);
 }
 
 }  // namespace tmg

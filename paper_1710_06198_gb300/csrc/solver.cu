@@ -263,7 +263,8 @@ static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu) {
   c.cw_cr.alloc(nco * esize(pc));
   c.cw_ce.alloc(nco * esize(pc));
   restrict_(c, pf, r, c.cw_cr.p, pc);
-  coarse_gmres_persistent(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
+  if (c.l2_ready) kcycle(c, pc, c.cw_cr.p, c.cw_ce.p, mu, 0);   // three levels: the level-1 K-cycle
+  else coarse_gmres_persistent(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
   prolong(c, pf, c.cw_ce.p, pc, z, 0);
   sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
 }
@@ -282,6 +283,7 @@ static void set_vectors(Ctx& c, int sp) {
 }
 
 void mg_setup(Ctx& c, const double* v0_lex) {
+  c.l2_ready = false;
   const int nv = c.mg.nv;
   c.cl.nv = nv;
   c.cl.nd = 2 * nv;
@@ -322,6 +324,61 @@ void mg_setup(Ctx& c, const double* v0_lex) {
       blas_scale(c, 1.0 / nrm, 0.0, vj, sp, n);
     }
     set_vectors(c, sp);
+  }
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// ---------------------------------------------------------------- level-2 setup (three levels)
+static void set_vectors2(Ctx& c, int pc) {
+  const size_t n1 = (size_t)c.cl.nc * c.cl.nd;
+  convert_field(c, c.sv2.p, pc, c.cl2.W64.p, TMG_PREC_F64, n1 * c.cl2.nv);
+  orthonormalise_c(c);
+  convert_field(c, c.cl2.W64.p, TMG_PREC_F64, c.cl2.W32.p, TMG_PREC_F32, n1 * c.cl2.nv);
+  build_coarse_c(c);
+}
+
+void mg_setup2(Ctx& c, const double* v1_dev) {
+  const tmg_level2_params& p = c.l2p;
+  c.l2_ready = false;
+  Coarse2& q = c.cl2;
+  for (int mu = 0; mu < 4; mu++) {
+    q.agg[mu] = p.agg[mu];
+    q.cgeom[mu] = c.g.NB[mu] / p.agg[mu];
+  }
+  q.nv = p.nv;
+  q.nd = 2 * p.nv;
+  q.nc = q.cgeom[0] * q.cgeom[1] * q.cgeom[2] * q.cgeom[3];
+  const size_t n1 = (size_t)c.cl.nc * c.cl.nd;
+  const int pc = c.mg.prec_coarse;
+  const size_t es = esize(pc);
+  q.W64.alloc(p.nv * n1 * 16);
+  q.W32.alloc(p.nv * n1 * 8);
+  c.sv2.alloc(p.nv * n1 * es);
+  DBuf tmp;
+  tmp.alloc(n1 * es);
+  char* raw = (char*)c.sv2.p;
+  convert_field(c, v1_dev, TMG_PREC_F64, raw, pc, n1 * p.nv);
+  auto normalise_into = [&](void* vj) {
+    const double nrm = std::sqrt(blas_norm2(c, tmp.p, pc, n1));
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) throw Error{TMG_ERR_BREAKDOWN, "level-2 setup: test vector vanished"};
+    blas_copy(c, tmp.p, vj, pc, n1);
+    blas_scale(c, 1.0 / nrm, 0.0, vj, pc, n1);
+  };
+  for (int pass = 0; pass < p.n_init; pass++)
+    for (int j = 0; j < p.nv; j++) {
+      void* vj = raw + j * n1 * es;
+      kcycle(c, pc, vj, tmp.p, c.mu, 2);
+      normalise_into(vj);
+    }
+  set_vectors2(c, pc);
+  c.l2_ready = true;
+  for (int it = 0; it < p.n_iter; it++) {
+    for (int j = 0; j < p.nv; j++) {
+      void* vj = raw + j * n1 * es;
+      kcycle(c, pc, vj, tmp.p, c.mu, 1);
+      normalise_into(vj);
+    }
+    set_vectors2(c, pc);
   }
   TMG_CUDA(cudaStreamSynchronize(c.stream));
 }
@@ -598,7 +655,13 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
       float2* zj = Zp + (size_t)it * istride;
       // z = M v (one batched cycle)
       restrict_mrhs(c, ncol, vj, cr.p);
-      coarse_gmres_batched(c, ncol, cr.p, ce.p, mu_dev.as<float>());
+      if (c.l2_ready) {   // three levels: one K-cycle per column
+        const size_t nco = (size_t)c.cl.nc * c.cl.nd;
+        for (int col = 0; col < ncol; col++)
+          kcycle(c, TMG_PREC_F32, cr.as<float2>() + col * nco, ce.as<float2>() + col * nco, mu[col], 0);
+      } else {
+        coarse_gmres_batched(c, ncol, cr.p, ce.p, mu_dev.as<float>());
+      }
       prolong_mrhs(c, ncol, ce.p, zj);
       sap_mrhs(c, pf, ncol, zj, vj, mu_dev.as<float>(), c.mg.sap_sweeps);
       dslash_mrhs(c, pf, ncol, w.p, zj, nullptr, mu_dev.as<float>(), 0);

@@ -15,6 +15,8 @@ struct SolveStats {
 
 // Adaptive setup from nv FP64 lexicographic vectors on the device (Sec. 1.1, Sec. 2).
 void mg_setup(Ctx& c, const double* v0_lex);
+// Level-2 setup (three levels) from nv2 FP64 level-1 vectors on the device, parameters in c.l2p.
+void mg_setup2(Ctx& c, const double* v1_dev);
 // z = M_MG r in the fine storage precision of the multigrid parameters (r is not modified).
 void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // Solve D(mu) x = b on FP64 internal fields (b, x: F64 storage).  Returns a tmg_status.

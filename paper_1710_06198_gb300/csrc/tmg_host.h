@@ -91,6 +91,16 @@ struct Coarse {
   DBuf nbr;                    // coarse neighbour table [nc][9] (slot 0 self, 1 + 2 mu: +mu, 2 + 2 mu: -mu)
 };
 
+// Level 2 of the three-level hierarchy: aggregates of level-1 sites (Sec. 1.2 runs three levels).
+struct Coarse2 {
+  int agg[4] = {1, 1, 1, 1};   // level-2 aggregate in level-1 sites
+  int nv = 0, nd = 0, nc = 0;  // level-2 test vectors, dofs per level-2 site, level-2 sites
+  int cgeom[4];                // level-2 lattice dims
+  DBuf W64, W32;               // orthonormalised level-2 basis, [nv][nc1 * nd1]
+  DBuf Dc64, Dc32;             // level-2 stencil [nc][9][nd(col)][nd(row)]
+  DBuf nbr;                    // level-2 neighbour table [nc][9]
+};
+
 // Optional per-kernel-class timing with CUDA events on the context stream (tmg_profile).
 enum { PK_DSLASH_F64 = 0, PK_DSLASH_F32, PK_DSLASH_F16, PK_SAP_F64, PK_SAP_F32, PK_SAP_F16, PK_RESTRICT,
        PK_PROLONG, PK_COARSE, PK_COARSE_SOLVE, PK_COUNT };
@@ -129,6 +139,12 @@ struct Ctx {
   tmg_mg_params mg{};
   bool mg_ready = false;
   Coarse cl;
+  tmg_level2_params l2p{};
+  bool l2_ready = false;   // level 2 built: the coarse solve of the cycle is the level-1 K-cycle
+  Coarse2 cl2;
+  DBuf kw;                 // K-cycle scratch (k_coarse_gmres.cu)
+  DBuf sv2;                // raw level-1 test vectors of the level-2 setup
+  DBuf l2_iter_dev;        // device counter of level-2 GMRES steps (K-cycle steps go to coarse_iter_dev)
   // solver workspaces (solver.cu)
   DBuf cw_V, cw_w, cw_state, cw_part, cw_cr, cw_ce;   // coarse GMRES
   DBuf fw_V, fw_Z, fw_w, fw_r64, fw_e, fw_x, fw_t, fw_part, fw_h;  // outer FGMRES / CG
@@ -144,6 +160,7 @@ struct Ctx {
   // launch-shape tuning knobs (tmg_tune)
   int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
   int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
+  int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
   Prof prof;
 };
 
@@ -228,6 +245,22 @@ void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_d
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
 void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);
 void build_coarse(Ctx& c);
+
+// ---------------------------------------------------------------- level 2 (k_level2.cu)
+// level-1 vectors [nc1][nd1] <-> level-2 vectors [nc2][nd2] in precision F64 / F32
+void restrict_c(Ctx& c, int prec, const void* r, void* c2);
+void prolong_c(Ctx& c, int prec, const void* c2, void* e);
+// per (level-2 aggregate, level-1 chirality) modified Gram-Schmidt, twice, on cl2.W64
+void orthonormalise_c(Ctx& c);
+// cl2.Dc64 / Dc32 / nbr from cl.Dc64 and cl2.W64
+void build_coarse_c(Ctx& c);
+// y = D_cc(mu) x on level 2
+void coarse_apply_c(Ctx& c, int prec, const void* x, void* y, double mu);
+// Level-1 K-cycle as one persistent cooperative kernel (k_coarse_gmres.cu), precision F64 / F32:
+// mode 0: x ~= D_c(mu)^-1 b by FGMRES preconditioned by the level-1 cycle (the coarse solve of the
+//         three-level cycle); mode 1: x = level-1 cycle applied to b; mode 2: x = smoother applied
+//         to b from zero (GMRES steps on D_c).
+void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode);
 
 }  // namespace tmg
 

@@ -57,3 +57,14 @@ def test_null_context_calls_fail_cleanly(L):
     p = tmg.MGParams()
     assert L.tmg_mg_defaults(ctypes.byref(p)) == 0
     assert p.nv == 8 and p.sap_sweeps == 3 and p.restart == 10
+
+
+def test_level2_defaults_and_null_context(L):
+    q = tmg.Level2Params()
+    assert L.tmg_level2_defaults(ctypes.byref(q)) == 0
+    assert list(q.agg) == [2, 2, 2, 2] and q.nv == 8 and q.smooth_m == 3
+    assert q.k_restart == 10 and abs(q.k_rtol - 0.1) < 1e-15 and q.coarse_m == 30
+    assert L.tmg_level2_defaults(None) == -1
+    assert L.tmg_setup_level2(None, ctypes.byref(q), None, 0) == -1
+    assert L.tmg_kcycle(None, None, None, 0.0, 0, 0, 0) == -1
+    assert L.tmg_coarse_apply2(None, None, None, 0.0, 0, 0) == -1
