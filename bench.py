@@ -34,17 +34,15 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(name="tm_clover_16x16x16x32_mixed_2lvl", dims=(16, 16, 16, 32), block=(4, 4, 4, 4), eps=0.35,
-                seed=3, csw=1.5, mu=0.003, nv=16, rhs_seed=4, tol=1e-10, sigma_target=5e-4, setup_seed=103)
+from synth import workloads  # noqa: E402
+
+WORKLOAD = dict(name="tm_clover_16x16x16x32_mixed_2lvl", tol=1e-10,
+                **workloads.WORKLOADS["tm_clover_16x16x16x32_mixed_2lvl"])
 METRIC = "DD-alphaAMG solve s to 1e-10 (mixed+batched vs FP64) ; dslash GB/s vs HBM peak"
 
 
 def workload_kappa(w):
-    path = os.path.join(ROOT, "synth", "kappa.json")
-    with open(path) as f:
-        table = json.load(f)
-    e = table[w["name"]]
-    return e["kappa"], e
+    return workloads.kappa(w["name"])
 
 
 def peaks():
@@ -154,7 +152,6 @@ def run_kernel_case(args):
     import torch
     import paper_1710_06198_gb300 as tmg
     from synth import fields
-    from oracle import dirac  # noqa: F401  (kappa conversion only)
     dims = (24, 24, 24, 48)
     U = fields.gauge_field(dims, 0.3, 4)
     ctx = tmg.Context(dims, (4, 4, 4, 4))
