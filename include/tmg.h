@@ -180,6 +180,24 @@ int tmg_coarse_apply2(tmg_ctx *ctx, const double *x, double *y, double mu, int p
  * mode 2: x = smoother of b from zero (smooth_m GMRES steps). */
 int tmg_kcycle(tmg_ctx *ctx, const double *b, double *x, double mu, int mode, int prec, int where);
 
+/* ---- the non-degenerate doublet (Eq. 2, coarsened with P_ND = P x I2 as in Sec. 1.2) ----
+ * Doublet vectors are flavour pairs: fine [2][V][4][3], coarse [2][V_c][2 N_v].  The operator
+ * parameters are the context's mubar and epsbar; P (and P2 with three levels) come from the
+ * single-flavour setup, which a caller runs with mu = mubar (the flavour-diagonal part of D_ND).
+ *   tmg_sap_nd:          x <- k SAP sweeps on D_ND x = b (block MR on the flavour-coupled
+ *                        Dirichlet block operator) starting from the given x;
+ *   tmg_coarse_apply_nd: y = D_ND,c x = (D_c x I2 + i mubar G5_c x tau3 - epsbar I x tau1) x;
+ *   tmg_coarse_solve_nd: x ~= D_ND,c^-1 b by the coarse GMRES of the cycle (with three levels
+ *                        use tmg_kcycle_nd);
+ *   tmg_kcycle_nd:       the level-1 K-cycle kernel on doublet level-1 vectors (modes as
+ *                        tmg_kcycle);
+ *   tmg_cycle_nd:        z = one doublet preconditioner cycle of r. */
+int tmg_sap_nd(tmg_ctx *ctx, const double *b, double *x, int prec, int where);
+int tmg_coarse_apply_nd(tmg_ctx *ctx, const double *x, double *y, int prec, int where);
+int tmg_coarse_solve_nd(tmg_ctx *ctx, const double *b, double *x, int prec, int where);
+int tmg_kcycle_nd(tmg_ctx *ctx, const double *b, double *x, int mode, int prec, int where);
+int tmg_cycle_nd(tmg_ctx *ctx, const double *r, double *z, int where);
+
 /* ---- solves ---- */
 typedef struct {
   int iterations;        /* outer FGMRES (or CG) iterations summed over restarts/refinements */
@@ -194,8 +212,12 @@ enum {
   TMG_SOLVE_MG_MIXED = 1, /* FP64 defect correction around FGMRES + DD-alpha-AMG in the MG   */
                           /* params' fine/coarse precisions                                 */
   TMG_SOLVE_CG_F64 = 2,   /* CG on D D^dag in FP64 (comparator of Sec. 1.1 / Fig. 1)       */
-  TMG_SOLVE_MG_BATCHED = 3 /* as TMG_SOLVE_MG_MIXED, all n_rhs (<= 32) columns in lock-step: */
+  TMG_SOLVE_MG_BATCHED = 3, /* as TMG_SOLVE_MG_MIXED, all n_rhs (<= 32) columns in lock-step: */
                           /* one launch per operation for every column, FP32 coarse level    */
+  TMG_SOLVE_ND_F64 = 4,   /* doublet D_ND x = b (Eq. 2), b and x [n_rhs][2][V][4][3], multigrid */
+                          /* with P_ND = P x I2 (Sec. 1.2), everything in FP64                */
+  TMG_SOLVE_ND_MIXED = 5  /* the same with FP64 defect correction around the MG params'      */
+                          /* fine/coarse precisions                                          */
 };
 
 /* Solve D(mu) x = b (relative FP64 residual tol) for n_rhs right-hand sides, one after another.

@@ -24,6 +24,7 @@ PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 OP_D, OP_DDAG, OP_DND, OP_HOP = 0, 1, 2, 3
 SOLVE_MG_F64, SOLVE_MG_MIXED, SOLVE_CG_F64, SOLVE_MG_BATCHED = 0, 1, 2, 3
+SOLVE_ND_F64, SOLVE_ND_MIXED = 4, 5
 STATUS = {0: "TMG_OK", -1: "TMG_ERR_ARG", -2: "TMG_ERR_CUDA", -3: "TMG_ERR_OOM", -4: "TMG_ERR_NOCONV",
           -5: "TMG_ERR_BREAKDOWN", -6: "TMG_ERR_TIMEOUT", -7: "TMG_ERR_STATE"}
 
@@ -92,6 +93,11 @@ _SIGS = {
     "tmg_prolong2": [_P, _P, _P, _I, _I],
     "tmg_coarse_apply2": [_P, _P, _P, _D, _I, _I],
     "tmg_kcycle": [_P, _P, _P, _D, _I, _I, _I],
+    "tmg_sap_nd": [_P, _P, _P, _I, _I],
+    "tmg_coarse_apply_nd": [_P, _P, _P, _I, _I],
+    "tmg_coarse_solve_nd": [_P, _P, _P, _I, _I],
+    "tmg_kcycle_nd": [_P, _P, _P, _I, _I, _I],
+    "tmg_cycle_nd": [_P, _P, _P, _I],
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
@@ -340,6 +346,37 @@ class Context:
         self._check(lib().tmg_kcycle(self._h, pb, px, float(mu), int(mode), prec, wh))
         return x
 
+    # ---- non-degenerate doublet (flavour pairs: fine [2, ..., 4, 3], coarse [2, ..., 2 Nv])
+    def sap_nd(self, b2, x2, prec=PREC_F64):
+        x = x2.copy() if not _is_torch_cuda(x2) else x2.clone()
+        pb, wh = _ptr(b2)
+        px, _ = _ptr(x)
+        self._check(lib().tmg_sap_nd(self._h, pb, px, prec, wh))
+        return x
+
+    def _coarse_nd(self, fn, x2, *extra):
+        y = _empty_like(x2, x2.shape)
+        px, wh = _ptr(x2)
+        py, _ = _ptr(y)
+        self._check(fn(self._h, px, py, *extra, wh))
+        return y
+
+    def coarse_apply_nd(self, x2, prec=PREC_F64):
+        return self._coarse_nd(lib().tmg_coarse_apply_nd, x2, prec)
+
+    def coarse_solve_nd(self, b2, prec=PREC_F64):
+        return self._coarse_nd(lib().tmg_coarse_solve_nd, b2, prec)
+
+    def kcycle_nd(self, b2, mode=0, prec=PREC_F64):
+        return self._coarse_nd(lib().tmg_kcycle_nd, b2, int(mode), prec)
+
+    def cycle_nd(self, r2):
+        z = _empty_like(r2, r2.shape)
+        pr, wh = _ptr(r2)
+        pz, _ = _ptr(z)
+        self._check(lib().tmg_cycle_nd(self._h, pr, pz, wh))
+        return z
+
     def cycle(self, r):
         z = _empty_like(r, r.shape)
         pr, wh = _ptr(r)
@@ -350,6 +387,8 @@ class Context:
     def solve(self, b, tol=1e-10, method=SOLVE_MG_MIXED, maxiter=10000, mu_per_col=None, out=None,
               check=True):
         n = int(np.prod(b.shape)) // (self.V * 12)
+        if method in (SOLVE_ND_F64, SOLVE_ND_MIXED):
+            n //= 2                                   # flavour pairs
         x = _empty_like(b, b.shape) if out is None else out
         pb, wh = _ptr(b)
         px, _ = _ptr(x)

@@ -80,6 +80,27 @@ int level2_op(tmg_ctx* ctx, const char* name, const double* in, double* out, siz
   });
 }
 
+// coarse doublet vectors in (FP64) -> op in precision prec -> out
+template <typename F>
+int coarse_nd_op(tmg_ctx* ctx, const char* name, const double* in, double* out, int prec, int where, F&& op) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!in || !out || (prec != TMG_PREC_F64 && prec != TMG_PREC_F32) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, std::string(name) + ": bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, std::string(name) + ": no setup");
+    const size_t n = (size_t)2 * c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, in, 2 * n, where);
+    tmg::CField xi, yo;
+    xi.create(prec, n);
+    yo.create(prec, n);
+    convert_field(c, d, TMG_PREC_F64, xi.buf.p, prec, n);
+    op(xi.buf.p, yo.buf.p);
+    double* o = stage_out_ptr(c, c.stage_b, out, 2 * n, where);
+    convert_field(c, yo.buf.p, prec, o, TMG_PREC_F64, n);
+    stage_out_finish(c, c.stage_b, out, 2 * n, where);
+    return TMG_OK;
+  });
+}
 
 }  // namespace
 
@@ -648,6 +669,79 @@ int tmg_kcycle(tmg_ctx* ctx, const double* b, double* x, double mu, int mode, in
                    [&](const void* bb, void* xx) { kcycle(c, prec, bb, xx, mu, mode); });
 }
 
+// ---------------------------------------------------------------- doublet pieces
+int tmg_sap_nd(tmg_ctx* ctx, const double* b, double* x, int prec, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || !valid_prec(prec) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_sap_nd: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_sap_nd: no setup");
+    const int sp = storage_of(prec);
+    const size_t col = (size_t)24 * c.g.V;
+    tmg::Field bf, xf;
+    bf.create(c.g, sp, 2);
+    xf.create(c.g, sp, 2);
+    const double* bd = stage_in(c, c.stage_a, b, 2 * col, where);
+    for (int f = 0; f < 2; f++) spinor_from_lex(c, bd + f * col, bf.col(c.g, f), sp);
+    const double* xd = stage_in(c, c.stage_a, x, 2 * col, where);
+    for (int f = 0; f < 2; f++) spinor_from_lex(c, xd + f * col, xf.col(c.g, f), sp);
+    sap_sweeps_nd(c, prec, xf.buf.p, bf.buf.p, c.mg.sap_sweeps);
+    double* o = stage_out_ptr(c, c.stage_b, x, 2 * col, where);
+    for (int f = 0; f < 2; f++) spinor_to_lex(c, xf.col(c.g, f), sp, o + f * col);
+    stage_out_finish(c, c.stage_b, x, 2 * col, where);
+    return TMG_OK;
+  });
+}
+
+int tmg_coarse_apply_nd(tmg_ctx* ctx, const double* x, double* y, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  return coarse_nd_op(ctx, "tmg_coarse_apply_nd", x, y, prec, where, [&](const void* xi, void* yo) {
+    const size_t n1 = (size_t)c.cl.nc * c.cl.nd, es = prec == TMG_PREC_F64 ? 16 : 8;
+    const char* xu = (const char*)xi;
+    char* yu = (char*)yo;
+    coarse_apply(c, prec, xu, yu, c.mubar);
+    coarse_apply(c, prec, xu + n1 * es, yu + n1 * es, -c.mubar);
+    blas_axpy(c, -c.epsbar, 0.0, xu + n1 * es, yu, prec, n1);
+    blas_axpy(c, -c.epsbar, 0.0, xu, yu + n1 * es, prec, n1);
+  });
+}
+
+int tmg_coarse_solve_nd(tmg_ctx* ctx, const double* b, double* x, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  return coarse_nd_op(ctx, "tmg_coarse_solve_nd", b, x, prec, where,
+                      [&](const void* bi, void* xo) { coarse_gmres_persistent_nd(c, prec, bi, xo); });
+}
+
+int tmg_kcycle_nd(tmg_ctx* ctx, const double* b, double* x, int mode, int prec, int where) {
+  if (!ctx) return TMG_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (mode < 0 || mode > 2) return fail(ctx, TMG_ERR_ARG, "tmg_kcycle_nd: mode must be 0, 1 or 2");
+  if (!c.l2_ready) return fail(ctx, TMG_ERR_STATE, "tmg_kcycle_nd: no level-2 setup");
+  return coarse_nd_op(ctx, "tmg_kcycle_nd", b, x, prec, where,
+                      [&](const void* bi, void* xo) { kcycle(c, prec, bi, xo, c.mubar, mode, 2); });
+}
+
+int tmg_cycle_nd(tmg_ctx* ctx, const double* r, double* z, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!r || !z || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_cycle_nd: bad argument");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_cycle_nd: no setup");
+    const int sp = storage_of(c.mg.prec_fine);
+    const size_t col = (size_t)24 * c.g.V;
+    tmg::Field rf, zf;
+    rf.create(c.g, sp, 2);
+    zf.create(c.g, sp, 2);
+    const double* rd = stage_in(c, c.stage_a, r, 2 * col, where);
+    for (int f = 0; f < 2; f++) spinor_from_lex(c, rd + f * col, rf.col(c.g, f), sp);
+    mg_cycle_nd(c, rf.buf.p, zf.buf.p);
+    double* o = stage_out_ptr(c, c.stage_b, z, 2 * col, where);
+    for (int f = 0; f < 2; f++) spinor_to_lex(c, zf.col(c.g, f), sp, o + f * col);
+    stage_out_finish(c, c.stage_b, z, 2 * col, where);
+    return TMG_OK;
+  });
+}
+
 int tmg_cycle(tmg_ctx* ctx, const double* r, double* z, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
@@ -666,7 +760,7 @@ int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double*
               int maxiter, tmg_stats* stats, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
-    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 3)
+    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 5)
       return fail(ctx, TMG_ERR_ARG, "tmg_solve: bad argument");
     if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no gauge field loaded");
     if (method != TMG_SOLVE_CG_F64 && !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no multigrid setup");
@@ -699,33 +793,37 @@ int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double*
       if (rc != TMG_OK && c.err.empty()) c.err = "solver did not converge";
       return rc;
     }
+    // doublet methods: every column is a flavour pair [2][V][4][3]
+    const int nf = (method == TMG_SOLVE_ND_F64 || method == TMG_SOLVE_ND_MIXED) ? 2 : 1;
+    const int m1 = nf == 2 ? (method == TMG_SOLVE_ND_F64 ? TMG_SOLVE_MG_F64 : TMG_SOLVE_MG_MIXED) : method;
+    const size_t ccol = nf * col;
     for (int j = 0; j < n_rhs; j++) {
       const double mu = mu_per_col ? mu_per_col[j] : c.mu;
       tmg::Field bf, xf;
-      bf.create(c.g, TMG_PREC_F64, 1);
-      const double* bd = b + j * col;
+      bf.create(c.g, TMG_PREC_F64, nf);
+      const double* bd = b + j * ccol;
       if (where == TMG_HOST) {
-        c.stage_a.alloc(col * sizeof(double));
-        TMG_CUDA(cudaMemcpyAsync(c.stage_a.p, b + j * col, col * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        c.stage_a.alloc(ccol * sizeof(double));
+        TMG_CUDA(cudaMemcpyAsync(c.stage_a.p, b + j * ccol, ccol * sizeof(double), cudaMemcpyHostToDevice, c.stream));
         bd = c.stage_a.as<double>();
       }
-      spinor_from_lex(c, bd, bf.buf.p, TMG_PREC_F64);
-      xf.create(c.g, TMG_PREC_F64, 1);
+      for (int f = 0; f < nf; f++) spinor_from_lex(c, bd + f * col, bf.col(c.g, f), TMG_PREC_F64);
+      xf.create(c.g, TMG_PREC_F64, nf);
       SolveStats st{};
-      const int r = solve_one(c, method, bf.buf.p, xf.buf.p, mu, tol, maxiter, st);
+      const int r = solve_one(c, m1, bf.buf.p, xf.buf.p, mu, tol, maxiter, st, nf);
       if (r != TMG_OK && rc == TMG_OK) rc = r;
       acc.iterations += st.iterations;
       acc.refinements += st.refinements;
       acc.coarse_iterations += st.coarse_iterations;
       acc.true_residual = std::max(acc.true_residual, st.true_residual);
-      double* out = where == TMG_DEVICE ? x + j * col : nullptr;
+      double* out = where == TMG_DEVICE ? x + j * ccol : nullptr;
       if (where == TMG_HOST) {
-        c.stage_b.alloc(col * sizeof(double));
+        c.stage_b.alloc(ccol * sizeof(double));
         out = c.stage_b.as<double>();
       }
-      spinor_to_lex(c, xf.buf.p, TMG_PREC_F64, out);
+      for (int f = 0; f < nf; f++) spinor_to_lex(c, xf.col(c.g, f), TMG_PREC_F64, out + f * col);
       if (where == TMG_HOST) {
-        TMG_CUDA(cudaMemcpyAsync(x + j * col, out, col * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        TMG_CUDA(cudaMemcpyAsync(x + j * ccol, out, ccol * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       }
     }
     TMG_CUDA(cudaStreamSynchronize(c.stream));

@@ -29,6 +29,7 @@ template <> struct CplxT<double> { using T2 = double2; };
 template <typename S>
 struct CgArgs {
   int nd, nv, nc, m, passes;
+  int nf;                            // flavours: 1, or 2 for the doublet (vectors [nf][nc][nd])
   const typename CplxT<S>::T2* Dc;   // [nc][9][nd(l)][nd(k)]
   const int* nbr;                    // [nc][9]
   const typename CplxT<S>::T2* b;
@@ -36,7 +37,8 @@ struct CgArgs {
   typename CplxT<S>::T2* V;          // (m + 1) x n basis
   typename CplxT<S>::T2* w;
   typename CplxT<S>::T2* rows;       // [nc][9][nd] partial stencil rows
-  S mu;
+  S mu;                              // twist (doublet: mubar, flavour 1 gets -mubar)
+  S epsbar;                          // doublet flavour mixing -epsbar tau1 (unused for nf = 1)
   double rtol;
   double2* part;                     // [CMAXM + 1][grid] dot partials
   double* npart;                     // [grid] norm partials
@@ -74,7 +76,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   __shared__ double2 hp[CMAXM + 1];
   __shared__ int s_done, s_k;
   __shared__ double s_beta, s_hn;
-  const int n = a.nc * a.nd;
+  const int n1 = a.nc * a.nd, n = a.nf * n1;
   const int G = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
   // contiguous chunk of the vector owned by this CTA (the CTA that writes an element is the only
@@ -117,13 +119,15 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     const T2* src = j == 0 ? a.V : a.w;
     const S scale = j == 0 ? (S)1 : (S)(1.0 / s_hn);
     T2* vj = a.V + (size_t)j * n;
-    // (1) stencil products, one warp per (coarse site, stencil block) spread over the whole grid:
-    //     lanes are rows, so every column of a block is one coalesced 32-row read.
-    for (int task = gwarp; task < a.nc * 9; task += nwarps_total) {
-      const int site = task / 9;
-      const int nb = a.nbr[task];
-      const T2* blk = a.Dc + (size_t)task * a.nd * a.nd;
-      const T2* xv = src + (size_t)nb * a.nd;
+    // (1) stencil products, one warp per (flavour, coarse site, stencil block) spread over the
+    //     whole grid: lanes are rows, so every column of a block is one coalesced 32-row read.  The
+    //     doublet's flavour mixing is added to the self block's row here, while src is read-only.
+    for (int task = gwarp; task < a.nf * a.nc * 9; task += nwarps_total) {
+      const int f = task / (a.nc * 9), t9 = task - f * a.nc * 9;
+      const int site = t9 / 9;
+      const int nb = a.nbr[t9];
+      const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
+      const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
       for (int k = lane; k < a.nd; k += 32) {
         S ar = 0, ai = 0;
 #pragma unroll 8
@@ -133,24 +137,30 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
           ar += m.x * v.x - m.y * v.y;
           ai += m.x * v.y + m.y * v.x;
         }
+        if (a.nf == 2 && t9 == site * 9) {
+          const T2 xo = src[(size_t)(1 - f) * n1 + (size_t)site * a.nd + k];
+          ar -= a.epsbar * xo.x;
+          ai -= a.epsbar * xo.y;
+        }
         T2 o;
         o.x = ar * scale;
         o.y = ai * scale;
         a.rows[(size_t)task * a.nd + k] = o;
-        (void)site;
       }
     }
     grid.sync();                                     // partial rows complete
     // (2) own chunk: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int site = e / a.nd, k = e - site * a.nd;
+      const int f = e / n1, e1f = e - f * n1;
+      const int site = e1f / a.nd, k = e1f - site * a.nd;
       T2 xs = src[e];
       xs.x *= scale;
       xs.y *= scale;
       if (j > 0) vj[e] = xs;
       S ar = 0, ai = 0;
-      for (int d = 0; d < 9; d++) { const T2 r = a.rows[((size_t)site * 9 + d) * a.nd + k]; ar += r.x; ai += r.y; }
-      const S tw = k < a.nv ? a.mu : -a.mu;
+      const T2* rw = a.rows + ((size_t)(f * a.nc + site) * 9) * a.nd + k;
+      for (int d = 0; d < 9; d++) { const T2 r = rw[(size_t)d * a.nd]; ar += r.x; ai += r.y; }
+      const S tw = (k < a.nv) == (f == 0) ? a.mu : -a.mu;
       T2 o;
       o.x = ar - tw * xs.y;
       o.y = ai + tw * xs.x;
@@ -318,9 +328,12 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int gwarp = blockIdx.x * nwarp + (threadIdx.x >> 5), nwarps_total = gridDim.x * nwarp;
-  for (int task = gwarp; task < op.nc * 9; task += nwarps_total) {
-    const T2* blk = op.Dc + (size_t)task * op.nd * op.nd;
-    const T2* xv = src + (size_t)op.nbr[task] * op.nd;
+  const int n1 = op.nc * op.nd;
+  for (int task = gwarp; task < op.nf * op.nc * 9; task += nwarps_total) {
+    const int f = task / (op.nc * 9), t9 = task - f * op.nc * 9;
+    const int site = t9 / 9;
+    const T2* blk = op.Dc + (size_t)t9 * op.nd * op.nd;
+    const T2* xv = src + (size_t)f * n1 + (size_t)op.nbr[t9] * op.nd;
     for (int k = lane; k < op.nd; k += 32) {
       S ar = 0, ai = 0;
 #pragma unroll 8
@@ -330,6 +343,11 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
         ar += m.x * v.x - m.y * v.y;
         ai += m.x * v.y + m.y * v.x;
       }
+      if (op.nf == 2 && t9 == site * 9) {
+        const T2 xo = src[(size_t)(1 - f) * n1 + (size_t)site * op.nd + k];
+        ar -= op.epsbar * xo.x;
+        ai -= op.epsbar * xo.y;
+      }
       T2 o;
       o.x = ar;
       o.y = ai;
@@ -337,13 +355,15 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
     }
   }
   grid.sync();
-  const int n = op.nc * op.nd;
+  const int n = op.nf * n1;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int site = e / op.nd, k = e - site * op.nd;
+    const int f = e / n1, e1f = e - f * n1;
+    const int site = e1f / op.nd, k = e1f - site * op.nd;
     S ar = 0, ai = 0;
-    for (int d = 0; d < 9; d++) { const T2 r = op.rows[((size_t)site * 9 + d) * op.nd + k]; ar += r.x; ai += r.y; }
+    const T2* rw = op.rows + ((size_t)(f * op.nc + site) * 9) * op.nd + k;
+    for (int d = 0; d < 9; d++) { const T2 r = rw[(size_t)d * op.nd]; ar += r.x; ai += r.y; }
     const T2 xs = src[e];
-    const S tw = k < op.nv ? op.mu : -op.mu;
+    const S tw = (k < op.nv) == (f == 0) ? op.mu : -op.mu;
     ar -= tw * xs.y;
     ai += tw * xs.x;
     T2 o;
@@ -415,18 +435,19 @@ template <typename S>
 __device__ void l1_cycle_dev(const KcArgs<S>& a, const typename CplxT<S>::T2* v, typename CplxT<S>::T2* z) {
   using T2 = typename CplxT<S>::T2;
   cg::grid_group grid = cg::this_grid();
-  restrict2_dev<S>(a.q, a.W2, v, const_cast<T2*>(a.l2.b));
+  const size_t n1 = (size_t)a.q.nc1 * a.q.nd1, n2 = (size_t)a.q.nc2 * 2 * a.q.nv2;
+  for (int f = 0; f < a.sm.nf; f++) restrict2_dev<S>(a.q, a.W2, v + f * n1, const_cast<T2*>(a.l2.b) + f * n2);
   grid.sync();
   gmres_dev(a.l2);
   grid.sync();
-  prolong2_dev<S>(a.q, a.W2, a.l2.x, z);
+  for (int f = 0; f < a.sm.nf; f++) prolong2_dev<S>(a.q, a.W2, a.l2.x + f * n2, z + f * n1);
   grid.sync();
   stencil_dev(a.sm, z, const_cast<T2*>(a.sm.b), v);
   grid.sync();
   gmres_dev(a.sm);
   grid.sync();
-  const int n1 = a.q.nc1 * a.q.nd1;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1; e += gridDim.x * blockDim.x) {
+  const int n = (int)(a.sm.nf * n1);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     T2 o = z[e];
     const T2 d = a.sm.x[e];
     o.x += d.x;
@@ -453,7 +474,7 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
   __shared__ double2 cs[KMAXR], sn[KMAXR], gv[KMAXR + 1];
   __shared__ int s_done, s_k;
   __shared__ double s_beta, s_hn;
-  const int n = a.q.nc1 * a.q.nd1;
+  const int n = a.sm.nf * a.q.nc1 * a.q.nd1;
   const int G = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
   const int chunk = (n + G - 1) / G;
@@ -900,10 +921,10 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
 }
 
 template <typename S>
-void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
+void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 1, double epsbar = 0.0) {
   using T2 = typename CplxT<S>::T2;
   const int m = std::min(c.mg.coarse_m, CMAXM);
-  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  const size_t n = (size_t)nf * c.cl.nc * c.cl.nd;
   static int max_per_sm[2] = {-1, -1};
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
@@ -920,6 +941,8 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc) {
   a.nv = c.cl.nv;
   a.nc = c.cl.nc;
   a.m = m;
+  a.nf = nf;
+  a.epsbar = (S)epsbar;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -977,6 +1000,8 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.nv = c.cl.nv;
   a.nc = c.cl.nc;
   a.m = std::min(c.mg.coarse_m, CMAXM);
+  a.nf = 1;
+  a.epsbar = (S)0;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1061,6 +1086,12 @@ void coarse_gmres_persistent(Ctx& c, int cp, const void* b, void* x, double mu) 
   else launch<float>(c, b, x, mu, c.cl.Dc32.p);
 }
 
+void coarse_gmres_persistent_nd(Ctx& c, int cp, const void* b, void* x) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (cp == TMG_PREC_F64) launch<double>(c, b, x, c.mubar, c.cl.Dc64.p, 2, c.epsbar);
+  else launch<float>(c, b, x, c.mubar, c.cl.Dc32.p, 2, c.epsbar);
+}
+
 }  // namespace tmg
 
 namespace tmg {
@@ -1068,10 +1099,10 @@ namespace tmg {
 namespace {
 
 template <typename S>
-void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode) {
+void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, double epsbar) {
   using T2 = typename CplxT<S>::T2;
   const tmg_level2_params& p = c.l2p;
-  const size_t n1 = (size_t)c.cl.nc * c.cl.nd, n2 = (size_t)c.cl2.nc * c.cl2.nd;
+  const size_t n1 = (size_t)nf * c.cl.nc * c.cl.nd, n2 = (size_t)nf * c.cl2.nc * c.cl2.nd;
   static int max_per_sm[2] = {-1, -1};
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_kcycle<S>, 256, 0));
@@ -1113,6 +1144,8 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode) {
   s.nv = c.cl.nv;
   s.nc = c.cl.nc;
   s.m = sm_m;
+  s.nf = nf;
+  s.epsbar = (S)epsbar;
   s.passes = passes;
   s.Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
   s.nbr = c.cl.nbr.as<int>();
@@ -1133,6 +1166,8 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode) {
   l.nv = c.cl2.nv;
   l.nc = c.cl2.nc;
   l.m = cm;
+  l.nf = nf;
+  l.epsbar = (S)epsbar;
   l.passes = passes;
   l.Dc = (const T2*)(sizeof(S) == 8 ? c.cl2.Dc64.p : c.cl2.Dc32.p);
   l.nbr = c.cl2.nbr.as<int>();
@@ -1170,11 +1205,13 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode) {
 
 }  // namespace
 
-void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode) {
+void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode, int nf) {
   ProfScope ps(c, PK_COARSE_SOLVE);
   if (!c.l2_ready && mode != 2) throw Error{TMG_ERR_STATE, "K-cycle: level 2 not built"};
-  if (prec == TMG_PREC_F64) kcycle_launch<double>(c, b, x, mu, mode);
-  else kcycle_launch<float>(c, b, x, mu, mode);
+  const double eb = nf == 2 ? c.epsbar : 0.0;
+  if (nf == 2) mu = c.mubar;
+  if (prec == TMG_PREC_F64) kcycle_launch<double>(c, b, x, mu, mode, nf, eb);
+  else kcycle_launch<float>(c, b, x, mu, mode, nf, eb);
 }
 
 }  // namespace tmg

@@ -164,6 +164,188 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
   x.store(s, xs);
 }
 
+// SAP on the non-degenerate doublet (Eq. 2): the same colouring and block MR, on flavour pairs.
+// The block operator is [[D_B(mubar), -epsbar], [-epsbar, D_B(-mubar)]] (the flavour mixing is
+// site-local); MR step lengths come from inner products over both flavours.
+template <typename R, class S, class G, class C>
+__global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S xu, S xd, S bu, S bd, G U, C A, R mubar,
+                                                         R epsbar, int n_mr) {
+  // shared memory: r [2][12][VB] complex; for FP32 arithmetic also the block's links [4][9][VB]
+  extern __shared__ double smem_d[];
+  cpx<R>* rs = reinterpret_cast<cpx<R>*>(smem_d);
+  constexpr bool kCacheLinks = sizeof(R) == 4;
+  cpx<R>* ls = rs + 24 * g.VB;
+  double* red = smem_d + (sizeof(cpx<R>) * (kCacheLinks ? 60 : 24) * g.VB) / sizeof(double);
+  const int blk = colour_block(g, colour, blockIdx.x);
+  const int t = threadIdx.x;
+  const int s = blk * g.VB + t;
+  const SiteCoord sc = decode_site(g, s);
+  if (kCacheLinks) {
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      Link<R> u;
+      U.load(s, mu, u);
+#pragma unroll
+      for (int k = 0; k < 9; k++) ls[(mu * 9 + k) * g.VB + t] = u.m[k];
+    }
+  }
+  Spinor<R> r[2];
+  {
+    Spinor<R> du, dd, xs_u, xs_d, bs;
+    apply_D_site<R>(g, sc, s, xu, U, A, mubar, du);
+    apply_D_site<R>(g, sc, s, xd, U, A, -mubar, dd);
+    xu.load(s, xs_u);
+    xd.load(s, xs_d);
+    bu.load(s, bs);
+#pragma unroll
+    for (int k = 0; k < 12; k++) r[0].c[k] = bs.c[k] - (du.c[k] - epsbar * xs_d.c[k]);
+    bd.load(s, bs);
+#pragma unroll
+    for (int k = 0; k < 12; k++) r[1].c[k] = bs.c[k] - (dd.c[k] - epsbar * xs_u.c[k]);
+  }
+  Spinor<R> e[2];
+#pragma unroll
+  for (int f = 0; f < 2; f++)
+#pragma unroll
+    for (int k = 0; k < 12; k++) e[f].c[k] = mk<R>(0, 0);
+  for (int it = 0; it < n_mr; it++) {
+#pragma unroll
+    for (int f = 0; f < 2; f++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) rs[(f * 12 + k) * g.VB + t] = r[f].c[k];
+    __syncthreads();
+    Spinor<R> acc[2];
+#pragma unroll
+    for (int f = 0; f < 2; f++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[f].c[k] = mk<R>(0, 0);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      if (sc.l[mu] + 1 < g.B[mu]) {
+        const int tf = t + g.ls[mu];
+        Link<R> u;
+        if (kCacheLinks) {
+#pragma unroll
+          for (int k = 0; k < 9; k++) u.m[k] = ls[(mu * 9 + k) * g.VB + t];
+        } else {
+          U.load(s, mu, u);
+        }
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+          Spinor<R> p;
+#pragma unroll
+          for (int k = 0; k < 12; k++) p.c[k] = rs[(f * 12 + k) * g.VB + tf];
+          cpx<R> h[6], uh[6];
+          spin_project(mu, +1, p, h);
+          su3_mul_half(u, false, h, uh);
+          spin_reconstruct_add(mu, +1, uh, acc[f]);
+        }
+      }
+      if (sc.l[mu] > 0) {
+        const int tb = t - g.ls[mu];
+        Link<R> u;
+        if (kCacheLinks) {
+#pragma unroll
+          for (int k = 0; k < 9; k++) u.m[k] = ls[(mu * 9 + k) * g.VB + tb];
+        } else {
+          U.load(s - g.ls[mu], mu, u);
+        }
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+          Spinor<R> p;
+#pragma unroll
+          for (int k = 0; k < 12; k++) p.c[k] = rs[(f * 12 + k) * g.VB + tb];
+          cpx<R> h[6], uh[6];
+          spin_project(mu, -1, p, h);
+          su3_mul_half(u, true, h, uh);
+          spin_reconstruct_add(mu, -1, uh, acc[f]);
+        }
+      }
+    }
+    Spinor<R> q[2];
+#pragma unroll
+    for (int chi = 0; chi < 2; chi++) {
+      CloverBlock<R> a;
+      A.load(s, chi, a);
+      clover_mul(a, chi == 0 ? mubar : -mubar, &r[0].c[6 * chi], &q[0].c[6 * chi]);
+      clover_mul(a, chi == 0 ? -mubar : mubar, &r[1].c[6 * chi], &q[1].c[6 * chi]);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const cpx<R> q0 = q[0].c[k] - R(0.5) * acc[0].c[k] - epsbar * r[1].c[k];
+      const cpx<R> q1 = q[1].c[k] - R(0.5) * acc[1].c[k] - epsbar * r[0].c[k];
+      q[0].c[k] = q0;
+      q[1].c[k] = q1;
+    }
+    R v[3] = {0, 0, 0};
+#pragma unroll
+    for (int f = 0; f < 2; f++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        v[0] += q[f].c[k].re * q[f].c[k].re + q[f].c[k].im * q[f].c[k].im;
+        const cpx<R> w = cmul_conj(q[f].c[k], r[f].c[k]);
+        v[1] += w.re;
+        v[2] += w.im;
+      }
+    cta_allreduce<3, R>(v, red);
+    const cpx<R> alpha = v[0] > R(0) ? mk(v[1] / v[0], v[2] / v[0]) : mk<R>(0, 0);
+#pragma unroll
+    for (int f = 0; f < 2; f++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        e[f].c[k] = e[f].c[k] + alpha * r[f].c[k];
+        r[f].c[k] = r[f].c[k] - alpha * q[f].c[k];
+      }
+  }
+  Spinor<R> xs;
+  xu.load(s, xs);
+#pragma unroll
+  for (int k = 0; k < 12; k++) xs.c[k] = xs.c[k] + e[0].c[k];
+  xu.store(s, xs);
+  xd.load(s, xs);
+#pragma unroll
+  for (int k = 0; k < 12; k++) xs.c[k] = xs.c[k] + e[1].c[k];
+  xd.store(s, xs);
+}
+
+template <typename R, class S, class G, class C>
+static void launch_sap_nd(Ctx& c, S xu, S xd, S bu, S bd, G U, C A, R mubar, R epsbar, int n_sweeps, int kind) {
+  const size_t smem = sizeof(cpx<R>) * (sizeof(R) == 4 ? 60 : 24) * c.g.VB + 33 * 3 * sizeof(double);
+  if (smem > 48 * 1024)
+    TMG_CUDA(cudaFuncSetAttribute(k_sap_block_nd<R, S, G, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int sw = 0; sw < n_sweeps; sw++)
+    for (int colour = 0; colour < 2; colour++) {
+      ProfScope ps(c, kind);
+      ++c.launches, k_sap_block_nd<R, S, G, C><<<c.g.nblk / 2, c.g.VB, smem, c.stream>>>(c.g, colour, xu, xd, bu, bd, U, A, mubar,
+                                                                                     epsbar, c.mg.sap_mr);
+      TMG_CHECK_LAUNCH();
+    }
+}
+
+void sap_sweeps_nd(Ctx& c, int prec, void* x, const void* b, int n_sweeps) {
+  const size_t col = (size_t)12 * c.g.V;
+  if (prec == TMG_PREC_F64) {
+    double2* xp = (double2*)x;
+    double2* bp = (double2*)b;
+    launch_sap_nd<double>(c, SpinorF64{xp, c.g.V}, SpinorF64{xp + col, c.g.V}, SpinorF64{bp, c.g.V}, SpinorF64{bp + col, c.g.V},
+                          GaugeF64{c.op[0].U.as<double2>(), c.g.V}, CloverF64{c.op[0].A.as<double2>(), c.g.V}, c.mubar, c.epsbar,
+                          n_sweeps, PK_SAP_F64);
+  } else {
+    float4* xp = (float4*)x;
+    float4* bp = (float4*)b;
+    const size_t col4 = col / 2;   // float4 per flavour column
+    if (prec == TMG_PREC_F32)
+      launch_sap_nd<float>(c, SpinorF32{xp, c.g.V}, SpinorF32{xp + col4, c.g.V}, SpinorF32{bp, c.g.V}, SpinorF32{bp + col4, c.g.V},
+                           GaugeF32{c.op[1].U.as<float4>(), c.g.V}, CloverF32{c.op[1].A.as<float4>(), c.g.V}, (float)c.mubar,
+                           (float)c.epsbar, n_sweeps, PK_SAP_F32);
+    else
+      launch_sap_nd<float>(c, SpinorF32{xp, c.g.V}, SpinorF32{xp + col4, c.g.V}, SpinorF32{bp, c.g.V}, SpinorF32{bp + col4, c.g.V},
+                           GaugeF16{c.op[2].U.as<short4>(), c.g.V},
+                           CloverF16{c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>(), c.g.V}, (float)c.mubar,
+                           (float)c.epsbar, n_sweeps, PK_SAP_F16);
+  }
+}
+
 template <typename R, class S, class G, class C>
 static void launch_sap(Ctx& c, S x, S b, G U, C A, R tw, int n_sweeps, int kind) {
   const size_t smem = sizeof(cpx<R>) * (sizeof(R) == 4 ? 48 : 12) * c.g.VB + 33 * 3 * sizeof(double);

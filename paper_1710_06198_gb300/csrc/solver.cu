@@ -258,18 +258,27 @@ static int storage(int prec) { return prec == TMG_PREC_F64 ? TMG_PREC_F64 : TMG_
 
 // z = P D_c^-1 P^dag r, then k SAP sweeps on D z = r starting from z (pf: fine precision of the
 // SAP / P operations, pc: coarse precision).
-static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu) {
+// nf = 2: the doublet cycle (P_ND = P x I2, D_ND,c, SAP on D_ND); fields [2][12 V], mu unused.
+static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu, int nf = 1) {
   const size_t nco = (size_t)c.cl.nc * c.cl.nd;
-  c.cw_cr.alloc(nco * esize(pc));
-  c.cw_ce.alloc(nco * esize(pc));
-  restrict_(c, pf, r, c.cw_cr.p, pc);
-  if (c.l2_ready) kcycle(c, pc, c.cw_cr.p, c.cw_ce.p, mu, 0);   // three levels: the level-1 K-cycle
-  else coarse_gmres_persistent(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
-  prolong(c, pf, c.cw_ce.p, pc, z, 0);
-  sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
+  const size_t nfi = (size_t)12 * c.g.V, ef = esize(storage(pf)), ec = esize(pc);
+  c.cw_cr.alloc(nf * nco * ec);
+  c.cw_ce.alloc(nf * nco * ec);
+  for (int f = 0; f < nf; f++) restrict_(c, pf, (const char*)r + f * nfi * ef, (char*)c.cw_cr.p + f * nco * ec, pc);
+  if (nf == 2) {
+    if (c.l2_ready) kcycle(c, pc, c.cw_cr.p, c.cw_ce.p, c.mubar, 0, 2);
+    else coarse_gmres_persistent_nd(c, pc, c.cw_cr.p, c.cw_ce.p);
+  } else {
+    if (c.l2_ready) kcycle(c, pc, c.cw_cr.p, c.cw_ce.p, mu, 0);   // three levels: the level-1 K-cycle
+    else coarse_gmres_persistent(c, pc, c.cw_cr.p, c.cw_ce.p, mu);
+  }
+  for (int f = 0; f < nf; f++) prolong(c, pf, (const char*)c.cw_ce.p + f * nco * ec, pc, (char*)z + f * nfi * ef, 0);
+  if (nf == 2) sap_sweeps_nd(c, pf, z, r, c.mg.sap_sweeps);
+  else sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
 }
 
 void mg_cycle(Ctx& c, const void* r, void* z, double mu) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, mu); }
+void mg_cycle_nd(Ctx& c, const void* r, void* z) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, 0.0, 2); }
 
 // ---------------------------------------------------------------- setup
 static void set_vectors(Ctx& c, int sp) {
@@ -387,8 +396,8 @@ void mg_setup2(Ctx& c, const double* v1_dev) {
 // One FGMRES cycle of at most m steps on D(mu) e = r from zero (vectors in storage sp, operator
 // precision op, preconditioner = cycle in (pf, pc)).  Host-side Givens; dots accumulate in FP64.
 static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, void* e, double mu, int m,
-                         double rtol, int& steps) {
-  const size_t n = (size_t)12 * c.g.V;
+                         double rtol, int& steps, int nf = 1) {
+  const size_t n = (size_t)nf * 12 * c.g.V;
   const size_t es = esize(sp);
   c.fw_V.alloc((m + 1) * n * es);
   c.fw_Z.alloc(m * n * es);
@@ -414,8 +423,9 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
   for (int j = 0; j < m; j++) {
     void* vj = V + j * n * es;
     void* zj = Z + j * n * es;
-    cycle_p(c, pf, pc, vj, zj, mu);
-    dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
+    cycle_p(c, pf, pc, vj, zj, mu, nf);
+    if (nf == 2) dslash_nd(c, op, c.fw_w.p, zj);
+    else dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
     std::vector<double2> hc(j + 1), hc2(j + 1);
     std::vector<double2> nn_parts(NPART);
     dispatch(sp, [&](auto tag) {
@@ -512,9 +522,18 @@ static int cg_solve(Ctx& c, const void* b, void* x, double mu, double tol, int m
 }
 
 // ---------------------------------------------------------------- solve
-int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st) {
+int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st, int nf) {
   if (method == TMG_SOLVE_CG_F64) return cg_solve(c, b, x, mu, tol, maxiter, st);
-  const size_t n = (size_t)12 * c.g.V;
+  const size_t n = (size_t)nf * 12 * c.g.V;
+  // r = b - D x in FP64 (D_ND for the doublet)
+  auto residual = [&](void* r) {
+    if (nf == 2) {
+      dslash_nd(c, TMG_PREC_F64, r, x);
+      blas_xpay(c, b, -1.0, 0.0, r, TMG_PREC_F64, n);
+    } else {
+      dslash(c, TMG_PREC_F64, r, x, b, mu, 1, 0);
+    }
+  };
   const bool f64 = method == TMG_SOLVE_MG_F64;
   const int pf = f64 ? TMG_PREC_F64 : c.mg.prec_fine;
   const int pc = f64 ? TMG_PREC_F64 : c.mg.prec_coarse;
@@ -550,10 +569,10 @@ int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol,
     double target = tol * bn / rn;
     if (!f64) target = std::max(target, 1e-6);
     int k = 0;
-    fgmres_cycle(c, sp, op, pf, pc, c.fw_x.p, c.fw_e.p, mu, std::min(c.mg.restart, MAXM), target, k);
+    fgmres_cycle(c, sp, op, pf, pc, c.fw_x.p, c.fw_e.p, mu, std::min(c.mg.restart, MAXM), target, k, nf);
     st.iterations += k;
     blas_axpy_mixed(c, rn, c.fw_e.p, sp, x, TMG_PREC_F64, n);
-    dslash(c, TMG_PREC_F64, c.fw_r64.p, x, b, mu, 1, 0);
+    residual(c.fw_r64.p);
     st.refinements++;
     if (k == 0) {
       rc = TMG_ERR_BREAKDOWN;

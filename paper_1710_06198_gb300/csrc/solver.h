@@ -20,7 +20,11 @@ void mg_setup2(Ctx& c, const double* v1_dev);
 // z = M_MG r in the fine storage precision of the multigrid parameters (r is not modified).
 void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // Solve D(mu) x = b on FP64 internal fields (b, x: F64 storage).  Returns a tmg_status.
-int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st);
+// nf = 2: the doublet D_ND (Eq. 2) on F64 fields [2][12 V] (mu unused; mubar, epsbar of the context).
+int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st,
+              int nf = 1);
+// z = doublet cycle of r (fields [2][12 V] in the fine storage precision)
+void mg_cycle_nd(Ctx& c, const void* r, void* z);
 // ncol systems D(mu_c) x_c = b_c (F64 fields, column c at c * 12 V) solved in lock-step.
 int solve_batched(Ctx& c, int ncol, const void* b, void* x, const double* mu, double tol, int maxiter, SolveStats& st);
 

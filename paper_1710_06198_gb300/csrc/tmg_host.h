@@ -231,6 +231,10 @@ void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const in
 void orthonormalise(Ctx& c, void* W64);
 // x ~= D_c(mu)^-1 b: one persistent cooperative GMRES kernel (k_coarse_gmres.cu)
 void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double mu);
+// the same on doublet coarse vectors [2][nc][nd] with D_ND,c = D_c x I2 + i mubar G5_c x tau3 - epsbar tau1
+void coarse_gmres_persistent_nd(Ctx& c, int cprec, const void* b, void* x);
+// SAP sweeps on the doublet (Eq. 2) for fields [2][12 V] in precision prec (mubar, epsbar of the context)
+void sap_sweeps_nd(Ctx& c, int prec, void* x, const void* b, int n_sweeps);
 // ncol columns in lock-step (FP32 coarse vectors [col][nc * nd], twists mu_dev[ncol] on the device)
 void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev);
 // multi-column fine-level kernels (k_batch.cu), FP32 spinors [col][12 V], twists per column
@@ -260,7 +264,9 @@ void coarse_apply_c(Ctx& c, int prec, const void* x, void* y, double mu);
 // mode 0: x ~= D_c(mu)^-1 b by FGMRES preconditioned by the level-1 cycle (the coarse solve of the
 //         three-level cycle); mode 1: x = level-1 cycle applied to b; mode 2: x = smoother applied
 //         to b from zero (GMRES steps on D_c).
-void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode);
+//         nf = 2: the same on doublet vectors [2][nc1][nd1] with D_ND,c and D_ND,cc (mu = mubar, the
+//         context's epsbar).
+void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode, int nf = 1);
 
 }  // namespace tmg
 
