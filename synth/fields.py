@@ -16,6 +16,8 @@ eigendecomposition, then re-unitarise by Gram-Schmidt of rows 0 and 1 with row 2
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 
@@ -58,13 +60,31 @@ def exp_i_hermitian(h, eps):
     return np.einsum("...ab,...b,...cb->...ac", v, ph, np.conj(v))
 
 
+def _links(z, eps):
+    return reunitarise(exp_i_hermitian(_hermitian_from_normals(z), eps))
+
+
 def gauge_field(dims, eps, seed):
-    """Random SU(3) links U = exp(i eps H), H traceless Hermitian with N(0,1) entries."""
+    """Random SU(3) links U = exp(i eps H), H traceless Hermitian with N(0,1) entries.
+
+    Large lattices are built in chunks of time slices on a thread pool; every link is computed by
+    the same per-link arithmetic from the same random numbers, so the result does not depend on the
+    chunking."""
     shp = lattice_shape(dims)
     rng = np.random.default_rng(seed)
     z = rng.standard_normal(shp + (4, 9))
-    h = _hermitian_from_normals(z)
-    return reunitarise(exp_i_hermitian(h, eps))
+    if int(np.prod(shp)) < (1 << 20) or shp[0] < 2:
+        return _links(z, eps)
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty(shp + (4, 3, 3), dtype=np.complex128)
+    bounds = np.linspace(0, shp[0], min(shp[0], 96) + 1).astype(int)
+
+    def work(i):
+        out[bounds[i]:bounds[i + 1]] = _links(z[bounds[i]:bounds[i + 1]], eps)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(work, range(len(bounds) - 1)))
+    return out
 
 
 def unit_gauge(dims):
@@ -99,6 +119,17 @@ def gaussian_spinor(dims, seed, n=None, flavours=None):
     rng = np.random.default_rng(seed)
     z = rng.standard_normal(lead + shp + (2,))
     return z[..., 0] + 1j * z[..., 1]
+
+
+def gaussian_spinor_columns(dims, seed, n, flavours=None):
+    """The n columns of gaussian_spinor(dims, seed, n=n, flavours=...) one at a time (the same
+    random stream, drawn column by column), for lattices where all n do not fit in host memory."""
+    shp = lattice_shape(dims) + (4, 3)
+    lead = () if flavours is None else (int(flavours),)
+    rng = np.random.default_rng(seed)
+    for _ in range(int(n)):
+        z = rng.standard_normal(lead + shp + (2,))
+        yield z[..., 0] + 1j * z[..., 1]
 
 
 def gaussian_coarse(coarse_dims, ndof, seed, n=None):

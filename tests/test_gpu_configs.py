@@ -168,3 +168,55 @@ def test_force_16x16x16x16_finite_differences():
         fd = (action(rot(h)) - action(rot(-h))) / (2 * h)
         an = float(np.real(np.einsum("...ab,...ba->...", H, F).sum()))
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_doublet_three_level_48x48x48x96():
+    """The largest workload: D_ND (Eq. 2) on 48^3 x 96, three-level doublet multigrid, 8 right-hand
+    sides solved one after another to 1e-10, with the device memory in use recorded."""
+    torch = pytest.importorskip("torch")
+    name = "nd_clover_48x48x48x96_3lvl"
+    w, p = _params(name)
+    dims = w["dims"]
+    U = fields.gauge_field(dims, w["eps"], w["seed"])
+    ctx = tmg.Context(dims, w["block"])
+    ctx.set_params(p.kappa, p.csw, p.mubar, p.mubar, p.epsbar)   # setup on D(mubar)
+    ctx.load_gauge(U, -1)
+    # D_ND at sampled sites against the oracle
+    x2 = fields.gaussian_spinor(dims, 190, flavours=2)
+    sites = sampled.random_sites(dims, 16, 191)
+    want = sampled.apply_DND_at(U, x2, p, dims, sites)
+    for prec, tol in ((F64, 1e-13), (F32, 1e-6), (F16, 5e-3)):
+        y = ctx.apply(x2, op=tmg.OP_DND, prec=prec)
+        got = np.array([y[:, t, z, yy, x] for x, yy, z, t in sites])
+        assert rel(got, want) < tol, prec
+    del x2, y
+    # setup from 24 Gaussian vectors streamed to the device one at a time
+    shape = fields.lattice_shape(dims) + (4, 3)
+    v0 = torch.empty((w["nv"],) + shape, dtype=torch.complex128, device="cuda")
+    for j, v in enumerate(fields.gaussian_spinor_columns(dims, w["seed"] + 100, w["nv"])):
+        v0[j].copy_(torch.from_numpy(v))
+    prm = tmg.Context.mg_defaults()
+    prm.nv, prm.restart = w["nv"], w["restart"]
+    prm.prec_fine, prm.prec_coarse = F32, F32
+    ctx.setup(v0, prm)
+    del v0
+    torch.cuda.empty_cache()
+    q = tmg.Context.level2_defaults()
+    q.agg[:] = w["agg2"]
+    q.nv = w["nv2"]
+    c1 = ctx.coarse_lat
+    ctx.setup_level2(fields.gaussian_coarse((c1[3], c1[2], c1[1], c1[0]), 2 * w["nv"], w["seed"] + 200, n=w["nv2"]), q)
+    free, total = torch.cuda.mem_get_info()
+    used_setup = total - free
+    for seed in w["rhs_seeds"]:
+        b = torch.from_numpy(fields.gaussian_spinor(dims, seed, flavours=2)).cuda()
+        x, st = ctx.solve(b, tol=1e-10, method=tmg.SOLVE_ND_MIXED)
+        r = ctx.apply(x, op=tmg.OP_DND, prec=F64) - b
+        assert float(torch.linalg.vector_norm(r)) <= 1.01e-10 * float(torch.linalg.vector_norm(b)), seed
+        print(f"ND 48^3x96 rhs seed {seed}: iterations {st['iterations']} refinements {st['refinements']} "
+              f"coarse {st['coarse_iterations']} seconds {st['seconds']:.3f}")
+        del b, x, r
+    free, total = torch.cuda.mem_get_info()
+    print(f"ND 48^3x96 device memory in use: after setup {used_setup / 2**30:.1f} GiB, "
+          f"after solves {(total - free) / 2**30:.1f} GiB of {total / 2**30:.1f} GiB")
+    assert total - free < total
