@@ -156,3 +156,50 @@ def search_m0(U, csw, tbc, target, step=0.05, rel_tol=0.02, m0_min=-2.0, log=Non
             fd = s(d_)
     m_best, s_best = min(log, key=lambda t: t[1])
     return m_best, s_best, False
+
+
+def mg_steps(U, m0, csw, mu, block, nv, b, v0, tol=1e-10, max_steps=50):
+    """Outer FGMRES steps of the oracle's two-level DD-alpha-AMG (paper defaults: SAP k = 3, MR 4,
+    coarse GMRES 30 / 5e-2, setup 5 + 3, restart 10) on D(mu) at this m0; max_steps + 1 if it does
+    not reach tol within max_steps."""
+    from . import mg
+    p = dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=csw, mu=mu, tbc=-1)
+    H = mg.Hierarchy(U, p, mg.MGParams(block=block, agg=block, nv=nv, restart=10))
+    H.setup(v0)
+    x, steps, res = H.solve(b, tol=tol, maxiter=max_steps)
+    return steps if res <= tol else max_steps + 1
+
+
+def search_m0_mg(U, csw, mu, block, nv, b, v0, max_steps=50, step=0.1, n_bisect=2, log=None, progress=None):
+    """The most critical m0 at which the two-level method still converges: walk m0 = 0, -step, ...
+    and stop at the first m0 whose solve needs more than max_steps outer steps; then bisect n_bisect
+    times between the last converging m0 and that one.  Returns the last converging m0."""
+    log = [] if log is None else log
+
+    def ok(m0):
+        n = mg_steps(U, m0, csw, mu, block, nv, b, v0, max_steps=max_steps)
+        log.append((m0, n))
+        if progress is not None:
+            progress(m0, n)
+        return n <= max_steps
+
+    if not ok(0.0):
+        raise ValueError("the method does not converge at m0 = 0")
+    good, bad = 0.0, None
+    k = 1
+    while bad is None:
+        m0 = -k * step
+        if m0 < -4.0:
+            raise ValueError("no divergence edge above m0 = -4")
+        if ok(m0):
+            good = m0
+        else:
+            bad = m0
+        k += 1
+    for _ in range(n_bisect):
+        mid = 0.5 * (good + bad)
+        if ok(mid):
+            good = mid
+        else:
+            bad = mid
+    return good
