@@ -157,6 +157,9 @@ def run_kernel_case(args):
     ctx = tmg.Context(dims, (4, 4, 4, 4))
     ctx.set_params(1.0 / (2.0 * (4.0 - 0.4)), 1.6, 0.002)
     ctx.load_gauge(U, -1)
+    for kv in args.tune:
+        k, v = kv.split("=")
+        ctx.tune(k, float(v))
     if args.kernel_case == "dslash":
         ms = ctx.bench_dslash(tmg.PREC_F32, 3)
         print(json.dumps({"kernel_case": "dslash", "ms": ms}))
@@ -166,9 +169,21 @@ def run_kernel_case(args):
         ctx.setup(fields.gaussian_spinor(dims, 5, n=16), prm)
         clat = ctx.coarse_lat
         xc = torch.from_numpy(fields.gaussian_coarse((clat[3], clat[2], clat[1], clat[0]), 32, 7, n=20)).cuda()
-        yc = ctx.coarse_apply_multi(xc, np.linspace(0.001, 0.01, 20))
+        mus = np.linspace(0.001, 0.01, 20)
+        yc = ctx.coarse_apply_multi(xc, mus)
+        tmg.profile(ctx, True)
+        for _ in range(5):
+            yc = ctx.coarse_apply_multi(xc, mus)
+        prof = tmg.profile_read(ctx)
+        tmg.profile(ctx, False)
         torch.cuda.synchronize()
-        print(json.dumps({"kernel_case": "coarse_tc", "norm": float(torch.linalg.vector_norm(yc))}))
+        n_l, ms = prof["coarse_apply"]
+        nc, nd = int(np.prod(clat)), 32
+        algo = nc * 9 * nd * nd * 8 + 2 * 20 * nc * nd * 8
+        us = 1e3 * ms / max(1, n_l)
+        print(json.dumps({"kernel_case": "coarse_tc", "norm": float(torch.linalg.vector_norm(yc)), "us_per_launch": round(us, 2),
+                          "algo_bytes": algo, "gbs": round(algo / (us * 1e-6) / 1e9, 1),
+                          "tflops": round(nc * 9 * (2 * nd) ** 2 * 2 * 20 / (us * 1e-6) / 1e12, 2)}))
     elif args.kernel_case == "sap":
         prm = tmg.Context.mg_defaults()
         prm.nv, prm.n_init, prm.n_iter, prm.sap_sweeps = 2, 0, 0, 1
@@ -212,6 +227,7 @@ def run_ours(args):
     ctx.setup(v0, prm)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    autotune_ms = None if args.no_autotune else ctx.autotune()
 
     dev = torch.device("cuda", local)
     b = torch.from_numpy(b_host).to(dev)
@@ -259,6 +275,21 @@ def run_ours(args):
         tt = torch.tensor([t_step], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_step = float(tt.item())
+    # the same solves with the cycle launched kernel by kernel instead of replayed as a CUDA graph
+    ctx.tune("cycle_graph", 0)
+    t_eager = []
+    for _ in range(max(1, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        t_eager.append(e0.elapsed_time(e1) / 1e3)
+    ctx.tune("cycle_graph", 1)
+    step()
+    graphs = {"cycle_graphs": tmg.graph_count(ctx), "s_with_graphs": round(t_step, 6),
+              "s_kernel_by_kernel": round(sum(t_eager) / len(t_eager), 6)}
     # verify the last solve in FP64 on the device (true residual through the FP64 operator)
     r = (ctx.apply(x, tmg.OP_D, tmg.PREC_F64) - b)
     true_res = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b))
@@ -388,6 +419,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": iters[-1], "refinements": stats["refinements"], "coarse_iterations": stats["coarse_iterations"],
         "true_residual": true_res, "setup_s": round(setup_s, 3),
+        "autotune_coarse_ms": None if autotune_ms is None else round(autotune_ms, 4), "graphs": graphs,
         "fp64_solve_s": round(fp64_s, 4), "fp64_iterations": st64["iterations"],
         "batched": batched,
         "speedup_vs_fp64": {"mixed_single": round(fp64_s / t_step, 2),
@@ -478,6 +510,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fine", default="f32", choices=["f32", "f16"])
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-large-dslash", action="store_true")
     ap.add_argument("--batch", type=int, default=12, help="right-hand sides of the batched solve (0: skip)")
     ap.add_argument("--cg-maxiter", type=int, default=20000)

@@ -127,7 +127,8 @@ int tmg_coarse_apply(tmg_ctx *ctx, const double *x, double *y, double mu, int pr
 int tmg_cycle(tmg_ctx *ctx, const double *r, double *z, int where);
 /* Multi-RHS coarse operator Y = D_c(mu_n) X (Eq. 1's D_c, twist per column, Sec. 1.1) for
  * n_rhs (1..32) coarse vectors ([n_rhs][V_c][2 N_v]) on the tensor cores (tcgen05, split TF32,
- * FP32-level accuracy), N_v <= 32.  TMG_ERR_TIMEOUT if a bounded device-side wait gave up. */
+ * FP32-level accuracy), N_v one of 4, 8, 12, 16, 24, 32 (compiled tile shapes; TMG_ERR_ARG
+ * otherwise).  TMG_ERR_TIMEOUT if a bounded device-side wait gave up. */
 int tmg_coarse_apply_multi(tmg_ctx *ctx, const double *x, double *y, int n_rhs, const double *mu_per_col, int where);
 /* x ~= D_c(mu)^-1 b (Eq. 1's coarse solve): GMRES from zero with at most coarse_m steps, stopping
  * at relative residual coarse_rtol; coarse vectors [V_c][2 N_v], computed in precision prec. */
@@ -270,8 +271,23 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
 /* Launch-shape knobs (not paper quantities): "coarse_ctas_per_sm" (1..8, CTAs per SM of the
  * persistent coarse GMRES, capped by occupancy) and "coarse_gs_passes" (1 or 2 classical
  * Gram-Schmidt passes in the coarse GMRES; 0 = 1 in FP32, 2 in FP64), "kcycle_ctas_per_sm" (1..4,
- * CTAs per SM of the persistent level-1 K-cycle).  TMG_ERR_ARG for an unknown key or value. */
+ * CTAs per SM of the persistent level-1 K-cycle), "cycle_graph" (1, the default: the preconditioner
+ * cycle inside the outer FGMRES is captured once per set of buffers and parameters as a CUDA graph
+ * and replayed with one launch; 0: launched kernel by kernel), "tc_steps_per_range" (1, 2 or 4 K = 8
+ * steps accumulated in one tensor-memory range by tmg_coarse_apply_multi; 1 keeps FP32-level
+ * accuracy for any N_v).  TMG_ERR_ARG for an unknown key or value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
+
+/* Autotuner (not a paper quantity): after tmg_setup (and tmg_setup_level2), time the coarse solve of
+ * the cycle for every allowed launch shape ("coarse_ctas_per_sm" x "coarse_gs_passes", or with
+ * three levels "kcycle_ctas_per_sm") on a fixed right-hand side with the stopping test disabled,
+ * keep the fastest shape in the context and write its time per coarse solve (ms) to *best_ms
+ * (may be NULL).  CUDA events on the context stream; synchronises. */
+int tmg_autotune(tmg_ctx *ctx, double *best_ms);
+
+/* Number of preconditioner-cycle CUDA graphs the context holds (0 when "cycle_graph" is off or
+ * capture is not available). */
+int tmg_graph_count(const tmg_ctx *ctx, int *n);
 
 /* Number of CUDA kernels this context has launched so far (every launcher counts its launches;
  * lets a caller count the kernels inside a timed region).  Not a paper quantity. */

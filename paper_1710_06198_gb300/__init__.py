@@ -98,6 +98,8 @@ _SIGS = {
     "tmg_coarse_solve_nd": [_P, _P, _P, _I, _I],
     "tmg_kcycle_nd": [_P, _P, _P, _I, _I, _I],
     "tmg_cycle_nd": [_P, _P, _P, _I],
+    "tmg_autotune": [_P, ctypes.POINTER(_D)],
+    "tmg_graph_count": [_P, ctypes.POINTER(_I)],
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
@@ -421,6 +423,12 @@ class Context:
         self._check(lib().tmg_force(self._h, pp, pf, float(tol), ctypes.byref(S), ctypes.byref(st), wh))
         return S.value, F, st.as_dict()
 
+    def autotune(self):
+        """Pick the fastest launch shape of the coarse solve; returns its time per solve in ms."""
+        ms = ctypes.c_double()
+        self._check(lib().tmg_autotune(self._h, ctypes.byref(ms)))
+        return ms.value
+
     def tune(self, key, value):
         self._check(lib().tmg_tune(self._h, key.encode(), float(value)))
 
@@ -447,6 +455,12 @@ def profile_read(ctx: "Context"):
 def launch_count(ctx: "Context"):
     n = ctypes.c_longlong()
     ctx._check(lib().tmg_launch_count(ctx._h, ctypes.byref(n)))
+    return n.value
+
+
+def graph_count(ctx: "Context"):
+    n = ctypes.c_int()
+    ctx._check(lib().tmg_graph_count(ctx._h, ctypes.byref(n)))
     return n.value
 
 

@@ -388,9 +388,29 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     if (k == "coarse_ctas_per_sm" && v >= 1 && v <= 8) ctx->c.coarse_ctas_per_sm = v;
     else if (k == "coarse_gs_passes" && (v >= 0 && v <= 2)) ctx->c.coarse_gs_passes = v;
     else if (k == "kcycle_ctas_per_sm" && v >= 1 && v <= 4) ctx->c.kcycle_ctas_per_sm = v;
+    else if (k == "tc_steps_per_range" && (v == 1 || v == 2 || v == 4)) ctx->c.tc_steps_per_range = v;
+    else if (k == "cycle_graph" && (v == 0 || v == 1)) {
+      ctx->c.cycle_graphs = v;
+      if (!v) ctx->c.graphs.clear();
+    }
     else return fail(ctx, TMG_ERR_ARG, "tmg_tune: unknown key or value out of range: " + k);
     return TMG_OK;
   });
+}
+
+int tmg_autotune(tmg_ctx* ctx, double* best_ms) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_autotune: no setup");
+    const double t = autotune(ctx->c);
+    if (best_ms) *best_ms = t;
+    return TMG_OK;
+  });
+}
+
+int tmg_graph_count(const tmg_ctx* ctx, int* n) {
+  if (!ctx || !n) return TMG_ERR_ARG;
+  *n = (int)ctx->c.graphs.g.size();
+  return TMG_OK;
 }
 
 int tmg_launch_count(const tmg_ctx* ctx, long long* n) {

@@ -9,14 +9,17 @@
 //   B = real embedding of the neighbour's column vectors [Re x; Im x] (N columns, padded to 16/32),
 // and one elected thread issues tcgen05.mma kind::tf32.  FP32 accuracy comes from split TF32:
 // v = hi + lo with hi = tf32(v), lo = tf32(v - hi), and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (the dropped A_lo B_lo term is below FP32 rounding).  Each K = 8 step accumulates its three
-// products in its own TMEM column range, and the partial results are summed in FP32 registers
-// after tcgen05.ld: the tensor core never adds more than 24 products into one accumulator, which
-// keeps its accumulation rounding below the FP32 tolerance for any N_v.  The twist i mu_n G5_c
-// is added in the epilogue.
+// (the dropped A_lo B_lo term is below FP32 rounding).  Each group of R consecutive K = 8 steps
+// (R = 1 by default, "tc_steps_per_range" of tmg_tune) accumulates its products in its own TMEM
+// column range, and the partial results are summed in FP32 registers after tcgen05.ld: with R = 1
+// the tensor core never adds more than 24 products into one accumulator, which keeps its
+// accumulation rounding below the FP32 tolerance for any N_v.  The twist i mu_n G5_c is added in
+// the epilogue.
 //
 // Every wait on the MMA-completion mbarrier is bounded; a wait that gives up sets *err and the
 // CTA still frees its tensor memory before returning.
+#include <algorithm>
+
 #include "tmg_host.h"
 
 namespace tmg {
@@ -97,13 +100,91 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 16; i++) { v[i] = a[i]; v[16 + i] = b[i]; }
 }
 
-template <int NPAD>
-__global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv, int ncol, const float2* __restrict__ Dc,
+// Per-thread share of one raw tile: the stencil block (ND x ND complex) and the neighbour's column
+// vectors (ncol <= NPAD columns of ND complex) with 128 threads.  ND (= 2 N_v) and the padded K are
+// compile-time constants so that the per-element index arithmetic reduces to shifts and constant
+// multiplies.
+template <int ND, int NPAD>
+struct RawTile {
+  static constexpr int kA = (ND * ND + 127) / 128;
+  static constexpr int kB = (NPAD * ND + 127) / 128;
+  float2 a[kA];
+  float2 b[kB];
+};
+
+template <int ND, int NPAD>
+__device__ __forceinline__ void load_tile(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ X,
+                                          size_t n, int nbr_site, int ncol, int tid) {
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
+    const int i = q * 128 + tid;
+    if (i < ND * ND) t.a[q] = blk[i];
+  }
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
+    const int i = q * 128 + tid;
+    const int col = i / ND, l = i - col * ND;
+    if (col < ncol) t.b[q] = X[(size_t)col * n + (size_t)nbr_site * ND + l];
+  }
+}
+
+template <int ND, int NPAD>
+__device__ __forceinline__ void store_tile(const RawTile<ND, NPAD>& t, float* Ahi, float* Alo, float* Bhi, float* Blo, int ncol,
+                                           int tid) {
+  constexpr int KP = ((2 * ND + 7) / 8) * 8;
+  // A real embedding: row r < ND -> (Re, -Im); row ND + r -> (Im, Re)
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
+    const int i = q * 128 + tid;
+    if (i < ND * ND) {
+      const int l = i / ND, k = i - l * ND;
+      const float2 z = t.a[q];
+      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+      const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
+      const int o00 = core_off(k, l, KP), o01 = core_off(k, ND + l, KP);
+      const int o10 = core_off(ND + k, l, KP), o11 = core_off(ND + k, ND + l, KP);
+      Ahi[o00] = re_h;
+      Ahi[o01] = -im_h;
+      Ahi[o10] = im_h;
+      Ahi[o11] = re_h;
+      Alo[o00] = re_l;
+      Alo[o01] = -im_l;
+      Alo[o10] = im_l;
+      Alo[o11] = re_l;
+    }
+  }
+  // B: column vectors of the neighbour (NPAD rows of K-major data)
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
+    const int i = q * 128 + tid;
+    const int col = i / ND, l = i - col * ND;
+    if (col < ncol) {
+      const float2 z = t.b[q];
+      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+      const int o0 = core_off(col, l, KP), o1 = core_off(col, ND + l, KP);
+      Bhi[o0] = re_h;
+      Bhi[o1] = im_h;
+      Blo[o0] = tf32_round(z.x - re_h);
+      Blo[o1] = tf32_round(z.y - im_h);
+    }
+  }
+}
+
+// Persistent CTAs: CTA b handles coarse sites b, b + G, b + 2 G, ...; the 9 stencil tiles of its
+// sites form one sequence, and the global loads of tile t + 1 are issued into registers while the
+// MMAs of tile t run.  Tensor memory, the mbarrier and the zero padding of the operand tiles are set
+// up once per CTA.
+template <int ND, int NPAD, int R>
+__global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int ncol, const float2* __restrict__ Dc,
                                                          const int* __restrict__ nbr, const float2* __restrict__ X,
                                                          float2* __restrict__ Y, const float* __restrict__ mu,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int KP = ((2 * nd + 7) / 8) * 8;                 // K padded to the MMA step
+  constexpr int KP = ((2 * ND + 7) / 8) * 8;             // K padded to the MMA step
+  constexpr int nsteps = KP / 8;                          // K = 8 MMA steps per stencil block
+  constexpr int nranges = (nsteps + R - 1) / R;           // R consecutive K steps share one TMEM range
+  constexpr uint32_t kCols = nranges * NPAD <= 32 ? 32 : nranges * NPAD <= 64 ? 64 : nranges * NPAD <= 128 ? 128
+                             : nranges * NPAD <= 256 ? 256 : 512;
   float* Ahi = reinterpret_cast<float*>(sm);
   float* Alo = Ahi + TC_M * KP;
   float* Bhi = Alo + TC_M * KP;
@@ -112,11 +193,9 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv,
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   volatile int* s_ok = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int site = blockIdx.x;
-  const size_t n = (size_t)nc * nd;
-  const int nsteps = KP / 8;                                // K = 8 MMA steps per stencil block
-  uint32_t kCols = 32;
-  while (kCols < (uint32_t)(nsteps * NPAD)) kCols <<= 1;    // TMEM columns: one range per step
+  const size_t n = (size_t)nc * ND;
+  const int my_sites = blockIdx.x < nc ? (nc - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int ntiles = 9 * my_sites;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(kCols));
@@ -126,61 +205,43 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv,
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // rows >= 2 nd of A stay zero for the whole kernel; zero everything once
+  // rows >= 2 ND of A, K columns >= 2 ND and B columns >= ncol stay zero for the whole kernel
   for (int i = tid; i < 2 * TC_M * KP; i += blockDim.x) Ahi[i] = 0.f;
   for (int i = tid; i < 2 * NPAD * KP; i += blockDim.x) Bhi[i] = 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = idesc_tf32(TC_M, NPAD);
-  const uint32_t lbo = 128, sboA = (uint32_t)(KP / 4) * 128, sboB = sboA;
+  constexpr uint32_t idesc = idesc_tf32(TC_M, NPAD);
+  constexpr uint32_t lbo = 128, sbo = (uint32_t)(KP / 4) * 128;
   bool ok = true;
   float acc[NPAD];
 #pragma unroll
   for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
 
-  for (int d = 0; d < 9 && ok; d++) {
-    const float2* blk = Dc + (size_t)(site * 9 + d) * nd * nd;   // [l][k]: element (row k, col l)
-    // A real embedding: row r < nd -> (Re, -Im); row nd + r -> (Im, Re)
-    for (int i = tid; i < nd * nd; i += blockDim.x) {
-      const int l = i / nd, k = i - l * nd;
-      const float2 z = blk[i];
-      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
-      const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
-      Ahi[core_off(k, l, KP)] = re_h;
-      Ahi[core_off(k, nd + l, KP)] = -im_h;
-      Ahi[core_off(nd + k, l, KP)] = im_h;
-      Ahi[core_off(nd + k, nd + l, KP)] = re_h;
-      Alo[core_off(k, l, KP)] = re_l;
-      Alo[core_off(k, nd + l, KP)] = -im_l;
-      Alo[core_off(nd + k, l, KP)] = im_l;
-      Alo[core_off(nd + k, nd + l, KP)] = re_l;
-    }
-    // B: column vectors of the neighbour (N rows of K-major data)
-    const int nb = nbr[site * 9 + d];
-    for (int i = tid; i < ncol * nd; i += blockDim.x) {
-      const int col = i / nd, l = i - col * nd;
-      const float2 z = X[(size_t)col * n + (size_t)nb * nd + l];
-      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
-      Bhi[core_off(col, l, KP)] = re_h;
-      Bhi[core_off(col, nd + l, KP)] = im_h;
-      Blo[core_off(col, l, KP)] = tf32_round(z.x - re_h);
-      Blo[core_off(col, nd + l, KP)] = tf32_round(z.y - im_h);
-    }
+  RawTile<ND, NPAD> raw;
+  auto tile_site = [&](int t) { return blockIdx.x + (t / 9) * gridDim.x; };
+  if (ntiles > 0) {
+    const int s0 = tile_site(0);
+    load_tile<ND, NPAD>(raw, Dc + (size_t)(s0 * 9) * ND * ND, X, n, nbr[s0 * 9], ncol, tid);
+  }
+  for (int t = 0; t < ntiles && ok; t++) {
+    const int site = tile_site(t), d = t % 9;
+    store_tile<ND, NPAD>(raw, Ahi, Alo, Bhi, Blo, ncol, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t aH = smem_u32(Ahi), aL = smem_u32(Alo), bH = smem_u32(Bhi), bL = smem_u32(Blo);
+#pragma unroll
       for (int s = 0; s < nsteps; s++) {
         const uint32_t koff = (uint32_t)s * 2 * 128;     // two core matrices per K = 8 step
-        const uint32_t dcol = tmem + (uint32_t)(s * NPAD);
-        const uint64_t dAh = smem_desc(aH + koff, lbo, sboA), dAl = smem_desc(aL + koff, lbo, sboA);
-        const uint64_t dBh = smem_desc(bH + koff, lbo, sboB), dBl = smem_desc(bL + koff, lbo, sboB);
+        const uint32_t dcol = tmem + (uint32_t)((s / R) * NPAD);
+        const uint64_t dAh = smem_desc(aH + koff, lbo, sbo), dAl = smem_desc(aL + koff, lbo, sbo);
+        const uint64_t dBh = smem_desc(bH + koff, lbo, sbo), dBl = smem_desc(bL + koff, lbo, sbo);
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                     ::"r"(dcol), "l"(dAh), "l"(dBh), "r"(idesc), "r"(0u));
+                     ::"r"(dcol), "l"(dAh), "l"(dBh), "r"(idesc), "r"((s % R) ? 1u : 0u));
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
                      ::"r"(dcol), "l"(dAh), "l"(dBl), "r"(idesc), "r"(1u));
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
@@ -189,20 +250,26 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv,
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                    : "memory");
     }
+    // the next tile's global loads overlap the MMAs of this one
+    if (t + 1 < ntiles) {
+      const int s1 = tile_site(t + 1), d1 = (t + 1) % 9;
+      load_tile<ND, NPAD>(raw, Dc + (size_t)(s1 * 9 + d1) * ND * ND, X, n, nbr[s1 * 9 + d1], ncol, tid);
+    }
     // the MMAs read shared memory asynchronously: thread 0 waits (bounded) for their completion,
     // then the whole CTA learns the outcome at one barrier, so every thread leaves the loop together
     if (tid == 0) {
-      const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(d & 1));
+      const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(t & 1));
       *s_ok = done ? 1 : 0;
       if (!done) atomicExch(err, 1);
     }
     __syncthreads();
     ok = *s_ok != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    if (ok && warp * 32 < 2 * ND) {
       // warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the real-embedded result), one column
-      // range per K step, and sums them in FP32
-      for (int s2 = 0; s2 < nsteps; s2++) {
+      // range per K step, and sums them in FP32 (warps above row 2 ND hold only padding)
+#pragma unroll
+      for (int s2 = 0; s2 < nranges; s2++) {
         float part[NPAD];
         tmem_load<NPAD>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s2 * NPAD), part);
 #pragma unroll
@@ -210,22 +277,24 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv,
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();   // TMEM reads done before the next block's MMAs overwrite the ranges
+    __syncthreads();   // TMEM reads and shared-memory tiles consumed before the next tile's MMAs
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
-  __syncthreads();
-  if (ok) {
-    const int r = warp * 32 + lane;
-    if (r < 2 * nd) {
-      const bool imag = r >= nd;
-      const int k = imag ? r - nd : r;
-      for (int col = 0; col < ncol; col++) {
-        const float2 xs = X[(size_t)col * n + (size_t)site * nd + k];
-        const float tw = k < nv ? mu[col] : -mu[col];
-        float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * nd + k);
-        if (!imag) yp[0] = acc[col] - tw * xs.y;
-        else yp[1] = acc[col] + tw * xs.x;
+    if (ok && d == 8) {
+      // epilogue of this site: twist and store, then a fresh accumulator
+      const int r = warp * 32 + lane;
+      if (r < 2 * ND) {
+        const bool imag = r >= ND;
+        const int k = imag ? r - ND : r;
+        for (int col = 0; col < ncol; col++) {
+          const float2 xs = X[(size_t)col * n + (size_t)site * ND + k];
+          const float tw = k < nv ? mu[col] : -mu[col];
+          float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * ND + k);
+          if (!imag) yp[0] = acc[col] - tw * xs.y;
+          else yp[1] = acc[col] + tw * xs.x;
+        }
       }
+#pragma unroll
+      for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -236,26 +305,49 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nd, int nv,
   }
 }
 
+template <int ND, int NPAD, int R>
+void launch_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+  constexpr int KP = ((2 * ND + 7) / 8) * 8;
+  constexpr int cols = ((KP / 8 + R - 1) / R) * NPAD;
+  const size_t smem = sizeof(float) * (size_t)(2 * TC_M * KP + 2 * NPAD * KP) + 32;
+  // persistent CTAs, as many as can be resident: tensor memory (512 columns per SM) holds two CTAs
+  // when one needs at most 256 columns, shared memory two when one needs at most 113 KB
+  const int per_sm = (cols <= 256 && smem <= 113 * 1024) ? 2 : 1;
+  const int grid = std::max(1, std::min(c.cl.nc, per_sm * c.sms));
+  TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<ND, NPAD, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ++c.launches, k_coarse_apply_tc<ND, NPAD, R><<<grid, 128, smem, c.stream>>>(c.cl.nc, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
+                                                                           c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
+                                                                           mu_dev, err_dev);
+}
+
+template <int ND, int NPAD>
+void launch_tc_r(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+  if (c.tc_steps_per_range >= 4) launch_tc<ND, NPAD, 4>(c, ncol, X, Y, mu_dev, err_dev);
+  else if (c.tc_steps_per_range == 2) launch_tc<ND, NPAD, 2>(c, ncol, X, Y, mu_dev, err_dev);
+  else launch_tc<ND, NPAD, 1>(c, ncol, X, Y, mu_dev, err_dev);
+}
+
+template <int ND>
+void launch_tc_nd(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+  if (ncol <= 16) launch_tc_r<ND, 16>(c, ncol, X, Y, mu_dev, err_dev);
+  else launch_tc_r<ND, 32>(c, ncol, X, Y, mu_dev, err_dev);
+}
+
 }  // namespace
 
 // Y = D_c(mu_col) X for ncol FP32 coarse vectors ([col][nc * nd] complex) on the tensor cores.
 void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
   ProfScope ps(c, PK_COARSE);
   const int nd = c.cl.nd;
-  if (ncol < 1 || ncol > 32 || 2 * nd > TC_M) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns, N_v <= 64"};
-  const int KP = ((2 * nd + 7) / 8) * 8;
-  const int npad = ncol <= 16 ? 16 : 32;
-  const size_t smem = sizeof(float) * (size_t)(2 * TC_M * KP + 2 * npad * KP) + 32;
-  if (npad == 16) {
-    TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ++c.launches, k_coarse_apply_tc<16><<<c.cl.nc, 128, smem, c.stream>>>(c.cl.nc, nd, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
-                                                                          c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
-                                                                          mu_dev, err_dev);
-  } else {
-    TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ++c.launches, k_coarse_apply_tc<32><<<c.cl.nc, 128, smem, c.stream>>>(c.cl.nc, nd, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
-                                                                          c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
-                                                                          mu_dev, err_dev);
+  if (ncol < 1 || ncol > 32) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns"};
+  switch (nd) {
+    case 8: launch_tc_nd<8>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 16: launch_tc_nd<16>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 24: launch_tc_nd<24>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 32: launch_tc_nd<32>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 48: launch_tc_nd<48>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 64: launch_tc_nd<64>(c, ncol, X, Y, mu_dev, err_dev); break;
+    default: throw Error{TMG_ERR_ARG, "tensor-core coarse apply: N_v must be 4, 8, 12, 16, 24 or 32"};
   }
   TMG_CHECK_LAUNCH();
 }

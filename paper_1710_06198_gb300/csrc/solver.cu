@@ -11,6 +11,9 @@
 
 #include "solver.h"
 
+#include <cstdint>
+#include <cstring>
+
 namespace tmg {
 
 namespace {
@@ -277,7 +280,164 @@ static void cycle_p(Ctx& c, int pf, int pc, const void* r, void* z, double mu, i
   else sap_sweeps(c, pf, z, r, nullptr, mu, c.mg.sap_sweeps);
 }
 
+// ---------------------------------------------------------------- cycle as a CUDA graph
+// The cycle's launches (P^dag, the persistent coarse solve, P, the SAP sweeps) are captured once per
+// key and replayed with one cudaGraphLaunch.  The key holds everything the launches bake in, so a
+// changed parameter, knob or (re)allocated buffer leads to a new capture instead of a stale graph.
+static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, const void* r, const void* z, double mu,
+                                                 int nf) {
+  auto u = [](const void* p) { return (unsigned long long)(uintptr_t)p; };
+  auto d = [](double v) {
+    unsigned long long b;
+    memcpy(&b, &v, sizeof b);
+    return b;
+  };
+  std::vector<unsigned long long> k = {u(r), u(z), (unsigned long long)pf, (unsigned long long)pc, (unsigned long long)nf,
+                                       d(mu), d(c.mubar), d(c.epsbar), (unsigned long long)(c.g.tbc + 2),
+                                       (unsigned long long)c.l2_ready, (unsigned long long)c.mg.sap_sweeps,
+                                       (unsigned long long)c.mg.sap_mr, (unsigned long long)c.mg.coarse_m, d(c.mg.coarse_rtol),
+                                       (unsigned long long)c.coarse_ctas_per_sm, (unsigned long long)c.coarse_gs_passes,
+                                       (unsigned long long)c.kcycle_ctas_per_sm, (unsigned long long)c.l2p.smooth_m,
+                                       (unsigned long long)c.l2p.k_restart, d(c.l2p.k_rtol), (unsigned long long)c.l2p.coarse_m,
+                                       d(c.l2p.coarse_rtol)};
+  for (int i = 0; i < 3; i++) {
+    k.push_back(u(c.op[i].U.p));
+    k.push_back(u(c.op[i].A.p));
+    k.push_back(u(c.op[i].Ascale.p));
+  }
+  for (const DBuf* b : {&c.cl.W64, &c.cl.W32, &c.cl.Dc64, &c.cl.Dc32, &c.cl.nbr, &c.cl2.W64, &c.cl2.W32, &c.cl2.Dc64,
+                        &c.cl2.Dc32, &c.cl2.nbr, &c.cw_cr, &c.cw_ce, &c.cw_V, &c.cw_w, &c.cw_part, &c.coarse_iter_dev,
+                        &c.kw, &c.l2_iter_dev}) {
+    k.push_back(u(b->p));
+    k.push_back((unsigned long long)b->bytes);
+  }
+  return k;
+}
+
+static void cycle_run(Ctx& c, int pf, int pc, const void* r, void* z, double mu, int nf = 1) {
+  if (!c.cycle_graphs || c.prof.on) {
+    cycle_p(c, pf, pc, r, z, mu, nf);
+    return;
+  }
+  std::vector<unsigned long long> key = cycle_key(c, pf, pc, r, z, mu, nf);
+  for (auto& e : c.graphs.g)
+    if (e.key == key) {
+      TMG_CUDA(cudaGraphLaunch(e.exec, c.stream));
+      c.launches += e.kernels;
+      return;
+    }
+  // miss: run the cycle eagerly (its result is this call's result and every buffer it needs is now
+  // allocated), then capture the same launches for the next call with this key
+  cycle_p(c, pf, pc, r, z, mu, nf);
+  if (cycle_key(c, pf, pc, r, z, mu, nf) != key) return;   // the eager run allocated: capture next time
+  if (!c.graphs.cap) TMG_CUDA(cudaStreamCreateWithFlags(&c.graphs.cap, cudaStreamNonBlocking));
+  if (c.graphs.g.size() >= 64) c.graphs.clear();
+  cudaStream_t saved = c.stream;
+  const long long l0 = c.launches;
+  cudaGraph_t graph = nullptr;
+  c.stream = c.graphs.cap;
+  cudaError_t err = cudaStreamBeginCapture(c.graphs.cap, cudaStreamCaptureModeRelaxed);
+  if (err == cudaSuccess) {
+    try {
+      cycle_p(c, pf, pc, r, z, mu, nf);
+    } catch (const Error&) {
+      err = cudaErrorStreamCaptureInvalidated;
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c.graphs.cap, &graph);
+    if (err == cudaSuccess) err = e2;
+  }
+  c.stream = saved;
+  const long long kernels = c.launches - l0;
+  c.launches = l0;
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess && graph) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess || !exec) {
+    cudaGetLastError();   // clear the capture error; this context runs the cycle eagerly from now on
+    c.cycle_graphs = 0;
+    return;
+  }
+  c.graphs.g.push_back(CycleGraph{key, exec, kernels});
+}
+
 void mg_cycle(Ctx& c, const void* r, void* z, double mu) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, mu); }
+
+// ---------------------------------------------------------------- launch-shape autotuner
+// Times the persistent coarse solve (and, with three levels, the K-cycle) for every allowed launch
+// shape on a fixed right-hand side with the stopping test disabled (fixed work per call), keeps the
+// fastest shape in the context and returns its time in milliseconds.
+double autotune(Ctx& c) {
+  const int pc = c.mg.prec_coarse;
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  DBuf b, x;
+  b.alloc(n * esize(pc));
+  x.alloc(n * esize(pc));
+  std::vector<double> ones(2 * n, 0.0);
+  for (size_t i = 0; i < n; i++) ones[2 * i] = 1.0;
+  DBuf h;
+  h.alloc(2 * n * sizeof(double));
+  TMG_CUDA(cudaMemcpyAsync(h.p, ones.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  convert_field(c, h.p, TMG_PREC_F64, b.p, pc, n);
+  cudaEvent_t e0, e1;
+  TMG_CUDA(cudaEventCreate(&e0));
+  TMG_CUDA(cudaEventCreate(&e1));
+  const bool prof = c.prof.on;
+  c.prof.on = false;
+  auto time_of = [&](auto&& run) {
+    run();
+    std::vector<float> t(3);
+    for (auto& v : t) {
+      TMG_CUDA(cudaEventRecord(e0, c.stream));
+      run();
+      TMG_CUDA(cudaEventRecord(e1, c.stream));
+      TMG_CUDA(cudaEventSynchronize(e1));
+      TMG_CUDA(cudaEventElapsedTime(&v, e0, e1));
+    }
+    std::sort(t.begin(), t.end());
+    return (double)t[1];
+  };
+  double best = 0.0;
+  const double rtol = c.mg.coarse_rtol;
+  c.mg.coarse_rtol = 0.0;
+  try {
+    if (c.l2_ready) {
+      const double krtol = c.l2p.k_rtol;
+      c.l2p.k_rtol = 0.0;
+      int best_k = c.kcycle_ctas_per_sm;
+      best = 1e30;
+      for (int k = 1; k <= 4; k++) {
+        c.kcycle_ctas_per_sm = k;
+        const double t = time_of([&] { kcycle(c, pc, b.p, x.p, c.mu, 0); });
+        if (t < best) { best = t; best_k = k; }
+      }
+      c.kcycle_ctas_per_sm = best_k;
+      c.l2p.k_rtol = krtol;
+    } else {
+      int best_ctas = c.coarse_ctas_per_sm, best_pass = c.coarse_gs_passes;
+      best = 1e30;
+      for (int ctas = 1; ctas <= 4; ctas++)
+        for (int pass = (pc == TMG_PREC_F64 ? 2 : 1); pass <= 2; pass++) {
+          c.coarse_ctas_per_sm = ctas;
+          c.coarse_gs_passes = pass;
+          const double t = time_of([&] { coarse_gmres_persistent(c, pc, b.p, x.p, c.mu); });
+          if (t < best) { best = t; best_ctas = ctas; best_pass = pass; }
+        }
+      c.coarse_ctas_per_sm = best_ctas;
+      c.coarse_gs_passes = best_pass;
+    }
+  } catch (...) {
+    c.mg.coarse_rtol = rtol;
+    c.prof.on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  c.mg.coarse_rtol = rtol;
+  c.prof.on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
 void mg_cycle_nd(Ctx& c, const void* r, void* z) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, 0.0, 2); }
 
 // ---------------------------------------------------------------- setup
@@ -423,7 +583,7 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
   for (int j = 0; j < m; j++) {
     void* vj = V + j * n * es;
     void* zj = Z + j * n * es;
-    cycle_p(c, pf, pc, vj, zj, mu, nf);
+    cycle_run(c, pf, pc, vj, zj, mu, nf);
     if (nf == 2) dslash_nd(c, op, c.fw_w.p, zj);
     else dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
     std::vector<double2> hc(j + 1), hc2(j + 1);

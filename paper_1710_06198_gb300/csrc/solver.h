@@ -23,6 +23,9 @@ void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // nf = 2: the doublet D_ND (Eq. 2) on F64 fields [2][12 V] (mu unused; mubar, epsbar of the context).
 int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st,
               int nf = 1);
+// Launch-shape autotuner of the coarse solve (coarse_ctas_per_sm, coarse_gs_passes; with three
+// levels kcycle_ctas_per_sm); keeps the fastest shape, returns its time per coarse solve in ms.
+double autotune(Ctx& c);
 // z = doublet cycle of r (fields [2][12 V] in the fine storage precision)
 void mg_cycle_nd(Ctx& c, const void* r, void* z);
 // ncol systems D(mu_c) x_c = b_c (F64 fields, column c at c * 12 V) solved in lock-step.

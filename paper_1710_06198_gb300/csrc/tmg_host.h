@@ -128,6 +128,28 @@ struct Prof {
   }
 };
 
+// Captured CUDA graphs of the preconditioner cycle (solver.cu), keyed by everything the captured
+// launches bake in: buffer addresses, twists, parameters and launch-shape knobs.
+struct CycleGraph {
+  std::vector<unsigned long long> key;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;   // launches inside the graph (added to Ctx::launches per replay)
+};
+
+struct GraphCache {
+  std::vector<CycleGraph> g;
+  cudaStream_t cap = nullptr;   // private stream used only while capturing
+  void clear() {
+    for (auto& e : g)
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+    g.clear();
+  }
+  ~GraphCache() {
+    clear();
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -161,6 +183,9 @@ struct Ctx {
   int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
   int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
   int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
+  int tc_steps_per_range = 1;   // K steps sharing one TMEM accumulator range in the tensor-core coarse apply
+  int cycle_graphs = 1;         // replay the preconditioner cycle of the outer FGMRES as a CUDA graph
+  GraphCache graphs;
   Prof prof;
 };
 
