@@ -203,3 +203,12 @@ def search_m0_mg(U, csw, mu, block, nv, b, v0, max_steps=50, step=0.1, n_bisect=
         else:
             bad = mid
     return good
+
+
+def select_m0(mg_log, ratio=2.0):
+    """From a convergence-edge walk [(m0, steps), ...]: the most critical m0 whose outer step count
+    is at most ratio times the count at m0 = 0 (a margin below the edge, where the step count on the
+    small search lattice still carries over to the workload's lattice)."""
+    base = dict(mg_log)[0.0]
+    ok = [m for m, n in mg_log if n <= ratio * base]
+    return min(ok)

@@ -14,6 +14,12 @@ stall at the same residual).  The workloads therefore take kappa from the conver
 
     python -m oracle.kappa_search --edge NAME EPS SEED CSW MU NV TARGET [--write synth/kappa.json]
     python -m oracle.kappa_search --merge synth/kappa.json RECORD.json ...
+    python -m oracle.kappa_search --select synth/kappa.json NAME ...
+
+The edge itself is too close to breakdown to carry over to the workloads' lattices (at the edge m0
+of the 16^3 x 32 recipe the GPU needs 481 outer steps against 39 on the 8^4 search lattice), so
+--select moves each record to the most critical m0 of the recorded walk whose step count is at
+most twice the count at m0 = 0.
 
 walks m0 down with the oracle's two-level DD-alpha-AMG on an 8^4 lattice of the workload's recipe
 (4^4 blocks and aggregates, N_v test vectors, Gaussian right-hand side), keeps the most critical m0
@@ -82,7 +88,31 @@ def merge(argv):
         f.write("\n")
 
 
+def select(argv):
+    """--select TABLE NAME...: move each named record of TABLE from the convergence edge to the
+    margin rule of kappa.select_m0 (recorded walk, ratio 2) and recompute sigma_min there."""
+    table_path, names = argv[0], argv[1:]
+    with open(table_path) as f:
+        table = json.load(f)
+    from synth import fields
+    for name in names:
+        rec = table[name]
+        m0 = kappa.select_m0([tuple(e) for e in rec["mg_log"]], 2.0)
+        U6 = fields.gauge_field(tuple(rec["sigma_lattice"]), rec["eps"], rec["seed"])
+        smin = kappa.sigma_min(U6, dirac.Params(kappa=dirac.kappa_from_m0(m0), csw=rec["csw"], tbc=-1))
+        rec.update({"edge_m0": rec.get("edge_m0", rec["m0"]), "m0": m0, "kappa": dirac.kappa_from_m0(m0), "sigma_min": smin,
+                    "reached_target": bool(smin <= rec["target"]),
+                    "rule": "most critical m0 of the walk whose oracle two-level steps are at most twice those at m0 = 0",
+                    "source": f"oracle kappa_search --select: m0 = {m0:.4f}, sigma_min(D_W, 6^4) = {smin:.3e}"})
+        with open(table_path, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+            f.write("\n")
+        print(name, m0, smin, flush=True)
+
+
 def main(argv):
+    if argv and argv[0] == "--select":
+        return select(argv[1:])
     if argv and argv[0] == "--edge":
         return edge(argv[1:])
     if argv and argv[0] == "--merge":

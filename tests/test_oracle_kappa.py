@@ -42,3 +42,9 @@ def test_convergence_edge_walk_and_bisection(monkeypatch):
     assert -1.25 <= m0 <= -1.2 + 1e-12
     assert [m for m, _ in log][:3] == [0.0, -0.1, -0.2]
     assert all(n == 20 for m, n in log if m > edge) and all(n == 51 for m, n in log if m <= edge)
+
+
+def test_margin_rule_selects_most_critical_m0_within_twice_the_base_steps():
+    log = [(0.0, 6), (-0.1, 7), (-0.2, 9), (-0.3, 12), (-0.4, 13), (-0.5, 30), (-0.45, 20)]
+    assert kappa.select_m0(log) == -0.3
+    assert kappa.select_m0(log, ratio=5.0) == -0.5
