@@ -130,7 +130,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
       for (int k = lane; k < a.nd; k += 32) {
         S ar = 0, ai = 0;
-#pragma unroll 8
+#pragma unroll 16
         for (int l = 0; l < a.nd; l++) {
           const T2 m = blk[(size_t)l * a.nd + k];
           const T2 v = xv[l];
@@ -199,6 +199,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         T2 q = a.w[e];
         S qr = q.x, qi = q.y;
+        #pragma unroll 4
         for (int i = 0; i <= j; i++) {
           const T2 p = a.V[(size_t)i * n + e];
           const S hr = (S)hp[i].x, hi = (S)hp[i].y;
@@ -276,6 +277,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   __syncthreads();
   for (int e = tid; e < n; e += nth) {
     S xr = 0, xi = 0;
+    #pragma unroll 4
     for (int i = 0; i < k; i++) {
       const T2 v = a.V[(size_t)i * n + e];
       xr += yr[i] * v.x - yi[i] * v.y;
@@ -289,7 +291,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) k_coarse_gmres(CgArgs<S> a) {
+__global__ void __launch_bounds__(256, 2) k_coarse_gmres(CgArgs<S> a) {
   gmres_dev(a);
 }
 
@@ -336,7 +338,7 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
     const T2* xv = src + (size_t)f * n1 + (size_t)op.nbr[t9] * op.nd;
     for (int k = lane; k < op.nd; k += 32) {
       S ar = 0, ai = 0;
-#pragma unroll 8
+#pragma unroll 16
       for (int l = 0; l < op.nd; l++) {
         const T2 m = blk[(size_t)l * op.nd + k];
         const T2 v = xv[l];
