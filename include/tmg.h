@@ -275,7 +275,9 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * cycle inside the outer FGMRES is captured once per set of buffers and parameters as a CUDA graph
  * and replayed with one launch; 0: launched kernel by kernel), "tc_steps_per_range" (1, 2 or 4 K = 8
  * steps accumulated in one tensor-memory range by tmg_coarse_apply_multi; 1 keeps FP32-level
- * accuracy for any N_v).  TMG_ERR_ARG for an unknown key or value. */
+ * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
+ * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs).  TMG_ERR_ARG for an unknown key or
+ * value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 
 /* Autotuner (not a paper quantity): after tmg_setup (and tmg_setup_level2), time the coarse solve of

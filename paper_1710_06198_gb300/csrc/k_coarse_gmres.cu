@@ -64,6 +64,75 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   return t;
 }
 
+// One stencil task, by one warp: out[k] = scale * (sum_l blk[l][k] x[l] - epsbar xo[k]) for the
+// nd rows k of one (nd x nd) block (xo: the doublet's other flavour on the self block, or null).
+// FP32 blocks whose half width divides 32 are read as float4 (two rows per load) with the columns
+// split over lane groups, so every lane keeps all its loads in flight at once; the group partial
+// sums are combined with shuffles.  Other shapes: lanes are rows and every column is one coalesced
+// read.
+template <typename S>
+__device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __restrict__ blk,
+                                             const typename CplxT<S>::T2* __restrict__ xv, int nd, S scale,
+                                             const typename CplxT<S>::T2* xo, S epsbar,
+                                             typename CplxT<S>::T2* __restrict__ out, int lane) {
+  using T2 = typename CplxT<S>::T2;
+  const int half = nd >> 1;
+  if constexpr (sizeof(S) == 4) {
+    if (half > 0 && (32 % half) == 0) {
+      const int groups = 32 / half;
+      const int kp = lane % half, lg = lane / half;
+      const float4* bl = reinterpret_cast<const float4*>(blk);
+      float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
+#pragma unroll 16
+      for (int l = lg; l < nd; l += groups) {
+        const float4 m = bl[(size_t)l * half + kp];
+        const float2 v = xv[l];
+        ar0 += m.x * v.x - m.y * v.y;
+        ai0 += m.x * v.y + m.y * v.x;
+        ar1 += m.z * v.x - m.w * v.y;
+        ai1 += m.z * v.y + m.w * v.x;
+      }
+      for (int o = half; o < 32; o <<= 1) {
+        ar0 += __shfl_xor_sync(0xffffffffu, ar0, o);
+        ai0 += __shfl_xor_sync(0xffffffffu, ai0, o);
+        ar1 += __shfl_xor_sync(0xffffffffu, ar1, o);
+        ai1 += __shfl_xor_sync(0xffffffffu, ai1, o);
+      }
+      if (lg == 0) {
+        const int k = 2 * kp;
+        if (xo) {
+          const float2 a0 = xo[k], a1 = xo[k + 1];
+          ar0 -= epsbar * a0.x;
+          ai0 -= epsbar * a0.y;
+          ar1 -= epsbar * a1.x;
+          ai1 -= epsbar * a1.y;
+        }
+        out[k] = make_float2(ar0 * scale, ai0 * scale);
+        out[k + 1] = make_float2(ar1 * scale, ai1 * scale);
+      }
+      return;
+    }
+  }
+  for (int k = lane; k < nd; k += 32) {
+    S ar = 0, ai = 0;
+#pragma unroll 16
+    for (int l = 0; l < nd; l++) {
+      const T2 m = blk[(size_t)l * nd + k];
+      const T2 v = xv[l];
+      ar += m.x * v.x - m.y * v.y;
+      ai += m.x * v.y + m.y * v.x;
+    }
+    if (xo) {
+      ar -= epsbar * xo[k].x;
+      ai -= epsbar * xo[k].y;
+    }
+    T2 o;
+    o.x = ar * scale;
+    o.y = ai * scale;
+    out[k] = o;
+  }
+}
+
 // GMRES from zero on the operator of a (any level): grid-wide phases, the caller's grid must be a
 // cooperative launch; a.x is complete after the caller's next grid barrier.
 template <typename S>
@@ -128,25 +197,8 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       const int nb = a.nbr[t9];
       const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
       const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
-      for (int k = lane; k < a.nd; k += 32) {
-        S ar = 0, ai = 0;
-#pragma unroll 16
-        for (int l = 0; l < a.nd; l++) {
-          const T2 m = blk[(size_t)l * a.nd + k];
-          const T2 v = xv[l];
-          ar += m.x * v.x - m.y * v.y;
-          ai += m.x * v.y + m.y * v.x;
-        }
-        if (a.nf == 2 && t9 == site * 9) {
-          const T2 xo = src[(size_t)(1 - f) * n1 + (size_t)site * a.nd + k];
-          ar -= a.epsbar * xo.x;
-          ai -= a.epsbar * xo.y;
-        }
-        T2 o;
-        o.x = ar * scale;
-        o.y = ai * scale;
-        a.rows[(size_t)task * a.nd + k] = o;
-      }
+      const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
+      stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.rows + (size_t)task * a.nd, lane);
     }
     grid.sync();                                     // partial rows complete
     // (2) own chunk: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
@@ -336,25 +388,8 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
     const int site = t9 / 9;
     const T2* blk = op.Dc + (size_t)t9 * op.nd * op.nd;
     const T2* xv = src + (size_t)f * n1 + (size_t)op.nbr[t9] * op.nd;
-    for (int k = lane; k < op.nd; k += 32) {
-      S ar = 0, ai = 0;
-#pragma unroll 16
-      for (int l = 0; l < op.nd; l++) {
-        const T2 m = blk[(size_t)l * op.nd + k];
-        const T2 v = xv[l];
-        ar += m.x * v.x - m.y * v.y;
-        ai += m.x * v.y + m.y * v.x;
-      }
-      if (op.nf == 2 && t9 == site * 9) {
-        const T2 xo = src[(size_t)(1 - f) * n1 + (size_t)site * op.nd + k];
-        ar -= op.epsbar * xo.x;
-        ai -= op.epsbar * xo.y;
-      }
-      T2 o;
-      o.x = ar;
-      o.y = ai;
-      op.rows[(size_t)task * op.nd + k] = o;
-    }
+    const T2* xo = (op.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * op.nd : nullptr;
+    stencil_task<S>(blk, xv, op.nd, (S)1, xo, op.epsbar, op.rows + (size_t)task * op.nd, lane);
   }
   grid.sync();
   const int n = op.nf * n1;
@@ -930,7 +965,9 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   static int max_per_sm[2] = {-1, -1};
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
-  const int G = std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
+  const int G = c.coarse_grid > 0
+                    ? std::max(1, std::min(c.coarse_grid, c.sms * std::max(1, mps)))
+                    : std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
   c.cw_w.alloc(10 * n * sizeof(T2));
   c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
@@ -1109,7 +1146,8 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   int& mps = max_per_sm[sizeof(S) == 8];
   if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_kcycle<S>, 256, 0));
   if (mps < 1) throw Error{TMG_ERR_CUDA, "K-cycle kernel cannot be resident"};
-  const int G = c.sms * std::max(1, std::min(mps, c.kcycle_ctas_per_sm));
+  const int G = c.kcycle_grid > 0 ? std::max(1, std::min(c.kcycle_grid, c.sms * mps))
+                                  : c.sms * std::max(1, std::min(mps, c.kcycle_ctas_per_sm));
   const int sm_m = std::min(p.smooth_m, CMAXM), cm = std::min(p.coarse_m, CMAXM), kr = std::min(p.k_restart, KMAXR);
   // one scratch allocation, carved 256-byte aligned
   const size_t vec_elems[] = {(kr + 1) * n1, kr * n1, n1, n1, n1, (sm_m + 1) * n1, 10 * n1, n2, n2, (cm + 1) * n2, 10 * n2};

@@ -28,6 +28,8 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr unsigned kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+constexpr uint32_t kSuspendHintNs = 1000;     // each poll suspends for at most ~1 us
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -62,15 +64,25 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the mbarrier phase; gives up after kWaitNs of wall time (and after kSpinLimit polls),
+// so a completion that never arrives costs at most about a second instead of hanging the kernel.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
   for (unsigned it = 0; it < kSpinLimit; it++) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }

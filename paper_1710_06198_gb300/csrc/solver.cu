@@ -297,7 +297,8 @@ static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, c
                                        (unsigned long long)c.l2_ready, (unsigned long long)c.mg.sap_sweeps,
                                        (unsigned long long)c.mg.sap_mr, (unsigned long long)c.mg.coarse_m, d(c.mg.coarse_rtol),
                                        (unsigned long long)c.coarse_ctas_per_sm, (unsigned long long)c.coarse_gs_passes,
-                                       (unsigned long long)c.kcycle_ctas_per_sm, (unsigned long long)c.l2p.smooth_m,
+                                       (unsigned long long)c.kcycle_ctas_per_sm, (unsigned long long)c.coarse_grid,
+                                       (unsigned long long)c.kcycle_grid, (unsigned long long)c.l2p.smooth_m,
                                        (unsigned long long)c.l2p.k_restart, d(c.l2p.k_rtol), (unsigned long long)c.l2p.coarse_m,
                                        d(c.l2p.coarse_rtol)};
   for (int i = 0; i < 3; i++) {
@@ -403,27 +404,39 @@ double autotune(Ctx& c) {
     if (c.l2_ready) {
       const double krtol = c.l2p.k_rtol;
       c.l2p.k_rtol = 0.0;
-      int best_k = c.kcycle_ctas_per_sm;
+      int best_k = c.kcycle_ctas_per_sm, best_g = 0;
       best = 1e30;
       for (int k = 1; k <= 4; k++) {
         c.kcycle_ctas_per_sm = k;
+        c.kcycle_grid = 0;
         const double t = time_of([&] { kcycle(c, pc, b.p, x.p, c.mu, 0); });
-        if (t < best) { best = t; best_k = k; }
+        if (t < best) { best = t; best_k = k; best_g = 0; }
+      }
+      for (int g : {c.sms / 4, c.sms / 2}) {   // fewer CTAs than SMs: cheaper grid-wide barriers
+        c.kcycle_ctas_per_sm = 1;
+        c.kcycle_grid = g;
+        const double t = time_of([&] { kcycle(c, pc, b.p, x.p, c.mu, 0); });
+        if (t < best) { best = t; best_k = 1; best_g = g; }
       }
       c.kcycle_ctas_per_sm = best_k;
+      c.kcycle_grid = best_g;
       c.l2p.k_rtol = krtol;
     } else {
-      int best_ctas = c.coarse_ctas_per_sm, best_pass = c.coarse_gs_passes;
+      int best_ctas = c.coarse_ctas_per_sm, best_pass = c.coarse_gs_passes, best_g = 0;
       best = 1e30;
-      for (int ctas = 1; ctas <= 4; ctas++)
+      // grids of k CTAs per SM, and grids smaller than the SM count (cheaper grid-wide barriers)
+      const int grids[] = {0, 0, 0, 0, c.sms / 4, c.sms / 2};
+      for (int gi = 0; gi < 6; gi++)
         for (int pass = (pc == TMG_PREC_F64 ? 2 : 1); pass <= 2; pass++) {
-          c.coarse_ctas_per_sm = ctas;
+          c.coarse_ctas_per_sm = gi < 4 ? gi + 1 : 1;
+          c.coarse_grid = grids[gi];
           c.coarse_gs_passes = pass;
           const double t = time_of([&] { coarse_gmres_persistent(c, pc, b.p, x.p, c.mu); });
-          if (t < best) { best = t; best_ctas = ctas; best_pass = pass; }
+          if (t < best) { best = t; best_ctas = c.coarse_ctas_per_sm; best_pass = pass; best_g = grids[gi]; }
         }
       c.coarse_ctas_per_sm = best_ctas;
       c.coarse_gs_passes = best_pass;
+      c.coarse_grid = best_g;
     }
   } catch (...) {
     c.mg.coarse_rtol = rtol;

@@ -172,3 +172,24 @@ def test_solve_rejects_nan(solve_case):
     with pytest.raises(tmg.TmgError) as e:
         ctx.solve(bad, tol=1e-10, method=tmg.SOLVE_MG_MIXED)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("nv", [4, 8, 16])
+def test_coarse_solve_f32_vector_stencil(nv):
+    """FP32 coarse GMRES for N_v whose block rows are read two at a time (float4 tiles split over
+    lane groups), against the oracle's GMRES with the same fixed step count."""
+    dims, block = (8, 8, 4, 4), (4, 4, 2, 2)
+    U = fields.gauge_field(dims, 0.5, 230)
+    p = dirac.Params(kappa=dirac.kappa_from_m0(-0.25), csw=1.2, mu=0.05, tbc=-1)
+    ctx = tmg.Context(dims, block)
+    ctx.set_params(p.kappa, p.csw, p.mu)
+    ctx.load_gauge(U, -1)
+    prm = tmg.Context.mg_defaults()
+    prm.nv, prm.n_init, prm.n_iter, prm.coarse_m, prm.coarse_rtol = nv, 0, 0, 12, 0.0
+    prm.prec_fine, prm.prec_coarse = F32, F32
+    v0 = fields.gaussian_spinor(dims, 231, n=nv)
+    ctx.setup(v0, prm)
+    H = mg.Hierarchy(U, p, mg.MGParams(block=block, agg=block, nv=nv, coarse_m=12, coarse_rtol=0.0))
+    H.set_vectors(v0)
+    c = fields.gaussian_coarse((2, 2, 2, 2), 2 * nv, 232)
+    assert rel(ctx.coarse_solve(c, p.mu, F32), H.coarse_solve(c, p.mu)) < 1e-4

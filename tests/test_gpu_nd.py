@@ -94,6 +94,28 @@ def test_coarse_doublet_gmres_and_cycle(two):
     assert rel(ctx.cycle_nd(r), HN.cycle(r)) < 1e-10
 
 
+def test_coarse_doublet_gmres_f32_vector_stencil():
+    """FP32 doublet coarse GMRES with N_v = 4 (block rows read two at a time, flavour mixing added
+    by the lane group that writes the row) against the oracle's GMRES, fixed step count."""
+    dims, block = (8, 8, 4, 4), (4, 4, 2, 2)
+    U = fields.gauge_field(dims, 0.45, 233)
+    p = dirac.Params(kappa=dirac.kappa_from_m0(-0.3), csw=1.1, mu=0.12, tbc=-1, mubar=0.12, epsbar=0.13)
+    ctx = tmg.Context(dims, block)
+    ctx.set_params(p.kappa, p.csw, p.mu, p.mubar, p.epsbar)
+    ctx.load_gauge(U, -1)
+    prm = tmg.Context.mg_defaults()
+    prm.nv, prm.n_init, prm.n_iter, prm.coarse_m, prm.coarse_rtol = 4, 0, 0, 12, 0.0
+    prm.prec_fine, prm.prec_coarse = F32, F32
+    v0 = fields.gaussian_spinor(dims, 234, n=4)
+    ctx.setup(v0, prm)
+    H = mg.Hierarchy(U, p, mg.MGParams(block=block, agg=block, nv=4, coarse_m=12, coarse_rtol=0.0))
+    H.set_vectors(v0)
+    HN = nd.HierarchyND(H)
+    c = fields.gaussian_coarse((2, 2, 2, 2), 8, 235, n=2)
+    want, _ = krylov.gmres_fixed(HN.coarse_apply, c, 12, 0.0)
+    assert rel(ctx.coarse_solve_nd(c, F32), want) < 1e-4
+
+
 @pytest.mark.parametrize("method", [tmg.SOLVE_ND_F64, tmg.SOLVE_ND_MIXED])
 def test_two_level_doublet_solve(method):
     ctx, HN, U, p = build(prec=F64 if method == tmg.SOLVE_ND_F64 else F32, coarse_rtol=5e-2, coarse_m=30,
