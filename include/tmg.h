@@ -276,7 +276,9 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * and replayed with one launch; 0: launched kernel by kernel), "tc_steps_per_range" (1, 2 or 4 K = 8
  * steps accumulated in one tensor-memory range by tmg_coarse_apply_multi; 1 keeps FP32-level
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
- * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs).  TMG_ERR_ARG for an unknown key or
+ * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
+ * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
+ * the basis for up to 10 basis vectors; 0: separate kernels).  TMG_ERR_ARG for an unknown key or
  * value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 

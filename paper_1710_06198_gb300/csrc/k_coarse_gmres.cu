@@ -19,7 +19,6 @@ namespace tmg {
 namespace {
 
 constexpr int CMAXM = 64;
-constexpr int CMAXND = 64;   // largest coarse dof count per site (N_v <= 32)
 
 template <typename S>
 struct CplxT;

@@ -77,6 +77,66 @@ __global__ void k_mdot_final(const double2* __restrict__ part, int np, int count
   }
 }
 
+// First Gram-Schmidt pass's update fused with the second pass's dot products (count <= 10):
+// w -= sum_i coef[i] v_i, then part[i * NPART + b] = partial of <v_i, w> over block b's elements,
+// with each v_i read once for both.
+constexpr int FUSED_MAX = 10;
+
+template <typename T2>
+__global__ void __launch_bounds__(256, 2) k_mgs_update_dot(const T2* __restrict__ Vb, size_t stride, int count,
+                                                        const double2* __restrict__ coef, T2* __restrict__ w, size_t n,
+                                                        double2* __restrict__ part) {
+  using S = typename ScalarOf<T2>::T;
+  __shared__ S cfr[FUSED_MAX], cfi[FUSED_MAX];
+  __shared__ double sre[FUSED_MAX][8], sim[FUSED_MAX][8];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) { cfr[i] = (S)coef[i].x; cfi[i] = (S)coef[i].y; }
+  __syncthreads();
+  S dr[FUSED_MAX], di[FUSED_MAX];
+#pragma unroll
+  for (int i = 0; i < FUSED_MAX; i++) { dr[i] = 0; di[i] = 0; }
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    T2 v[FUSED_MAX];
+    S xr = w[e].x, xi = w[e].y;
+#pragma unroll
+    for (int i = 0; i < FUSED_MAX; i++) {
+      if (i < count) {
+        v[i] = Vb[(size_t)i * stride + e];
+        xr -= cfr[i] * v[i].x - cfi[i] * v[i].y;
+        xi -= cfr[i] * v[i].y + cfi[i] * v[i].x;
+      }
+    }
+    T2 o;
+    o.x = xr;
+    o.y = xi;
+    w[e] = o;
+#pragma unroll
+    for (int i = 0; i < FUSED_MAX; i++) {
+      if (i < count) {
+        dr[i] += v[i].x * xr + v[i].y * xi;
+        di[i] += v[i].x * xi - v[i].y * xr;
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < FUSED_MAX; i++) {
+    if (i < count) {
+      double re = dr[i], im = di[i];
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) { sre[i][wp] = re; sim[i][wp] = im; }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    double a = 0, b = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { a += sre[i][k]; b += sim[i][k]; }
+    part[(size_t)i * NPART + blockIdx.x] = make_double2(a, b);
+  }
+}
+
 // w -= sum_i coef[i] v_i  (coef on the device); optionally partial ||w||^2 into part[b]
 template <typename T2>
 __global__ void k_mgs_update(const T2* __restrict__ Vb, size_t stride, int count, const double2* __restrict__ coef,
@@ -603,12 +663,23 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
     std::vector<double2> nn_parts(NPART);
     dispatch(sp, [&](auto tag) {
       using T2 = decltype(tag);
-      for (int pass = 0; pass < 2; pass++) {
+      if (c.outer_gs_fused && j + 1 <= FUSED_MAX) {
+        // classical Gram-Schmidt, two passes, with pass 1's update and pass 2's dots in one sweep
         ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
-        ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
-        ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + pass * (MAXM + 1), (T2*)c.fw_w.p, n,
-                                                   pass == 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
+        ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev, nullptr);
+        ++c.launches, k_mgs_update_dot<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev, (T2*)c.fw_w.p, n, part);
+        ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev + (MAXM + 1), nullptr);
+        ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + (MAXM + 1), (T2*)c.fw_w.p, n,
+                                                   part + NPART * (MAXM + 1), nullptr);
         TMG_CHECK_LAUNCH();
+      } else {
+        for (int pass = 0; pass < 2; pass++) {
+          ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
+          ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
+          ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + pass * (MAXM + 1), (T2*)c.fw_w.p, n,
+                                                     pass == 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
+          TMG_CHECK_LAUNCH();
+        }
       }
     });
     TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
