@@ -378,6 +378,21 @@ void sap_sweeps(Ctx& c, int prec, void* x, const void* b, void* /*r_scratch*/, d
 // ------------------------------------------------------------------ restriction P^dag
 // out[blk][chi * nv + j] = sum_{s in blk} W_j(s)_chi^dag r(s)_chi, test vectors handled in chunks of
 // 8 to bound the registers.
+// One round of a warp-wide multi-value reduction: of the 2 O values a lane still holds, it keeps
+// the upper O if bit O of its lane index is set and the lower O otherwise, adding the partner's
+// copy of the kept half.  After rounds O = 16, 8, 4, 2, 1 on 32 values, lane l holds in v[0] the
+// warp sum of value l.
+template <int O, typename R>
+__device__ __forceinline__ void warp_transpose_reduce(R (&v)[32], int lane) {
+  const bool upper = (lane & O) != 0;
+#pragma unroll
+  for (int i = 0; i < O; i++) {
+    const R send = upper ? v[i] : v[i + O];
+    const R keep = upper ? v[i + O] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+  }
+}
+
 template <typename R, class S, typename OUT2>
 __global__ void __launch_bounds__(256) k_restrict(Geom g, S r, S W, int nv, OUT2* __restrict__ out) {
   extern __shared__ double red[];
@@ -406,16 +421,32 @@ __global__ void __launch_bounds__(256) k_restrict(Geom g, S r, S W, int nv, OUT2
         }
       }
     }
-    cta_allreduce<32, R>(v, red);
+    // warp sums by a butterfly in which every lane ends up holding the sum of one of the 32 values
+    // (31 shuffles instead of 32 x 5), then one FP64 sum over the warps per value
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    warp_transpose_reduce<16>(v, lane);
+    warp_transpose_reduce<8>(v, lane);
+    warp_transpose_reduce<4>(v, lane);
+    warp_transpose_reduce<2>(v, lane);
+    warp_transpose_reduce<1>(v, lane);
+    red[wp * 32 + lane] = (double)v[0];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k * 32 + threadIdx.x];
+      red[32 * 32 + threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x < 16) {
       const int chi = threadIdx.x / 8, jj = threadIdx.x % 8, j = j0 + jj;
       if (j < nv) {
         OUT2 o;
-        o.x = v[(chi * 8 + jj) * 2];
-        o.y = v[(chi * 8 + jj) * 2 + 1];
+        o.x = red[32 * 32 + (chi * 8 + jj) * 2];
+        o.y = red[32 * 32 + (chi * 8 + jj) * 2 + 1];
         out[(size_t)blk * nd + chi * nv + j] = o;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -456,7 +487,7 @@ __global__ void __launch_bounds__(256) k_prolong(Geom g, const IN2* __restrict__
 void restrict_(Ctx& c, int prec, const void* r, void* cvec, int cprec) {
   ProfScope ps(c, PK_RESTRICT);
   const int nv = c.cl.nv;
-  const size_t smem = 33 * 32 * sizeof(double);
+  const size_t smem = 33 * 32 * sizeof(double);   // per-warp sums (8 x 32) and the 32 totals
   if (prec == TMG_PREC_F64) {
     SpinorF64 rs{(double2*)r, c.g.V}, ws{c.cl.W64.as<double2>(), c.g.V};
     if (cprec == TMG_PREC_F64) ++c.launches, k_restrict<double><<<c.g.nblk, c.g.VB, smem, c.stream>>>(c.g, rs, ws, nv, (double2*)cvec);
