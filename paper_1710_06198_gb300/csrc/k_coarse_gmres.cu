@@ -236,6 +236,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       grid.sync();                                   // partials complete
       for (int i = warp; i <= j; i += nwarp) {
         double re = 0.0, im = 0.0;
+#pragma unroll 8
         for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
         re = warp_sum(re);
         im = warp_sum(im);
@@ -272,36 +273,47 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     grid.sync();                                     // w and norm partials complete
     if (warp == 0) {
       double t = 0.0;
+#pragma unroll 8
       for (int q = lane; q < G; q += 32) t += a.npart[q];
       t = warp_sum(t);
       if (lane == 0) s_hn = sqrt(t);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+      // previous rotations [[conj c, conj s], [-s, c]] applied down the new column; the running
+      // entry stays in registers (only the loads of the untouched entries and of the rotations,
+      // which do not depend on the chain, touch shared memory)
       const double hn = s_hn;
-      hcol[j + 1] = make_double2(hn, 0.0);
-      for (int i = 0; i < j; i++) {                  // previous rotations [[conj c, conj s], [-s, c]]
-        const double2 x0 = hcol[i], x1 = hcol[i + 1];
+      double2 x0 = hcol[0];
+      for (int i = 0; i < j; i++) {
+        const double2 x1 = hcol[i + 1];
         const double2 c = cs[i], s = sn[i];
         hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
                                c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
-        hcol[i + 1] = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
-                                   -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+        x0 = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                          -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
       }
-      const double2 p = hcol[j], q = hcol[j + 1];
-      const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
-      cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
-      sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
+      // new rotation from (p, q) = (running entry, hn): one reciprocal square root instead of a
+      // square root and four divisions
+      const double2 p = x0;
+      const double n2 = p.x * p.x + p.y * p.y + hn * hn;
+      const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+      const double den = n2 * inv;
+      const double2 c = n2 > 0.0 ? make_double2(p.x * inv, p.y * inv) : make_double2(1.0, 0.0);
+      const double2 sr = make_double2(hn * inv, 0.0);
+      cs[j] = c;
+      sn[j] = sr;
       hcol[j] = make_double2(den, 0.0);
       hcol[j + 1] = make_double2(0.0, 0.0);
       const double2 g = gv[j];
-      gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
-      gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+      gv[j + 1] = make_double2(-(sr.x * g.x), -(sr.x * g.y));
+      gv[j] = make_double2(c.x * g.x + c.y * g.y, c.x * g.y - c.y * g.x);
       if (blockIdx.x == 0)
         for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
       s_k = j + 1;
-      const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
-      if (res <= a.rtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
+      const double res2 = gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y;
+      const double lim = a.rtol * s_beta;
+      if (res2 <= lim * lim || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
     }
     __syncthreads();
   }
