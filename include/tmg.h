@@ -278,7 +278,9 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels).  TMG_ERR_ARG for an unknown key or
+ * the basis for up to 10 basis vectors; 0: separate kernels), "force_prec" (TMG_PREC_F64, the default,
+ * or TMG_PREC_F32: the force kernels of tmg_force / tmg_force_xy run in FP32 on FP32 copies of X, Y
+ * and the 12-real FP32 links; F is returned in FP64 either way).  TMG_ERR_ARG for an unknown key or
  * value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 

@@ -391,6 +391,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "tc_steps_per_range" && (v == 1 || v == 2 || v == 4)) ctx->c.tc_steps_per_range = v;
     else if (k == "coarse_grid" && v >= 0 && v <= 4096) ctx->c.coarse_grid = v;
     else if (k == "outer_gs_fused" && (v == 0 || v == 1)) ctx->c.outer_gs_fused = v;
+    else if (k == "force_prec" && (v == TMG_PREC_F64 || v == TMG_PREC_F32)) ctx->c.force_prec = v;
     else if (k == "kcycle_grid" && v >= 0 && v <= 4096) ctx->c.kcycle_grid = v;
     else if (k == "cycle_graph" && (v == 0 || v == 1)) {
       ctx->c.cycle_graphs = v;

@@ -16,39 +16,44 @@ namespace tmg {
 
 namespace {
 
-struct M3d { cpx<double> m[9]; };
+template <typename R>
+struct M3 { cpx<R> m[9]; };
 
-__device__ __forceinline__ M3d mmul(const M3d& a, const M3d& b) {
-  M3d r;
+template <typename R>
+__device__ __forceinline__ M3<R> mmul(const M3<R>& a, const M3<R>& b) {
+  M3<R> r;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      cpx<double> acc = a.m[i * 3] * b.m[j];
+      cpx<R> acc = a.m[i * 3] * b.m[j];
       acc = acc + a.m[i * 3 + 1] * b.m[3 + j];
       acc = acc + a.m[i * 3 + 2] * b.m[6 + j];
       r.m[i * 3 + j] = acc;
     }
   return r;
 }
-__device__ __forceinline__ M3d mdag(const M3d& a) {
-  M3d r;
+template <typename R>
+__device__ __forceinline__ M3<R> mdag(const M3<R>& a) {
+  M3<R> r;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) r.m[i * 3 + j] = conj(a.m[j * 3 + i]);
   return r;
 }
-__device__ __forceinline__ M3d mident() {
-  M3d r;
+template <typename R>
+__device__ __forceinline__ M3<R> mident() {
+  M3<R> r;
 #pragma unroll
-  for (int k = 0; k < 9; k++) r.m[k] = mk(k % 4 == 0 ? 1.0 : 0.0, 0.0);
+  for (int k = 0; k < 9; k++) r.m[k] = mk<R>(k % 4 == 0 ? R(1) : R(0), R(0));
   return r;
 }
-__device__ __forceinline__ M3d load_link(const GaugeF64& U, int s, int mu) {
-  Link<double> l;
+template <typename R, class G>
+__device__ __forceinline__ M3<R> load_link(const G& U, int s, int mu) {
+  Link<R> l;
   U.load(s, mu, l);
-  M3d r;
+  M3<R> r;
 #pragma unroll
   for (int k = 0; k < 9; k++) r.m[k] = l.m[k];
   return r;
@@ -61,15 +66,17 @@ __device__ __forceinline__ int plane_index(int a, int b) {
 
 // sigma_ab (a < b) restricted to chirality chi, chiral basis (see k_fields.cu):
 // spatial (j,k): -eps_jkl s_l; (k,t): +s_k for chi = 0, -s_k for chi = 1.
-__device__ __forceinline__ void sigma_chi(int a, int b, int chi, cpx<double> sg[4]) {
+template <typename R>
+__device__ __forceinline__ void sigma_chi(int a, int b, int chi, cpx<R> sg[4]) {
   int l;
-  double sign;
-  if (b == 3) { l = a; sign = chi == 0 ? 1.0 : -1.0; }
-  else { l = 3 - a - b; sign = (a == 0 && b == 2) ? 1.0 : -1.0; }
-  cpx<double> p[4];
-  if (l == 0) { p[0] = mk(0., 0.); p[1] = mk(1., 0.); p[2] = mk(1., 0.); p[3] = mk(0., 0.); }
-  else if (l == 1) { p[0] = mk(0., 0.); p[1] = mk(0., -1.); p[2] = mk(0., 1.); p[3] = mk(0., 0.); }
-  else { p[0] = mk(1., 0.); p[1] = mk(0., 0.); p[2] = mk(0., 0.); p[3] = mk(-1., 0.); }
+  R sign;
+  if (b == 3) { l = a; sign = chi == 0 ? R(1) : R(-1); }
+  else { l = 3 - a - b; sign = (a == 0 && b == 2) ? R(1) : R(-1); }
+  cpx<R> p[4];
+  const R o = 1, z = 0;
+  if (l == 0) { p[0] = mk<R>(z, z); p[1] = mk<R>(o, z); p[2] = mk<R>(o, z); p[3] = mk<R>(z, z); }
+  else if (l == 1) { p[0] = mk<R>(z, z); p[1] = mk<R>(z, -o); p[2] = mk<R>(z, o); p[3] = mk<R>(z, z); }
+  else { p[0] = mk<R>(o, z); p[1] = mk<R>(z, z); p[2] = mk<R>(z, z); p[3] = mk<R>(-o, z); }
 #pragma unroll
   for (int k = 0; k < 4; k++) sg[k] = sign * p[k];
 }
@@ -88,47 +95,54 @@ __device__ __forceinline__ int shifted_site(const Geom& g, const int c[4], int r
   return site_index(g, d);
 }
 
-__global__ void k_force_lambda(Geom g, SpinorF64 X, SpinorF64 Y, double2* __restrict__ lam) {
+template <typename R, class S, typename T2>
+__global__ void k_force_lambda(Geom g, S X, S Y, T2* __restrict__ lam) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  Spinor<double> x, y;
+  Spinor<R> x, y;
   X.load(s, x);
   Y.load(s, y);
   for (int a = 0; a < 4; a++)
     for (int b = a + 1; b < 4; b++) {
       const int p = plane_index(a, b);
-      cpx<double> L[9];
-      for (int k = 0; k < 9; k++) L[k] = mk(0.0, 0.0);
+      cpx<R> L[9];
+      for (int k = 0; k < 9; k++) L[k] = mk<R>(0, 0);
       for (int chi = 0; chi < 2; chi++) {
-        cpx<double> sg[4];
-        sigma_chi(a, b, chi, sg);
+        cpx<R> sg[4];
+        sigma_chi<R>(a, b, chi, sg);
         for (int si = 0; si < 2; si++)
           for (int ti = 0; ti < 2; ti++) {
-            const cpx<double> w = sg[si * 2 + ti];
-            if (w.re == 0.0 && w.im == 0.0) continue;
+            const cpx<R> w = sg[si * 2 + ti];
+            if (w.re == R(0) && w.im == R(0)) continue;
             const int s_ = 2 * chi + si, t_ = 2 * chi + ti;
             for (int bb = 0; bb < 3; bb++)
               for (int aa = 0; aa < 3; aa++)
                 L[bb * 3 + aa] = L[bb * 3 + aa] + w * (y.c[t_ * 3 + bb] * conj(x.c[s_ * 3 + aa]));
           }
       }
-      for (int k = 0; k < 9; k++) lam[((size_t)p * 9 + k) * g.V + s] = make_double2(L[k].re, L[k].im);
+      for (int k = 0; k < 9; k++) {
+        T2 o;
+        o.x = L[k].re;
+        o.y = L[k].im;
+        lam[((size_t)p * 9 + k) * g.V + s] = o;
+      }
     }
 }
 
 // full-spinor (1 + sgn g_mu) applied to p (chiral basis; see spin_project in tmg_internal.cuh)
-__device__ __forceinline__ void proj_full(int mu, int sgn, const Spinor<double>& p, Spinor<double>& o) {
+template <typename R>
+__device__ __forceinline__ void proj_full(int mu, int sgn, const Spinor<R>& p, Spinor<R>& o) {
   // (1 - s g) p = [h ; -s B^dag h], h = p_up - s B p_dn ; here s = -sgn so that (1 + sgn g) is formed
-  cpx<double> h[6];
+  cpx<R> h[6];
   spin_project(mu, -sgn, p, h);
-  Spinor<double> acc;
-  for (int k = 0; k < 12; k++) acc.c[k] = mk(0.0, 0.0);
+  Spinor<R> acc;
+  for (int k = 0; k < 12; k++) acc.c[k] = mk<R>(0, 0);
   spin_reconstruct_add(mu, -sgn, h, acc);
   o = acc;
 }
 
-__global__ void k_force_link(Geom g, GaugeF64 U, SpinorF64 X, SpinorF64 Y, const double2* __restrict__ lam,
-                             double csw, double2* __restrict__ G) {
+template <typename R, class GT, class S, typename T2>
+__global__ void k_force_link(Geom g, GT U, S X, S Y, const T2* __restrict__ lam, R csw, T2* __restrict__ G) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int mu = blockIdx.y;
   if (s >= g.V) return;
@@ -136,19 +150,19 @@ __global__ void k_force_link(Geom g, GaugeF64 U, SpinorF64 X, SpinorF64 Y, const
   site_coords(g, s, c);
   const SiteCoord sc = decode_site(g, s);
   const int sf = nbr_fwd(g, sc, mu);
-  cpx<double> Gm[9];
+  cpx<R> Gm[9];
   // ---- hopping term: G = (i sgn / 2) (A2 - A1)
   {
-    const M3d u = load_link(U, s, mu);
-    const double sgn = (mu == 3 && c[3] == g.L[3] - 1 && g.tbc < 0) ? -1.0 : 1.0;
-    Spinor<double> xs, ys, xf, yf, uy, P, W, ux;
+    const M3<R> u = load_link<R>(U, s, mu);
+    const R sgn = (mu == 3 && c[3] == g.L[3] - 1 && g.tbc < 0) ? R(-1) : R(1);
+    Spinor<R> xs, ys, xf, yf, uy, P, W, ux;
     X.load(s, xs);
     Y.load(s, ys);
     X.load(sf, xf);
     Y.load(sf, yf);
     for (int sp = 0; sp < 4; sp++)
       for (int a = 0; a < 3; a++) {
-        cpx<double> t1 = mk(0.0, 0.0), t2 = mk(0.0, 0.0);
+        cpx<R> t1 = mk<R>(0, 0), t2 = mk<R>(0, 0);
         for (int b = 0; b < 3; b++) {
           t1 = t1 + u.m[a * 3 + b] * yf.c[sp * 3 + b];
           t2 = t2 + u.m[a * 3 + b] * xf.c[sp * 3 + b];
@@ -161,23 +175,23 @@ __global__ void k_force_link(Geom g, GaugeF64 U, SpinorF64 X, SpinorF64 Y, const
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++) {
         // A1[i][j] = sum_s P[s][i] conj(X[s][j]) ; A2[i][j] = sum_s W[s][i] conj(UX[s][j])
-        cpx<double> a1 = mk(0.0, 0.0), a2 = mk(0.0, 0.0);
+        cpx<R> a1 = mk<R>(0, 0), a2 = mk<R>(0, 0);
         for (int sp = 0; sp < 4; sp++) {
           a1 = a1 + P.c[sp * 3 + i] * conj(xs.c[sp * 3 + j]);
           a2 = a2 + W.c[sp * 3 + i] * conj(ux.c[sp * 3 + j]);
         }
-        Gm[i * 3 + j] = mul_i((0.5 * sgn) * (a2 - a1));
+        Gm[i * 3 + j] = mul_i((R(0.5) * sgn) * (a2 - a1));
       }
   }
   // ---- clover term
-  if (csw != 0.0) {
-    const cpx<double> coef = mk(0.0, csw / 16.0);
+  if (csw != R(0)) {
+    const cpx<R> coef = mk<R>(0, csw / R(16));
     for (int nu = 0; nu < 4; nu++) {
       if (nu == mu) continue;
       const int a = min(mu, nu), b = max(mu, nu), p = plane_index(a, b);
       for (int orient = 0; orient < 2; orient++) {
         const int rho = orient == 0 ? a : b, sig = orient == 0 ? b : a;
-        const double sign = orient == 0 ? 1.0 : -1.0;
+        const R sign = orient == 0 ? R(1) : R(-1);
         for (int leaf = 0; leaf < 4; leaf++) {
           for (int k = 0; k < 4; k++) {
             const int dk = c_leaf_sig[leaf][k] ? sig : rho;
@@ -187,41 +201,47 @@ __global__ void k_force_link(Geom g, GaugeF64 U, SpinorF64 X, SpinorF64 Y, const
             yc[rho] = (yc[rho] - c_leaf_or[leaf][k] + 2 * g.L[rho]) % g.L[rho];
             yc[sig] = (yc[sig] - c_leaf_os[leaf][k] + 2 * g.L[sig]) % g.L[sig];
             const int ys = site_index(g, yc);
-            M3d f[4];
+            M3<R> f[4];
             for (int q = 0; q < 4; q++) {
               const int site = shifted_site(g, yc, rho, c_leaf_or[leaf][q], sig, c_leaf_os[leaf][q]);
-              const M3d l = load_link(U, site, c_leaf_sig[leaf][q] ? sig : rho);
+              const M3<R> l = load_link<R>(U, site, c_leaf_sig[leaf][q] ? sig : rho);
               f[q] = c_leaf_dag[leaf][q] ? mdag(l) : l;
             }
-            M3d L;
+            M3<R> L;
             for (int e = 0; e < 9; e++) {
-              const double2 v = lam[((size_t)p * 9 + e) * g.V + ys];
-              L.m[e] = mk(v.x, v.y);
+              const T2 v = lam[((size_t)p * 9 + e) * g.V + ys];
+              L.m[e] = mk<R>(v.x, v.y);
             }
-            M3d after = mident(), before = mident();
+            M3<R> after = mident<R>(), before = mident<R>();
             for (int q = k + 1; q < 4; q++) after = mmul(after, f[q]);
             for (int q = 0; q < k; q++) before = mmul(before, f[q]);
-            M3d M;
-            cpx<double> ph;
+            M3<R> M;
+            cpx<R> ph;
             if (!c_leaf_dag[leaf][k]) {
               M = mmul(mmul(mmul(f[k], after), L), before);
-              ph = mk(0.0, 1.0);
+              ph = mk<R>(0, 1);
             } else {
               M = mmul(mmul(mmul(after, L), before), f[k]);
-              ph = mk(0.0, -1.0);
+              ph = mk<R>(0, -1);
             }
-            const cpx<double> w = (sign * coef) * ph;
+            const cpx<R> w = (sign * coef) * ph;
             for (int e = 0; e < 9; e++) Gm[e] = Gm[e] + w * M.m[e];
           }
         }
       }
     }
   }
-  for (int e = 0; e < 9; e++) G[((size_t)mu * 9 + e) * g.V + s] = make_double2(Gm[e].re, Gm[e].im);
+  for (int e = 0; e < 9; e++) {
+    T2 o;
+    o.x = Gm[e].re;
+    o.y = Gm[e].im;
+    G[((size_t)mu * 9 + e) * g.V + s] = o;
+  }
 }
 
 // F = traceless Hermitian part of -2 G, lexicographic output [V][4][3][3]
-__global__ void k_force_project(Geom g, const double2* __restrict__ G, double2* __restrict__ F) {
+template <typename T2>
+__global__ void k_force_project(Geom g, const T2* __restrict__ G, double2* __restrict__ F) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int mu = blockIdx.y;
   if (s >= g.V) return;
@@ -229,7 +249,7 @@ __global__ void k_force_project(Geom g, const double2* __restrict__ G, double2* 
   site_coords(g, s, c);
   const int lex = lex_index(g, c);
   cpx<double> m[9], h[9];
-  for (int e = 0; e < 9; e++) { const double2 v = G[((size_t)mu * 9 + e) * g.V + s]; m[e] = mk(-2.0 * v.x, -2.0 * v.y); }
+  for (int e = 0; e < 9; e++) { const T2 v = G[((size_t)mu * 9 + e) * g.V + s]; m[e] = mk(-2.0 * v.x, -2.0 * v.y); }
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++) h[i * 3 + j] = 0.5 * (m[i * 3 + j] + conj(m[j * 3 + i]));
   const double tr = (h[0].re + h[4].re + h[8].re) / 3.0;
@@ -241,19 +261,40 @@ __global__ void k_force_project(Geom g, const double2* __restrict__ G, double2* 
 
 }  // namespace
 
-// F (lexicographic [V][4][3][3], device) from internal F64 fields X, Y (tbc/clover from the context)
+// F (lexicographic [V][4][3][3], device) from internal F64 fields X, Y (tbc/clover from the context).
+// With c.force_prec == TMG_PREC_F32 the kernels run in FP32 on FP32 copies of X, Y and the 12-real
+// FP32 links; F is written in FP64 either way.
 void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex) {
   const size_t V = c.g.V;
+  const dim3 grid1((c.g.V + 127) / 128), grid4((c.g.V + 127) / 128, 4);
+  if (c.force_prec == TMG_PREC_F32) {
+    c.fw_t.alloc(V * (6 * 9 + 4 * 9) * sizeof(float2) + 2 * 12 * V * sizeof(float2));
+    float2* lam = c.fw_t.as<float2>();
+    float2* G = lam + V * 6 * 9;
+    float2* x32 = G + V * 4 * 9;
+    float2* y32 = x32 + 12 * V;
+    convert_field(c, X, TMG_PREC_F64, x32, TMG_PREC_F32, 12 * V);
+    convert_field(c, Y, TMG_PREC_F64, y32, TMG_PREC_F32, 12 * V);
+    const SpinorF32 xs{(float4*)x32, c.g.V}, ys{(float4*)y32, c.g.V};
+    ++c.launches, k_force_lambda<float><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
+    TMG_CHECK_LAUNCH();
+    ++c.launches, k_force_link<float><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF32{c.op[1].U.as<float4>(), c.g.V}, xs, ys, lam,
+                                                                   (float)c.csw, G);
+    TMG_CHECK_LAUNCH();
+    ++c.launches, k_force_project<<<grid4, 128, 0, c.stream>>>(c.g, (const float2*)G, (double2*)F_lex);
+    TMG_CHECK_LAUNCH();
+    return;
+  }
   c.fw_t.alloc(V * (6 * 9 + 4 * 9) * sizeof(double2));
   double2* lam = c.fw_t.as<double2>();
   double2* G = lam + V * 6 * 9;
   const SpinorF64 xs{(double2*)X, c.g.V}, ys{(double2*)Y, c.g.V};
-  ++c.launches, k_force_lambda<<<(c.g.V + 127) / 128, 128, 0, c.stream>>>(c.g, xs, ys, lam);
+  ++c.launches, k_force_lambda<double><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
   TMG_CHECK_LAUNCH();
-  ++c.launches, k_force_link<<<dim3((c.g.V + 127) / 128, 4), 128, 0, c.stream>>>(c.g, GaugeF64{c.op[0].U.as<double2>(), c.g.V},
-                                                                            xs, ys, lam, c.csw, G);
+  ++c.launches, k_force_link<double><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF64{c.op[0].U.as<double2>(), c.g.V}, xs, ys, lam,
+                                                                  c.csw, G);
   TMG_CHECK_LAUNCH();
-  ++c.launches, k_force_project<<<dim3((c.g.V + 127) / 128, 4), 128, 0, c.stream>>>(c.g, G, (double2*)F_lex);
+  ++c.launches, k_force_project<<<grid4, 128, 0, c.stream>>>(c.g, (const double2*)G, (double2*)F_lex);
   TMG_CHECK_LAUNCH();
 }
 

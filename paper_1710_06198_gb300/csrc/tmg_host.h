@@ -183,6 +183,7 @@ struct Ctx {
   int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
   int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
   int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
+  int force_prec = TMG_PREC_F64;   // precision of the force kernels (TMG_PREC_F64 or TMG_PREC_F32)
   int outer_gs_fused = 1;       // outer FGMRES: fuse pass 1's update with pass 2's dot products
   int coarse_grid = 0;          // CTAs of the persistent coarse GMRES (0: coarse_ctas_per_sm x SMs)
   int kcycle_grid = 0;          // CTAs of the persistent K-cycle (0: kcycle_ctas_per_sm x SMs)

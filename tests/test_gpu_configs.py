@@ -8,8 +8,8 @@ At these sizes the oracle cannot solve, so parity is checked on what it can comp
   and solutions are judged by their true residual, computed with the oracle's operator on the
   whole lattice where that is affordable (16^3 x 32, 16^4) and with the GPU FP64 operator (itself
   compared site by site with the oracle at the same size) on 24^3 x 48;
-* the force on 16^4 against central finite differences of the action (32 random su(3)
-  directions, step 1e-5), each action from a multigrid solve on the rotated field warm-started from
+* the force on 16^4 (FP64 force kernels, mixed-precision solves) against central finite
+  differences of the action (32 random su(3) directions, step 1e-5), each action from a multigrid solve on the rotated field warm-started from
   the solution on the unrotated field.
 """
 import numpy as np
