@@ -68,3 +68,15 @@ def test_level2_defaults_and_null_context(L):
     assert L.tmg_setup_level2(None, ctypes.byref(q), None, 0) == -1
     assert L.tmg_kcycle(None, None, None, 0.0, 0, 0, 0) == -1
     assert L.tmg_coarse_apply2(None, None, None, 0.0, 0, 0) == -1
+
+
+def test_doublet_tuning_and_graph_entries_reject_null_context(L):
+    assert L.tmg_sap_nd(None, None, None, 0, 0) == -1
+    assert L.tmg_coarse_apply_nd(None, None, None, 0, 0) == -1
+    assert L.tmg_coarse_solve_nd(None, None, None, 0, 0) == -1
+    assert L.tmg_kcycle_nd(None, None, None, 0, 0, 0) == -1
+    assert L.tmg_cycle_nd(None, None, None, 0) == -1
+    assert L.tmg_autotune(None, None) == -1
+    assert L.tmg_graph_count(None, None) == -1
+    assert L.tmg_tune(None, b"cycle_graph", 1.0) == -1
+    assert L.tmg_coarse_solve_noalloc(None, None, None, 0.0, 0) == -1
