@@ -74,8 +74,18 @@ const char *tmg_version(void);
 
 /* Load the gauge field U (FP64, [V][4][3][3] complex) and set the time boundary sign t_bc
  * (+1 periodic, -1 antiperiodic).  Rebuilds the clover field on the device (Sec. 1.1: the
- * clover-improved operator) and the FP32 / FP16 copies of links and clover. */
+ * clover-improved operator) and the FP32 / FP16 copies of links and clover.  Every link must be
+ * in SU(3) (the compressed formats rebuild the third row from the first two): a link with
+ * max(|U U^dag - 1|, |det U - 1|) > TMG_SU3_TOL, or a non-finite entry, returns TMG_ERR_ARG
+ * (the message names the site and direction) and leaves the loaded field unchanged. */
+#define TMG_SU3_TOL 1e-8
 int tmg_load_gauge(tmg_ctx *ctx, const double *U, int where, int t_bc);
+
+/* Host-only SU(3) check (needs no context and no GPU): the largest defect
+ * max(|U U^dag - 1|_max, |det U - 1|) over n_links FP64 links ([n_links][3][3] complex, host
+ * memory) into *worst and the index of that link into *worst_index (either may be NULL).
+ * TMG_OK if it is <= TMG_SU3_TOL, TMG_ERR_ARG otherwise or for a NULL U / negative count. */
+int tmg_check_links(const double *U, long long n_links, double *worst, long long *worst_index);
 
 /* Operator parameters: kappa (m0 = 1/(2 kappa) - 4), c_sw, the twist mu (Sec. 1.1) and the
  * non-degenerate doublet's mubar, epsbar (Eq. 2).  Must precede tmg_load_gauge's clover build or

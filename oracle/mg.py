@@ -31,7 +31,11 @@ project adopts (listed with their reasons in the design notes):
 
 Pinned by (tests/test_oracle_mg.py): P^dag P = I, G5 P = P G5_c, D_c x_c = P^dag D P x_c,
 D_c(mu) - D_c(0) = i mu G5_c, D_c^dag = G5_c D_c G5_c, the dense SAP error propagator, exact
-coarse correction with full-rank P, and dense LU solutions.
+coarse correction with full-rank P, dense LU solutions, and the cycle's dense error propagator
+I - C D = (I - M D)^k (I - P D_c^-1 P^dag D) of Eq. 1 with exact inner solves.
+
+Parity unpinned: Hierarchy.setup.  The adaptive setup has many correct results (any test vectors
+that span the near-null space do); it is compared only through what it feeds, never by value.
 """
 from __future__ import annotations
 
@@ -359,6 +363,7 @@ class Hierarchy:
         return self.smooth(r, z, mu)
 
     def setup(self, v0):
+        """Adaptive setup (Sec. 1.1, Sec. 2).  Parity unpinned: its result is not unique."""
         v = np.array(v0, dtype=np.complex128, copy=True)
         for _ in range(self.mg.n_init):
             for j in range(v.shape[0]):

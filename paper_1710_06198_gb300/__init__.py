@@ -100,6 +100,7 @@ _SIGS = {
     "tmg_cycle_nd": [_P, _P, _P, _I],
     "tmg_autotune": [_P, ctypes.POINTER(_D)],
     "tmg_graph_count": [_P, ctypes.POINTER(_I)],
+    "tmg_check_links": [_P, ctypes.c_longlong, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
@@ -466,3 +467,13 @@ def graph_count(ctx: "Context"):
 
 def version():
     return lib().tmg_version().decode()
+
+
+def check_links(U):
+    """(ok, worst defect, index of the worst link) of a host field of SU(3) links [..., 3, 3]
+    (complex128); runs on the host, needs no GPU."""
+    if not isinstance(U, np.ndarray) or U.dtype != np.complex128 or not U.flags.c_contiguous:
+        raise TypeError("host arrays must be C-contiguous complex128 numpy arrays")
+    w, i = ctypes.c_double(), ctypes.c_longlong()
+    rc = lib().tmg_check_links(ctypes.c_void_p(U.ctypes.data), U.size // 9, ctypes.byref(w), ctypes.byref(i))
+    return rc == 0, w.value, i.value

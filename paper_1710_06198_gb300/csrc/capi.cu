@@ -1,6 +1,7 @@
 // C ABI of libtmg (declared in include/tmg.h).  Every entry point validates its arguments, runs
 // the work on the context stream and converts exceptions from the launchers into status codes.
 #include <chrono>
+#include <string>
 #include <cstring>
 #include <new>
 
@@ -185,12 +186,31 @@ int tmg_set_params(tmg_ctx* ctx, double kappa, double csw, double mu, double mub
   });
 }
 
+int tmg_check_links(const double* U, long long n_links, double* worst, long long* worst_index) {
+  if (!U || n_links < 0) return TMG_ERR_ARG;
+  long long at = -1;
+  const double w = tmg::su3_defect_host(U, (size_t)n_links, &at);
+  if (worst) *worst = w;
+  if (worst_index) *worst_index = at;
+  return w <= TMG_SU3_TOL ? TMG_OK : TMG_ERR_ARG;
+}
+
 int tmg_load_gauge(tmg_ctx* ctx, const double* U, int where, int t_bc) {
   return guarded(ctx, [&]() -> int {
     if (!U || !valid_where(where) || (t_bc != 1 && t_bc != -1)) return fail(ctx, TMG_ERR_ARG, "tmg_load_gauge: bad argument");
     Ctx& c = ctx->c;
-    c.g.tbc = t_bc;
     const size_t n = (size_t)c.g.V * 72;
+    // every link must be special unitary: the compressed link formats rebuild row 2 from rows 0
+    // and 1, which is exact for SU(3) only
+    long long at = -1;
+    double defect = 0.0;
+    if (where == TMG_HOST) defect = su3_defect_host(U, (size_t)c.g.V * 4, &at);
+    else defect = su3_defect_device(c, U, (size_t)c.g.V * 4, &at);
+    if (!(defect <= TMG_SU3_TOL))
+      return fail(ctx, TMG_ERR_ARG, "tmg_load_gauge: link " + std::to_string(at) + " (site " + std::to_string(at / 4) +
+                                        ", direction " + std::to_string(at % 4) + ") is not in SU(3): max(|U U^dag - 1|, |det U - 1|) = " +
+                                        std::to_string(defect));
+    c.g.tbc = t_bc;
     const double* d = stage_in(c, c.U_lex, U, n, where);
     gauge_lex_to_internal(c, d);
     build_clover(c);

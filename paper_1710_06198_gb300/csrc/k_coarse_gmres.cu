@@ -968,17 +968,24 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
   }
 }
 
+// CTAs of the persistent coarse GMRES: the "coarse_grid" knob if set, else "coarse_ctas_per_sm" per
+// SM (at most one CTA per coarse site), both capped by the kernel's residency.  The allocating and
+// the allocation-free launch both size their grid here, so they reduce in the same order.
+template <typename S>
+int coarse_grid_ctas(Ctx& c) {
+  static int max_per_sm[2] = {-1, -1};
+  int& mps = max_per_sm[sizeof(S) == 8];
+  if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
+  return c.coarse_grid > 0 ? std::max(1, std::min(c.coarse_grid, c.sms * std::max(1, mps)))
+                           : std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
+}
+
 template <typename S>
 void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 1, double epsbar = 0.0) {
   using T2 = typename CplxT<S>::T2;
   const int m = std::min(c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)nf * c.cl.nc * c.cl.nd;
-  static int max_per_sm[2] = {-1, -1};
-  int& mps = max_per_sm[sizeof(S) == 8];
-  if (mps < 0) TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
-  const int G = c.coarse_grid > 0
-                    ? std::max(1, std::min(c.coarse_grid, c.sms * std::max(1, mps)))
-                    : std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
+  const int G = coarse_grid_ctas<S>(c);
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
   c.cw_w.alloc(10 * n * sizeof(T2));
   c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
@@ -1011,13 +1018,6 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   void* args[] = {&a};
   ++c.launches;
   TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
-}
-
-template <typename S>
-int grid_size(Ctx& c) {
-  int mps = 0;
-  TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps, k_coarse_gmres<S>, 256, 0));
-  return std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, 2))));
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -1077,13 +1077,13 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
 
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cp) {
   size_t off[8];
-  if (cp == TMG_PREC_F64) return scratch_layout<double>(c, grid_size<double>(c), off);
-  return scratch_layout<float>(c, grid_size<float>(c), off);
+  if (cp == TMG_PREC_F64) return scratch_layout<double>(c, coarse_grid_ctas<double>(c), off);
+  return scratch_layout<float>(c, coarse_grid_ctas<float>(c), off);
 }
 
 void coarse_gmres_on_scratch(Ctx& c, int cp, const void* b, void* x, double mu, void* scratch) {
-  if (cp == TMG_PREC_F64) launch_on<double>(c, b, x, mu, c.cl.Dc64.p, (char*)scratch, grid_size<double>(c));
-  else launch_on<float>(c, b, x, mu, c.cl.Dc32.p, (char*)scratch, grid_size<float>(c));
+  if (cp == TMG_PREC_F64) launch_on<double>(c, b, x, mu, c.cl.Dc64.p, (char*)scratch, coarse_grid_ctas<double>(c));
+  else launch_on<float>(c, b, x, mu, c.cl.Dc32.p, (char*)scratch, coarse_grid_ctas<float>(c));
 }
 
 void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {

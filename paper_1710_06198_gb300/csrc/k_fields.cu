@@ -1,6 +1,8 @@
 // Field layout conversion, clover construction and complex BLAS kernels of libtmg.
 #include <algorithm>
 #include <cmath>
+#include <thread>
+#include <vector>
 
 #include "tmg_host.h"
 
@@ -10,6 +12,107 @@ static inline int grid_for(const Ctx& c, size_t n, int threads = 256) {
   size_t b = (n + threads - 1) / threads;
   size_t cap = (size_t)c.sms * 16;
   return (int)std::max<size_t>(1, std::min(b, cap));
+}
+
+// ------------------------------------------------------------------ SU(3) check of a loaded field
+// max(|U U^dag - 1|_max, |det U - 1|) of one link (row-major 3x3, interleaved re/im); a non-finite
+// entry gives +inf.
+__host__ __device__ inline double su3_defect_one(const double* u) {
+  double d = 0.0;
+  for (int k = 0; k < 18; k++)
+    if (!(u[k] == u[k]) || u[k] > 1e300 || u[k] < -1e300) return HUGE_VAL;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      double re = (i == j) ? -1.0 : 0.0, im = 0.0;
+      for (int k = 0; k < 3; k++) {   // sum_k U_ik conj(U_jk)
+        const double ar = u[2 * (3 * i + k)], ai = u[2 * (3 * i + k) + 1];
+        const double br = u[2 * (3 * j + k)], bi = u[2 * (3 * j + k) + 1];
+        re += ar * br + ai * bi;
+        im += ai * br - ar * bi;
+      }
+      d = fmax(d, fmax(fabs(re), fabs(im)));
+    }
+  auto R = [&](int i, int j) { return u[2 * (3 * i + j)]; };
+  auto I = [&](int i, int j) { return u[2 * (3 * i + j) + 1]; };
+  // det = sum over the first row of U_0j times its cofactor
+  double dr = 0.0, di = 0.0;
+  for (int j = 0; j < 3; j++) {
+    const int a = (j + 1) % 3, b = (j + 2) % 3;
+    const double cr = R(1, a) * R(2, b) - I(1, a) * I(2, b) - (R(1, b) * R(2, a) - I(1, b) * I(2, a));
+    const double ci = R(1, a) * I(2, b) + I(1, a) * R(2, b) - (R(1, b) * I(2, a) + I(1, b) * R(2, a));
+    dr += R(0, j) * cr - I(0, j) * ci;
+    di += R(0, j) * ci + I(0, j) * cr;
+  }
+  return fmax(d, hypot(dr - 1.0, di));
+}
+
+double su3_defect_host(const double* U, size_t n_links, long long* at) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::max<size_t>(1, std::min<size_t>({(size_t)(hw ? hw : 1), (size_t)32, n_links / 4096 + 1}));
+  std::vector<double> worst(nt, 0.0);
+  std::vector<long long> idx(nt, -1);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; t++)
+    th.emplace_back([&, t] {
+      const size_t a = n_links * t / nt, b = n_links * (t + 1) / nt;
+      for (size_t l = a; l < b; l++) {
+        const double d = su3_defect_one(U + 18 * l);
+        if (d > worst[t] || idx[t] < 0) { worst[t] = d; idx[t] = (long long)l; }
+      }
+    });
+  for (auto& x : th) x.join();
+  double w = 0.0;
+  long long i = -1;
+  for (int t = 0; t < nt; t++)
+    if (idx[t] >= 0 && (i < 0 || worst[t] > w)) { w = worst[t]; i = idx[t]; }
+  if (at) *at = i;
+  return w;
+}
+
+// per-CTA maximum defect and the index where it occurs
+__global__ void k_su3_defect(const double* __restrict__ U, size_t n, double* __restrict__ wout, long long* __restrict__ iout) {
+  double w = -1.0;
+  long long wi = -1;
+  for (size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+    double u[18];
+    for (int k = 0; k < 18; k++) u[k] = U[18 * l + k];
+    const double d = su3_defect_one(u);
+    if (d > w) { w = d; wi = (long long)l; }
+  }
+  __shared__ double sw[256];
+  __shared__ long long si[256];
+  sw[threadIdx.x] = w;
+  si[threadIdx.x] = wi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o && sw[threadIdx.x + o] > sw[threadIdx.x]) {
+      sw[threadIdx.x] = sw[threadIdx.x + o];
+      si[threadIdx.x] = si[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { wout[blockIdx.x] = sw[0]; iout[blockIdx.x] = si[0]; }
+}
+
+double su3_defect_device(Ctx& c, const double* U_dev, size_t n_links, long long* at) {
+  const int G = grid_for(c, n_links);
+  DBuf buf;
+  buf.alloc((size_t)G * (sizeof(double) + sizeof(long long)));
+  double* w = buf.as<double>();
+  long long* ix = reinterpret_cast<long long*>(w + G);
+  ++c.launches, k_su3_defect<<<G, 256, 0, c.stream>>>(U_dev, n_links, w, ix);
+  TMG_CHECK_LAUNCH();
+  std::vector<double> hw(G);
+  std::vector<long long> hi(G);
+  TMG_CUDA(cudaMemcpyAsync(hw.data(), w, G * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TMG_CUDA(cudaMemcpyAsync(hi.data(), ix, G * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+  double best = 0.0;
+  long long bi = -1;
+  for (int b = 0; b < G; b++)
+    if (hi[b] >= 0 && (bi < 0 || hw[b] > best)) { best = hw[b]; bi = hi[b]; }
+  if (at) *at = bi;
+  return best;
 }
 
 // ------------------------------------------------------------------ gauge field

@@ -12,7 +12,10 @@
 // cached; that lookup happens in the first call on each device, which should therefore come before
 // any stream capture.  All calls share the array: two calls that overlap on the GPU (different
 // streams, or different contexts on one device) race on it.
+#include <exception>
 #include <mutex>
+#include <new>
+#include <string>
 
 #include "tmg_host.h"
 
@@ -105,5 +108,11 @@ extern "C" int tmg_coarse_solve_noalloc(tmg_ctx* ctx, const double* b, double* x
   } catch (const tmg::Error& e) {
     c.err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    c.err = "tmg_coarse_solve_noalloc: host allocation failed";
+    return TMG_ERR_OOM;
+  } catch (const std::exception& e) {
+    c.err = std::string("tmg_coarse_solve_noalloc: ") + e.what();
+    return TMG_ERR_CUDA;
   }
 }

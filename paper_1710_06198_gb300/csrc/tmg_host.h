@@ -214,6 +214,11 @@ struct ProfScope {
 };
 
 // ---------------------------------------------------------------- launchers (k_fields.cu)
+// Largest SU(3) defect max(|U U^dag - 1|_max, |det U - 1|) over n_links FP64 3x3 complex links
+// ([n][3][3] interleaved), on the host (threads) or on the device (U a device pointer); *at gets
+// the index of the worst link (the first NaN link if there is one; NaN makes the result NaN).
+double su3_defect_host(const double* U, size_t n_links, long long* at);
+double su3_defect_device(Ctx& c, const double* U_dev, size_t n_links, long long* at);
 void gauge_lex_to_internal(Ctx& c, const double* lex_dev);
 void build_clover(Ctx& c);
 void convert_op_precisions(Ctx& c);

@@ -80,3 +80,22 @@ def test_doublet_tuning_and_graph_entries_reject_null_context(L):
     assert L.tmg_graph_count(None, None) == -1
     assert L.tmg_tune(None, b"cycle_graph", 1.0) == -1
     assert L.tmg_coarse_solve_noalloc(None, None, None, 0.0, 0) == -1
+
+
+def test_check_links_accepts_su3_and_names_the_bad_link(L):
+    """tmg_check_links (the host-side check behind tmg_load_gauge): the synthetic SU(3) fields pass;
+    a link scaled by 1.001, one with a unit-modulus phase on the whole matrix (unitary but det != 1),
+    and one with a NaN each fail, with the index of the bad link reported."""
+    import numpy as np
+    from synth import fields
+    U = fields.gauge_field((4, 4, 4, 4), 0.4, 120)
+    ok, w, _ = tmg.check_links(U)
+    assert ok and w < 1e-12
+    flat = U.reshape(-1, 3, 3)
+    for k, spoil in ((17, lambda u: 1.001 * u), (203, lambda u: np.exp(0.3j) * u), (511, lambda u: u * np.nan)):
+        V = flat.copy()
+        V[k] = spoil(V[k])
+        ok, w, i = tmg.check_links(V.reshape(U.shape))
+        assert not ok and i == k and not (w <= 1e-8)
+    h = ctypes.c_double()
+    assert L.tmg_check_links(None, 4, ctypes.byref(h), None) != 0

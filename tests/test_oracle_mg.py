@@ -197,3 +197,52 @@ def test_two_level_solve_against_dense_lu():
     y, _, _ = H.solve(dirac.apply_g5(x1), tol=1e-12)
     want = np.linalg.solve(D.conj().T @ D, b.ravel())
     assert rel(y.ravel(), want) < 1e-8
+
+
+def test_cycle_error_propagator_is_eq1_product():
+    """Eq. 1 fixes the order of the two factors: with exact block solves and an exact coarse
+    solve, the error propagator of one cycle applied to the zero initial guess is
+        I - C D = (I - M D)^k (I - P D_c^-1 P^dag D),
+    with one SAP sweep's propagator (I - K1 D)(I - K0 D) (colour 0 first), K_c the sum of the
+    colour-c block inverses.  The cycle is linear once its inner solves are exact, so the identity
+    is checked on random errors e (r = D e).  Swapping the factors (smoothing first), starting the
+    smoother from zero instead of from the coarse correction, or dropping a sweep all fail it."""
+    dims, bdims, nv, k = (4, 4, 4, 4), (2, 2, 2, 2), 2, 2
+    U = fields.gauge_field(dims, 0.3, 110)
+    p = _params(m0=0.4, mu=0.05)
+    # the GMRES coarse solve is exact when it may take as many steps as D_c has rows (16 x 4)
+    prm = mg.MGParams(block=bdims, agg=bdims, nv=nv, sap_sweeps=k, sap_mr=120, coarse_m=64,
+                      coarse_rtol=1e-15)
+    H = mg.Hierarchy(U, p, prm)
+    H.set_vectors(fields.gaussian_spinor(dims, 111, n=nv))
+    shape = fields.lattice_shape(dims) + (4, 3)
+    D = dirac.dense_matrix(H.D, shape)
+    n = D.shape[0]
+    # dense P from the oracle's prolongation of unit coarse vectors; dense D_c = P^dag D P
+    clat = H.P.coarse_lat + (2 * nv,)
+    nc = int(np.prod(clat))
+    Pm = np.stack([mg.prolong(H.P, e.reshape(clat)).ravel() for e in np.eye(nc)], axis=1)
+    Ac = Pm.conj().T @ D @ Pm
+    cgc = np.eye(n) - Pm @ np.linalg.solve(Ac, Pm.conj().T @ D)
+    col = np.repeat(mg.block_colour(fields.lattice_shape(dims), bdims).ravel(), 12)
+    bid = mg.coords(fields.lattice_shape(dims))
+    blk = np.repeat(sum((bid[mu] // bdims[mu]) * (10 ** mu) for mu in range(4)).ravel(), 12)
+    sweep = np.eye(n)
+    for c in (0, 1):
+        Kc = np.zeros_like(D)
+        for bval in np.unique(blk[col == c]):
+            idx = np.where(blk == bval)[0]
+            Kc[np.ix_(idx, idx)] = np.linalg.inv(D[np.ix_(idx, idx)])
+        sweep = (np.eye(n) - Kc @ D) @ sweep
+    smooth = np.linalg.matrix_power(sweep, k)
+    want_prop = smooth @ cgc
+    wrong = {"smoothing first": cgc @ smooth, "smoother from zero": smooth,
+             "one sweep fewer": np.linalg.matrix_power(sweep, k - 1) @ cgc}
+    for seed in (112, 113):
+        e = fields.gaussian_spinor(dims, seed).ravel()
+        r = (D @ e).reshape(shape)
+        got = e - H.cycle(r).ravel()
+        want = want_prop @ e
+        assert rel(got, want) < 1e-10
+        for name, Wp in wrong.items():
+            assert rel(Wp @ e, want) > 1e-3, name

@@ -19,8 +19,10 @@ tmg = pytest.importorskip("paper_1710_06198_gb300")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [tmg.PREC_F64, tmg.PREC_F32])
-def test_coarse_solve_noalloc_matches_allocating_entry(prec):
+@pytest.mark.parametrize("prec,grid", [(tmg.PREC_F64, 0), (tmg.PREC_F32, 0), (tmg.PREC_F64, 8), (tmg.PREC_F32, 8)])
+def test_coarse_solve_noalloc_matches_allocating_entry(prec, grid):
+    """grid > 0 sets the coarse solve's CTA count first (tmg_tune "coarse_grid"): both entry
+    points must then launch the same grid and so agree to the same tolerance."""
     torch = pytest.importorskip("torch")
     dims, block, nv = (8, 8, 4, 4), (4, 4, 2, 2), 4
     U = fields.gauge_field(dims, 0.4, 71)
@@ -32,6 +34,8 @@ def test_coarse_solve_noalloc_matches_allocating_entry(prec):
     prm.nv, prm.n_init, prm.n_iter = nv, 2, 0
     prm.coarse_m, prm.coarse_rtol = 25, 1e-3
     ctx.setup(fields.gaussian_spinor(dims, 72, n=nv), prm)
+    if grid:
+        ctx.tune("coarse_grid", grid)
     L = tmg.lib()
     tol = 1e-12 if prec == tmg.PREC_F64 else 1e-6
     for call, seed in enumerate((73, 74)):
