@@ -247,6 +247,48 @@ int tmg_solve(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double 
 int tmg_force_xy(tmg_ctx *ctx, const double *X, const double *Y, double *F, int where);
 int tmg_force(tmg_ctx *ctx, const double *phi, double *F, double tol, double *action, tmg_stats *stats, int where);
 
+/* Link update U_mu(x) <- exp(i step sum_a omega_a(x, mu) lambda_a / 2) U_mu(x) (lambda_a the Gell-Mann
+ * matrices; the left-multiplied su(3) variation in which the force below is defined, i.e. the
+ * molecular-dynamics link update of the HMC of Sec. 2).  omega: [V][4][8] real FP64, lexicographic
+ * sites, host or device per `where`.  Computed in FP64 on the device (exp by Taylor series with
+ * scaling and squaring, the product projected back onto SU(3)); the clover field and the compressed
+ * copies are rebuilt, and an existing multigrid keeps its P but gets D_c (and D_cc) rebuilt for
+ * the new field.  A following tmg_setup_update adapts P itself. */
+int tmg_rotate_gauge(tmg_ctx *ctx, const double *omega, double step, int where);
+
+/* Setup update (Sec. 2: after the gauge field has changed, the previous subspace is refined by one
+ * setup iteration instead of a new setup): n_iter passes of v_j <- normalise(cycle(v_j)) on the
+ * current operator, starting from the test vectors the last tmg_setup kept, each followed by a
+ * rebuild of P and D_c; with three levels the level-2 basis gets n_iter passes of the level-1
+ * cycle too.  n_iter = 0 only rebuilds P and D_c.  TMG_ERR_STATE without an earlier setup. */
+int tmg_setup_update(tmg_ctx *ctx, int n_iter);
+
+/* Pseudofermion action S = phi^dag (D D^dag)^-1 phi = ||Y||^2, Y = D(mu)^-1 phi (Sec. 1.1, the
+ * monomials of Sec. 2): one mixed-precision multigrid solve to tolerance tol.  phi, Y: FP64 fine
+ * spinors (Y is written).  Y is what tmg_pf_force needs: the force is recomputed from it rather
+ * than kept from the action call. */
+int tmg_pf_action(tmg_ctx *ctx, const double *phi, double *Y, double tol, double *S, tmg_stats *stats, int where);
+
+/* Force of that action from Y: solves X = D(mu)^-dag Y = g5 D(-mu)^-1 g5 Y (the second step of the
+ * two-step D^dag D solve of Sec. 1.1) and writes f[V][4][8] = tr(lambda_a / 2 F_mu(x)), the su(3)
+ * coefficients of the traceless Hermitian F with dS/dt = sum tr(H F) under U -> exp(i t H) U, so
+ * that dS/domega_a(x, mu) = f_a(x, mu) at omega = 0 for tmg_rotate_gauge's parametrisation.
+ * Force kernels per "force_prec" (tmg_tune). */
+int tmg_pf_force(tmg_ctx *ctx, const double *Y, double *f, double tol, tmg_stats *stats, int where);
+
+/* sigma_min(D_W) = min |lambda(Q)|, Q = g5 D_W at mu = 0 (the smallest singular value of the Wilson-clover
+ * operator that fixes kappa in the workloads; the hermitian Q of Sec. 2, Eq. 3): Lanczos with full
+ * reorthogonalisation on (Q^2 + mu_s^2)^-1 = (D(mu_s)^dag D(mu_s))^-1, each product computed by the
+ * two-step solve of Sec. 1.1 (D(-mu_s) u = g5 b, then D(mu_s) v = g5 u) with solver `method`
+ * (TMG_SOLVE_MG_F64 / MG_MIXED / CG_F64) to relative residual solve_tol.  The largest Ritz value
+ * theta gives sigma = sqrt(1/theta - mu_s^2).  start: FP64 fine spinor (host/device); at most
+ * max_steps (2..64) Lanczos steps, stopping once the Ritz residual is <= rtol theta.  Writes sigma,
+ * the last relative Ritz residual and the number of solves; TMG_ERR_NOCONV if rtol was not reached
+ * (sigma still holds the estimate).  mu_s > 0 keeps every solve well posed; choose it near the
+ * expected sigma (1/theta - mu_s^2 loses relative accuracy when mu_s >> sigma). */
+int tmg_sigma_min(tmg_ctx *ctx, const double *start, double mu_s, int max_steps, double rtol, double solve_tol,
+                  int method, double *sigma, double *ritz_res, int *solves, int where);
+
 /* Time `n_iter` back-to-back launches of the dslash kernel (y = D x, one column, storage
  * precision prec) on the context stream with CUDA events; writes the mean milliseconds per
  * launch.  Inputs are the library's internal fields (random data is not needed: the timing
@@ -288,9 +330,10 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels), "force_prec" (TMG_PREC_F64, the default,
- * or TMG_PREC_F32: the force kernels of tmg_force / tmg_force_xy run in FP32 on FP32 copies of X, Y
- * and the 12-real FP32 links; F is returned in FP64 either way).  TMG_ERR_ARG for an unknown key or
+ * the basis for up to 10 basis vectors; 0: separate kernels), "force_prec" (TMG_PREC_F32, the default:
+ * the force kernels of tmg_force / tmg_force_xy / tmg_pf_force read FP32 copies of X, Y and the
+ * 12-real FP32 links and sum every product in FP64; TMG_PREC_F64: FP64 inputs; F is returned in
+ * FP64 either way).  TMG_ERR_ARG for an unknown key or
  * value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 

@@ -100,6 +100,11 @@ _SIGS = {
     "tmg_cycle_nd": [_P, _P, _P, _I],
     "tmg_autotune": [_P, ctypes.POINTER(_D)],
     "tmg_graph_count": [_P, ctypes.POINTER(_I)],
+    "tmg_rotate_gauge": [_P, _P, _D, _I],
+    "tmg_setup_update": [_P, _I],
+    "tmg_pf_action": [_P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(Stats), _I],
+    "tmg_pf_force": [_P, _P, _P, _D, ctypes.POINTER(Stats), _I],
+    "tmg_sigma_min": [_P, _P, _D, _I, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), _I],
     "tmg_check_links": [_P, ctypes.c_longlong, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
 
@@ -136,6 +141,25 @@ def _ptr(a):
     if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous:
         raise TypeError("host arrays must be C-contiguous complex128 numpy arrays")
     return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+def _ptr_real(a):
+    """(pointer, where) of a float64 numpy array or CUDA torch tensor."""
+    if _is_torch_cuda(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("device arrays must be contiguous float64 torch tensors")
+        return ctypes.c_void_p(a.data_ptr()), DEVICE
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("host arrays must be C-contiguous float64 numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+def _empty_real_like(a, shape):
+    if _is_torch_cuda(a):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=a.device)
+    return np.empty(shape, dtype=np.float64)
 
 
 def _empty_like(a, shape):
@@ -204,6 +228,46 @@ class Context:
     def load_gauge(self, U, t_bc=-1):
         p, wh = _ptr(U)
         self._check(lib().tmg_load_gauge(self._h, p, wh, int(t_bc)))
+        self.gauge_version = getattr(self, "gauge_version", 0) + 1
+
+    def rotate_gauge(self, omega, step=1.0):
+        """U_mu(x) <- exp(i step omega(x, mu) . lambda / 2) U_mu(x); omega float64 [T, Z, Y, X, 4, 8]."""
+        p, wh = _ptr_real(omega)
+        self._check(lib().tmg_rotate_gauge(self._h, p, float(step), wh))
+        self.gauge_version = getattr(self, "gauge_version", 0) + 1
+
+    def setup_update(self, n_iter=1):
+        """Refine the last setup's test vectors by n_iter cycle iterations on the current field."""
+        self._check(lib().tmg_setup_update(self._h, int(n_iter)))
+
+    def pf_action(self, phi, tol=1e-10):
+        """(S, Y, stats): S = ||D^-1 phi||^2 and the solution Y = D^-1 phi."""
+        Y = _empty_like(phi, phi.shape)
+        pp, wh = _ptr(phi)
+        py, _ = _ptr(Y)
+        S = ctypes.c_double()
+        st = Stats()
+        self._check(lib().tmg_pf_action(self._h, pp, py, float(tol), ctypes.byref(S), ctypes.byref(st), wh))
+        return S.value, Y, st.as_dict()
+
+    def pf_force(self, Y, tol=1e-10):
+        """(f, stats): su(3) force coefficients f[T, Z, Y, X, 4, 8] of S from its solution Y."""
+        f = _empty_real_like(Y, self.lat + (4, 8))
+        py, wh = _ptr(Y)
+        pf, _ = _ptr_real(f)
+        st = Stats()
+        self._check(lib().tmg_pf_force(self._h, py, pf, float(tol), ctypes.byref(st), wh))
+        return f, st.as_dict()
+
+    def sigma_min(self, start, mu_s, max_steps=40, rtol=1e-4, solve_tol=1e-9, method=SOLVE_MG_F64, check=True):
+        """(sigma, ritz_residual, solves): sigma_min(D_W) by Lanczos on (D(mu_s)^dag D(mu_s))^-1."""
+        ps, wh = _ptr(start)
+        sg, rr, ns = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        rc = lib().tmg_sigma_min(self._h, ps, float(mu_s), int(max_steps), float(rtol), float(solve_tol), int(method),
+                                 ctypes.byref(sg), ctypes.byref(rr), ctypes.byref(ns), wh)
+        if check and rc != -4:
+            self._check(rc)
+        return sg.value, rr.value, ns.value
 
     def set_params(self, kappa, csw=0.0, mu=0.0, mubar=0.0, epsbar=0.0):
         self._check(lib().tmg_set_params(self._h, kappa, csw, mu, mubar, epsbar))

@@ -400,6 +400,123 @@ int tmg_force(tmg_ctx* ctx, const double* phi, double* F, double tol, double* ac
   });
 }
 
+static void fill_stats(tmg_stats* stats, const SolveStats& a, const SolveStats& b, std::chrono::steady_clock::time_point t0) {
+  if (!stats) return;
+  stats->iterations = a.iterations + b.iterations;
+  stats->refinements = a.refinements + b.refinements;
+  stats->coarse_iterations = a.coarse_iterations + b.coarse_iterations;
+  stats->true_residual = std::max(a.true_residual, b.true_residual);
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int tmg_rotate_gauge(tmg_ctx* ctx, const double* omega, double step, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!omega || !valid_where(where) || !std::isfinite(step)) return fail(ctx, TMG_ERR_ARG, "tmg_rotate_gauge: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_rotate_gauge: no gauge field loaded");
+    const double* w = stage_in(c, c.stage_a, omega, (size_t)c.g.V * 32, where);
+    rotate_gauge(c, w, step);
+    build_clover(c);
+    convert_op_precisions(c);
+    if (c.mg_ready) {            // keep the hierarchy consistent with the new field: same P, new D_c
+      build_coarse(c);
+      if (c.l2_ready) build_coarse_c(c);
+    }
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (where == TMG_HOST) c.stage_a.release();
+    return TMG_OK;
+  });
+}
+
+int tmg_setup_update(tmg_ctx* ctx, int n_iter) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (n_iter < 0 || n_iter > 100) return fail(ctx, TMG_ERR_ARG, "tmg_setup_update: n_iter out of range");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_setup_update: no earlier setup to update");
+    mg_setup_update(c, n_iter);
+    return TMG_OK;
+  });
+}
+
+int tmg_pf_action(tmg_ctx* ctx, const double* phi, double* Y, double tol, double* S, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!phi || !Y || !(tol > 0.0) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_pf_action: bad argument");
+    if (!c.gauge_loaded || !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_pf_action: needs a gauge field and a setup");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    const size_t n = (size_t)12 * c.g.V;
+    tmg::Field pf, yf;
+    pf.create(c.g, TMG_PREC_F64, 1);
+    yf.create(c.g, TMG_PREC_F64, 1);
+    spinor_from_lex(c, stage_in(c, c.stage_a, phi, col, where), pf.buf.p, TMG_PREC_F64);
+    SolveStats s1{}, s0{};
+    const int rc = solve_one(c, TMG_SOLVE_MG_MIXED, pf.buf.p, yf.buf.p, c.mu, tol, 100000, s1);
+    if (rc != TMG_OK) return fail(ctx, rc, "tmg_pf_action: solve for Y failed");
+    if (S) *S = blas_norm2(c, yf.buf.p, TMG_PREC_F64, n);
+    double* yd = stage_out_ptr(c, c.stage_b, Y, col, where);
+    spinor_to_lex(c, yf.buf.p, TMG_PREC_F64, yd);
+    stage_out_finish(c, c.stage_b, Y, col, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    fill_stats(stats, s1, s0, t0);
+    return TMG_OK;
+  });
+}
+
+int tmg_pf_force(tmg_ctx* ctx, const double* Y, double* f, double tol, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!Y || !f || !(tol > 0.0) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_pf_force: bad argument");
+    if (!c.gauge_loaded || !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_pf_force: needs a gauge field and a setup");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    const size_t n = (size_t)12 * c.g.V;
+    tmg::Field yf, xf, tf;
+    yf.create(c.g, TMG_PREC_F64, 1);
+    xf.create(c.g, TMG_PREC_F64, 1);
+    tf.create(c.g, TMG_PREC_F64, 1);
+    spinor_from_lex(c, stage_in(c, c.stage_a, Y, col, where), yf.buf.p, TMG_PREC_F64);
+    // X = D(mu)^-dag Y = g5 D(-mu)^-1 g5 Y: the second solve of the two-step D^dag D scheme
+    blas_copy(c, yf.buf.p, tf.buf.p, TMG_PREC_F64, n);
+    gamma5_inplace(c, tf.buf.p, TMG_PREC_F64);
+    SolveStats s2{}, s0{};
+    const int rc = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, xf.buf.p, -c.mu, tol, 100000, s2);
+    if (rc != TMG_OK) return fail(ctx, rc, "tmg_pf_force: solve for X failed");
+    gamma5_inplace(c, xf.buf.p, TMG_PREC_F64);
+    const size_t nf = (size_t)c.g.V * 4 * 8;
+    DBuf fo;
+    double* fd = where == TMG_DEVICE ? f : (fo.alloc(nf * sizeof(double)), fo.as<double>());
+    force_from_xy(c, xf.buf.p, yf.buf.p, fd, 1);
+    if (where == TMG_HOST) TMG_CUDA(cudaMemcpyAsync(f, fd, nf * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    fill_stats(stats, s2, s0, t0);
+    return TMG_OK;
+  });
+}
+
+int tmg_sigma_min(tmg_ctx* ctx, const double* start, double mu_s, int max_steps, double rtol, double solve_tol,
+                  int method, double* sigma, double* ritz_res, int* solves, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!start || !sigma || !(mu_s > 0.0) || max_steps < 2 || max_steps > 64 || !(rtol > 0.0) || !(solve_tol > 0.0) ||
+        !valid_where(where) || (method != TMG_SOLVE_MG_F64 && method != TMG_SOLVE_MG_MIXED && method != TMG_SOLVE_CG_F64))
+      return fail(ctx, TMG_ERR_ARG, "tmg_sigma_min: bad argument");
+    if (!c.gauge_loaded || (method != TMG_SOLVE_CG_F64 && !c.mg_ready))
+      return fail(ctx, TMG_ERR_STATE, "tmg_sigma_min: needs a gauge field (and a setup for multigrid solves)");
+    const size_t col = (size_t)24 * c.g.V;
+    tmg::Field sf;
+    sf.create(c.g, TMG_PREC_F64, 1);
+    spinor_from_lex(c, stage_in(c, c.stage_a, start, col, where), sf.buf.p, TMG_PREC_F64);
+    int ns = 0, steps = 0;
+    double rr = 0.0;
+    *sigma = sigma_min_lanczos(c, sf.buf.p, mu_s, max_steps, rtol, solve_tol, method, &rr, &ns, &steps);
+    if (ritz_res) *ritz_res = rr;
+    if (solves) *solves = ns;
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    return rr <= rtol ? TMG_OK : TMG_ERR_NOCONV;
+  });
+}
+
 int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
   return guarded(ctx, [&]() -> int {
     if (!key) return fail(ctx, TMG_ERR_ARG, "tmg_tune: null key");

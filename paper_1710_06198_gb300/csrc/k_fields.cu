@@ -115,6 +115,96 @@ double su3_defect_device(Ctx& c, const double* U_dev, size_t n_links, long long*
   return best;
 }
 
+// ------------------------------------------------------------------ link update U <- exp(i A) U
+// A = step * sum_a omega_a lambda_a / 2 (lambda_a: Gell-Mann matrices), the su(3) direction of one
+// link.  exp(i A) by Taylor series with scaling and squaring: the matrix is divided by 2^s so that
+// its Frobenius norm is at most 1/2, summed to order 14 (truncation below 3e-17 relative), then
+// squared s times.  The product is projected back onto SU(3) (rows 0, 1 orthonormalised, row 2 =
+// conj(row0 x row1)) so that repeated updates stay special unitary.
+__device__ void su3_from_algebra(const double* w, double step, cpx<double> A[9]) {
+  const double r3 = 0.57735026918962576451;   // 1 / sqrt(3)
+  const double h = 0.5 * step;
+  A[0] = mk(h * (w[2] + r3 * w[7]), 0.0);
+  A[4] = mk(h * (-w[2] + r3 * w[7]), 0.0);
+  A[8] = mk(h * (-2.0 * r3 * w[7]), 0.0);
+  A[1] = mk(h * w[0], -h * w[1]);
+  A[3] = conj(A[1]);
+  A[2] = mk(h * w[3], -h * w[4]);
+  A[6] = conj(A[2]);
+  A[5] = mk(h * w[5], -h * w[6]);
+  A[7] = conj(A[5]);
+}
+
+__device__ void m3mul(const cpx<double> a[9], const cpx<double> b[9], cpx<double> r[9]) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) r[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+
+__device__ void exp_i_hermitian3(const cpx<double> A[9], cpx<double> E[9]) {
+  double nrm = 0.0;
+  for (int k = 0; k < 9; k++) nrm += A[k].re * A[k].re + A[k].im * A[k].im;
+  nrm = sqrt(nrm);
+  int sq = 0;
+  double scale = 1.0;
+  while (nrm * scale > 0.5 && sq < 60) { scale *= 0.5; sq++; }
+  cpx<double> B[9];
+  for (int k = 0; k < 9; k++) B[k] = mul_i(scale * A[k]);   // i A / 2^s
+  // Horner: E = I + B (I + B/2 (I + B/3 (... (I + B/14))))
+  for (int k = 0; k < 9; k++) E[k] = mk(k % 4 == 0 ? 1.0 : 0.0, 0.0);
+  for (int n = 14; n >= 1; n--) {
+    cpx<double> T[9];
+    m3mul(B, E, T);
+    for (int k = 0; k < 9; k++) E[k] = mk((k % 4 == 0 ? 1.0 : 0.0) + T[k].re / n, T[k].im / n);
+  }
+  for (int q = 0; q < sq; q++) {
+    cpx<double> T[9];
+    m3mul(E, E, T);
+    for (int k = 0; k < 9; k++) E[k] = T[k];
+  }
+}
+
+__device__ void reunitarise3(cpx<double> u[9]) {
+  double n0 = 0.0;
+  for (int b = 0; b < 3; b++) n0 += u[b].re * u[b].re + u[b].im * u[b].im;
+  n0 = 1.0 / sqrt(n0);
+  for (int b = 0; b < 3; b++) u[b] = n0 * u[b];
+  cpx<double> ov = mk(0.0, 0.0);
+  for (int b = 0; b < 3; b++) ov = ov + cmul_conj(u[b], u[3 + b]);
+  for (int b = 0; b < 3; b++) u[3 + b] = u[3 + b] - ov * u[b];
+  double n1 = 0.0;
+  for (int b = 0; b < 3; b++) n1 += u[3 + b].re * u[3 + b].re + u[3 + b].im * u[3 + b].im;
+  n1 = 1.0 / sqrt(n1);
+  for (int b = 0; b < 3; b++) u[3 + b] = n1 * u[3 + b];
+  u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+  u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+  u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+}
+
+// omega: lexicographic [V][4][8] algebra coefficients; U: internal F64 [4][9][V]
+__global__ void k_rotate_links(Geom g, const double* __restrict__ omega, double step, double2* __restrict__ U) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
+  if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
+  const size_t lex = lex_index(g, c);
+  double w[8];
+  for (int a = 0; a < 8; a++) w[a] = omega[(lex * 4 + mu) * 8 + a];
+  cpx<double> A[9], E[9], u[9], r[9];
+  su3_from_algebra(w, step, A);
+  exp_i_hermitian3(A, E);
+  for (int k = 0; k < 9; k++) { const double2 v = U[(size_t)(mu * 9 + k) * g.V + s]; u[k] = mk(v.x, v.y); }
+  m3mul(E, u, r);
+  reunitarise3(r);
+  for (int k = 0; k < 9; k++) U[(size_t)(mu * 9 + k) * g.V + s] = make_double2(r[k].re, r[k].im);
+}
+
+void rotate_gauge(Ctx& c, const double* omega_dev, double step) {
+  const dim3 grid((c.g.V + 127) / 128, 4);
+  ++c.launches, k_rotate_links<<<grid, 128, 0, c.stream>>>(c.g, omega_dev, step, c.op[0].U.as<double2>());
+  TMG_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ gauge field
 // lex [V][4][9] complex -> internal F64 [4][9][V]
 __global__ void k_gauge_lex_to_f64(Geom g, const double2* __restrict__ lex, double2* __restrict__ out) {

@@ -239,9 +239,48 @@ __global__ void k_force_link(Geom g, GT U, S X, S Y, const T2* __restrict__ lam,
   }
 }
 
-// F = traceless Hermitian part of -2 G, lexicographic output [V][4][3][3]
+// FP32 storage read into FP64 registers: the force kernels then sum every outer product and leaf
+// product in FP64 while moving half the bytes of the FP64 fields.
+struct SpinorF32in64 {
+  float4* p; int V;
+  __device__ __forceinline__ void load(int s, Spinor<double>& o) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float4 v = __ldg(p + (size_t)k * V + s);
+      o.c[2 * k] = {(double)v.x, (double)v.y};
+      o.c[2 * k + 1] = {(double)v.z, (double)v.w};
+    }
+  }
+};
+struct GaugeF32in64 {
+  float4* p; int V;
+  __device__ __forceinline__ void load(int s, int mu, Link<double>& u) const {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const float4 v = __ldg(p + (size_t)(mu * 3 + k) * V + s);
+      u.m[2 * k] = {(double)v.x, (double)v.y};
+      u.m[2 * k + 1] = {(double)v.z, (double)v.w};
+    }
+    reconstruct_row2(u);
+  }
+};
+
+// su(3) coefficients f_a = tr(lambda_a / 2 F) of a traceless Hermitian F (row-major 3x3)
+__device__ __forceinline__ void algebra_coeffs(const cpx<double> h[9], double f[8]) {
+  f[0] = h[1].re;
+  f[1] = -h[1].im;
+  f[2] = 0.5 * (h[0].re - h[4].re);
+  f[3] = h[2].re;
+  f[4] = -h[2].im;
+  f[5] = h[5].re;
+  f[6] = -h[5].im;
+  f[7] = (h[0].re + h[4].re - 2.0 * h[8].re) * 0.28867513459481288225;   // 1 / (2 sqrt 3)
+}
+
+// F = traceless Hermitian part of -2 G, lexicographic output [V][4][3][3] (alg = 0) or its su(3)
+// coefficients [V][4][8] (alg = 1)
 template <typename T2>
-__global__ void k_force_project(Geom g, const T2* __restrict__ G, double2* __restrict__ F) {
+__global__ void k_force_project(Geom g, const T2* __restrict__ G, double2* __restrict__ F, int alg) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int mu = blockIdx.y;
   if (s >= g.V) return;
@@ -256,45 +295,47 @@ __global__ void k_force_project(Geom g, const T2* __restrict__ G, double2* __res
   h[0].re -= tr;
   h[4].re -= tr;
   h[8].re -= tr;
+  if (alg) {
+    double f[8];
+    algebra_coeffs(h, f);
+    double* out = reinterpret_cast<double*>(F) + ((size_t)lex * 4 + mu) * 8;
+    for (int a = 0; a < 8; a++) out[a] = f[a];
+    return;
+  }
   for (int e = 0; e < 9; e++) F[((size_t)lex * 4 + mu) * 9 + e] = make_double2(h[e].re, h[e].im);
 }
 
 }  // namespace
 
-// F (lexicographic [V][4][3][3], device) from internal F64 fields X, Y (tbc/clover from the context).
-// With c.force_prec == TMG_PREC_F32 the kernels run in FP32 on FP32 copies of X, Y and the 12-real
-// FP32 links; F is written in FP64 either way.
-void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex) {
+// F (lexicographic [V][4][3][3], or its su(3) coefficients [V][4][8] when alg != 0; device) from
+// internal F64 fields X, Y (tbc/clover from the context).  With c.force_prec == TMG_PREC_F32 the
+// kernels read FP32 copies of X, Y and the 12-real FP32 links and accumulate in FP64.
+void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex, int alg) {
   const size_t V = c.g.V;
   const dim3 grid1((c.g.V + 127) / 128), grid4((c.g.V + 127) / 128, 4);
+  c.fw_t.alloc(V * (6 * 9 + 4 * 9) * sizeof(double2) + (c.force_prec == TMG_PREC_F32 ? 2 * 12 * V * sizeof(float2) : 0));
+  double2* lam = c.fw_t.as<double2>();
+  double2* G = lam + V * 6 * 9;
   if (c.force_prec == TMG_PREC_F32) {
-    c.fw_t.alloc(V * (6 * 9 + 4 * 9) * sizeof(float2) + 2 * 12 * V * sizeof(float2));
-    float2* lam = c.fw_t.as<float2>();
-    float2* G = lam + V * 6 * 9;
-    float2* x32 = G + V * 4 * 9;
+    float2* x32 = reinterpret_cast<float2*>(G + V * 4 * 9);
     float2* y32 = x32 + 12 * V;
     convert_field(c, X, TMG_PREC_F64, x32, TMG_PREC_F32, 12 * V);
     convert_field(c, Y, TMG_PREC_F64, y32, TMG_PREC_F32, 12 * V);
-    const SpinorF32 xs{(float4*)x32, c.g.V}, ys{(float4*)y32, c.g.V};
-    ++c.launches, k_force_lambda<float><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
+    const SpinorF32in64 xs{(float4*)x32, c.g.V}, ys{(float4*)y32, c.g.V};
+    ++c.launches, k_force_lambda<double><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
     TMG_CHECK_LAUNCH();
-    ++c.launches, k_force_link<float><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF32{c.op[1].U.as<float4>(), c.g.V}, xs, ys, lam,
-                                                                   (float)c.csw, G);
+    ++c.launches, k_force_link<double><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF32in64{c.op[1].U.as<float4>(), c.g.V}, xs, ys,
+                                                                    lam, c.csw, G);
     TMG_CHECK_LAUNCH();
-    ++c.launches, k_force_project<<<grid4, 128, 0, c.stream>>>(c.g, (const float2*)G, (double2*)F_lex);
+  } else {
+    const SpinorF64 xs{(double2*)X, c.g.V}, ys{(double2*)Y, c.g.V};
+    ++c.launches, k_force_lambda<double><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
     TMG_CHECK_LAUNCH();
-    return;
+    ++c.launches, k_force_link<double><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF64{c.op[0].U.as<double2>(), c.g.V}, xs, ys,
+                                                                    lam, c.csw, G);
+    TMG_CHECK_LAUNCH();
   }
-  c.fw_t.alloc(V * (6 * 9 + 4 * 9) * sizeof(double2));
-  double2* lam = c.fw_t.as<double2>();
-  double2* G = lam + V * 6 * 9;
-  const SpinorF64 xs{(double2*)X, c.g.V}, ys{(double2*)Y, c.g.V};
-  ++c.launches, k_force_lambda<double><<<grid1, 128, 0, c.stream>>>(c.g, xs, ys, lam);
-  TMG_CHECK_LAUNCH();
-  ++c.launches, k_force_link<double><<<grid4, 128, 0, c.stream>>>(c.g, GaugeF64{c.op[0].U.as<double2>(), c.g.V}, xs, ys, lam,
-                                                                  c.csw, G);
-  TMG_CHECK_LAUNCH();
-  ++c.launches, k_force_project<<<grid4, 128, 0, c.stream>>>(c.g, (const double2*)G, (double2*)F_lex);
+  ++c.launches, k_force_project<<<grid4, 128, 0, c.stream>>>(c.g, (const double2*)G, (double2*)F_lex, alg);
   TMG_CHECK_LAUNCH();
 }
 

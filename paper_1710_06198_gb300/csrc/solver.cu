@@ -514,6 +514,7 @@ double autotune(Ctx& c) {
 void mg_cycle_nd(Ctx& c, const void* r, void* z) { cycle_p(c, c.mg.prec_fine, c.mg.prec_coarse, r, z, 0.0, 2); }
 
 // ---------------------------------------------------------------- setup
+static void set_vectors2(Ctx& c, int pc);
 static void set_vectors(Ctx& c, int sp) {
   const size_t n = (size_t)12 * c.g.V;
   const size_t es = esize(sp);
@@ -566,6 +567,56 @@ void mg_setup(Ctx& c, const double* v0_lex) {
       blas_scale(c, 1.0 / nrm, 0.0, vj, sp, n);
     }
     set_vectors(c, sp);
+  }
+  TMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// Setup update (Sec. 2: the subspace of the previous setup is refined by one setup iteration
+// whenever the gauge field has moved): n_iter passes of v_j <- normalise(cycle(v_j)) on the current
+// operator, starting from the raw test vectors the last setup kept, each pass followed by a
+// rebuild of P and D_c; with three levels the level-2 vectors then get the same number of passes
+// of the level-1 cycle.
+void mg_setup_update(Ctx& c, int n_iter) {
+  const size_t n = (size_t)12 * c.g.V;
+  const int pf = c.mg.prec_fine, sp = storage(pf);
+  const size_t es = esize(sp);
+  const bool three = c.l2_ready;
+  c.l2_ready = false;   // level 1 alone while its vectors move (the level-2 basis refers to them)
+  set_vectors(c, sp);   // P and D_c of the current field from the kept vectors
+  c.fw_t.alloc(2 * n * es);
+  char* raw = (char*)c.sv_raw.p;
+  void* xb = c.fw_t.p;
+  for (int it = 0; it < n_iter; it++) {
+    for (int j = 0; j < c.cl.nv; j++) {
+      void* vj = raw + j * n * es;
+      cycle_p(c, pf, c.mg.prec_coarse, vj, xb, c.mu);
+      const double nrm = std::sqrt(blas_norm2(c, xb, sp, n));
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) throw Error{TMG_ERR_BREAKDOWN, "setup update: test vector vanished"};
+      blas_copy(c, xb, vj, sp, n);
+      blas_scale(c, 1.0 / nrm, 0.0, vj, sp, n);
+    }
+    set_vectors(c, sp);
+  }
+  if (three) {
+    const int pc = c.mg.prec_coarse;
+    const size_t n1 = (size_t)c.cl.nc * c.cl.nd;
+    const size_t ec = esize(pc);
+    set_vectors2(c, pc);
+    c.l2_ready = true;
+    DBuf tmp;
+    tmp.alloc(n1 * ec);
+    char* raw2 = (char*)c.sv2.p;
+    for (int it = 0; it < n_iter; it++) {
+      for (int j = 0; j < c.cl2.nv; j++) {
+        void* vj = raw2 + j * n1 * ec;
+        kcycle(c, pc, vj, tmp.p, c.mu, 1);
+        const double nrm = std::sqrt(blas_norm2(c, tmp.p, pc, n1));
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) throw Error{TMG_ERR_BREAKDOWN, "setup update: level-2 vector vanished"};
+        blas_copy(c, tmp.p, vj, pc, n1);
+        blas_scale(c, 1.0 / nrm, 0.0, vj, pc, n1);
+      }
+      set_vectors2(c, pc);
+    }
   }
   TMG_CUDA(cudaStreamSynchronize(c.stream));
 }
@@ -829,6 +880,119 @@ int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol,
     st.coarse_iterations = c1 - c0;
   }
   return rc;
+}
+
+// ---------------------------------------------------------------- smallest singular value of D_W
+// Eigenvalues of a small symmetric matrix (row-major n x n, n <= 64) by cyclic Jacobi rotations;
+// on return a holds them on its diagonal and z the eigenvectors in its columns.
+static void jacobi_eig(std::vector<double>& a, std::vector<double>& z, int n) {
+  z.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) z[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; sweep++) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < n; j++) (i == j ? diag : off) += a[(size_t)i * n + j] * a[(size_t)i * n + j];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n; p++)
+      for (int q = p + 1; q < n; q++) {
+        const double apq = a[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double th = (a[(size_t)q * n + q] - a[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double cth = 1.0 / std::sqrt(t * t + 1.0), sth = t * cth;
+        for (int k = 0; k < n; k++) {   // columns p, q
+          const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+          a[(size_t)k * n + p] = cth * akp - sth * akq;
+          a[(size_t)k * n + q] = sth * akp + cth * akq;
+        }
+        for (int k = 0; k < n; k++) {   // rows p, q
+          const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+          a[(size_t)p * n + k] = cth * apk - sth * aqk;
+          a[(size_t)q * n + k] = sth * apk + cth * aqk;
+        }
+        for (int k = 0; k < n; k++) {
+          const double zkp = z[(size_t)k * n + p], zkq = z[(size_t)k * n + q];
+          z[(size_t)k * n + p] = cth * zkp - sth * zkq;
+          z[(size_t)k * n + q] = sth * zkp + cth * zkq;
+        }
+      }
+  }
+}
+
+// sigma_min(D_W) = min |lambda(Q)|, Q = g5 D_W: Lanczos with full reorthogonalisation on
+// A = (D(mu_s)^dag D(mu_s))^-1 = (Q^2 + mu_s^2)^-1, each product computed by the two-step solve of
+// Sec. 1.1 (D(-mu_s) u = g5 b, then D(mu_s) v = g5 u).  The largest Ritz value theta of A gives
+// sigma_min^2 = 1/theta - mu_s^2.  Stops when the Ritz residual beta_j |s_j| <= rtol theta or after k
+// steps; *ritz_res gets the last relative Ritz residual, *solves the number of solves.
+double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double rtol, double solve_tol, int method,
+                         double* ritz_res, int* solves, int* steps_out) {
+  const size_t n = (size_t)12 * c.g.V;
+  k = std::max(2, std::min(k, 64));
+  DBuf Vb, w, t, u;
+  Vb.alloc((size_t)(k + 1) * n * 16);
+  w.alloc(n * 16);
+  t.alloc(n * 16);
+  u.alloc(n * 16);
+  char* V = Vb.as<char>();
+  auto vec = [&](int j) { return (void*)(V + (size_t)j * n * 16); };
+  blas_copy(c, start, vec(0), TMG_PREC_F64, n);
+  const double n0 = std::sqrt(blas_norm2(c, vec(0), TMG_PREC_F64, n));
+  if (!(n0 > 0.0) || !std::isfinite(n0)) throw Error{TMG_ERR_ARG, "sigma_min: start vector is zero or not finite"};
+  blas_scale(c, 1.0 / n0, 0.0, vec(0), TMG_PREC_F64, n);
+  std::vector<double> alpha, beta;
+  int nsolve = 0;
+  double theta = 0.0, res = 1.0;
+  int j = 0;
+  for (; j < k; j++) {
+    // w = A v_j
+    blas_copy(c, vec(j), t.p, TMG_PREC_F64, n);
+    gamma5_inplace(c, t.p, TMG_PREC_F64);
+    SolveStats s1{}, s2{};
+    // bounded inner solves: a stalled solve ends with its best iterate instead of running on
+    const int maxit = method == TMG_SOLVE_CG_F64 ? 200000 : 4000;
+    int rc = solve_one(c, method, t.p, u.p, -mu_s, solve_tol, maxit, s1);
+    if (rc != TMG_OK && rc != TMG_ERR_NOCONV) throw Error{rc, "sigma_min: inner solve failed"};
+    gamma5_inplace(c, u.p, TMG_PREC_F64);
+    rc = solve_one(c, method, u.p, w.p, mu_s, solve_tol, maxit, s2);
+    if (rc != TMG_OK && rc != TMG_ERR_NOCONV) throw Error{rc, "sigma_min: inner solve failed"};
+    nsolve += 2;
+    double are, aim;
+    blas_dot(c, vec(j), w.p, TMG_PREC_F64, n, &are, &aim);
+    alpha.push_back(are);
+    // full reorthogonalisation (twice) against v_0 .. v_j
+    for (int pass = 0; pass < 2; pass++)
+      for (int i = 0; i <= j; i++) {
+        double hr, hi;
+        blas_dot(c, vec(i), w.p, TMG_PREC_F64, n, &hr, &hi);
+        blas_axpy(c, -hr, -hi, vec(i), w.p, TMG_PREC_F64, n);
+      }
+    const double b = std::sqrt(blas_norm2(c, w.p, TMG_PREC_F64, n));
+    // Ritz values of the (j+1) x (j+1) tridiagonal
+    const int m = j + 1;
+    std::vector<double> T((size_t)m * m, 0.0), Z;
+    for (int i = 0; i < m; i++) {
+      T[(size_t)i * m + i] = alpha[i];
+      if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = beta[i];
+    }
+    jacobi_eig(T, Z, m);
+    int imax = 0;
+    for (int i = 1; i < m; i++)
+      if (T[(size_t)i * m + i] > T[(size_t)imax * m + imax]) imax = i;
+    theta = T[(size_t)imax * m + imax];
+    res = theta > 0.0 ? b * std::fabs(Z[(size_t)(m - 1) * m + imax]) / theta : 1.0;
+    if (res <= rtol || !(b > 0.0) || j + 1 == k) {
+      j++;
+      break;
+    }
+    beta.push_back(b);
+    blas_copy(c, w.p, vec(j + 1), TMG_PREC_F64, n);
+    blas_scale(c, 1.0 / b, 0.0, vec(j + 1), TMG_PREC_F64, n);
+  }
+  if (ritz_res) *ritz_res = res;
+  if (solves) *solves = nsolve;
+  if (steps_out) *steps_out = j;
+  const double s2 = 1.0 / theta - mu_s * mu_s;
+  return s2 > 0.0 ? std::sqrt(s2) : 0.0;
 }
 
 // ---------------------------------------------------------------- batched mixed-precision solve

@@ -15,6 +15,8 @@ struct SolveStats {
 
 // Adaptive setup from nv FP64 lexicographic vectors on the device (Sec. 1.1, Sec. 2).
 void mg_setup(Ctx& c, const double* v0_lex);
+// Setup update after the gauge field changed: n_iter cycle-based iterations from the kept vectors.
+void mg_setup_update(Ctx& c, int n_iter);
 // Level-2 setup (three levels) from nv2 FP64 level-1 vectors on the device, parameters in c.l2p.
 void mg_setup2(Ctx& c, const double* v1_dev);
 // z = M_MG r in the fine storage precision of the multigrid parameters (r is not modified).
@@ -23,6 +25,10 @@ void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // nf = 2: the doublet D_ND (Eq. 2) on F64 fields [2][12 V] (mu unused; mubar, epsbar of the context).
 int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st,
               int nf = 1);
+// sigma_min(D_W) by Lanczos on (D(mu_s)^dag D(mu_s))^-1 from the FP64 field `start` (two solves of
+// method `method` per step, to solve_tol); see solver.cu.
+double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double rtol, double solve_tol, int method,
+                         double* ritz_res, int* solves, int* steps);
 // Launch-shape autotuner of the coarse solve (coarse_ctas_per_sm, coarse_gs_passes; with three
 // levels kcycle_ctas_per_sm); keeps the fastest shape, returns its time per coarse solve in ms.
 double autotune(Ctx& c);

@@ -183,7 +183,7 @@ struct Ctx {
   int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
   int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
   int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
-  int force_prec = TMG_PREC_F64;   // precision of the force kernels (TMG_PREC_F64 or TMG_PREC_F32)
+  int force_prec = TMG_PREC_F32;   // force kernels: FP32 inputs with FP64 sums (TMG_PREC_F32) or all FP64
   int outer_gs_fused = 1;       // outer FGMRES: fuse pass 1's update with pass 2's dot products
   int coarse_grid = 0;          // CTAs of the persistent coarse GMRES (0: coarse_ctas_per_sm x SMs)
   int kcycle_grid = 0;          // CTAs of the persistent K-cycle (0: kcycle_ctas_per_sm x SMs)
@@ -220,6 +220,9 @@ struct ProfScope {
 double su3_defect_host(const double* U, size_t n_links, long long* at);
 double su3_defect_device(Ctx& c, const double* U_dev, size_t n_links, long long* at);
 void gauge_lex_to_internal(Ctx& c, const double* lex_dev);
+// U_mu(x) <- exp(i step sum_a omega_a lambda_a / 2) U_mu(x) on the internal F64 links, omega
+// lexicographic [V][4][8] on the device; the caller rebuilds clover and compressed copies
+void rotate_gauge(Ctx& c, const double* omega_dev, double step);
 void build_clover(Ctx& c);
 void convert_op_precisions(Ctx& c);
 // lex FP64 [V][12] complex -> internal field column (prec F64 or F32)
@@ -254,7 +257,9 @@ void dslash_nd(Ctx& c, int prec, void* y, const void* x);
 // ---------------------------------------------------------------- force (k_force.cu)
 // F (lexicographic [V][4][3][3] complex, device) of S = ||D^-1 phi||^2 from internal F64 fields
 // X = D^-dag D^-1 phi and Y = D^-1 phi
-void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex);
+// alg = 0: F as [V][4][3][3] complex; alg = 1: f[V][4][8] = tr(lambda_a / 2 F) (real), the
+// su(3) coefficients of the force
+void force_from_xy(Ctx& c, const void* X, const void* Y, double* F_lex, int alg = 0);
 
 // ---------------------------------------------------------------- multigrid (k_mg.cu)
 void sap_sweeps(Ctx& c, int prec, void* x, const void* b, void* r_scratch, double mu, int n_sweeps);

@@ -109,3 +109,18 @@ def test_D_full_mixed_precision_lattice(prec):
     ctx, U, p, C = make((16, 16, 16, 32), (4, 4, 4, 4), 0.35, 3, csw=1.5, mu=0.003)
     x = fields.gaussian_spinor(ctx.dims, 4)
     assert rel(ctx.apply(x, tmg.OP_D, prec), dirac.apply_D(U, x, p, clover=C)) < TOL[prec]
+
+
+def test_load_gauge_rejects_non_su3(small):
+    """A link off SU(3) (scaled by 1.01) is rejected from host and from device memory, with the site
+    named; the field loaded before stays in use."""
+    torch = pytest.importorskip("torch")
+    ctx, U, p, C = small
+    bad = U.copy()
+    bad[1, 2, 3, 0, 2] *= 1.01
+    for arr in (bad, torch.from_numpy(bad).cuda()):
+        with pytest.raises(tmg.TmgError) as e:
+            ctx.load_gauge(arr, -1)
+        assert e.value.code == -1 and "not in SU(3)" in str(e.value)
+    x = fields.gaussian_spinor(ctx.dims, 29)
+    assert rel(ctx.apply(x, tmg.OP_D, tmg.PREC_F64), dirac.apply_D(U, x, p, clover=C)) < 1e-13
