@@ -58,7 +58,14 @@ enum {
   TMG_OP_D = 0,      /* y = D(mu) x                          (Sec. 1.1)            */
   TMG_OP_DDAG = 1,   /* y = D(mu)^dag x = G5 D(-mu) G5 x     (Sec. 1.1)            */
   TMG_OP_DND = 2,    /* y = D_ND(mubar, epsbar) x, x = [2 flavours][V][4][3] (Eq. 2) */
-  TMG_OP_HOP = 3     /* y = hopping term only (for tests and bandwidth runs)        */
+  TMG_OP_HOP = 3,    /* y = hopping term only (for tests and bandwidth runs)        */
+  TMG_OP_DHAT = 4,   /* y_o = Dhat(mu) x_o, the even-odd reduced operator on the odd
+                        sites, Dhat = M_o - H_oe M_e^-1 H_eo with M = A + i mu g5 the
+                        site-local part and H the hopping part of D (Sec. 1.2 runs on the
+                        even-odd reduced operator); x, y full-lattice fields of which the
+                        odd sites (x + y + z + t odd) are read / written, y zero on the
+                        even sites; F64 (12-real links) or F32 (8-real links) only; Lx even */
+  TMG_OP_DHAT_DAG = 5 /* y_o = Dhat(mu)^dag x_o = g5 Dhat(-mu) g5 x_o, same conventions */
 };
 
 /* Create a context for a Lx x Ly x Lz x T lattice on `device`.  `block` is the SAP block, which is
@@ -93,7 +100,11 @@ int tmg_check_links(const double *U, long long n_links, double *worst, long long
 int tmg_set_params(tmg_ctx *ctx, double kappa, double csw, double mu, double mubar, double epsbar);
 
 /* y = op x for n_rhs fine spinors ([n_rhs][V][4][3], or [n_rhs][2][V][4][3] for TMG_OP_DND) in
- * the storage precision `prec` (inputs rounded to it; FP16 storage computes in FP32).
+ * the storage precision `prec` (inputs rounded to it; FP16 storage computes in FP32).  With
+ * TMG_PREC_F16, D, D^dag and the hopping term keep every field in 16-bit fixed point: spinors with
+ * one FP32 norm per site (the site's largest |component|; value = q / 32767 * norm, rounded to
+ * nearest), links as two rows at scale 1, the clover field with a per-site scale (348 bytes per
+ * site and application); the doublet operator in F16 keeps FP32 spinors.
  * mu_per_col (n_rhs values) overrides the twist per column; NULL uses the context's mu. */
 int tmg_apply(tmg_ctx *ctx, int op, const double *x, double *y, int n_rhs,
               const double *mu_per_col, int prec, int where);
@@ -227,8 +238,11 @@ enum {
                           /* one launch per operation for every column, FP32 coarse level    */
   TMG_SOLVE_ND_F64 = 4,   /* doublet D_ND x = b (Eq. 2), b and x [n_rhs][2][V][4][3], multigrid */
                           /* with P_ND = P x I2 (Sec. 1.2), everything in FP64                */
-  TMG_SOLVE_ND_MIXED = 5  /* the same with FP64 defect correction around the MG params'      */
+  TMG_SOLVE_ND_MIXED = 5, /* the same with FP64 defect correction around the MG params'      */
                           /* fine/coarse precisions                                          */
+  TMG_SOLVE_CG_EO = 6     /* odd-even CG (Fig. 1's comparator): FP64 CG on Dhat Dhat^dag for  */
+                          /* the odd sites, rhs b_o - H_oe M_e^-1 b_e, then x_e = M_e^-1 (b_e */
+                          /* - H_eo x_o); needs no multigrid setup; Lx even                   */
 };
 
 /* Solve D(mu) x = b (relative FP64 residual tol) for n_rhs right-hand sides, one after another.
@@ -263,6 +277,35 @@ int tmg_rotate_gauge(tmg_ctx *ctx, const double *omega, double step, int where);
  * cycle too.  n_iter = 0 only rebuilds P and D_c.  TMG_ERR_STATE without an earlier setup. */
 int tmg_setup_update(tmg_ctx *ctx, int n_iter);
 
+/* Shifted systems D(mu_k) x_k = b, k = 0 .. n_shift-1 (1..64) in the given order, one right-hand side
+ * b ([V][4][3]) and x [n_shift][V][4][3], each solved by the mixed-precision multigrid to the FP64
+ * residual tol with the same P (Sec. 1.1: one P serves every twist).  guess selects the initial
+ * guess of system k > 0: 0 zero, 1 the solution x_{k-1}, 2 the first-order Taylor expansion of
+ * Sec. 3, (Q + i mu + i delta)^-1 ~ (Q + i mu)^-1 - i delta (Q + i mu)^-2 with g5 D(mu) = Q + i mu:
+ * x_k^0 = x_{k-1} - i (mu_k - mu_{k-1}) D(mu_{k-1})^-1 g5 x_{k-1}, the correction solved only to the
+ * relative residual taylor_tol.  iterations (may be NULL) gets n_shift outer-iteration counts of the
+ * systems themselves; stats sums every solve, the Taylor corrections included.  Shifted normal
+ * equations (D^dag D + sigma) map to twists mu_k = sqrt(mu^2 + sigma) (Sec. 1.1). */
+int tmg_solve_shifts(tmg_ctx *ctx, const double *b, double *x, int n_shift, const double *mu, double tol, int guess,
+                     double taylor_tol, int *iterations, tmg_stats *stats, int where);
+
+/* Multi-shift CG (the MMS-CG of Sec. 3): x_s = (A + sigma_s)^-1 b for n_shift (1..64) shifts
+ * sigma_s >= 0 at once, FP64, with A = D(mu)^dag D(mu) (flavours = 1; b [V][4][3], x
+ * [n_shift][V][4][3]) or A = Q_ND^2 = D_ND^dag D_ND, Q_ND = (g5 x tau1) D_ND (flavours = 2, Eqs. 2
+ * and 4; b [2][V][4][3], x [n_shift][2][V][4][3]).  One Krylov space (the seed system A) serves all
+ * shifts.  Stops when every shifted residual is <= tol ||b||; stats: seed iterations and the
+ * largest recomputed residual ||b - (A + sigma_s) x_s|| / ||b||.  Needs no multigrid setup. */
+int tmg_mms_cg(tmg_ctx *ctx, const double *b, double *x, int n_shift, const double *sigma, double tol, int flavours,
+               tmg_stats *stats, int where);
+
+/* Rational function of A (the RHMC approximation R of Eq. 5, for 1/sqrt(Q_ND^2)):
+ * out = a prod_{l=1..n} (A + num_l)(A + den_l)^-1 phi, n <= 32, distinct den_l >= 0, evaluated
+ * through its partial fractions a (phi + sum_l r_l (A + den_l)^-1 phi) with the multi-shift CG
+ * above (same A, flavours, tolerance and stats).  The coefficients (Zolotarev's for 1/sqrt(x))
+ * come from the caller. */
+int tmg_rational_apply(tmg_ctx *ctx, const double *phi, double *out, int n, double a, const double *num,
+                       const double *den, double tol, int flavours, tmg_stats *stats, int where);
+
 /* Pseudofermion action S = phi^dag (D D^dag)^-1 phi = ||Y||^2, Y = D(mu)^-1 phi (Sec. 1.1, the
  * monomials of Sec. 2): one mixed-precision multigrid solve to tolerance tol.  phi, Y: FP64 fine
  * spinors (Y is written).  Y is what tmg_pf_force needs: the force is recomputed from it rather
@@ -290,10 +333,15 @@ int tmg_sigma_min(tmg_ctx *ctx, const double *start, double mu_s, int max_steps,
                   int method, double *sigma, double *ritz_res, int *solves, int where);
 
 /* Time `n_iter` back-to-back launches of the dslash kernel (y = D x, one column, storage
- * precision prec) on the context stream with CUDA events; writes the mean milliseconds per
- * launch.  Inputs are the library's internal fields (random data is not needed: the timing
+ * precision prec as in tmg_apply, so TMG_PREC_F16 is the all-FP16 form) on the context stream with
+ * CUDA events; writes the mean milliseconds per launch.  Inputs are the library's internal fields (random data is not needed: the timing
  * does not depend on values). */
 int tmg_bench_dslash(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_launch);
+
+/* Time `n_iter` back-to-back applications of the even-odd reduced operator Dhat (the two kernels of
+ * one application; F64 with 12-real links or F32 with 8-real links) on the context stream with CUDA
+ * events; writes the mean milliseconds per application. */
+int tmg_bench_schur(tmg_ctx *ctx, int prec, int n_iter, double *ms_per_application);
 
 /* Coarse solve that allocates nothing, for callers that cannot call cudaMalloc: code running
  * under CUDA stream capture, hosts whose memory manager forbids allocation on the call path, and
@@ -312,7 +360,8 @@ int tmg_coarse_solve_noalloc(tmg_ctx *ctx, const double *b, double *x, double mu
 enum {
   TMG_PK_DSLASH_F64 = 0, TMG_PK_DSLASH_F32 = 1, TMG_PK_DSLASH_F16 = 2,
   TMG_PK_SAP_F64 = 3, TMG_PK_SAP_F32 = 4, TMG_PK_SAP_F16 = 5,
-  TMG_PK_RESTRICT = 6, TMG_PK_PROLONG = 7, TMG_PK_COARSE = 8, TMG_PK_COARSE_SOLVE = 9, TMG_PK_COUNT = 10
+  TMG_PK_RESTRICT = 6, TMG_PK_PROLONG = 7, TMG_PK_COARSE = 8, TMG_PK_COARSE_SOLVE = 9,
+  TMG_PK_EO_F64 = 10, TMG_PK_EO_F32 = 11, TMG_PK_COUNT = 12
 };
 /* enable != 0: reset the records and start timing every launch of the classes above;
  * enable == 0: stop (records are kept until the next call). */
@@ -330,10 +379,12 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels), "force_prec" (TMG_PREC_F32, the default:
- * the force kernels of tmg_force / tmg_force_xy / tmg_pf_force read FP32 copies of X, Y and the
- * 12-real FP32 links and sum every product in FP64; TMG_PREC_F64: FP64 inputs; F is returned in
- * FP64 either way).  TMG_ERR_ARG for an unknown key or
+ * the basis for up to 10 basis vectors; 0: separate kernels), "eo_stage" (1, the default: the FP32 even-odd kernels copy
+ * each CTA's tile of the clover field / clover inverse into shared memory with bulk copies while
+ * the neighbour loads run; 0: direct loads), "force_prec" (TMG_PREC_F64, the default: the force kernels of
+ * tmg_force / tmg_force_xy / tmg_pf_force read FP64 X, Y and links; TMG_PREC_F32: they read FP32
+ * copies of X, Y and the 12-real FP32 links and sum every product in FP64; F is returned in FP64
+ * either way).  TMG_ERR_ARG for an unknown key or
  * value. */
 int tmg_tune(tmg_ctx *ctx, const char *key, double value);
 

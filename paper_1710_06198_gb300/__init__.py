@@ -22,9 +22,9 @@ LIB_PATH = os.path.join(HERE, "libtmg.so")
 
 PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
 HOST, DEVICE = 0, 1
-OP_D, OP_DDAG, OP_DND, OP_HOP = 0, 1, 2, 3
+OP_D, OP_DDAG, OP_DND, OP_HOP, OP_DHAT, OP_DHAT_DAG = 0, 1, 2, 3, 4, 5
 SOLVE_MG_F64, SOLVE_MG_MIXED, SOLVE_CG_F64, SOLVE_MG_BATCHED = 0, 1, 2, 3
-SOLVE_ND_F64, SOLVE_ND_MIXED = 4, 5
+SOLVE_ND_F64, SOLVE_ND_MIXED, SOLVE_CG_EO = 4, 5, 6
 STATUS = {0: "TMG_OK", -1: "TMG_ERR_ARG", -2: "TMG_ERR_CUDA", -3: "TMG_ERR_OOM", -4: "TMG_ERR_NOCONV",
           -5: "TMG_ERR_BREAKDOWN", -6: "TMG_ERR_TIMEOUT", -7: "TMG_ERR_STATE"}
 
@@ -105,11 +105,15 @@ _SIGS = {
     "tmg_pf_action": [_P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(Stats), _I],
     "tmg_pf_force": [_P, _P, _P, _D, ctypes.POINTER(Stats), _I],
     "tmg_sigma_min": [_P, _P, _D, _I, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), _I],
+    "tmg_solve_shifts": [_P, _P, _P, _I, _P, _D, _I, _D, _P, ctypes.POINTER(Stats), _I],
+    "tmg_bench_schur": [_P, _I, _I, ctypes.POINTER(_D)],
+    "tmg_mms_cg": [_P, _P, _P, _I, _P, _D, _I, ctypes.POINTER(Stats), _I],
+    "tmg_rational_apply": [_P, _P, _P, _I, _D, _P, _P, _D, _I, ctypes.POINTER(Stats), _I],
     "tmg_check_links": [_P, ctypes.c_longlong, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
 
 PROFILE_KINDS = ["dslash_f64", "dslash_f32", "dslash_f16", "sap_f64", "sap_f32", "sap_f16", "restrict",
-                 "prolong", "coarse_apply", "coarse_solve"]
+                 "prolong", "coarse_apply", "coarse_solve", "eo_f64", "eo_f32"]
 
 
 def lib():
@@ -469,6 +473,44 @@ class Context:
             self._check(rc)
         return x, st.as_dict()
 
+    def solve_shifts(self, b, mus, tol=1e-10, guess=2, taylor_tol=1e-2):
+        """(x[n_shift, ...], per-system outer iterations, stats) for D(mu_k) x_k = b in order, with zero
+        (0), previous-solution (1) or first-order Taylor (2) initial guesses."""
+        mu_arr = np.ascontiguousarray(np.asarray(mus, dtype=np.float64).reshape(-1))
+        n = mu_arr.size
+        x = _empty_like(b, (n,) + tuple(b.shape))
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        its = (ctypes.c_int * n)()
+        st = Stats()
+        self._check(lib().tmg_solve_shifts(self._h, pb, px, n, mu_arr.ctypes.data_as(ctypes.c_void_p), float(tol),
+                                           int(guess), float(taylor_tol), its, ctypes.byref(st), wh))
+        return x, list(its), st.as_dict()
+
+    def mms_cg(self, b, sigma, tol=1e-10, flavours=1):
+        """(x[n_shift, ...], stats): (A + sigma_s)^-1 b for all shifts, A = D^dag D or Q_ND^2."""
+        sg = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(-1))
+        x = _empty_like(b, (sg.size,) + tuple(b.shape))
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        st = Stats()
+        self._check(lib().tmg_mms_cg(self._h, pb, px, sg.size, sg.ctypes.data_as(ctypes.c_void_p), float(tol),
+                                     int(flavours), ctypes.byref(st), wh))
+        return x, st.as_dict()
+
+    def rational_apply(self, phi, a, num, den, tol=1e-10, flavours=1):
+        """(a prod (A + num_l)/(A + den_l) phi, stats) through the multi-shift CG."""
+        nu = np.ascontiguousarray(np.asarray(num, dtype=np.float64).reshape(-1))
+        de = np.ascontiguousarray(np.asarray(den, dtype=np.float64).reshape(-1))
+        out = _empty_like(phi, phi.shape)
+        pp, wh = _ptr(phi)
+        po, _ = _ptr(out)
+        st = Stats()
+        self._check(lib().tmg_rational_apply(self._h, pp, po, nu.size, float(a), nu.ctypes.data_as(ctypes.c_void_p),
+                                             de.ctypes.data_as(ctypes.c_void_p), float(tol), int(flavours),
+                                             ctypes.byref(st), wh))
+        return out, st.as_dict()
+
     def force_xy(self, X, Y):
         """F[T, Z, Y, X, mu, 3, 3] of S = ||D^-1 phi||^2 from X = D^-dag Y, Y = D^-1 phi."""
         F = _empty_like(X, self.lat + (4, 3, 3))
@@ -496,6 +538,12 @@ class Context:
 
     def tune(self, key, value):
         self._check(lib().tmg_tune(self._h, key.encode(), float(value)))
+
+    def bench_schur(self, prec=PREC_F32, n_iter=100):
+        """Mean milliseconds per application of the even-odd reduced operator (two kernels)."""
+        ms = ctypes.c_double()
+        self._check(lib().tmg_bench_schur(self._h, prec, n_iter, ctypes.byref(ms)))
+        return ms.value
 
     def bench_dslash(self, prec=PREC_F32, n_iter=100):
         ms = ctypes.c_double()

@@ -181,6 +181,7 @@ int tmg_set_params(tmg_ctx* ctx, double kappa, double csw, double mu, double mub
       build_clover(c);
       convert_op_precisions(c);
       c.mg_ready = false;
+      c.eo.ready = false;
     }
     return TMG_OK;
   });
@@ -218,6 +219,7 @@ int tmg_load_gauge(tmg_ctx* ctx, const double* U, int where, int t_bc) {
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     c.U_lex.release();
     c.gauge_loaded = true;
+    c.eo.ready = false;
     c.mg_ready = false;
     return TMG_OK;
   });
@@ -227,13 +229,42 @@ int tmg_apply(tmg_ctx* ctx, int op, const double* x, double* y, int n_rhs, const
               int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
-    if (!x || !y || n_rhs <= 0 || !valid_prec(prec) || !valid_where(where) || op < 0 || op > 3)
+    if (!x || !y || n_rhs <= 0 || !valid_prec(prec) || !valid_where(where) || op < 0 || op > 5)
       return fail(ctx, TMG_ERR_ARG, "tmg_apply: bad argument");
     if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_apply: no gauge field loaded");
-    const int sp = storage_of(prec);
+    if (op == TMG_OP_DHAT || op == TMG_OP_DHAT_DAG) {
+      if (prec == TMG_PREC_F16) return fail(ctx, TMG_ERR_ARG, "tmg_apply: the even-odd operator has F64 and F32 forms");
+      const size_t col = (size_t)24 * c.g.V;
+      const size_t hb = (size_t)12 * (c.g.V / 2) * (prec == TMG_PREC_F64 ? 16 : 8);
+      const double mu0 = c.mu;
+      DBuf w;
+      w.alloc(3 * hb);
+      for (int j = 0; j < n_rhs; j++) {
+        c.mu = mu_per_col ? mu_per_col[j] : mu0;
+        try {
+          eo_prepare(c);
+        } catch (...) {
+          c.mu = mu0;
+          throw;
+        }
+        const double* xd = stage_in(c, c.stage_a, x + j * col, col, where);
+        eo_from_lex(c, xd, w.p, 1, prec);
+        eo_apply(c, prec, w.as<char>() + hb, w.p, w.as<char>() + 2 * hb, op == TMG_OP_DHAT_DAG);
+        double* yd = stage_out_ptr(c, c.stage_b, y + j * col, col, where);
+        eo_to_lex(c, w.as<char>() + hb, yd, 1, prec, 1);
+        stage_out_finish(c, c.stage_b, y + j * col, col, where);
+      }
+      c.mu = mu0;
+      eo_check(c);
+      return TMG_OK;
+    }
+    // FP16 storage of D, D^dag and the hopping term: spinors too are 16-bit fixed point
+    const bool h16 = prec == TMG_PREC_F16 && op != TMG_OP_DND;
+    const int sp = h16 ? PREC_H16 : storage_of(prec);
+    const int kp = h16 ? PREC_H16 : prec;
     const int nfl = op == TMG_OP_DND ? 2 : 1;
     const size_t col = (size_t)24 * c.g.V;  // doubles per flavour column
-    if (op == TMG_OP_D && prec != TMG_PREC_F64 && n_rhs > 1) {
+    if (op == TMG_OP_D && prec == TMG_PREC_F32 && n_rhs > 1) {
       // all columns through the multi-column kernel (links and clover fetched once per site)
       ctx->fin.create(c.g, sp, n_rhs);
       ctx->fout.create(c.g, sp, n_rhs);
@@ -264,9 +295,9 @@ int tmg_apply(tmg_ctx* ctx, int op, const double* x, double* y, int n_rhs, const
       }
       for (int f = 0; f < nfl; f++) spinor_from_lex(c, xd + f * col, ctx->fin.col(c.g, f), sp);
       const double mu = mu_per_col ? mu_per_col[j] : c.mu;
-      if (op == TMG_OP_D) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 0);
-      else if (op == TMG_OP_DDAG) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 1);
-      else if (op == TMG_OP_HOP) dslash(c, prec, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 2, 0);
+      if (op == TMG_OP_D) dslash(c, kp, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 0);
+      else if (op == TMG_OP_DDAG) dslash(c, kp, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 0, 1);
+      else if (op == TMG_OP_HOP) dslash(c, kp, ctx->fout.col(c.g, 0), ctx->fin.col(c.g, 0), nullptr, mu, 2, 0);
       else dslash_nd(c, prec, ctx->fout.buf.p, ctx->fin.buf.p);
       double* yd = where == TMG_DEVICE ? y + off : nullptr;
       if (where == TMG_HOST) {
@@ -288,22 +319,52 @@ int tmg_bench_dslash(tmg_ctx* ctx, int prec, int n_iter, double* ms) {
     Ctx& c = ctx->c;
     if (!ms || n_iter <= 0 || !valid_prec(prec)) return fail(ctx, TMG_ERR_ARG, "tmg_bench_dslash: bad argument");
     if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_bench_dslash: no gauge field loaded");
-    const int sp = storage_of(prec);
+    const int sp = prec == TMG_PREC_F16 ? PREC_H16 : storage_of(prec);
+    const int kp = prec == TMG_PREC_F16 ? PREC_H16 : prec;
     ctx->fin.create(c.g, sp, 1);
     ctx->fout.create(c.g, sp, 1);
-    blas_zero(c, ctx->fin.buf.p, sp, (size_t)12 * c.g.V);
-    for (int i = 0; i < 3; i++) dslash(c, prec, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
+    TMG_CUDA(cudaMemsetAsync(ctx->fin.buf.p, 0, spinor_col_bytes(c.g, sp), c.stream));
+    for (int i = 0; i < 3; i++) dslash(c, kp, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
     cudaEvent_t e0, e1;
     TMG_CUDA(cudaEventCreate(&e0));
     TMG_CUDA(cudaEventCreate(&e1));
     TMG_CUDA(cudaEventRecord(e0, c.stream));
-    for (int i = 0; i < n_iter; i++) dslash(c, prec, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
+    for (int i = 0; i < n_iter; i++) dslash(c, kp, ctx->fout.buf.p, ctx->fin.buf.p, nullptr, c.mu, 0, 0);
     TMG_CUDA(cudaEventRecord(e1, c.stream));
     TMG_CUDA(cudaEventSynchronize(e1));
     float t = 0.f;
     TMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    *ms = (double)t / n_iter;
+    return TMG_OK;
+  });
+}
+
+int tmg_bench_schur(tmg_ctx* ctx, int prec, int n_iter, double* ms) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!ms || n_iter <= 0 || (prec != TMG_PREC_F64 && prec != TMG_PREC_F32))
+      return fail(ctx, TMG_ERR_ARG, "tmg_bench_schur: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_bench_schur: no gauge field loaded");
+    eo_prepare(c);
+    const size_t hb = (size_t)12 * (c.g.V / 2) * (prec == TMG_PREC_F64 ? 16 : 8);
+    DBuf w;
+    w.alloc(3 * hb);
+    TMG_CUDA(cudaMemsetAsync(w.p, 0, 3 * hb, c.stream));
+    for (int i = 0; i < 3; i++) eo_apply(c, prec, w.as<char>() + hb, w.p, w.as<char>() + 2 * hb, 0);
+    cudaEvent_t e0, e1;
+    TMG_CUDA(cudaEventCreate(&e0));
+    TMG_CUDA(cudaEventCreate(&e1));
+    TMG_CUDA(cudaEventRecord(e0, c.stream));
+    for (int i = 0; i < n_iter; i++) eo_apply(c, prec, w.as<char>() + hb, w.p, w.as<char>() + 2 * hb, 0);
+    TMG_CUDA(cudaEventRecord(e1, c.stream));
+    TMG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    TMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    eo_check(c);
     *ms = (double)t / n_iter;
     return TMG_OK;
   });
@@ -418,6 +479,7 @@ int tmg_rotate_gauge(tmg_ctx* ctx, const double* omega, double step, int where) 
     rotate_gauge(c, w, step);
     build_clover(c);
     convert_op_precisions(c);
+    c.eo.ready = false;
     if (c.mg_ready) {            // keep the hierarchy consistent with the new field: same P, new D_c
       build_coarse(c);
       if (c.l2_ready) build_coarse_c(c);
@@ -517,6 +579,111 @@ int tmg_sigma_min(tmg_ctx* ctx, const double* start, double mu_s, int max_steps,
   });
 }
 
+int tmg_solve_shifts(tmg_ctx* ctx, const double* b, double* x, int n_shift, const double* mu, double tol, int guess,
+                     double taylor_tol, int* iterations, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || !mu || n_shift < 1 || n_shift > 64 || !(tol > 0.0) || guess < 0 || guess > 2 ||
+        (guess == 2 && !(taylor_tol > 0.0)) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_solve_shifts: bad argument");
+    for (int k = 0; k < n_shift; k++)
+      if (!std::isfinite(mu[k])) return fail(ctx, TMG_ERR_ARG, "tmg_solve_shifts: twist not finite");
+    if (!c.gauge_loaded || !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_solve_shifts: needs a gauge field and a setup");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    tmg::Field bf, xf;
+    bf.create(c.g, TMG_PREC_F64, 1);
+    xf.create(c.g, TMG_PREC_F64, n_shift);
+    spinor_from_lex(c, stage_in(c, c.stage_a, b, col, where), bf.buf.p, TMG_PREC_F64);
+    SolveStats st{};
+    const int rc = solve_shifts(c, bf.buf.p, xf.buf.p, n_shift, mu, tol, guess, taylor_tol, 100000, st, iterations);
+    double* xd = stage_out_ptr(c, c.stage_b, x, col * n_shift, where);
+    for (int k = 0; k < n_shift; k++) spinor_to_lex(c, xf.col(c.g, k), TMG_PREC_F64, xd + k * col);
+    stage_out_finish(c, c.stage_b, x, col * n_shift, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    SolveStats s0{};
+    fill_stats(stats, st, s0, t0);
+    if (stats) stats->true_residual = st.true_residual;
+    return rc == TMG_OK ? TMG_OK : fail(ctx, rc, "tmg_solve_shifts: a shifted solve did not converge");
+  });
+}
+
+int tmg_mms_cg(tmg_ctx* ctx, const double* b, double* x, int n_shift, const double* sigma, double tol, int flavours,
+               tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || !sigma || n_shift < 1 || n_shift > 64 || !(tol > 0.0) || (flavours != 1 && flavours != 2) ||
+        !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_mms_cg: bad argument");
+    for (int s = 0; s < n_shift; s++)
+      if (!(sigma[s] >= 0.0) || !std::isfinite(sigma[s])) return fail(ctx, TMG_ERR_ARG, "tmg_mms_cg: shifts must be >= 0");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_mms_cg: no gauge field loaded");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t col = (size_t)24 * c.g.V;
+    const int nf = flavours;
+    tmg::Field bf, xf;
+    bf.create(c.g, TMG_PREC_F64, nf);
+    xf.create(c.g, TMG_PREC_F64, nf * n_shift);
+    const double* bd = stage_in(c, c.stage_a, b, col * nf, where);
+    for (int f = 0; f < nf; f++) spinor_from_lex(c, bd + f * col, bf.col(c.g, f), TMG_PREC_F64);
+    SolveStats st{}, s0{};
+    const int rc = mms_cg_solve(c, bf.buf.p, xf.buf.p, n_shift, sigma, tol, 1000000, nf, st);
+    double* xd = stage_out_ptr(c, c.stage_b, x, col * nf * n_shift, where);
+    for (int k = 0; k < nf * n_shift; k++) spinor_to_lex(c, xf.col(c.g, k), TMG_PREC_F64, xd + k * col);
+    stage_out_finish(c, c.stage_b, x, col * nf * n_shift, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    fill_stats(stats, st, s0, t0);
+    if (stats) stats->true_residual = st.true_residual;
+    return rc == TMG_OK ? TMG_OK : fail(ctx, rc, "tmg_mms_cg: not converged");
+  });
+}
+
+int tmg_rational_apply(tmg_ctx* ctx, const double* phi, double* out, int n, double a, const double* num,
+                       const double* den, double tol, int flavours, tmg_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!phi || !out || !num || !den || n < 1 || n > 32 || !(tol > 0.0) || !std::isfinite(a) ||
+        (flavours != 1 && flavours != 2) || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_rational_apply: bad argument");
+    for (int l = 0; l < n; l++) {
+      if (!(den[l] >= 0.0) || !std::isfinite(num[l])) return fail(ctx, TMG_ERR_ARG, "tmg_rational_apply: bad coefficients");
+      for (int k = 0; k < l; k++)
+        if (den[k] == den[l]) return fail(ctx, TMG_ERR_ARG, "tmg_rational_apply: repeated denominator shift");
+    }
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_rational_apply: no gauge field loaded");
+    const auto t0 = std::chrono::steady_clock::now();
+    // partial fractions a prod (x + num_l)/(x + den_l) = a (1 + sum_l r_l / (x + den_l))
+    std::vector<double> r(n);
+    for (int l = 0; l < n; l++) {
+      double pr = 1.0;
+      for (int k = 0; k < n; k++) {
+        pr *= num[k] - den[l];
+        if (k != l) pr /= den[k] - den[l];
+      }
+      r[l] = pr;
+    }
+    const size_t col = (size_t)24 * c.g.V;
+    const size_t nn = (size_t)flavours * 12 * c.g.V;
+    const int nf = flavours;
+    tmg::Field bf, xf;
+    bf.create(c.g, TMG_PREC_F64, nf);
+    xf.create(c.g, TMG_PREC_F64, nf * n);
+    const double* bd = stage_in(c, c.stage_a, phi, col * nf, where);
+    for (int f = 0; f < nf; f++) spinor_from_lex(c, bd + f * col, bf.col(c.g, f), TMG_PREC_F64);
+    SolveStats st{}, s0{};
+    const int rc = mms_cg_solve(c, bf.buf.p, xf.buf.p, n, den, tol, 1000000, nf, st);
+    for (int l = 0; l < n; l++) blas_axpy(c, r[l], 0.0, xf.col(c.g, l * nf), bf.buf.p, TMG_PREC_F64, nn);
+    blas_scale(c, a, 0.0, bf.buf.p, TMG_PREC_F64, nn);
+    double* od = stage_out_ptr(c, c.stage_b, out, col * nf, where);
+    for (int f = 0; f < nf; f++) spinor_to_lex(c, bf.col(c.g, f), TMG_PREC_F64, od + f * col);
+    stage_out_finish(c, c.stage_b, out, col * nf, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    fill_stats(stats, st, s0, t0);
+    if (stats) stats->true_residual = st.true_residual;
+    return rc == TMG_OK ? TMG_OK : fail(ctx, rc, "tmg_rational_apply: multi-shift CG not converged");
+  });
+}
+
 int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
   return guarded(ctx, [&]() -> int {
     if (!key) return fail(ctx, TMG_ERR_ARG, "tmg_tune: null key");
@@ -527,6 +694,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "kcycle_ctas_per_sm" && v >= 1 && v <= 4) ctx->c.kcycle_ctas_per_sm = v;
     else if (k == "tc_steps_per_range" && (v == 1 || v == 2 || v == 4)) ctx->c.tc_steps_per_range = v;
     else if (k == "coarse_grid" && v >= 0 && v <= 4096) ctx->c.coarse_grid = v;
+    else if (k == "eo_stage" && (v == 0 || v == 1)) ctx->c.eo_stage = v;
     else if (k == "outer_gs_fused" && (v == 0 || v == 1)) ctx->c.outer_gs_fused = v;
     else if (k == "force_prec" && (v == TMG_PREC_F64 || v == TMG_PREC_F32)) ctx->c.force_prec = v;
     else if (k == "kcycle_grid" && v >= 0 && v <= 4096) ctx->c.kcycle_grid = v;
@@ -921,14 +1089,41 @@ int tmg_solve(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double*
               int maxiter, tmg_stats* stats, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
-    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 5)
+    if (!b || !x || n_rhs <= 0 || !(tol > 0.0) || maxiter <= 0 || !valid_where(where) || method < 0 || method > 6)
       return fail(ctx, TMG_ERR_ARG, "tmg_solve: bad argument");
     if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no gauge field loaded");
-    if (method != TMG_SOLVE_CG_F64 && !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_solve: no multigrid setup");
+    if (method != TMG_SOLVE_CG_F64 && method != TMG_SOLVE_CG_EO && !c.mg_ready)
+      return fail(ctx, TMG_ERR_STATE, "tmg_solve: no multigrid setup");
     const auto t0 = std::chrono::steady_clock::now();
     const size_t col = (size_t)24 * c.g.V;
     tmg_stats acc{};
     int rc = TMG_OK;
+    if (method == TMG_SOLVE_CG_EO) {
+      const double mu0 = c.mu;
+      for (int j = 0; j < n_rhs; j++) {
+        c.mu = mu_per_col ? mu_per_col[j] : mu0;
+        const double* bd = stage_in(c, c.stage_a, b + j * col, col, where);
+        double* xd = stage_out_ptr(c, c.stage_b, x + j * col, col, where);
+        SolveStats st{};
+        int r;
+        try {
+          r = cg_eo_solve(c, bd, xd, tol, maxiter, st);
+        } catch (...) {
+          c.mu = mu0;
+          throw;
+        }
+        stage_out_finish(c, c.stage_b, x + j * col, col, where);
+        if (r != TMG_OK && rc == TMG_OK) rc = r;
+        acc.iterations += st.iterations;
+        acc.true_residual = std::max(acc.true_residual, st.true_residual);
+      }
+      c.mu = mu0;
+      TMG_CUDA(cudaStreamSynchronize(c.stream));
+      acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (stats) *stats = acc;
+      if (rc != TMG_OK) c.err = "odd-even CG did not converge";
+      return rc;
+    }
     if (method == TMG_SOLVE_MG_BATCHED) {
       if (n_rhs > 32) return fail(ctx, TMG_ERR_ARG, "tmg_solve: at most 32 columns per batched solve");
       tmg::Field bf, xf;

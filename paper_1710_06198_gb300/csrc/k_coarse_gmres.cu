@@ -152,7 +152,6 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   const int chunk = (n + G - 1) / G;
   const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int gwarp = blockIdx.x * nwarp + warp, nwarps_total = G * nwarp;
 
   // beta = ||b||
   {
@@ -182,24 +181,76 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
   }
   grid.sync();                                       // v_0 complete
-  for (int j = 0; j < a.m && !s_done; j++) {
+  // Hessenberg column j: previous rotations [[conj c, conj s], [-s, c]] applied down the new column
+  // (the running entry stays in registers), then the new rotation from (running entry, h_{j+1,j}),
+  // the residual estimate and the stopping test.  Run by one thread of every CTA from the same
+  // reduced values, so every CTA takes the same decision.
+  auto hessenberg_update = [&](int j) {
+    const double hn = s_hn;
+    double2 x0 = hcol[0];
+    for (int i = 0; i < j; i++) {
+      const double2 x1 = hcol[i + 1];
+      const double2 c = cs[i], s = sn[i];
+      hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
+                             c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
+      x0 = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                        -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+    }
+    // one reciprocal square root instead of a square root and four divisions
+    const double2 p = x0;
+    const double n2 = p.x * p.x + p.y * p.y + hn * hn;
+    const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+    const double den = n2 * inv;
+    const double2 c = n2 > 0.0 ? make_double2(p.x * inv, p.y * inv) : make_double2(1.0, 0.0);
+    const double2 sr = make_double2(hn * inv, 0.0);
+    cs[j] = c;
+    sn[j] = sr;
+    hcol[j] = make_double2(den, 0.0);
+    hcol[j + 1] = make_double2(0.0, 0.0);
+    const double2 g = gv[j];
+    gv[j + 1] = make_double2(-(sr.x * g.x), -(sr.x * g.y));
+    gv[j] = make_double2(c.x * g.x + c.y * g.y, c.x * g.y - c.y * g.x);
+    if (blockIdx.x == 0)
+      for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
+    s_k = j + 1;
+    const double res2 = gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y;
+    const double lim = a.rtol * s_beta;
+    if (res2 <= lim * lim || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
+  };
+  // Warp 0 of every CTA keeps out of the stencil products so that its first thread can update the
+  // Hessenberg column of the previous step meanwhile: the stencil of step j only needs the norm
+  // h_{j,j-1} (known before the rotations), and if the rotations of step j-1 stop the solve, the
+  // stencil rows of step j are simply not used.
+  const int swarp = warp - 1, snwarp = nwarp - 1;
+  const int sgwarp = blockIdx.x * snwarp + swarp, snwarps_total = G * snwarp;
+  // s_done is read only right after a grid barrier (or before the loop, where it is settled): the
+  // thread that updates the Hessenberg column may set it while other warps are still starting a
+  // step, and every thread must take the same number of grid barriers.
+  const bool zero_rhs = s_done;
+  for (int j = 0; j < a.m && !zero_rhs; j++) {
     // v_j = v_0, or the previous step's orthogonalised w scaled by 1 / h_{j,j-1}.
     const T2* src = j == 0 ? a.V : a.w;
     const S scale = j == 0 ? (S)1 : (S)(1.0 / s_hn);
     T2* vj = a.V + (size_t)j * n;
-    // (1) stencil products, one warp per (flavour, coarse site, stencil block) spread over the
-    //     whole grid: lanes are rows, so every column of a block is one coalesced 32-row read.  The
-    //     doublet's flavour mixing is added to the self block's row here, while src is read-only.
-    for (int task = gwarp; task < a.nf * a.nc * 9; task += nwarps_total) {
-      const int f = task / (a.nc * 9), t9 = task - f * a.nc * 9;
-      const int site = t9 / 9;
-      const int nb = a.nbr[t9];
-      const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
-      const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
-      const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
-      stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.rows + (size_t)task * a.nd, lane);
+    if (warp == 0) {
+      if (lane == 0 && j > 0) hessenberg_update(j - 1);
+    } else {
+      // (1) stencil products, one warp per (flavour, coarse site, stencil block) spread over the
+      //     grid's other warps: lanes are rows, so every column of a block is one coalesced read.
+      //     The doublet's flavour mixing is added to the self block's row here, while src is
+      //     read-only.
+      for (int task = sgwarp; task < a.nf * a.nc * 9; task += snwarps_total) {
+        const int f = task / (a.nc * 9), t9 = task - f * a.nc * 9;
+        const int site = t9 / 9;
+        const int nb = a.nbr[t9];
+        const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
+        const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
+        const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
+        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.rows + (size_t)task * a.nd, lane);
+      }
     }
-    grid.sync();                                     // partial rows complete
+    grid.sync();                                     // partial rows and the previous column complete
+    if (s_done) break;                               // the previous step met the stopping test
     // (2) own chunk: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const int f = e / n1, e1f = e - f * n1;
@@ -276,47 +327,17 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
 #pragma unroll 8
       for (int q = lane; q < G; q += 32) t += a.npart[q];
       t = warp_sum(t);
-      if (lane == 0) s_hn = sqrt(t);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // previous rotations [[conj c, conj s], [-s, c]] applied down the new column; the running
-      // entry stays in registers (only the loads of the untouched entries and of the rotations,
-      // which do not depend on the chain, touch shared memory)
-      const double hn = s_hn;
-      double2 x0 = hcol[0];
-      for (int i = 0; i < j; i++) {
-        const double2 x1 = hcol[i + 1];
-        const double2 c = cs[i], s = sn[i];
-        hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
-                               c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
-        x0 = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
-                          -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+      if (lane == 0) {
+        s_hn = sqrt(t);
+        s_k = j + 1;
+        // the last allowed step has no following stencil to hide its column update behind
+        if (j == a.m - 1) hessenberg_update(j);
       }
-      // new rotation from (p, q) = (running entry, hn): one reciprocal square root instead of a
-      // square root and four divisions
-      const double2 p = x0;
-      const double n2 = p.x * p.x + p.y * p.y + hn * hn;
-      const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
-      const double den = n2 * inv;
-      const double2 c = n2 > 0.0 ? make_double2(p.x * inv, p.y * inv) : make_double2(1.0, 0.0);
-      const double2 sr = make_double2(hn * inv, 0.0);
-      cs[j] = c;
-      sn[j] = sr;
-      hcol[j] = make_double2(den, 0.0);
-      hcol[j + 1] = make_double2(0.0, 0.0);
-      const double2 g = gv[j];
-      gv[j + 1] = make_double2(-(sr.x * g.x), -(sr.x * g.y));
-      gv[j] = make_double2(c.x * g.x + c.y * g.y, c.x * g.y - c.y * g.x);
-      if (blockIdx.x == 0)
-        for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
-      s_k = j + 1;
-      const double res2 = gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y;
-      const double lim = a.rtol * s_beta;
-      if (res2 <= lim * lim || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
     }
     __syncthreads();
   }
+  // a step whose column update was deferred and that ended the loop by reaching m: done above;
+  // a stop found after the stencil of the next step: done in that stencil phase
   grid.sync();                                       // rotated Hessenberg stored by CTA 0
   const int k = s_k;
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -84,8 +84,15 @@ void dslash(Ctx& c, int prec, void* y, const void* x, const void* b, double mu, 
   const int threads = 128;
   const int blocks = (c.g.V + threads - 1) / threads;
   if (!b) b = x;
-  ProfScope ps(c, PK_DSLASH_F64 + prec);
-  if (prec == TMG_PREC_F64) {
+  ProfScope ps(c, prec == PREC_H16 ? PK_DSLASH_F16 : PK_DSLASH_F64 + prec);
+  if (prec == PREC_H16) {
+    // all-FP16 storage: fixed-point spinors with per-site norms, FP16 links and clover; FP32 math
+    ++c.launches, k_dslash<float><<<blocks, threads, 0, c.stream>>>(c.g, spinor_h16(c, y), spinor_h16(c, (void*)x),
+                                                      spinor_h16(c, (void*)b),
+                                                      GaugeF16{c.op[2].U.as<short4>(), c.g.V},
+                                                      CloverF16{c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>(), c.g.V},
+                                                      (float)mu, mode, dagger);
+  } else if (prec == TMG_PREC_F64) {
     ++c.launches, k_dslash<double><<<blocks, threads, 0, c.stream>>>(c.g, sp64(c, y), sp64(c, x), sp64(c, b),
                                                        GaugeF64{c.op[0].U.as<double2>(), c.g.V},
                                                        CloverF64{c.op[0].A.as<double2>(), c.g.V}, mu, mode, dagger);

@@ -400,10 +400,6 @@ void convert_op_precisions(Ctx& c) {
 }
 
 // ------------------------------------------------------------------ spinor lex <-> internal
-// internal flat complex index of (site s, component k) = 2 ((k/2) V + s) + (k%2)
-__device__ __forceinline__ size_t spinor_flat(int V, int s, int k) {
-  return 2 * ((size_t)(k >> 1) * V + s) + (k & 1);
-}
 
 template <typename T2>
 __global__ void k_spinor_from_lex(Geom g, const double2* __restrict__ lex, T2* __restrict__ out) {
@@ -433,7 +429,43 @@ __global__ void k_spinor_to_lex(Geom g, const T2* __restrict__ in, double2* __re
   }
 }
 
+// lex FP64 <-> 16-bit fixed-point spinors with a per-site FP32 norm (value = q / 32767 * norm,
+// norm = the site's largest |component|, rounding to nearest-even)
+__global__ void k_spinor_lex_to_h16(Geom g, const double2* __restrict__ lex, SpinorF16 out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    Spinor<float> v;
+    for (int k = 0; k < 12; k++) {
+      const double2 z = lex[(size_t)i * 12 + k];
+      v.c[k] = {(float)z.x, (float)z.y};
+    }
+    out.store(s, v);
+  }
+}
+
+__global__ void k_spinor_h16_to_lex(Geom g, SpinorF16 in, double2* __restrict__ lex) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    Spinor<float> v;
+    in.load(s, v);
+    for (int k = 0; k < 12; k++) lex[(size_t)i * 12 + k] = make_double2((double)v.c[k].re, (double)v.c[k].im);
+  }
+}
+
+SpinorF16 spinor_h16(const Ctx& c, void* p) {
+  return SpinorF16{(int4*)p, reinterpret_cast<float*>((char*)p + (size_t)48 * c.g.V), c.g.V};
+}
+
 void spinor_from_lex(Ctx& c, const double* lex_dev, void* dst, int prec) {
+  if (prec == PREC_H16) {
+    ++c.launches, k_spinor_lex_to_h16<<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, spinor_h16(c, dst));
+    TMG_CHECK_LAUNCH();
+    return;
+  }
   if (prec == TMG_PREC_F64)
     ++c.launches, k_spinor_from_lex<double2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, (double2*)dst);
   else
@@ -442,6 +474,11 @@ void spinor_from_lex(Ctx& c, const double* lex_dev, void* dst, int prec) {
 }
 
 void spinor_to_lex(Ctx& c, const void* src, int prec, double* lex_dev) {
+  if (prec == PREC_H16) {
+    ++c.launches, k_spinor_h16_to_lex<<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, spinor_h16(c, (void*)src), (double2*)lex_dev);
+    TMG_CHECK_LAUNCH();
+    return;
+  }
   if (prec == TMG_PREC_F64)
     ++c.launches, k_spinor_to_lex<double2><<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)src, (double2*)lex_dev);
   else

@@ -299,6 +299,18 @@ __global__ void k_combine_b(const float2* __restrict__ Zb, size_t istride, int k
   }
 }
 
+// y_c = s_c x_c for ncol FP32 columns of n complex each (s on the device); grid (G, ncol)
+__global__ void k_scale_cols(const float2* __restrict__ x, float2* __restrict__ y, const double* __restrict__ sc, size_t n) {
+  const int c = blockIdx.y;
+  const float s = (float)sc[c];
+  const float2* xc = x + (size_t)c * n;
+  float2* yc = y + (size_t)c * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = xc[e];
+    yc[e] = make_float2(s * v.x, s * v.y);
+  }
+}
+
 size_t esize(int prec) { return prec == TMG_PREC_F64 ? 16 : 8; }
 
 int red_grid(const Ctx& c, size_t n) {
@@ -817,7 +829,8 @@ static int cg_solve(Ctx& c, const void* b, void* x, double mu, double tol, int m
 }
 
 // ---------------------------------------------------------------- solve
-int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st, int nf) {
+int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st, int nf,
+              bool use_x0) {
   if (method == TMG_SOLVE_CG_F64) return cg_solve(c, b, x, mu, tol, maxiter, st);
   const size_t n = (size_t)nf * 12 * c.g.V;
   // r = b - D x in FP64 (D_ND for the doublet)
@@ -840,8 +853,12 @@ int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol,
   c.fw_x.alloc(n * es);
   int c0 = 0, c1 = 0;
   if (c.coarse_iter_dev.p) TMG_CUDA(cudaMemcpyAsync(&c0, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  blas_zero(c, x, TMG_PREC_F64, n);
-  blas_copy(c, b, c.fw_r64.p, TMG_PREC_F64, n);
+  if (use_x0) {
+    residual(c.fw_r64.p);            // start from the caller's x
+  } else {
+    blas_zero(c, x, TMG_PREC_F64, n);
+    blas_copy(c, b, c.fw_r64.p, TMG_PREC_F64, n);
+  }
   const double bn = std::sqrt(blas_norm2(c, b, TMG_PREC_F64, n));
   if (!std::isfinite(bn)) throw Error{TMG_ERR_BREAKDOWN, "solve: right-hand side is not finite"};
   if (!(bn > 0.0)) return TMG_OK;
@@ -878,6 +895,217 @@ int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol,
     TMG_CUDA(cudaMemcpyAsync(&c1, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     st.coarse_iterations = c1 - c0;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------- odd-even CG (FP64)
+// D(mu) x = b through the even-odd reduction (Sec. 1.2; the odd-even CG of Fig. 1): CG on
+// Dhat Dhat^dag y = rhs_o with x_o = Dhat^dag y, rhs_o = b_o - H_oe M_e^-1 b_e, then
+// x_e = M_e^-1 (b_e - H_eo x_o).  b, x: lexicographic FP64 full-lattice fields on the device.
+int cg_eo_solve(Ctx& c, const double* b_lex, double* x_lex, double tol, int maxiter, SolveStats& st) {
+  eo_prepare(c);
+  const size_t h = (size_t)c.g.V / 2, n = 12 * h;
+  DBuf buf;
+  buf.alloc(8 * n * 16);
+  char* base = buf.as<char>();
+  void* be = base;
+  void* bo = base + n * 16;
+  void* xo = base + 2 * n * 16;
+  void* r = base + 3 * n * 16;
+  void* p = base + 4 * n * 16;
+  void* q = base + 5 * n * 16;
+  void* Aq = base + 6 * n * 16;
+  void* t = base + 7 * n * 16;
+  eo_from_lex(c, b_lex, be, 0, TMG_PREC_F64);
+  eo_from_lex(c, b_lex, bo, 1, TMG_PREC_F64);
+  const double bn2 = blas_norm2(c, be, TMG_PREC_F64, n) + blas_norm2(c, bo, TMG_PREC_F64, n);
+  if (!std::isfinite(bn2)) throw Error{TMG_ERR_BREAKDOWN, "cg_eo: right-hand side is not finite"};
+  blas_zero(c, xo, TMG_PREC_F64, n);
+  if (!(bn2 > 0.0)) {
+    blas_zero(c, t, TMG_PREC_F64, n);
+    eo_to_lex(c, t, x_lex, 0, TMG_PREC_F64, 1);
+    return TMG_OK;
+  }
+  // rhs_o = b_o - H_oe M_e^-1 b_e
+  eo_kernel(c, TMG_PREC_F64, 0, t, nullptr, be, 1.0, 1, 0);
+  eo_kernel(c, TMG_PREC_F64, 1, r, bo, t, 1.0, 0, 0);
+  blas_copy(c, r, p, TMG_PREC_F64, n);
+  const double rhs2 = blas_norm2(c, r, TMG_PREC_F64, n);
+  double rr = rhs2;
+  int it = 0;
+  // the odd-site system is solved until its residual is tol ||b||: the reconstruction keeps the
+  // even-site residual at rounding level, so the full residual follows the odd one
+  while (it < maxiter && rr > tol * tol * bn2) {
+    eo_apply(c, TMG_PREC_F64, q, p, t, 1);
+    eo_apply(c, TMG_PREC_F64, Aq, q, t, 0);
+    const double qq = blas_norm2(c, q, TMG_PREC_F64, n);
+    if (!(qq > 0.0) || !std::isfinite(qq)) throw Error{TMG_ERR_BREAKDOWN, "cg_eo: breakdown"};
+    const double a = rr / qq;
+    blas_axpy(c, a, 0.0, q, xo, TMG_PREC_F64, n);
+    blas_axpy(c, -a, 0.0, Aq, r, TMG_PREC_F64, n);
+    const double rr_new = blas_norm2(c, r, TMG_PREC_F64, n);
+    blas_xpay(c, r, rr_new / rr, 0.0, p, TMG_PREC_F64, n);
+    rr = rr_new;
+    it++;
+  }
+  // x_e = M_e^-1 (b_e - H_eo x_o)
+  eo_kernel(c, TMG_PREC_F64, 0, t, xo, be, -1.0, 1, 0);
+  eo_to_lex(c, t, x_lex, 0, TMG_PREC_F64, 0);
+  eo_to_lex(c, xo, x_lex, 1, TMG_PREC_F64, 0);
+  eo_check(c);
+  // true residual of the full system with the full-lattice FP64 operator
+  c.fw_t.alloc(2 * 12 * (size_t)c.g.V * 16);
+  void* xf = c.fw_t.p;
+  void* rf = c.fw_t.as<char>() + 12 * (size_t)c.g.V * 16;
+  void* bf = c.fw_r64.p;
+  c.fw_r64.alloc(12 * (size_t)c.g.V * 16);
+  bf = c.fw_r64.p;
+  spinor_from_lex(c, x_lex, xf, TMG_PREC_F64);
+  spinor_from_lex(c, b_lex, bf, TMG_PREC_F64);
+  dslash(c, TMG_PREC_F64, rf, xf, bf, c.mu, 1, 0);
+  st.iterations = it;
+  st.true_residual = std::sqrt(blas_norm2(c, rf, TMG_PREC_F64, 12 * (size_t)c.g.V) / bn2);
+  return st.true_residual <= tol ? TMG_OK : TMG_ERR_NOCONV;
+}
+
+// ---------------------------------------------------------------- multi-shift CG (FP64)
+// x_s = (A + sigma_s)^-1 b for all shifts at once with A = D(mu)^dag D(mu) (nf = 1) or
+// A = Q_ND^2 = D_ND^dag D_ND, Q_ND = (g5 x tau1) D_ND (nf = 2, Eqs. 2 and 4): the comparator of the
+// rational approximation's shifted solves (Sec. 3, MMS-CG).  The Krylov space is that of the seed
+// system A x = b; system s keeps a residual collinear with the seed's, r_s = zeta_s r, with the
+// shifted coefficients from the seed's alpha, beta (the recurrences of the shifted-CG
+// literature).  X: ns internal FP64 fields (nf flavours each).  Stops when every shifted residual is
+// <= tol ||b||; st.iterations = seed iterations, st.true_residual = the largest recomputed
+// ||b - (A + sigma_s) x_s|| / ||b||.
+int mms_cg_solve(Ctx& c, const void* b, void* X, int ns, const double* sigma, double tol, int maxiter, int nf,
+                 SolveStats& st) {
+  const size_t n1 = (size_t)12 * c.g.V, n = nf * n1;
+  DBuf buf;
+  buf.alloc((size_t)(4 + ns) * n * 16);
+  char* base = buf.as<char>();
+  void* r = base;
+  void* p = base + n * 16;
+  void* Ap = base + 2 * n * 16;
+  void* t = base + 3 * n * 16;
+  auto ps = [&](int s) { return (void*)(base + (size_t)(4 + s) * n * 16); };
+  auto xs = [&](int s) { return (void*)((char*)X + (size_t)s * n * 16); };
+  // y = g5 tau1 v for doublet fields [2][12 V]
+  auto g5_tau1 = [&](const void* v, void* y) {
+    blas_copy(c, v, (char*)y + n1 * 16, TMG_PREC_F64, n1);
+    blas_copy(c, (const char*)v + n1 * 16, y, TMG_PREC_F64, n1);
+    gamma5_inplace(c, y, TMG_PREC_F64);
+    gamma5_inplace(c, (char*)y + n1 * 16, TMG_PREC_F64);
+  };
+  auto applyA = [&](const void* v, void* out) {
+    if (nf == 1) {
+      dslash(c, TMG_PREC_F64, t, v, nullptr, c.mu, 0, 0);
+      dslash(c, TMG_PREC_F64, out, t, nullptr, c.mu, 0, 1);
+    } else {
+      dslash_nd(c, TMG_PREC_F64, out, v);
+      g5_tau1(out, t);
+      dslash_nd(c, TMG_PREC_F64, out, t);
+      g5_tau1(out, t);
+      blas_copy(c, t, out, TMG_PREC_F64, n);
+    }
+  };
+  const double bn2 = blas_norm2(c, b, TMG_PREC_F64, n);
+  if (!std::isfinite(bn2)) throw Error{TMG_ERR_BREAKDOWN, "mms_cg: right-hand side is not finite"};
+  for (int s = 0; s < ns; s++) blas_zero(c, xs(s), TMG_PREC_F64, n);
+  if (!(bn2 > 0.0)) return TMG_OK;
+  blas_copy(c, b, r, TMG_PREC_F64, n);
+  blas_copy(c, b, p, TMG_PREC_F64, n);
+  for (int s = 0; s < ns; s++) blas_copy(c, b, ps(s), TMG_PREC_F64, n);
+  std::vector<double> zc(ns, 1.0), zo(ns, 1.0);
+  std::vector<char> active(ns, 1);
+  double alpha_old = 1.0, beta_old = 0.0, rr = bn2;
+  int it = 0, n_active = ns;
+  while (it < maxiter && n_active > 0) {
+    applyA(p, Ap);
+    double pre, pim;
+    blas_dot(c, p, Ap, TMG_PREC_F64, n, &pre, &pim);
+    if (!(pre > 0.0) || !std::isfinite(pre)) throw Error{TMG_ERR_BREAKDOWN, "mms_cg: breakdown"};
+    const double alpha = rr / pre;
+    blas_axpy(c, -alpha, 0.0, Ap, r, TMG_PREC_F64, n);
+    const double rr_new = blas_norm2(c, r, TMG_PREC_F64, n);
+    const double beta = rr_new / rr;
+    for (int s = 0; s < ns; s++) {
+      if (!active[s]) continue;
+      const double zn = zc[s] * zo[s] * alpha_old /
+                        (alpha * beta_old * (zo[s] - zc[s]) + zo[s] * alpha_old * (1.0 + sigma[s] * alpha));
+      const double as = alpha * zn / zc[s];
+      const double bs = beta * (zn / zc[s]) * (zn / zc[s]);
+      blas_axpy(c, as, 0.0, ps(s), xs(s), TMG_PREC_F64, n);
+      blas_scale(c, bs, 0.0, ps(s), TMG_PREC_F64, n);
+      blas_axpy(c, zn, 0.0, r, ps(s), TMG_PREC_F64, n);
+      zo[s] = zc[s];
+      zc[s] = zn;
+      if (std::fabs(zn) * std::sqrt(rr_new) <= tol * std::sqrt(bn2)) {
+        active[s] = 0;
+        n_active--;
+      }
+    }
+    blas_xpay(c, r, beta, 0.0, p, TMG_PREC_F64, n);
+    alpha_old = alpha;
+    beta_old = beta;
+    rr = rr_new;
+    it++;
+  }
+  st.iterations = it;
+  double worst = 0.0;
+  for (int s = 0; s < ns; s++) {   // recomputed residuals b - (A + sigma_s) x_s
+    applyA(xs(s), Ap);
+    blas_axpy(c, sigma[s], 0.0, xs(s), Ap, TMG_PREC_F64, n);
+    blas_xpay(c, b, -1.0, 0.0, Ap, TMG_PREC_F64, n);
+    worst = std::max(worst, std::sqrt(blas_norm2(c, Ap, TMG_PREC_F64, n) / bn2));
+  }
+  st.true_residual = worst;
+  return n_active == 0 ? TMG_OK : TMG_ERR_NOCONV;
+}
+
+// ---------------------------------------------------------------- shifted systems, Taylor guesses
+// D(mu_k) x_k = b for k = 0 .. n-1 in order, every x_k to the FP64 residual tol by the mixed
+// multigrid.  guess 0: every solve from zero; 1: x_k starts from x_{k-1}; 2: first-order Taylor
+// expansion in the twist (Sec. 3: (Q + i mu + i delta)^-1 ~ (Q + i mu)^-1 - i delta (Q + i mu)^-2
+// with g5 D(mu) = Q + i mu): x_k^0 = x_{k-1} - i (mu_k - mu_{k-1}) D(mu_{k-1})^-1 g5 x_{k-1}, the
+// correction solved only to taylor_tol.  X: n internal FP64 columns.  st accumulates all solves
+// (the Taylor corrections included); iters[k] gets the outer iterations of system k alone.
+int solve_shifts(Ctx& c, const void* b, void* X, int n, const double* mu, double tol, int guess, double taylor_tol,
+                 int maxiter, SolveStats& st, int* iters) {
+  const size_t nf = (size_t)12 * c.g.V;
+  DBuf tb, tt;
+  if (guess == 2) {
+    tb.alloc(nf * 16);
+    tt.alloc(nf * 16);
+  }
+  int rc = TMG_OK;
+  for (int k = 0; k < n; k++) {
+    void* xk = (char*)X + (size_t)k * nf * 16;
+    bool x0 = false;
+    if (k > 0 && guess >= 1) {
+      const void* xp = (const char*)X + (size_t)(k - 1) * nf * 16;
+      blas_copy(c, xp, xk, TMG_PREC_F64, nf);
+      if (guess == 2) {
+        blas_copy(c, xp, tb.p, TMG_PREC_F64, nf);
+        gamma5_inplace(c, tb.p, TMG_PREC_F64);
+        SolveStats s1{};
+        const int r1 = solve_one(c, TMG_SOLVE_MG_MIXED, tb.p, tt.p, mu[k - 1], taylor_tol, maxiter, s1);
+        if (r1 != TMG_OK && r1 != TMG_ERR_NOCONV) return r1;
+        st.iterations += s1.iterations;
+        st.refinements += s1.refinements;
+        st.coarse_iterations += s1.coarse_iterations;
+        blas_axpy(c, 0.0, -(mu[k] - mu[k - 1]), tt.p, xk, TMG_PREC_F64, nf);   // x -= i delta t
+      }
+      x0 = true;
+    }
+    SolveStats sk{};
+    const int r = solve_one(c, TMG_SOLVE_MG_MIXED, b, xk, mu[k], tol, maxiter, sk, 1, x0);
+    if (iters) iters[k] = sk.iterations;
+    st.iterations += sk.iterations;
+    st.refinements += sk.refinements;
+    st.coarse_iterations += sk.coarse_iterations;
+    st.true_residual = std::max(st.true_residual, sk.true_residual);
+    if (r != TMG_OK && rc == TMG_OK) rc = r;
   }
   return rc;
 }
@@ -995,6 +1223,86 @@ double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double r
   return s2 > 0.0 ? std::sqrt(s2) : 0.0;
 }
 
+// ---------------------------------------------------------------- batched cycle (and its graph)
+// z = M v for ncol FP32 columns: P^dag, the batched coarse solve (three levels: one K-cycle per
+// column), P, SAP; one launch per operation for every column at two levels.
+static void batched_cycle_p(Ctx& c, int pf, int ncol, const void* v, void* z, void* cr, void* ce, const float* mu_dev,
+                            const double* mu) {
+  restrict_mrhs(c, ncol, v, cr);
+  if (c.l2_ready) {
+    const size_t nco = (size_t)c.cl.nc * c.cl.nd;
+    for (int col = 0; col < ncol; col++)
+      kcycle(c, TMG_PREC_F32, (const float2*)cr + col * nco, (float2*)ce + col * nco, mu[col], 0);
+  } else {
+    coarse_gmres_batched(c, ncol, cr, ce, mu_dev);
+  }
+  prolong_mrhs(c, ncol, ce, z);
+  sap_mrhs(c, pf, ncol, z, v, mu_dev, c.mg.sap_sweeps);
+}
+
+// The batched cycle replayed as a CUDA graph, captured once per key like the single-column cycle:
+// buffer addresses, column count, twists baked into host-side launches, parameters and knobs.
+static void batched_cycle_run(Ctx& c, int pf, int ncol, const void* v, void* z, void* cr, void* ce, const float* mu_dev,
+                              const double* mu) {
+  if (!c.cycle_graphs || c.prof.on) {
+    batched_cycle_p(c, pf, ncol, v, z, cr, ce, mu_dev, mu);
+    return;
+  }
+  auto keyf = [&]() {
+    std::vector<unsigned long long> k = cycle_key(c, pf, c.mg.prec_coarse, v, z, 0.0, 1);
+    auto u = [](const void* p) { return (unsigned long long)(uintptr_t)p; };
+    k.push_back(0xBA7C4ull);
+    k.push_back((unsigned long long)ncol);
+    k.push_back(u(cr));
+    k.push_back(u(ce));
+    k.push_back(u(mu_dev));
+    if (c.l2_ready)
+      for (int col = 0; col < ncol; col++) {
+        unsigned long long b;
+        memcpy(&b, &mu[col], sizeof b);
+        k.push_back(b);
+      }
+    return k;
+  };
+  std::vector<unsigned long long> key = keyf();
+  for (auto& e : c.graphs.g)
+    if (e.key == key) {
+      TMG_CUDA(cudaGraphLaunch(e.exec, c.stream));
+      c.launches += e.kernels;
+      return;
+    }
+  batched_cycle_p(c, pf, ncol, v, z, cr, ce, mu_dev, mu);
+  if (keyf() != key) return;
+  if (!c.graphs.cap) TMG_CUDA(cudaStreamCreateWithFlags(&c.graphs.cap, cudaStreamNonBlocking));
+  if (c.graphs.g.size() >= 64) c.graphs.clear();
+  cudaStream_t saved = c.stream;
+  const long long l0 = c.launches;
+  cudaGraph_t graph = nullptr;
+  c.stream = c.graphs.cap;
+  cudaError_t err = cudaStreamBeginCapture(c.graphs.cap, cudaStreamCaptureModeRelaxed);
+  if (err == cudaSuccess) {
+    try {
+      batched_cycle_p(c, pf, ncol, v, z, cr, ce, mu_dev, mu);
+    } catch (const Error&) {
+      err = cudaErrorStreamCaptureInvalidated;
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c.graphs.cap, &graph);
+    if (err == cudaSuccess) err = e2;
+  }
+  c.stream = saved;
+  const long long kernels = c.launches - l0;
+  c.launches = l0;
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess && graph) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess || !exec) {
+    cudaGetLastError();
+    c.cycle_graphs = 0;
+    return;
+  }
+  c.graphs.g.push_back(CycleGraph{key, exec, kernels});
+}
+
 // ---------------------------------------------------------------- batched mixed-precision solve
 // All columns advance in lock-step: one launch per operation for every column (multi-column
 // dslash, SAP, P, P^dag, and the batched coarse GMRES), per-column FGMRES recurrences on the host.
@@ -1007,7 +1315,11 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
   const int pf = c.mg.prec_fine == TMG_PREC_F64 ? TMG_PREC_F32 : c.mg.prec_fine;
   const size_t nco = (size_t)c.cl.nc * c.cl.nd;
   const int rg = red_grid(c, n);
-  DBuf r64, rin, e, V, Z, w, cr, ce, mu_dev, part, hdev, npart;
+  // workspaces kept in the context: a repeated batched solve allocates nothing
+  BatchWork& bw = c.bw;
+  DBuf &r64 = bw.r64, &rin = bw.rin, &e = bw.e, &V = bw.V, &Z = bw.Z, &w = bw.w, &cr = bw.cr, &ce = bw.ce,
+       &mu_dev = bw.mu, &part = bw.part, &hdev = bw.h, &npart = bw.npart, &inv_dev = bw.inv;
+  inv_dev.alloc(ncol * sizeof(double));
   r64.alloc(ncol * n * 16);
   rin.alloc(ncol * n * 8);
   e.alloc(ncol * n * 8);
@@ -1080,17 +1392,8 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
     for (int it = 0; it < m; it++) {
       float2* vj = Vp + (size_t)it * istride;
       float2* zj = Zp + (size_t)it * istride;
-      // z = M v (one batched cycle)
-      restrict_mrhs(c, ncol, vj, cr.p);
-      if (c.l2_ready) {   // three levels: one K-cycle per column
-        const size_t nco = (size_t)c.cl.nc * c.cl.nd;
-        for (int col = 0; col < ncol; col++)
-          kcycle(c, TMG_PREC_F32, cr.as<float2>() + col * nco, ce.as<float2>() + col * nco, mu[col], 0);
-      } else {
-        coarse_gmres_batched(c, ncol, cr.p, ce.p, mu_dev.as<float>());
-      }
-      prolong_mrhs(c, ncol, ce.p, zj);
-      sap_mrhs(c, pf, ncol, zj, vj, mu_dev.as<float>(), c.mg.sap_sweeps);
+      // z = M v (one batched cycle, replayed as a graph)
+      batched_cycle_run(c, pf, ncol, vj, zj, cr.p, ce.p, mu_dev.as<float>(), mu);
       dslash_mrhs(c, pf, ncol, w.p, zj, nullptr, mu_dev.as<float>(), 0);
       for (int pass = 0; pass < 2; pass++) {
         ++c.launches, k_mdot_partial_b<<<dim3(rg, it + 1, ncol), 256, 0, c.stream>>>(Vp, istride, w.as<float2>(), n, part.as<double2>());
@@ -1140,11 +1443,11 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
         inv[j] = hn > 0.0 ? 1.0 / hn : 0.0;
       }
       if (all_done || it == m - 1) break;
+      // v_{it+1} = w / h_{it+1,it} for every column in one launch
       float2* vn = Vp + (size_t)(it + 1) * istride;
-      for (int j = 0; j < ncol; j++) {
-        blas_copy(c, w.as<float2>() + (size_t)j * n, vn + (size_t)j * n, TMG_PREC_F32, n);
-        blas_scale(c, inv[j], 0.0, vn + (size_t)j * n, TMG_PREC_F32, n);
-      }
+      TMG_CUDA(cudaMemcpyAsync(inv_dev.p, inv.data(), ncol * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+      ++c.launches, k_scale_cols<<<dim3(egrid(c, n), ncol), 256, 0, c.stream>>>(w.as<float2>(), vn, inv_dev.as<double>(), n);
+      TMG_CHECK_LAUNCH();
     }
     // per-column back substitution (only over the steps each column has: all columns used k steps)
     std::vector<double2> yc((size_t)ncol * (MAXM + 1));

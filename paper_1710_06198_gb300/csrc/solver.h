@@ -23,8 +23,18 @@ void mg_setup2(Ctx& c, const double* v1_dev);
 void mg_cycle(Ctx& c, const void* r, void* z, double mu);
 // Solve D(mu) x = b on FP64 internal fields (b, x: F64 storage).  Returns a tmg_status.
 // nf = 2: the doublet D_ND (Eq. 2) on F64 fields [2][12 V] (mu unused; mubar, epsbar of the context).
+// use_x0: x holds the initial guess (multigrid methods; CG always starts from zero).
 int solve_one(Ctx& c, int method, const void* b, void* x, double mu, double tol, int maxiter, SolveStats& st,
-              int nf = 1);
+              int nf = 1, bool use_x0 = false);
+// D(c.mu) x = b by the odd-even CG on the Schur operator (FP64); b, x lexicographic on the device.
+int cg_eo_solve(Ctx& c, const double* b_lex, double* x_lex, double tol, int maxiter, SolveStats& st);
+// Multi-shift CG on A + sigma_s, A = D^dag D (nf = 1) or Q_ND^2 (nf = 2), FP64 internal fields.
+int mms_cg_solve(Ctx& c, const void* b, void* X, int ns, const double* sigma, double tol, int maxiter, int nf,
+                 SolveStats& st);
+// Shifted systems D(mu_k) x_k = b in order with zero / previous-solution / first-order Taylor
+// initial guesses (guess 0 / 1 / 2); see solver.cu.
+int solve_shifts(Ctx& c, const void* b, void* X, int n, const double* mu, double tol, int guess, double taylor_tol,
+                 int maxiter, SolveStats& st, int* iters);
 // sigma_min(D_W) by Lanczos on (D(mu_s)^dag D(mu_s))^-1 from the FP64 field `start` (two solves of
 // method `method` per step, to solve_tol); see solver.cu.
 double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double rtol, double solve_tol, int method,

@@ -48,9 +48,19 @@ struct DBuf {
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
-// Fine spinor field (one or more columns) in F64 or F32 storage; complex count per column 12 V.
+// Internal storage code of an all-FP16 fine field: spinors as 16-bit fixed point with one FP32
+// norm per site (SpinorF16), links and clover in their FP16 forms.  Not a public precision: the
+// ABI's TMG_PREC_F16 selects it for operator applications.
+constexpr int PREC_H16 = 3;
+
+// Bytes of one fine spinor column in storage precision prec (H16: 3 int4 + 1 float per site).
+inline size_t spinor_col_bytes(const Geom& g, int prec) {
+  return prec == TMG_PREC_F64 ? (size_t)192 * g.V : prec == PREC_H16 ? (size_t)52 * g.V : (size_t)96 * g.V;
+}
+
+// Fine spinor field (one or more columns) in F64, F32 or H16 storage; complex count per column 12 V.
 struct Field {
-  int prec = 1;       // TMG_PREC_F64 or TMG_PREC_F32
+  int prec = 1;       // TMG_PREC_F64, TMG_PREC_F32 or PREC_H16
   int ncol = 1;
   DBuf buf;
   size_t col_elems(const Geom& g) const { return (size_t)12 * g.V; }
@@ -58,9 +68,9 @@ struct Field {
   void create(const Geom& g, int prec_, int ncol_ = 1) {
     prec = prec_;
     ncol = ncol_;
-    buf.alloc(col_elems(g) * elem_bytes() * ncol);
+    buf.alloc(spinor_col_bytes(g, prec) * ncol);
   }
-  void* col(const Geom& g, int j) const { return (char*)buf.p + col_elems(g) * elem_bytes() * j; }
+  void* col(const Geom& g, int j) const { return (char*)buf.p + spinor_col_bytes(g, prec) * j; }
 };
 
 // Coarse vector: [ncoarse][nd] complex in F64 or F32.
@@ -103,7 +113,7 @@ struct Coarse2 {
 
 // Optional per-kernel-class timing with CUDA events on the context stream (tmg_profile).
 enum { PK_DSLASH_F64 = 0, PK_DSLASH_F32, PK_DSLASH_F16, PK_SAP_F64, PK_SAP_F32, PK_SAP_F16, PK_RESTRICT,
-       PK_PROLONG, PK_COARSE, PK_COARSE_SOLVE, PK_COUNT };
+       PK_PROLONG, PK_COARSE, PK_COARSE_SOLVE, PK_EO_F64, PK_EO_F32, PK_COUNT };
 
 struct Prof {
   bool on = false;
@@ -126,6 +136,23 @@ struct Prof {
       v.clear();
     }
   }
+};
+
+// Workspaces of the lock-step batched solve (solver.cu), grown on demand and kept between calls.
+struct BatchWork {
+  DBuf r64, rin, e, V, Z, w, cr, ce, mu, part, h, npart, inv;
+};
+
+// Even-odd reduced operator data (k_eo.cu): half-lattice links (FP64 12-real, FP32 8-real) of both
+// parities, the odd sites' clover field and the even sites' inverse (A + i mu g5)^-1, for the
+// context's field and the twist mu they were built at.
+struct EoData {
+  bool ready = false;   // links and clover packed for the current gauge field, kappa and c_sw
+  double mu = 0.0;      // twist of the stored inverse
+  DBuf U64[2], U32[2];
+  DBuf Ao64, Ao32, Mi64, Mi32;
+  DBuf flag;            // [0] singular block found, [1] a staging wait gave up
+  DBuf t, w;            // half-lattice work fields
 };
 
 // Captured CUDA graphs of the preconditioner cycle (solver.cu), keyed by everything the captured
@@ -183,7 +210,7 @@ struct Ctx {
   int coarse_ctas_per_sm = 2;   // CTAs per SM of the persistent coarse GMRES (bounded by occupancy)
   int coarse_gs_passes = 0;     // classical Gram-Schmidt passes in the coarse GMRES (0: 1 for FP32, 2 for FP64)
   int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
-  int force_prec = TMG_PREC_F32;   // force kernels: FP32 inputs with FP64 sums (TMG_PREC_F32) or all FP64
+  int force_prec = TMG_PREC_F64;   // force kernels: all FP64 (TMG_PREC_F64) or FP32 inputs with FP64 sums
   int outer_gs_fused = 1;       // outer FGMRES: fuse pass 1's update with pass 2's dot products
   int coarse_grid = 0;          // CTAs of the persistent coarse GMRES (0: coarse_ctas_per_sm x SMs)
   int kcycle_grid = 0;          // CTAs of the persistent K-cycle (0: kcycle_ctas_per_sm x SMs)
@@ -191,6 +218,9 @@ struct Ctx {
   int cycle_graphs = 1;         // replay the preconditioner cycle of the outer FGMRES as a CUDA graph
   GraphCache graphs;
   Prof prof;
+  EoData eo;
+  BatchWork bw;
+  int eo_stage = 1;             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
 };
 
 // Records a start event on construction and an end event on destruction when profiling is on.
@@ -225,9 +255,11 @@ void gauge_lex_to_internal(Ctx& c, const double* lex_dev);
 void rotate_gauge(Ctx& c, const double* omega_dev, double step);
 void build_clover(Ctx& c);
 void convert_op_precisions(Ctx& c);
-// lex FP64 [V][12] complex -> internal field column (prec F64 or F32)
+// lex FP64 [V][12] complex -> internal field column (prec F64, F32 or PREC_H16)
 void spinor_from_lex(Ctx& c, const double* lex_dev, void* dst, int prec);
 void spinor_to_lex(Ctx& c, const void* src, int prec, double* lex_dev);
+// view of an H16 spinor column: 3 int4 chunks per site, then the per-site norms
+SpinorF16 spinor_h16(const Ctx& c, void* p);
 void convert_field(Ctx& c, const void* src, int psrc, void* dst, int pdst, size_t n_complex);
 
 // complex BLAS on flat arrays of n complex numbers (prec F64: double2, F32: float2)
@@ -253,6 +285,19 @@ void blas_dot(Ctx& c, const void* x, const void* y, int prec, size_t n, double* 
 void dslash(Ctx& c, int prec, void* y, const void* x, const void* b, double mu, int mode, int dagger);
 // non-degenerate doublet (Eq. 2) on F64 / F32 fields with 2 flavour columns
 void dslash_nd(Ctx& c, int prec, void* y, const void* x);
+
+// ---------------------------------------------------------------- even-odd operator (k_eo.cu)
+// (re)build the even-odd data for the current field and c.mu
+void eo_prepare(Ctx& c);
+// y_o = Dhat(mu) x_o (dagger: Dhat^dag) on half-lattice fields of precision F64 / F32; t: scratch
+void eo_apply(Ctx& c, int prec, void* y, const void* x, void* t, int dagger);
+// which = 0: out = M_e^-1 (bt + hc H_eo x); which = 1: out = [M_o x | x] - H_oe bt (usem selects)
+void eo_kernel(Ctx& c, int prec, int which, void* out, const void* x, const void* bt, double hc, int usem, int dagger);
+// TMG_ERR_TIMEOUT if a staging wait of an even-odd kernel gave up (synchronises)
+void eo_check(Ctx& c);
+// full-lattice lexicographic FP64 <-> half-lattice field of one parity
+void eo_from_lex(Ctx& c, const double* lex, void* out, int parity, int prec);
+void eo_to_lex(Ctx& c, const void* in, double* lex, int parity, int prec, int zero_other);
 
 // ---------------------------------------------------------------- force (k_force.cu)
 // F (lexicographic [V][4][3][3] complex, device) of S = ||D^-1 phi||^2 from internal F64 fields

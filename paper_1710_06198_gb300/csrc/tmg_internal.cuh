@@ -143,6 +143,11 @@ __device__ __forceinline__ int neighbour(const Geom& g, const int c[4], int mu, 
 }
 
 // ------------------------------------------------------------------ spinor storage
+// internal flat complex index of (site s, component k) = 2 ((k/2) V + s) + (k%2)
+__device__ __forceinline__ size_t spinor_flat(int V, int s, int k) {
+  return 2 * ((size_t)(k >> 1) * V + s) + (k & 1);
+}
+
 // A spinor in registers: 12 complex, index spin*3 + colour.
 template <typename R> struct Spinor { cpx<R> c[12]; };
 

@@ -36,7 +36,77 @@ def sigma_at(ctx, U, w, m0, mu_s, start, v0, prm, log, t0):
     return sigma
 
 
-def search(name, start_m0=-0.5, step=0.1, band=0.02, mu_s=None, m0_min=-2.0, n_bisect=12):
+def find_crossing(sig, target, start_m0=-0.5, step=0.05, band=0.02, m0_min=-2.0, n_bisect=14, n_golden=14):
+    """The first crossing from above of sigma(m0) = target, with sigma(m0) evaluated by `sig`.
+
+    Walks m0 down from start_m0 in steps; stops at the first value below the target, or once sigma
+    has risen twice after a minimum: sigma_min of the Wilson operator moves with m0 like |m0 - m_c|
+    near a real eigenvalue m_c, so a walk can step over the dip.  A passed dip is searched by golden
+    sections for a point below the target.  The last interval (sigma above the target at its upper
+    end, below at its lower end) is then bisected until sigma is within the relative band of the
+    target.  Returns (m0 of the evaluation closest to the target, {m0: sigma} of all evaluations)."""
+    ev = {}
+
+    def f(m):
+        m = round(m, 10)
+        if m not in ev:
+            ev[m] = sig(m)
+        return ev[m]
+
+    lo = None
+    m, best_m, rises = start_m0, start_m0, 0
+    f(m)
+    while m - step >= m0_min - 1e-12:
+        m = round(m - step, 10)
+        if f(m) < target:
+            lo = m
+            break
+        if ev[m] < ev[round(best_m, 10)]:
+            best_m, rises = m, 0
+        else:
+            rises += 1
+            if rises >= 2:
+                break
+    if lo is None:
+        a, b = best_m - step, best_m + step
+        gr = 0.5 * (5.0 ** 0.5 - 1.0)
+        c, d = b - gr * (b - a), a + gr * (b - a)
+        for _ in range(n_golden):
+            if f(c) < target:
+                lo = c
+                break
+            if f(d) < target:
+                lo = d
+                break
+            if ev[round(c, 10)] < ev[round(d, 10)]:
+                b, d = d, c
+                c = b - gr * (b - a)
+            else:
+                a, c = c, d
+                d = a + gr * (b - a)
+    if lo is None:
+        return min(ev, key=lambda mm: abs(ev[mm] - target)), ev
+    # bisect the bracket [lo, hi] (sigma below the target at lo, at or above it at hi) onto the
+    # crossing nearest hi, i.e. the upper branch of the dip: every point strictly inside the dip has
+    # sigma below the target, so a midpoint at or above it lies on the upper branch
+    ups = [mm for mm, v in ev.items() if mm > lo and v >= target]
+    hi = min(ups) if ups else lo + step
+    for _ in range(n_bisect):
+        if abs(f(hi) - target) <= band * target:
+            break
+        mid = 0.5 * (hi + lo)
+        v = f(mid)
+        if v < target:
+            lo = mid
+        else:
+            hi = mid
+        if abs(v - target) <= band * target:
+            break
+    bracket = [mm for mm in ev if lo - 1e-9 <= mm <= hi + 1e-9]
+    return min(bracket, key=lambda mm: abs(ev[mm] - target)), ev
+
+
+def search(name, start_m0=-0.5, step=0.05, band=0.02, mu_s=None, m0_min=-2.0):
     from synth import fields, workloads
     w = workloads.WORKLOADS[name]
     target = w["sigma_target"]
@@ -50,44 +120,22 @@ def search(name, start_m0=-0.5, step=0.1, band=0.02, mu_s=None, m0_min=-2.0, n_b
     v0 = fields.gaussian_spinor(dims, w["seed"] + 100, n=w["nv"])
     start = fields.gaussian_spinor(dims, w["seed"] + 300)
     log, t0 = [], time.time()
-    hi, s_hi = start_m0, sigma_at(ctx, U, w, start_m0, mu_s, start, v0, prm, log, t0)
-    lo = None
-    m = hi
-    while lo is None and m - step >= m0_min - 1e-12:
-        m = round(m - step, 10)
-        s = sigma_at(ctx, U, w, m, mu_s, start, v0, prm, log, t0)
-        if s < target:
-            lo = m
-        else:
-            hi, s_hi = m, s
-    best = min(log, key=lambda e: abs(e["sigma_min"] - target))
-    if lo is not None:
-        for _ in range(n_bisect):
-            if abs(best["sigma_min"] - target) <= band * target:
-                break
-            mid = 0.5 * (hi + lo)
-            s = sigma_at(ctx, U, w, mid, mu_s, start, v0, prm, log, t0)
-            if s < target:
-                lo = mid
-            else:
-                hi = mid
-            best = min(log, key=lambda e: abs(e["sigma_min"] - target))
+    m0, ev = find_crossing(lambda m: sigma_at(ctx, U, w, m, mu_s, start, v0, prm, log, t0), target, start_m0, step,
+                           band, m0_min)
     ctx.close()
-    m0 = best["m0"]
-    return {"m0": m0, "kappa": kappa_of(m0), "sigma_min": best["sigma_min"], "target": target,
-            "reached_target": abs(best["sigma_min"] - target) <= band * target, "mu_s": mu_s,
+    return {"m0": m0, "kappa": kappa_of(m0), "sigma_min": ev[m0], "target": target,
+            "reached_target": abs(ev[m0] - target) <= band * target, "mu_s": mu_s,
             "sigma_lattice": list(dims), "eps": w["eps"], "seed": w["seed"], "csw": w["csw"],
             "rule": "first crossing from above of sigma_min(D_W) = target on the workload lattice (band %g)" % band,
             "log": log, "gpu_s": round(time.time() - t0, 1),
-            "source": "tmg_sigma_min on %s: m0 = %.5f, sigma_min(D_W) = %.3e" % ("x".join(map(str, dims)), m0,
-                                                                                best["sigma_min"])}
+            "source": "tmg_sigma_min on %s: m0 = %.6f, sigma_min(D_W) = %.3e" % ("x".join(map(str, dims)), m0, ev[m0])}
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("workload")
     ap.add_argument("--start", type=float, default=-0.5)
-    ap.add_argument("--step", type=float, default=0.1)
+    ap.add_argument("--step", type=float, default=0.05)
     ap.add_argument("--mu-s", type=float, default=None)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)

@@ -58,7 +58,10 @@ def test_force_with_multigrid_solves_matches_oracle():
     phi = fields.gaussian_spinor(DIMS, 86)
     ctx = _ctx(U, p)
     _setup(ctx)
-    S, F, st = ctx.force(phi, tol=1e-12)
+    S, F, st = ctx.force(phi, tol=1e-12)           # the default FP64 force kernels
+    ctx.tune("force_prec", tmg.PREC_F32)           # FP32 inputs, FP64 sums
+    S32, F32, _ = ctx.force(phi, tol=1e-12)
+    ctx.tune("force_prec", tmg.PREC_F64)
     C = dirac.clover_term(U, p.csw)
     D = lambda v: dirac.apply_D(U, v, p, clover=C)
     Dd = lambda v: dirac.apply_Ddag(U, v, p, clover=C)
@@ -72,6 +75,7 @@ def test_force_with_multigrid_solves_matches_oracle():
 
     want = force.force(U, phi, p, solve)
     assert rel(F, want) < 1e-8
+    assert rel(F32, want) < 1e-6
     assert abs(S - force.action(U, phi, p, solve)) < 1e-9 * S
 
 

@@ -1,6 +1,7 @@
 """GPU parity of the fine operators (called through the C ABI) against the FP64 oracle.
 
-Tolerances (relative L2 over the whole field): FP64 1e-13, FP32 1e-6, FP16 storage 5e-3.
+Tolerances (relative L2 over the whole field): FP64 1e-13, FP32 1e-6, FP16 storage 5e-3 (spinors,
+links and clover all in 16-bit fixed point for D, D^dag and the hopping term).
 Lattices: 8x4x4x4 with 4x2x2x2 blocks (16 blocks, every site on a block face in two directions),
 8^4 with 4^4 blocks, and the full 16^3x32 lattice of the mixed-precision workload.
 The lattice volume is always a multiple of 512 (16 blocks of >= 32 sites), so the 128-thread
