@@ -53,6 +53,7 @@ class Params:
     tbc: int = -1
     mubar: float = 0.0
     epsbar: float = 0.0
+    ndshift: float = 0.0   # delta of the shifted doublet D_ND + i delta G5 x tau1 (Sec. 3)
 
     @property
     def m0(self):
@@ -211,9 +212,14 @@ def apply_doublet(U, psi2, p: Params, clover=None):
 
 def apply_DND(U, psi2, p: Params, clover=None):
     """Non-degenerate doublet of Eq. 2 on psi2[2, ...]:
-       [[D(mubar), -epsbar], [-epsbar, D(-mubar)]]."""
+       [[D(mubar), -epsbar], [-epsbar, D(-mubar)]], plus i delta G5 x tau1 when p.ndshift = delta:
+       (G5 x tau1)(D_ND + i delta G5 x tau1) = Q_ND + i delta, the shifted systems of the rational
+       approximation (Sec. 3: Q_ND^2 + delta^2 = (Q_ND - i delta)(Q_ND + i delta))."""
     u = apply_D(U, psi2[0], p, p.mubar, clover) - p.epsbar * psi2[1]
     d = apply_D(U, psi2[1], p, -p.mubar, clover) - p.epsbar * psi2[0]
+    if p.ndshift:
+        u = u + 1j * p.ndshift * apply_g5(psi2[1])
+        d = d + 1j * p.ndshift * apply_g5(psi2[0])
     return np.stack([u, d])
 
 

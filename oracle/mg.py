@@ -304,10 +304,15 @@ def coarse_apply_definition(U, p, clover, P, x, mu=None):
     return restrict(P, dirac.apply_D(U, prolong(P, x), p, mu, clover))
 
 
-def coarse_apply_nd(Dc: CoarseOp, x2, mubar, epsbar):
-    """D_ND,c = D_c x I2 + i mubar G5_c x tau3 - epsbar I x tau1 (Sec. 1.1, Eq. 2 coarsened)."""
+def coarse_apply_nd(Dc: CoarseOp, x2, mubar, epsbar, delta=0.0):
+    """D_ND,c = D_c x I2 + i mubar G5_c x tau3 - epsbar I x tau1 (Sec. 1.1, Eq. 2 coarsened), plus
+    i delta G5_c x tau1 for the shifted doublet (P_ND^dag (G5 x tau1) P_ND = G5_c x tau1)."""
     u = coarse_apply(Dc, x2[0], mubar) - epsbar * x2[1]
     d = coarse_apply(Dc, x2[1], -mubar) - epsbar * x2[0]
+    if delta:
+        g = coarse_gamma5(Dc.nv)
+        u = u + 1j * delta * g * x2[1]
+        d = d + 1j * delta * g * x2[0]
     return np.stack([u, d])
 
 

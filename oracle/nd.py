@@ -6,6 +6,10 @@ of the single-flavour operator used flavour-diagonally, P_ND = P x I2, so
 D_ND,c = P_ND^dag D_ND P_ND = D_c x I2 + i mubar G5_c x tau3 - epsbar I x tau1 (P^dag P = I and
 G5 P = P G5_c); the third level repeats this with P2_ND = P2 x I2.
 
+The shifted doublet systems of the rational approximation (Sec. 3, Q_ND^2 + delta^2 =
+(Q_ND - i delta)(Q_ND + i delta) with Q_ND + i delta = (G5 x tau1)(D_ND + i delta G5 x tau1)) add the
+site-local term i delta G5 x tau1 (p.ndshift), which P_ND maps to i delta G5_c x tau1.
+
 Readings (the paper gives only the coarse operator): the smoother is SAP on D_ND, whose block
 solves are MR steps on the flavour-coupled block operator (inner products over both flavours);
 the cycle, the coarse GMRES, the level-1 K-cycle and the outer FGMRES are those of the single-flavour
@@ -29,6 +33,9 @@ def apply_DND_blocks(U, psi2, p: dirac.Params, clover, bdims):
     is site-local)."""
     u = mg.apply_D_blocks(U, psi2[0], p, clover, bdims, p.mubar) - p.epsbar * psi2[1]
     d = mg.apply_D_blocks(U, psi2[1], p, clover, bdims, -p.mubar) - p.epsbar * psi2[0]
+    if p.ndshift:
+        u = u + 1j * p.ndshift * dirac.apply_g5(psi2[1])
+        d = d + 1j * p.ndshift * dirac.apply_g5(psi2[0])
     return np.stack([u, d])
 
 
@@ -83,14 +90,14 @@ def prolong_c_nd(P2, c2):
 class Level1ND:
     """Level-1 K-cycle of the doublet on top of a single-flavour Level1 (its P2 and D_cc)."""
 
-    def __init__(self, L1: mg.Level1, mubar, epsbar):
-        self.L1, self.mubar, self.epsbar = L1, mubar, epsbar
+    def __init__(self, L1: mg.Level1, mubar, epsbar, delta=0.0):
+        self.L1, self.mubar, self.epsbar, self.delta = L1, mubar, epsbar, delta
 
     def A(self, x2):
-        return mg.coarse_apply_nd(self.L1.Dc, x2, self.mubar, self.epsbar)
+        return mg.coarse_apply_nd(self.L1.Dc, x2, self.mubar, self.epsbar, self.delta)
 
     def A2(self, x2):
-        return mg.coarse_apply_nd(self.L1.Dcc, x2, self.mubar, self.epsbar)
+        return mg.coarse_apply_nd(self.L1.Dcc, x2, self.mubar, self.epsbar, self.delta)
 
     def smooth(self, b2, x2):
         r = b2 - self.A(x2)
@@ -113,7 +120,7 @@ class HierarchyND:
 
     def __init__(self, H: mg.Hierarchy, L1: mg.Level1 = None):
         self.H, self.p = H, H.p
-        self.L1 = None if L1 is None else Level1ND(L1, H.p.mubar, H.p.epsbar)
+        self.L1 = None if L1 is None else Level1ND(L1, H.p.mubar, H.p.epsbar, H.p.ndshift)
 
     def D(self, x2):
         return dirac.apply_DND(self.H.U, x2, self.p, self.H.clover)
@@ -123,7 +130,7 @@ class HierarchyND:
         return sap_nd(self.H.U, self.p, self.H.clover, b2, m.block, m.sap_sweeps, m.sap_mr, x0)
 
     def coarse_apply(self, c2):
-        return mg.coarse_apply_nd(self.H.Dc, c2, self.p.mubar, self.p.epsbar)
+        return mg.coarse_apply_nd(self.H.Dc, c2, self.p.mubar, self.p.epsbar, self.p.ndshift)
 
     def coarse_solve(self, c2):
         if self.L1 is not None:

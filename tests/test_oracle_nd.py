@@ -119,3 +119,51 @@ def test_three_level_doublet_solve_equals_cg():
     xo, _, _ = krylov.cg_normal(D, Dd, b, tol=1e-13)
     assert res <= 1e-12
     assert rel(x, xo) < 1e-9
+
+
+def test_shifted_doublet_identities():
+    """The shifted doublet of the rational approximation (Sec. 3): (G5 x tau1) D_ND(delta) =
+    Q_ND + i delta, so solving D_ND(+delta) then D_ND(-delta) applies (Q_ND^2 + delta^2)^-1 (dense
+    on 2^4); its coarse operator equals P_ND^dag D_ND(delta) P_ND."""
+    import dataclasses
+    dims = (2, 2, 2, 2)
+    U = fields.gauge_field(dims, 0.5, 175)
+    p = dirac.Params(kappa=dirac.kappa_from_m0(-0.2), csw=1.2, tbc=-1, mubar=0.12, epsbar=0.13)
+    C = dirac.clover_term(U, p.csw)
+    delta = 0.07
+    pp, pm = dataclasses.replace(p, ndshift=delta), dataclasses.replace(p, ndshift=-delta)
+    g5t1 = lambda v: dirac.apply_g5(v[::-1])
+    x = fields.gaussian_spinor(dims, 176, n=2)
+    assert rel(g5t1(dirac.apply_DND(U, x, pp, C)), dirac.apply_QND(U, x, p, C) + 1j * delta * x) < 1e-15
+    shape = (2,) + fields.lattice_shape(dims) + (4, 3)
+    Q = dirac.dense_matrix(lambda v: dirac.apply_QND(U, v, p, C), shape)
+    Dp = dirac.dense_matrix(lambda v: dirac.apply_DND(U, v, pp, C), shape)
+    Dm = dirac.dense_matrix(lambda v: dirac.apply_DND(U, v, pm, C), shape)
+    phi = x.reshape(-1)
+    G = dirac.dense_matrix(g5t1, shape)
+    u = np.linalg.solve(Dp, G @ phi)
+    v = np.linalg.solve(Dm, G @ u)
+    want = np.linalg.solve(Q @ Q + delta ** 2 * np.eye(len(phi)), phi)
+    assert rel(v, want) < 1e-12
+
+
+def test_shifted_coarse_doublet_and_solve(small):
+    import dataclasses
+    dims, block, U, p, H, Dd = small
+    delta = 0.05
+    ps = dataclasses.replace(p, ndshift=delta)
+    clat = H.Dc.self_blk.shape[:4]
+    xc = fields.gaussian_coarse((clat[3], clat[2], clat[1], clat[0]), 8, 177, n=2)
+    want = nd.restrict_nd(H.P, dirac.apply_DND(U, nd.prolong_nd(H.P, xc), ps, H.clover))
+    assert rel(mg.coarse_apply_nd(H.Dc, xc, p.mubar, p.epsbar, delta), want) < 1e-13
+    H.p = ps
+    try:
+        HN = nd.HierarchyND(H)
+        b = fields.gaussian_spinor(dims, 178, n=2)
+        x, steps, res = HN.solve(b, tol=1e-12)
+        shape = (2,) + fields.lattice_shape(dims) + (4, 3)
+        Ds = dirac.dense_matrix(lambda v: dirac.apply_DND(U, v, ps, H.clover), shape)
+        assert res <= 1e-12
+        assert rel(x.reshape(-1), np.linalg.solve(Ds, b.reshape(-1))) < 1e-9
+    finally:
+        H.p = p
