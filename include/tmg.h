@@ -99,6 +99,12 @@ int tmg_check_links(const double *U, long long n_links, double *worst, long long
  * be followed by it: changing kappa or c_sw rebuilds the clover field if a gauge field is loaded. */
 int tmg_set_params(tmg_ctx *ctx, double kappa, double csw, double mu, double mubar, double epsbar);
 
+/* Shifted doublet (Sec. 3): every doublet operator of the context (TMG_OP_DND, the doublet SAP,
+ * coarse operators and solves) becomes D_ND + i delta (G5 x tau1), so that (G5 x tau1) times it is
+ * Q_ND + i delta and the shifted systems Q_ND^2 + delta^2 = (Q_ND - i delta)(Q_ND + i delta) of the
+ * rational approximation are two such solves.  delta = 0 (the default) is Eq. 2 itself. */
+int tmg_set_ndshift(tmg_ctx *ctx, double delta);
+
 /* y = op x for n_rhs fine spinors ([n_rhs][V][4][3], or [n_rhs][2][V][4][3] for TMG_OP_DND) in
  * the storage precision `prec` (inputs rounded to it; FP16 storage computes in FP32).  With
  * TMG_PREC_F16, D, D^dag and the hopping term keep every field in 16-bit fixed point: spinors with
@@ -300,11 +306,16 @@ int tmg_mms_cg(tmg_ctx *ctx, const double *b, double *x, int n_shift, const doub
 
 /* Rational function of A (the RHMC approximation R of Eq. 5, for 1/sqrt(Q_ND^2)):
  * out = a prod_{l=1..n} (A + num_l)(A + den_l)^-1 phi, n <= 32, distinct den_l >= 0, evaluated
- * through its partial fractions a (phi + sum_l r_l (A + den_l)^-1 phi) with the multi-shift CG
- * above (same A, flavours, tolerance and stats).  The coefficients (Zolotarev's for 1/sqrt(x))
- * come from the caller. */
+ * through its partial fractions a (phi + sum_l r_l (A + den_l)^-1 phi).  The coefficients
+ * (Zolotarev's for 1/sqrt(x)) come from the caller.  As in Sec. 3, the shifted systems are split
+ * between two solvers: shifts den_l >= mg_below go to one multi-shift CG (above; mg_below <= 0 sends
+ * every shift there), the smaller, worse-conditioned ones to the mixed-precision multigrid (needs
+ * tmg_setup), two solves per shift: one flavour, D^dag D + q = D(mu_q)^dag D(mu_q) with
+ * mu_q = sqrt(mu^2 + q); doublet, Q_ND^2 + q = (Q_ND - i d)(Q_ND + i d), d = sqrt(q), with
+ * Q_ND +- i d = (g5 x tau1)(D_ND +- i d g5 x tau1) solved by the doublet multigrid (P_ND = P x I2).
+ * Same A, flavours and tolerance; stats sum both solvers. */
 int tmg_rational_apply(tmg_ctx *ctx, const double *phi, double *out, int n, double a, const double *num,
-                       const double *den, double tol, int flavours, tmg_stats *stats, int where);
+                       const double *den, double tol, int flavours, double mg_below, tmg_stats *stats, int where);
 
 /* Pseudofermion action S = phi^dag (D D^dag)^-1 phi = ||Y||^2, Y = D(mu)^-1 phi (Sec. 1.1, the
  * monomials of Sec. 2): one mixed-precision multigrid solve to tolerance tol.  phi, Y: FP64 fine
@@ -331,6 +342,60 @@ int tmg_pf_force(tmg_ctx *ctx, const double *Y, double *f, double tol, tmg_stats
  * expected sigma (1/theta - mu_s^2 loses relative accuracy when mu_s >> sigma). */
 int tmg_sigma_min(tmg_ctx *ctx, const double *start, double mu_s, int max_steps, double rtol, double solve_tol,
                   int method, double *sigma, double *ritz_res, int *solves, int where);
+
+/* ---- HMC (Sec. 2) ----
+ * One molecular-dynamics trajectory of the Hasenbusch-split twisted-mass HMC: det[Q^2 + mu^2] (Eq. 3)
+ * written as fermion monomials m = 0 .. n_mono-1, each a ratio det[D(mu)^dag D(mu)] /
+ * det[D(mu')^dag D(mu')] (mu2[m] = mu' > 0) or a last det[D(mu)^dag D(mu)] (mu2[m] = 0), with
+ * pseudofermion actions ||D(mu)^-dag D(mu')^dag phi||^2 and ||D(mu)^-1 phi||^2, plus the Wilson
+ * plaquette gauge action beta sum (1 - Re tr P / 3) (the paper does not print its gauge action).
+ * Every fermion monomial sits on the time scale level[m] (0 = outermost) of a nested second-order
+ * minimal-norm integrator with steps[l] steps per call of scale l; the gauge action is on the
+ * innermost scale n_levels-1.  The heat bath draws phi from the caller's Gaussian eta ([n_mono][V][4][3]
+ * complex, seeded by the caller); the momenta P ([V][4][8] real su(3) coefficients, the caller's
+ * Gaussians) are updated in place and the context's gauge field is left at the end of the trajectory
+ * (the accept / reject step and restoring the old field, tmg_get_gauge / tmg_load_gauge, are the
+ * caller's).  Solves: mixed-precision DD-alpha-AMG (needs tmg_setup) to tol_action (heat bath,
+ * Hamiltonian) and tol_force (forces) -- Sec. 2 uses 1e-11 and 1e-9; the setup is updated by
+ * setup_iters_start iterations at the start and setup_iters_force before every force of the monomial
+ * with the smallest mu (Sec. 2: 3 and 1).  Writes dH = H_end - H_start. */
+typedef struct {
+  double beta;            /* gauge coupling */
+  double tau;             /* trajectory length */
+  int n_mono;             /* fermion monomials, 1..8 */
+  double mu[8];           /* twist of each monomial's D(mu) */
+  double mu2[8];          /* mu' of a ratio monomial, 0 for a det monomial */
+  int level[8];           /* time scale of each fermion monomial */
+  int n_levels;           /* time scales (1..8); the gauge action is on the last */
+  int steps[8];           /* minimal-norm steps per call of each time scale */
+  double tol_action;      /* heat bath and Hamiltonian solves */
+  double tol_force;       /* force solves */
+  int setup_iters_start;  /* setup-update iterations at the start (0: none) */
+  int setup_iters_force;  /* setup-update iterations before each force of the lightest monomial */
+  int keep_phi;           /* 1: skip the heat bath and reuse the pseudofermions of the context's
+                             previous trajectory (eta unused; for reversibility checks) */
+} tmg_hmc_params;
+
+typedef struct {
+  double H_start, H_end;  /* Hamiltonians (kinetic + gauge + fermion actions) */
+  long long solves;       /* multigrid solves */
+  long long outer_iterations;
+  long long fermion_forces, gauge_forces, link_updates;
+  double seconds;
+} tmg_hmc_stats;
+
+int tmg_hmc_trajectory(tmg_ctx *ctx, const tmg_hmc_params *p, double *P, const double *eta, double *dH,
+                       tmg_hmc_stats *stats, int where);
+
+/* Copy out the context's gauge field ([V][4][3][3] FP64 complex, lexicographic), e.g. to restore it
+ * with tmg_load_gauge after a rejected trajectory. */
+int tmg_get_gauge(tmg_ctx *ctx, double *U, int where);
+
+/* Wilson plaquette action beta sum_{x, mu<nu} (1 - Re tr P_mu_nu(x) / 3) of the context's field, and
+ * its force as su(3) coefficients f[V][4][8] = tr(lambda_a / 2 F), dS/dt = sum tr(H F) under
+ * U -> exp(i t H) U. */
+int tmg_gauge_action(tmg_ctx *ctx, double beta, double *S);
+int tmg_gauge_force(tmg_ctx *ctx, double beta, double *f, int where);
 
 /* Time `n_iter` back-to-back launches of the dslash kernel (y = D x, one column, storage
  * precision prec as in tmg_apply, so TMG_PREC_F16 is the all-FP16 form) on the context stream with
@@ -379,7 +444,9 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels), "eo_stage" (1, the default: the FP32 even-odd kernels copy
+ * the basis for up to 10 basis vectors; 0: separate kernels), "coarse_overlap" (0, the default, or 1: the coarse GMRES updates the
+ * Hessenberg column of step j on one warp per CTA while the other warps run the stencil of step
+ * j+1; tmg_autotune tries both), "eo_stage" (1, the default: the FP32 even-odd kernels copy
  * each CTA's tile of the clover field / clover inverse into shared memory with bulk copies while
  * the neighbour loads run; 0: direct loads), "force_prec" (TMG_PREC_F64, the default: the force kernels of
  * tmg_force / tmg_force_xy / tmg_pf_force read FP64 X, Y and links; TMG_PREC_F32: they read FP32

@@ -50,6 +50,24 @@ class Level2Params(ctypes.Structure):
                 ("coarse_rtol", ctypes.c_double), ("n_init", ctypes.c_int), ("n_iter", ctypes.c_int)]
 
 
+class HmcParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("n_mono", ctypes.c_int),
+                ("mu", ctypes.c_double * 8), ("mu2", ctypes.c_double * 8), ("level", ctypes.c_int * 8),
+                ("n_levels", ctypes.c_int), ("steps", ctypes.c_int * 8), ("tol_action", ctypes.c_double),
+                ("tol_force", ctypes.c_double), ("setup_iters_start", ctypes.c_int),
+                ("setup_iters_force", ctypes.c_int), ("keep_phi", ctypes.c_int)]
+
+
+class HmcStats(ctypes.Structure):
+    _fields_ = [("H_start", ctypes.c_double), ("H_end", ctypes.c_double), ("solves", ctypes.c_longlong),
+                ("outer_iterations", ctypes.c_longlong), ("fermion_forces", ctypes.c_longlong),
+                ("gauge_forces", ctypes.c_longlong), ("link_updates", ctypes.c_longlong),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("coarse_iterations", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
@@ -108,7 +126,12 @@ _SIGS = {
     "tmg_solve_shifts": [_P, _P, _P, _I, _P, _D, _I, _D, _P, ctypes.POINTER(Stats), _I],
     "tmg_bench_schur": [_P, _I, _I, ctypes.POINTER(_D)],
     "tmg_mms_cg": [_P, _P, _P, _I, _P, _D, _I, ctypes.POINTER(Stats), _I],
-    "tmg_rational_apply": [_P, _P, _P, _I, _D, _P, _P, _D, _I, ctypes.POINTER(Stats), _I],
+    "tmg_rational_apply": [_P, _P, _P, _I, _D, _P, _P, _D, _I, _D, ctypes.POINTER(Stats), _I],
+    "tmg_set_ndshift": [_P, _D],
+    "tmg_hmc_trajectory": [_P, ctypes.POINTER(HmcParams), _P, _P, ctypes.POINTER(_D), ctypes.POINTER(HmcStats), _I],
+    "tmg_get_gauge": [_P, _P, _I],
+    "tmg_gauge_action": [_P, _D, ctypes.POINTER(_D)],
+    "tmg_gauge_force": [_P, _D, _P, _I],
     "tmg_check_links": [_P, ctypes.c_longlong, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
 
@@ -233,6 +256,54 @@ class Context:
         p, wh = _ptr(U)
         self._check(lib().tmg_load_gauge(self._h, p, wh, int(t_bc)))
         self.gauge_version = getattr(self, "gauge_version", 0) + 1
+
+    @staticmethod
+    def hmc_params(beta, tau, monomials, steps, tol_action=1e-11, tol_force=1e-9, setup_iters_start=3,
+                   setup_iters_force=1, keep_phi=False):
+        """monomials: list of (mu, mu2 or 0, level); steps: minimal-norm steps per call of each time
+        scale (the gauge action on the last)."""
+        hp = HmcParams()
+        hp.beta, hp.tau, hp.n_mono, hp.n_levels = float(beta), float(tau), len(monomials), len(steps)
+        for i, (m, m2, lv) in enumerate(monomials):
+            hp.mu[i], hp.mu2[i], hp.level[i] = float(m), float(m2), int(lv)
+        for i, n in enumerate(steps):
+            hp.steps[i] = int(n)
+        hp.tol_action, hp.tol_force = float(tol_action), float(tol_force)
+        hp.setup_iters_start, hp.setup_iters_force, hp.keep_phi = int(setup_iters_start), int(setup_iters_force), int(keep_phi)
+        return hp
+
+    def hmc_trajectory(self, params, P, eta):
+        """(dH, stats): one trajectory; P (float64 [T, Z, Y, X, 4, 8]) is updated in place, eta
+        (complex128 [n_mono, T, Z, Y, X, 4, 3]) feeds the heat bath; the context keeps the new field."""
+        pp, wh = _ptr_real(P)
+        pe, we = _ptr(eta)
+        if wh != we:
+            raise TypeError("P and eta must both be host or both device arrays")
+        dH, st = ctypes.c_double(), HmcStats()
+        self._check(lib().tmg_hmc_trajectory(self._h, ctypes.byref(params), pp, pe, ctypes.byref(dH), ctypes.byref(st), wh))
+        self.gauge_version = getattr(self, "gauge_version", 0) + 1
+        return dH.value, st.as_dict()
+
+    def get_gauge(self, like=None):
+        U = _empty_like(like, self.lat + (4, 3, 3)) if like is not None else np.empty(self.lat + (4, 3, 3), np.complex128)
+        p, wh = _ptr(U)
+        self._check(lib().tmg_get_gauge(self._h, p, wh))
+        return U
+
+    def gauge_action(self, beta):
+        S = ctypes.c_double()
+        self._check(lib().tmg_gauge_action(self._h, float(beta), ctypes.byref(S)))
+        return S.value
+
+    def gauge_force(self, beta):
+        f = np.empty(self.lat + (4, 8), np.float64)
+        p, wh = _ptr_real(f)
+        self._check(lib().tmg_gauge_force(self._h, float(beta), p, wh))
+        return f
+
+    def set_ndshift(self, delta):
+        """Doublet operators become D_ND + i delta (G5 x tau1) (the shifted systems of Sec. 3)."""
+        self._check(lib().tmg_set_ndshift(self._h, float(delta)))
 
     def rotate_gauge(self, omega, step=1.0):
         """U_mu(x) <- exp(i step omega(x, mu) . lambda / 2) U_mu(x); omega float64 [T, Z, Y, X, 4, 8]."""
@@ -498,8 +569,9 @@ class Context:
                                      int(flavours), ctypes.byref(st), wh))
         return x, st.as_dict()
 
-    def rational_apply(self, phi, a, num, den, tol=1e-10, flavours=1):
-        """(a prod (A + num_l)/(A + den_l) phi, stats) through the multi-shift CG."""
+    def rational_apply(self, phi, a, num, den, tol=1e-10, flavours=1, mg_below=0.0):
+        """(a prod (A + num_l)/(A + den_l) phi, stats): shifts >= mg_below by the multi-shift CG, the
+        smaller ones by the multigrid (two solves each)."""
         nu = np.ascontiguousarray(np.asarray(num, dtype=np.float64).reshape(-1))
         de = np.ascontiguousarray(np.asarray(den, dtype=np.float64).reshape(-1))
         out = _empty_like(phi, phi.shape)
@@ -508,7 +580,7 @@ class Context:
         st = Stats()
         self._check(lib().tmg_rational_apply(self._h, pp, po, nu.size, float(a), nu.ctypes.data_as(ctypes.c_void_p),
                                              de.ctypes.data_as(ctypes.c_void_p), float(tol), int(flavours),
-                                             ctypes.byref(st), wh))
+                                             float(mg_below), ctypes.byref(st), wh))
         return out, st.as_dict()
 
     def force_xy(self, X, Y):

@@ -187,6 +187,14 @@ int tmg_set_params(tmg_ctx* ctx, double kappa, double csw, double mu, double mub
   });
 }
 
+int tmg_set_ndshift(tmg_ctx* ctx, double delta) {
+  return guarded(ctx, [&]() -> int {
+    if (!std::isfinite(delta)) return fail(ctx, TMG_ERR_ARG, "tmg_set_ndshift: delta not finite");
+    ctx->c.ndshift = delta;
+    return TMG_OK;
+  });
+}
+
 int tmg_check_links(const double* U, long long n_links, double* worst, long long* worst_index) {
   if (!U || n_links < 0) return TMG_ERR_ARG;
   long long at = -1;
@@ -639,12 +647,15 @@ int tmg_mms_cg(tmg_ctx* ctx, const double* b, double* x, int n_shift, const doub
 }
 
 int tmg_rational_apply(tmg_ctx* ctx, const double* phi, double* out, int n, double a, const double* num,
-                       const double* den, double tol, int flavours, tmg_stats* stats, int where) {
+                       const double* den, double tol, int flavours, double mg_below, tmg_stats* stats, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;
     if (!phi || !out || !num || !den || n < 1 || n > 32 || !(tol > 0.0) || !std::isfinite(a) ||
-        (flavours != 1 && flavours != 2) || !valid_where(where))
+        (flavours != 1 && flavours != 2) || !valid_where(where) || std::isnan(mg_below))
       return fail(ctx, TMG_ERR_ARG, "tmg_rational_apply: bad argument");
+    bool any_mg = false;
+    for (int l = 0; l < n; l++) any_mg = any_mg || den[l] < mg_below;
+    if (any_mg && !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_rational_apply: multigrid shifts need a setup");
     for (int l = 0; l < n; l++) {
       if (!(den[l] >= 0.0) || !std::isfinite(num[l])) return fail(ctx, TMG_ERR_ARG, "tmg_rational_apply: bad coefficients");
       for (int k = 0; k < l; k++)
@@ -671,7 +682,68 @@ int tmg_rational_apply(tmg_ctx* ctx, const double* phi, double* out, int n, doub
     const double* bd = stage_in(c, c.stage_a, phi, col * nf, where);
     for (int f = 0; f < nf; f++) spinor_from_lex(c, bd + f * col, bf.col(c.g, f), TMG_PREC_F64);
     SolveStats st{}, s0{};
-    const int rc = mms_cg_solve(c, bf.buf.p, xf.buf.p, n, den, tol, 1000000, nf, st);
+    // shifts at or above mg_below: one multi-shift CG; below it: the multigrid, two solves per shift
+    std::vector<double> sh_cg;
+    std::vector<int> at_cg, at_mg;
+    for (int l = 0; l < n; l++) {
+      if (den[l] < mg_below) at_mg.push_back(l);
+      else { at_cg.push_back(l); sh_cg.push_back(den[l]); }
+    }
+    int rc = TMG_OK;
+    tmg::Field cgf;
+    if (!at_cg.empty()) {
+      cgf.create(c.g, TMG_PREC_F64, nf * (int)at_cg.size());
+      rc = mms_cg_solve(c, bf.buf.p, cgf.buf.p, (int)at_cg.size(), sh_cg.data(), tol, 1000000, nf, st);
+      for (size_t i = 0; i < at_cg.size(); i++)
+        blas_copy(c, cgf.col(c.g, (int)i * nf), xf.col(c.g, at_cg[i] * nf), TMG_PREC_F64, nn);
+    }
+    if (!at_mg.empty()) {
+      tmg::Field tf, uf;
+      tf.create(c.g, TMG_PREC_F64, nf);
+      uf.create(c.g, TMG_PREC_F64, nf);
+      const size_t n1 = (size_t)12 * c.g.V;
+      // y = g5 x (one flavour) or (g5 x tau1) x (doublet)
+      auto g5t = [&](const void* x, void* y) {
+        if (nf == 1) {
+          blas_copy(c, x, y, TMG_PREC_F64, n1);
+        } else {
+          blas_copy(c, x, (char*)y + n1 * 16, TMG_PREC_F64, n1);
+          blas_copy(c, (const char*)x + n1 * 16, y, TMG_PREC_F64, n1);
+        }
+        for (int f = 0; f < nf; f++) gamma5_inplace(c, (char*)y + f * n1 * 16, TMG_PREC_F64);
+      };
+      const double shift0 = c.ndshift;
+      try {
+        for (int l : at_mg) {
+          SolveStats s1{}, s2{};
+          int r1, r2;
+          g5t(bf.buf.p, tf.buf.p);
+          if (nf == 1) {
+            // D^dag D + q = D(mu_q)^dag D(mu_q), mu_q = sqrt(mu^2 + q): two-step solve of Sec. 1.1
+            const double mq = std::sqrt(c.mu * c.mu + den[l]);
+            r1 = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, uf.buf.p, -mq, tol, 100000, s1);
+            g5t(uf.buf.p, tf.buf.p);
+            r2 = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, xf.col(c.g, l), mq, tol, 100000, s2);
+          } else {
+            // Q_ND^2 + q = (Q_ND - i delta)(Q_ND + i delta), Q_ND +- i delta = (g5 x tau1)(D_ND +- i delta g5 x tau1)
+            const double dl = std::sqrt(den[l]);
+            c.ndshift = dl;
+            r1 = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, uf.buf.p, 0.0, tol, 100000, s1, 2);
+            g5t(uf.buf.p, tf.buf.p);
+            c.ndshift = -dl;
+            r2 = solve_one(c, TMG_SOLVE_MG_MIXED, tf.buf.p, xf.col(c.g, l * nf), 0.0, tol, 100000, s2, 2);
+            c.ndshift = shift0;
+          }
+          if (rc == TMG_OK && r1 != TMG_OK) rc = r1;
+          if (rc == TMG_OK && r2 != TMG_OK) rc = r2;
+          st.iterations += s1.iterations + s2.iterations;
+          st.true_residual = std::max(st.true_residual, std::max(s1.true_residual, s2.true_residual));
+        }
+      } catch (...) {
+        c.ndshift = shift0;
+        throw;
+      }
+    }
     for (int l = 0; l < n; l++) blas_axpy(c, r[l], 0.0, xf.col(c.g, l * nf), bf.buf.p, TMG_PREC_F64, nn);
     blas_scale(c, a, 0.0, bf.buf.p, TMG_PREC_F64, nn);
     double* od = stage_out_ptr(c, c.stage_b, out, col * nf, where);
@@ -680,7 +752,79 @@ int tmg_rational_apply(tmg_ctx* ctx, const double* phi, double* out, int n, doub
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     fill_stats(stats, st, s0, t0);
     if (stats) stats->true_residual = st.true_residual;
-    return rc == TMG_OK ? TMG_OK : fail(ctx, rc, "tmg_rational_apply: multi-shift CG not converged");
+    return rc == TMG_OK ? TMG_OK : fail(ctx, rc, "tmg_rational_apply: a shifted solve did not converge");
+  });
+}
+
+int tmg_hmc_trajectory(tmg_ctx* ctx, const tmg_hmc_params* p, double* P, const double* eta, double* dH,
+                       tmg_hmc_stats* stats, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!p || !P || !eta || !dH || !valid_where(where) || p->n_mono < 1 || p->n_mono > 8 || p->n_levels < 1 ||
+        p->n_levels > 8 || !(p->tau > 0.0) || !std::isfinite(p->beta) || !(p->tol_action > 0.0) ||
+        !(p->tol_force > 0.0) || p->setup_iters_start < 0 || p->setup_iters_force < 0)
+      return fail(ctx, TMG_ERR_ARG, "tmg_hmc_trajectory: bad argument");
+    for (int l = 0; l < p->n_levels; l++)
+      if (p->steps[l] < 1 || p->steps[l] > 10000) return fail(ctx, TMG_ERR_ARG, "tmg_hmc_trajectory: steps out of range");
+    for (int m = 0; m < p->n_mono; m++)
+      if (!std::isfinite(p->mu[m]) || !(p->mu2[m] >= 0.0) || p->level[m] < 0 || p->level[m] >= p->n_levels)
+        return fail(ctx, TMG_ERR_ARG, "tmg_hmc_trajectory: bad monomial");
+    if (!c.gauge_loaded || !c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_hmc_trajectory: needs a gauge field and a setup");
+    const size_t np = (size_t)32 * c.g.V, ne = (size_t)p->n_mono * 24 * c.g.V;
+    DBuf Pd, Ed;
+    double* Pp = P;
+    const double* Ep = eta;
+    if (where == TMG_HOST) {
+      Pd.alloc(np * sizeof(double));
+      Ed.alloc(ne * sizeof(double));
+      TMG_CUDA(cudaMemcpyAsync(Pd.p, P, np * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+      TMG_CUDA(cudaMemcpyAsync(Ed.p, eta, ne * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+      Pp = Pd.as<double>();
+      Ep = Ed.as<double>();
+    }
+    const int rc = hmc_trajectory(c, *p, Pp, Ep, dH, stats);
+    if (where == TMG_HOST) {
+      TMG_CUDA(cudaMemcpyAsync(P, Pp, np * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      TMG_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    return rc;
+  });
+}
+
+int tmg_get_gauge(tmg_ctx* ctx, double* U, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!U || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_get_gauge: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_get_gauge: no gauge field loaded");
+    const size_t n = (size_t)c.g.V * 72;
+    double* d = stage_out_ptr(c, c.stage_b, U, n, where);
+    gauge_internal_to_lex(c, d);
+    stage_out_finish(c, c.stage_b, U, n, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    return TMG_OK;
+  });
+}
+
+int tmg_gauge_action(tmg_ctx* ctx, double beta, double* S) {
+  return guarded(ctx, [&]() -> int {
+    if (!S || !std::isfinite(beta)) return fail(ctx, TMG_ERR_ARG, "tmg_gauge_action: bad argument");
+    if (!ctx->c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_gauge_action: no gauge field loaded");
+    *S = gauge_action(ctx->c, beta);
+    return TMG_OK;
+  });
+}
+
+int tmg_gauge_force(tmg_ctx* ctx, double beta, double* f, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!f || !std::isfinite(beta) || !valid_where(where)) return fail(ctx, TMG_ERR_ARG, "tmg_gauge_force: bad argument");
+    if (!c.gauge_loaded) return fail(ctx, TMG_ERR_STATE, "tmg_gauge_force: no gauge field loaded");
+    const size_t n = (size_t)c.g.V * 32;
+    double* d = stage_out_ptr(c, c.stage_b, f, n, where);
+    gauge_force(c, beta, d);
+    stage_out_finish(c, c.stage_b, f, n, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    return TMG_OK;
   });
 }
 
@@ -695,6 +839,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "tc_steps_per_range" && (v == 1 || v == 2 || v == 4)) ctx->c.tc_steps_per_range = v;
     else if (k == "coarse_grid" && v >= 0 && v <= 4096) ctx->c.coarse_grid = v;
     else if (k == "eo_stage" && (v == 0 || v == 1)) ctx->c.eo_stage = v;
+    else if (k == "coarse_overlap" && (v == 0 || v == 1)) ctx->c.coarse_overlap = v;
     else if (k == "outer_gs_fused" && (v == 0 || v == 1)) ctx->c.outer_gs_fused = v;
     else if (k == "force_prec" && (v == TMG_PREC_F64 || v == TMG_PREC_F32)) ctx->c.force_prec = v;
     else if (k == "kcycle_grid" && v >= 0 && v <= 4096) ctx->c.kcycle_grid = v;
@@ -1032,6 +1177,10 @@ int tmg_coarse_apply_nd(tmg_ctx* ctx, const double* x, double* y, int prec, int 
     coarse_apply(c, prec, xu + n1 * es, yu + n1 * es, -c.mubar);
     blas_axpy(c, -c.epsbar, 0.0, xu + n1 * es, yu, prec, n1);
     blas_axpy(c, -c.epsbar, 0.0, xu, yu + n1 * es, prec, n1);
+    if (c.ndshift != 0.0) {   // i delta G5_c x tau1 of the shifted doublet
+      coarse_g5_axpy(c, prec, 0.0, c.ndshift, xu + n1 * es, yu);
+      coarse_g5_axpy(c, prec, 0.0, c.ndshift, xu, yu + n1 * es);
+    }
   });
 }
 

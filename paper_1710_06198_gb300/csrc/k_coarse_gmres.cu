@@ -38,12 +38,15 @@ struct CgArgs {
   typename CplxT<S>::T2* rows;       // [nc][9][nd] partial stencil rows
   S mu;                              // twist (doublet: mubar, flavour 1 gets -mubar)
   S epsbar;                          // doublet flavour mixing -epsbar tau1 (unused for nf = 1)
+  S delta;                           // shifted doublet: + i delta G5 x tau1 (0 for Eq. 2 itself)
   double rtol;
   double2* part;                     // [CMAXM + 1][grid] dot partials
   double* npart;                     // [grid] norm partials
   double2* R;                        // rotated Hessenberg, column-major (CMAXM + 1) x CMAXM
   double2* y;                        // solution coefficients
   int* counter;                      // accumulated step count
+  int overlap;                       // 1: the Hessenberg update of step j runs during the stencil of
+                                     // step j+1 (warp 0 of every CTA); 0: after step j, all warps stencil
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -63,8 +66,9 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   return t;
 }
 
-// One stencil task, by one warp: out[k] = scale * (sum_l blk[l][k] x[l] - epsbar xo[k]) for the
-// nd rows k of one (nd x nd) block (xo: the doublet's other flavour on the self block, or null).
+// One stencil task, by one warp: out[k] = scale * (sum_l blk[l][k] x[l] + (-epsbar + i delta g5_k) xo[k])
+// for the nd rows k of one (nd x nd) block (xo: the doublet's other flavour on the self block, or
+// null; g5_k = +1 for the first nd / 2 rows, -1 for the others).
 // FP32 blocks whose half width divides 32 are read as float4 (two rows per load) with the columns
 // split over lane groups, so every lane keeps all its loads in flight at once; the group partial
 // sums are combined with shuffles.  Other shapes: lanes are rows and every column is one coalesced
@@ -72,7 +76,7 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
 template <typename S>
 __device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __restrict__ blk,
                                              const typename CplxT<S>::T2* __restrict__ xv, int nd, S scale,
-                                             const typename CplxT<S>::T2* xo, S epsbar,
+                                             const typename CplxT<S>::T2* xo, S epsbar, S delta,
                                              typename CplxT<S>::T2* __restrict__ out, int lane) {
   using T2 = typename CplxT<S>::T2;
   const int half = nd >> 1;
@@ -101,10 +105,11 @@ __device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __rest
         const int k = 2 * kp;
         if (xo) {
           const float2 a0 = xo[k], a1 = xo[k + 1];
-          ar0 -= epsbar * a0.x;
-          ai0 -= epsbar * a0.y;
-          ar1 -= epsbar * a1.x;
-          ai1 -= epsbar * a1.y;
+          const float d0 = k < half ? delta : -delta, d1 = k + 1 < half ? delta : -delta;
+          ar0 += -epsbar * a0.x - d0 * a0.y;
+          ai0 += -epsbar * a0.y + d0 * a0.x;
+          ar1 += -epsbar * a1.x - d1 * a1.y;
+          ai1 += -epsbar * a1.y + d1 * a1.x;
         }
         out[k] = make_float2(ar0 * scale, ai0 * scale);
         out[k + 1] = make_float2(ar1 * scale, ai1 * scale);
@@ -122,8 +127,9 @@ __device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __rest
       ai += m.x * v.y + m.y * v.x;
     }
     if (xo) {
-      ar -= epsbar * xo[k].x;
-      ai -= epsbar * xo[k].y;
+      const S d = k < half ? delta : -delta;
+      ar += -epsbar * xo[k].x - d * xo[k].y;
+      ai += -epsbar * xo[k].y + d * xo[k].x;
     }
     T2 o;
     o.x = ar * scale;
@@ -221,7 +227,8 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   // Hessenberg column of the previous step meanwhile: the stencil of step j only needs the norm
   // h_{j,j-1} (known before the rotations), and if the rotations of step j-1 stop the solve, the
   // stencil rows of step j are simply not used.
-  const int swarp = warp - 1, snwarp = nwarp - 1;
+  const bool ovl = a.overlap != 0;
+  const int swarp = ovl ? warp - 1 : warp, snwarp = ovl ? nwarp - 1 : nwarp;
   const int sgwarp = blockIdx.x * snwarp + swarp, snwarps_total = G * snwarp;
   // s_done is read only right after a grid barrier (or before the loop, where it is settled): the
   // thread that updates the Hessenberg column may set it while other warps are still starting a
@@ -232,7 +239,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     const T2* src = j == 0 ? a.V : a.w;
     const S scale = j == 0 ? (S)1 : (S)(1.0 / s_hn);
     T2* vj = a.V + (size_t)j * n;
-    if (warp == 0) {
+    if (ovl && warp == 0) {
       if (lane == 0 && j > 0) hessenberg_update(j - 1);
     } else {
       // (1) stencil products, one warp per (flavour, coarse site, stencil block) spread over the
@@ -246,7 +253,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
         const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
         const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
         const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
-        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.rows + (size_t)task * a.nd, lane);
+        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.delta, a.rows + (size_t)task * a.nd, lane);
       }
     }
     grid.sync();                                     // partial rows and the previous column complete
@@ -330,11 +337,13 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       if (lane == 0) {
         s_hn = sqrt(t);
         s_k = j + 1;
-        // the last allowed step has no following stencil to hide its column update behind
-        if (j == a.m - 1) hessenberg_update(j);
+        // without overlap, and for the last allowed step (no following stencil to hide it behind),
+        // the column update runs here
+        if (!ovl || j == a.m - 1) hessenberg_update(j);
       }
     }
     __syncthreads();
+    if (!ovl && s_done) break;                       // every CTA decided alike from the same values
   }
   // a step whose column update was deferred and that ended the loop by reaching m: done above;
   // a stop found after the stencil of the next step: done in that stencil phase
@@ -421,7 +430,7 @@ __device__ void stencil_dev(const CgArgs<S>& op, const typename CplxT<S>::T2* sr
     const T2* blk = op.Dc + (size_t)t9 * op.nd * op.nd;
     const T2* xv = src + (size_t)f * n1 + (size_t)op.nbr[t9] * op.nd;
     const T2* xo = (op.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * op.nd : nullptr;
-    stencil_task<S>(blk, xv, op.nd, (S)1, xo, op.epsbar, op.rows + (size_t)task * op.nd, lane);
+    stencil_task<S>(blk, xv, op.nd, (S)1, xo, op.epsbar, op.delta, op.rows + (size_t)task * op.nd, lane);
   }
   grid.sync();
   const int n = op.nf * n1;
@@ -1021,6 +1030,8 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   a.m = m;
   a.nf = nf;
   a.epsbar = (S)epsbar;
+  a.delta = nf == 2 ? (S)c.ndshift : (S)0;
+  a.overlap = c.coarse_overlap;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1073,6 +1084,8 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.m = std::min(c.mg.coarse_m, CMAXM);
   a.nf = 1;
   a.epsbar = (S)0;
+  a.delta = (S)0;
+  a.overlap = c.coarse_overlap;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1218,6 +1231,8 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   s.m = sm_m;
   s.nf = nf;
   s.epsbar = (S)epsbar;
+  s.delta = nf == 2 ? (S)c.ndshift : (S)0;
+  s.overlap = c.coarse_overlap;
   s.passes = passes;
   s.Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
   s.nbr = c.cl.nbr.as<int>();
@@ -1240,6 +1255,8 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   l.m = cm;
   l.nf = nf;
   l.epsbar = (S)epsbar;
+  l.delta = nf == 2 ? (S)c.ndshift : (S)0;
+  l.overlap = c.coarse_overlap;
   l.passes = passes;
   l.Dc = (const T2*)(sizeof(S) == 8 ? c.cl2.Dc64.p : c.cl2.Dc32.p);
   l.nbr = c.cl2.nbr.as<int>();

@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, S y, S x, S b, G U, C A,
   y.store(s, out);
 }
 
-// Non-degenerate doublet (Eq. 2): y_u = D(mubar) x_u - epsbar x_d, y_d = D(-mubar) x_d - epsbar x_u.
+// Non-degenerate doublet (Eq. 2): y_u = D(mubar) x_u - epsbar x_d, y_d = D(-mubar) x_d - epsbar x_u,
+// plus i delta g5 x_d / i delta g5 x_u for the shifted doublet (delta = the context's ndshift).
 // Both flavours of a site are handled by one thread so the links and clover are read once.
 template <typename R, class S, class G, class C>
-__global__ void __launch_bounds__(128) k_dslash_nd(Geom g, S yu, S yd, S xu, S xd, G U, C A, R mubar, R epsbar) {
+__global__ void __launch_bounds__(128) k_dslash_nd(Geom g, S yu, S yd, S xu, S xd, G U, C A, R mubar, R epsbar,
+                                                   R delta) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const SiteCoord sc = decode_site(g, s);
@@ -70,8 +72,8 @@ __global__ void __launch_bounds__(128) k_dslash_nd(Geom g, S yu, S yd, S xu, S x
   }
 #pragma unroll
   for (int k = 0; k < 12; k++) {
-    ou.c[k] = ou.c[k] - R(0.5) * acc_u.c[k] - epsbar * sd.c[k];
-    od.c[k] = od.c[k] - R(0.5) * acc_d.c[k] - epsbar * su.c[k];
+    ou.c[k] = ou.c[k] - R(0.5) * acc_u.c[k] + nd_mix(epsbar, delta, k, sd.c[k]);
+    od.c[k] = od.c[k] - R(0.5) * acc_d.c[k] + nd_mix(epsbar, delta, k, su.c[k]);
   }
   yu.store(s, ou);
   yd.store(s, od);
@@ -118,19 +120,19 @@ void dslash_nd(Ctx& c, int prec, void* y, const void* x) {
     double2* yp = (double2*)y;
     ++c.launches, k_dslash_nd<double><<<blocks, threads, 0, c.stream>>>(c.g, sp64(c, yp), sp64(c, yp + col), sp64(c, xp), sp64(c, xp + col),
                                                           GaugeF64{c.op[0].U.as<double2>(), c.g.V},
-                                                          CloverF64{c.op[0].A.as<double2>(), c.g.V}, c.mubar, c.epsbar);
+                                                          CloverF64{c.op[0].A.as<double2>(), c.g.V}, c.mubar, c.epsbar, c.ndshift);
   } else {
     const float2* xp = (const float2*)x;
     float2* yp = (float2*)y;
     if (prec == TMG_PREC_F32)
       ++c.launches, k_dslash_nd<float><<<blocks, threads, 0, c.stream>>>(c.g, sp32(c, yp), sp32(c, yp + col), sp32(c, xp), sp32(c, xp + col),
                                                            GaugeF32{c.op[1].U.as<float4>(), c.g.V},
-                                                           CloverF32{c.op[1].A.as<float4>(), c.g.V}, (float)c.mubar, (float)c.epsbar);
+                                                           CloverF32{c.op[1].A.as<float4>(), c.g.V}, (float)c.mubar, (float)c.epsbar, (float)c.ndshift);
     else
       ++c.launches, k_dslash_nd<float><<<blocks, threads, 0, c.stream>>>(c.g, sp32(c, yp), sp32(c, yp + col), sp32(c, xp), sp32(c, xp + col),
                                                            GaugeF16{c.op[2].U.as<short4>(), c.g.V},
                                                            CloverF16{c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>(), c.g.V},
-                                                           (float)c.mubar, (float)c.epsbar);
+                                                           (float)c.mubar, (float)c.epsbar, (float)c.ndshift);
   }
   TMG_CHECK_LAUNCH();
 }

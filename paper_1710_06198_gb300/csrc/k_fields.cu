@@ -216,6 +216,21 @@ __global__ void k_gauge_lex_to_f64(Geom g, const double2* __restrict__ lex, doub
   }
 }
 
+// internal F64 [4][9][V] -> lex [V][4][9] complex
+__global__ void k_gauge_f64_to_lex(Geom g, const double2* __restrict__ in, double2* __restrict__ lex) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, s, c);
+    const int i = lex_index(g, c);
+    for (int k = 0; k < 36; k++) lex[(size_t)i * 36 + k] = in[(size_t)k * g.V + s];
+  }
+}
+
+void gauge_internal_to_lex(Ctx& c, double* lex_dev) {
+  ++c.launches, k_gauge_f64_to_lex<<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, c.op[0].U.as<double2>(), (double2*)lex_dev);
+  TMG_CHECK_LAUNCH();
+}
+
 void gauge_lex_to_internal(Ctx& c, const double* lex_dev) {
   c.op[0].U.alloc((size_t)36 * c.g.V * sizeof(double2));
   ++c.launches, k_gauge_lex_to_f64<<<grid_for(c, c.g.V), 256, 0, c.stream>>>(c.g, (const double2*)lex_dev, c.op[0].U.as<double2>());

@@ -265,18 +265,6 @@ struct GaugeF32in64 {
   }
 };
 
-// su(3) coefficients f_a = tr(lambda_a / 2 F) of a traceless Hermitian F (row-major 3x3)
-__device__ __forceinline__ void algebra_coeffs(const cpx<double> h[9], double f[8]) {
-  f[0] = h[1].re;
-  f[1] = -h[1].im;
-  f[2] = 0.5 * (h[0].re - h[4].re);
-  f[3] = h[2].re;
-  f[4] = -h[2].im;
-  f[5] = h[5].re;
-  f[6] = -h[5].im;
-  f[7] = (h[0].re + h[4].re - 2.0 * h[8].re) * 0.28867513459481288225;   // 1 / (2 sqrt 3)
-}
-
 // F = traceless Hermitian part of -2 G, lexicographic output [V][4][3][3] (alg = 0) or its su(3)
 // coefficients [V][4][8] (alg = 1)
 template <typename T2>

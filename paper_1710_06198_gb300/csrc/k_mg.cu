@@ -166,10 +166,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
 
 // SAP on the non-degenerate doublet (Eq. 2): the same colouring and block MR, on flavour pairs.
 // The block operator is [[D_B(mubar), -epsbar], [-epsbar, D_B(-mubar)]] (the flavour mixing is
-// site-local); MR step lengths come from inner products over both flavours.
+// site-local; the shifted doublet adds i delta g5 to it); MR step lengths come from inner products
+// over both flavours.
 template <typename R, class S, class G, class C>
 __global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S xu, S xd, S bu, S bd, G U, C A, R mubar,
-                                                         R epsbar, int n_mr) {
+                                                         R epsbar, R delta, int n_mr) {
   // shared memory: r [2][12][VB] complex; for FP32 arithmetic also the block's links [4][9][VB]
   extern __shared__ double smem_d[];
   cpx<R>* rs = reinterpret_cast<cpx<R>*>(smem_d);
@@ -198,10 +199,10 @@ __global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S x
     xd.load(s, xs_d);
     bu.load(s, bs);
 #pragma unroll
-    for (int k = 0; k < 12; k++) r[0].c[k] = bs.c[k] - (du.c[k] - epsbar * xs_d.c[k]);
+    for (int k = 0; k < 12; k++) r[0].c[k] = bs.c[k] - (du.c[k] + nd_mix(epsbar, delta, k, xs_d.c[k]));
     bd.load(s, bs);
 #pragma unroll
-    for (int k = 0; k < 12; k++) r[1].c[k] = bs.c[k] - (dd.c[k] - epsbar * xs_u.c[k]);
+    for (int k = 0; k < 12; k++) r[1].c[k] = bs.c[k] - (dd.c[k] + nd_mix(epsbar, delta, k, xs_u.c[k]));
   }
   Spinor<R> e[2];
 #pragma unroll
@@ -272,8 +273,8 @@ __global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S x
     }
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      const cpx<R> q0 = q[0].c[k] - R(0.5) * acc[0].c[k] - epsbar * r[1].c[k];
-      const cpx<R> q1 = q[1].c[k] - R(0.5) * acc[1].c[k] - epsbar * r[0].c[k];
+      const cpx<R> q0 = q[0].c[k] - R(0.5) * acc[0].c[k] + nd_mix(epsbar, delta, k, r[1].c[k]);
+      const cpx<R> q1 = q[1].c[k] - R(0.5) * acc[1].c[k] + nd_mix(epsbar, delta, k, r[0].c[k]);
       q[0].c[k] = q0;
       q[1].c[k] = q1;
     }
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S x
 }
 
 template <typename R, class S, class G, class C>
-static void launch_sap_nd(Ctx& c, S xu, S xd, S bu, S bd, G U, C A, R mubar, R epsbar, int n_sweeps, int kind) {
+static void launch_sap_nd(Ctx& c, S xu, S xd, S bu, S bd, G U, C A, R mubar, R epsbar, R delta, int n_sweeps, int kind) {
   const size_t smem = sizeof(cpx<R>) * (sizeof(R) == 4 ? 60 : 24) * c.g.VB + 33 * 3 * sizeof(double);
   if (smem > 48 * 1024)
     TMG_CUDA(cudaFuncSetAttribute(k_sap_block_nd<R, S, G, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -317,7 +318,7 @@ static void launch_sap_nd(Ctx& c, S xu, S xd, S bu, S bd, G U, C A, R mubar, R e
     for (int colour = 0; colour < 2; colour++) {
       ProfScope ps(c, kind);
       ++c.launches, k_sap_block_nd<R, S, G, C><<<c.g.nblk / 2, c.g.VB, smem, c.stream>>>(c.g, colour, xu, xd, bu, bd, U, A, mubar,
-                                                                                     epsbar, c.mg.sap_mr);
+                                                                                     epsbar, delta, c.mg.sap_mr);
       TMG_CHECK_LAUNCH();
     }
 }
@@ -329,7 +330,7 @@ void sap_sweeps_nd(Ctx& c, int prec, void* x, const void* b, int n_sweeps) {
     double2* bp = (double2*)b;
     launch_sap_nd<double>(c, SpinorF64{xp, c.g.V}, SpinorF64{xp + col, c.g.V}, SpinorF64{bp, c.g.V}, SpinorF64{bp + col, c.g.V},
                           GaugeF64{c.op[0].U.as<double2>(), c.g.V}, CloverF64{c.op[0].A.as<double2>(), c.g.V}, c.mubar, c.epsbar,
-                          n_sweeps, PK_SAP_F64);
+                          c.ndshift, n_sweeps, PK_SAP_F64);
   } else {
     float4* xp = (float4*)x;
     float4* bp = (float4*)b;
@@ -337,12 +338,12 @@ void sap_sweeps_nd(Ctx& c, int prec, void* x, const void* b, int n_sweeps) {
     if (prec == TMG_PREC_F32)
       launch_sap_nd<float>(c, SpinorF32{xp, c.g.V}, SpinorF32{xp + col4, c.g.V}, SpinorF32{bp, c.g.V}, SpinorF32{bp + col4, c.g.V},
                            GaugeF32{c.op[1].U.as<float4>(), c.g.V}, CloverF32{c.op[1].A.as<float4>(), c.g.V}, (float)c.mubar,
-                           (float)c.epsbar, n_sweeps, PK_SAP_F32);
+                           (float)c.epsbar, (float)c.ndshift, n_sweeps, PK_SAP_F32);
     else
       launch_sap_nd<float>(c, SpinorF32{xp, c.g.V}, SpinorF32{xp + col4, c.g.V}, SpinorF32{bp, c.g.V}, SpinorF32{bp + col4, c.g.V},
                            GaugeF16{c.op[2].U.as<short4>(), c.g.V},
                            CloverF16{c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>(), c.g.V}, (float)c.mubar,
-                           (float)c.epsbar, n_sweeps, PK_SAP_F16);
+                           (float)c.epsbar, (float)c.ndshift, n_sweeps, PK_SAP_F16);
   }
 }
 
@@ -789,6 +790,30 @@ __global__ void __launch_bounds__(256) k_orthonormalise(Geom g, int nv, double2*
 void orthonormalise(Ctx& c, void* W64) {
   const size_t smem = 33 * 2 * sizeof(double);
   ++c.launches, k_orthonormalise<<<2 * c.g.nblk, c.g.VB, smem, c.stream>>>(c.g, c.cl.nv, (double2*)W64);
+  TMG_CHECK_LAUNCH();
+}
+
+// y += (are + i aim) G5_c x on coarse vectors ([nc][nd], dofs [+: nv | -: nv])
+template <typename T2>
+__global__ void k_coarse_g5_axpy(const T2* __restrict__ x, T2* __restrict__ y, size_t n, int nd, double are, double aim) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % nd);
+    const double s = k < nd / 2 ? 1.0 : -1.0;
+    const T2 v = x[e];
+    T2 o = y[e];
+    o.x += s * (are * v.x - aim * v.y);
+    o.y += s * (are * v.y + aim * v.x);
+    y[e] = o;
+  }
+}
+
+void coarse_g5_axpy(Ctx& c, int prec, double are, double aim, const void* x, void* y) {
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  const int G = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)c.sms * 8));
+  if (prec == TMG_PREC_F64)
+    ++c.launches, k_coarse_g5_axpy<double2><<<G, 256, 0, c.stream>>>((const double2*)x, (double2*)y, n, c.cl.nd, are, aim);
+  else
+    ++c.launches, k_coarse_g5_axpy<float2><<<G, 256, 0, c.stream>>>((const float2*)x, (float2*)y, n, c.cl.nd, are, aim);
   TMG_CHECK_LAUNCH();
 }
 

@@ -365,12 +365,12 @@ static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, c
     return b;
   };
   std::vector<unsigned long long> k = {u(r), u(z), (unsigned long long)pf, (unsigned long long)pc, (unsigned long long)nf,
-                                       d(mu), d(c.mubar), d(c.epsbar), (unsigned long long)(c.g.tbc + 2),
+                                       d(mu), d(c.mubar), d(c.epsbar), d(c.ndshift), (unsigned long long)(c.g.tbc + 2),
                                        (unsigned long long)c.l2_ready, (unsigned long long)c.mg.sap_sweeps,
                                        (unsigned long long)c.mg.sap_mr, (unsigned long long)c.mg.coarse_m, d(c.mg.coarse_rtol),
                                        (unsigned long long)c.coarse_ctas_per_sm, (unsigned long long)c.coarse_gs_passes,
                                        (unsigned long long)c.kcycle_ctas_per_sm, (unsigned long long)c.coarse_grid,
-                                       (unsigned long long)c.kcycle_grid, (unsigned long long)c.l2p.smooth_m,
+                                       (unsigned long long)c.kcycle_grid, (unsigned long long)c.coarse_overlap, (unsigned long long)c.l2p.smooth_m,
                                        (unsigned long long)c.l2p.k_restart, d(c.l2p.k_rtol), (unsigned long long)c.l2p.coarse_m,
                                        d(c.l2p.coarse_rtol)};
   for (int i = 0; i < 3; i++) {
@@ -494,21 +494,25 @@ double autotune(Ctx& c) {
       c.kcycle_grid = best_g;
       c.l2p.k_rtol = krtol;
     } else {
-      int best_ctas = c.coarse_ctas_per_sm, best_pass = c.coarse_gs_passes, best_g = 0;
+      int best_ctas = c.coarse_ctas_per_sm, best_pass = c.coarse_gs_passes, best_g = 0, best_ovl = c.coarse_overlap;
       best = 1e30;
-      // grids of k CTAs per SM, and grids smaller than the SM count (cheaper grid-wide barriers)
+      // grids of k CTAs per SM, and grids smaller than the SM count (cheaper grid-wide barriers),
+      // with and without the Hessenberg update overlapped with the next stencil
       const int grids[] = {0, 0, 0, 0, c.sms / 4, c.sms / 2};
-      for (int gi = 0; gi < 6; gi++)
-        for (int pass = (pc == TMG_PREC_F64 ? 2 : 1); pass <= 2; pass++) {
-          c.coarse_ctas_per_sm = gi < 4 ? gi + 1 : 1;
-          c.coarse_grid = grids[gi];
-          c.coarse_gs_passes = pass;
-          const double t = time_of([&] { coarse_gmres_persistent(c, pc, b.p, x.p, c.mu); });
-          if (t < best) { best = t; best_ctas = c.coarse_ctas_per_sm; best_pass = pass; best_g = grids[gi]; }
-        }
+      for (int ovl = 0; ovl <= 1; ovl++)
+        for (int gi = 0; gi < 6; gi++)
+          for (int pass = (pc == TMG_PREC_F64 ? 2 : 1); pass <= 2; pass++) {
+            c.coarse_ctas_per_sm = gi < 4 ? gi + 1 : 1;
+            c.coarse_grid = grids[gi];
+            c.coarse_gs_passes = pass;
+            c.coarse_overlap = ovl;
+            const double t = time_of([&] { coarse_gmres_persistent(c, pc, b.p, x.p, c.mu); });
+            if (t < best) { best = t; best_ctas = c.coarse_ctas_per_sm; best_pass = pass; best_g = grids[gi]; best_ovl = ovl; }
+          }
       c.coarse_ctas_per_sm = best_ctas;
       c.coarse_gs_passes = best_pass;
       c.coarse_grid = best_g;
+      c.coarse_overlap = best_ovl;
     }
   } catch (...) {
     c.mg.coarse_rtol = rtol;

@@ -39,6 +39,13 @@ int solve_shifts(Ctx& c, const void* b, void* X, int n, const double* mu, double
 // method `method` per step, to solve_tol); see solver.cu.
 double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double rtol, double solve_tol, int method,
                          double* ritz_res, int* solves, int* steps);
+// HMC (hmc.cu): one trajectory on device momenta P_dev and Gaussians eta (lexicographic FP64)
+int hmc_trajectory(Ctx& c, const tmg_hmc_params& p, double* P_dev, const double* eta_lex_dev, double* dH,
+                   tmg_hmc_stats* stats);
+double gauge_action(Ctx& c, double beta);
+void gauge_force(Ctx& c, double beta, double* f_lex);
+// clover, compressed copies, even-odd data and coarse operators after the links changed
+void gauge_changed(Ctx& c);
 // Launch-shape autotuner of the coarse solve (coarse_ctas_per_sm, coarse_gs_passes; with three
 // levels kcycle_ctas_per_sm); keeps the fastest shape, returns its time per coarse solve in ms.
 double autotune(Ctx& c);

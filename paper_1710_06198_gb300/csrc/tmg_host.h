@@ -182,6 +182,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   Geom g{};
   double kappa = 0.125, csw = 0.0, mu = 0.0, mubar = 0.0, epsbar = 0.0;
+  double ndshift = 0.0;   // delta of the shifted doublet D_ND + i delta G5 x tau1 (0: Eq. 2 itself)
   bool gauge_loaded = false;
   OpData op[3];          // F64, F32, F16
   DBuf U_lex;            // staging for a host gauge field
@@ -220,7 +221,10 @@ struct Ctx {
   Prof prof;
   EoData eo;
   BatchWork bw;
-  int eo_stage = 1;             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
+  DBuf hmc_phi;                 // pseudofermions of the last HMC trajectory (hmc.cu)
+  int hmc_nmono = 0;
+  int eo_stage = 1;
+  int coarse_overlap = 0;       // coarse GMRES: overlap the Hessenberg update with the next stencil             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
 };
 
 // Records a start event on construction and an end event on destruction when profiling is on.
@@ -250,6 +254,7 @@ struct ProfScope {
 double su3_defect_host(const double* U, size_t n_links, long long* at);
 double su3_defect_device(Ctx& c, const double* U_dev, size_t n_links, long long* at);
 void gauge_lex_to_internal(Ctx& c, const double* lex_dev);
+void gauge_internal_to_lex(Ctx& c, double* lex_dev);
 // U_mu(x) <- exp(i step sum_a omega_a lambda_a / 2) U_mu(x) on the internal F64 links, omega
 // lexicographic [V][4][8] on the device; the caller rebuilds clover and compressed copies
 void rotate_gauge(Ctx& c, const double* omega_dev, double step);
@@ -313,6 +318,8 @@ void prolong(Ctx& c, int prec, const void* cvec, int cprec, void* e, int accumul
 // skip: optional device flag; when it is non-zero the launch does nothing
 void coarse_apply(Ctx& c, int cprec, const void* x, void* y, double mu, const int* skip = nullptr);
 void orthonormalise(Ctx& c, void* W64);
+// y += (are + i aim) G5_c x on level-1 coarse vectors
+void coarse_g5_axpy(Ctx& c, int prec, double are, double aim, const void* x, void* y);
 // x ~= D_c(mu)^-1 b: one persistent cooperative GMRES kernel (k_coarse_gmres.cu)
 void coarse_gmres_persistent(Ctx& c, int cprec, const void* b, void* x, double mu);
 // the same on doublet coarse vectors [2][nc][nd] with D_ND,c = D_c x I2 + i mubar G5_c x tau3 - epsbar tau1

@@ -323,6 +323,15 @@ template <> struct CloverOf<0> { using T = CloverF64; };
 template <> struct CloverOf<1> { using T = CloverF32; };
 template <> struct CloverOf<2> { using T = CloverF16; };
 
+// Flavour mixing of the doublet for spinor component k (spin-major, so k < 6 has g5 = +1):
+// (-epsbar + i delta g5) v, i.e. -epsbar tau1 of Eq. 2 plus the i delta G5 x tau1 of the shifted
+// systems (Q_ND + i delta = (G5 x tau1)(D_ND + i delta G5 x tau1)).
+template <typename R>
+__device__ __forceinline__ cpx<R> nd_mix(R epsbar, R delta, int k, cpx<R> v) {
+  const R d = k < 6 ? delta : -delta;
+  return {-epsbar * v.re - d * v.im, -epsbar * v.im + d * v.re};
+}
+
 // y = (A_chi + i tw) x for one chirality block (x, y: 6 complex).  A is Hermitian.
 template <typename R>
 __device__ __forceinline__ void clover_mul(const CloverBlock<R>& a, R tw, const cpx<R>* x, cpx<R>* y) {
@@ -338,6 +347,19 @@ __device__ __forceinline__ void clover_mul(const CloverBlock<R>& a, R tw, const 
       y[j] = y[j] + cmul_conj(l, x[i]);
     }
   }
+}
+
+// su(3) coefficients f_a = tr(lambda_a / 2 F) of a traceless Hermitian F (row-major 3x3; lambda_a
+// the Gell-Mann matrices)
+__device__ __forceinline__ void algebra_coeffs(const cpx<double> h[9], double f[8]) {
+  f[0] = h[1].re;
+  f[1] = -h[1].im;
+  f[2] = 0.5 * (h[0].re - h[4].re);
+  f[3] = h[2].re;
+  f[4] = -h[2].im;
+  f[5] = h[5].re;
+  f[6] = -h[5].im;
+  f[7] = (h[0].re + h[4].re - 2.0 * h[8].re) * 0.28867513459481288225;   // 1 / (2 sqrt 3)
 }
 
 // ------------------------------------------------------------------ gamma algebra (chiral basis)

@@ -148,3 +148,36 @@ def test_three_level_doublet_solve(method):
     xo, steps, res = HN.solve(b, tol=1e-12)
     assert res <= 1e-12
     assert rel(x, xo) < 1e-8
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_shifted_doublet_pieces_and_solve(levels):
+    """The shifted doublet D_ND + i delta (G5 x tau1) of the rational approximation's systems
+    (Sec. 3): fine operator, SAP, coarse operator and coarse solve (or K-cycle) in FP64 against the
+    oracle with the same delta, and a mixed-precision doublet solve to 1e-12 with the oracle's
+    operator as the judge."""
+    import dataclasses
+    ctx, HN, U, p = build(levels=levels)
+    delta = 0.04
+    ps = dataclasses.replace(p, ndshift=delta)
+    HN.H.p = ps
+    HN.p = ps
+    if HN.L1 is not None:
+        HN.L1.delta = delta
+    ctx.set_ndshift(delta)
+    C = HN.H.clover
+    x2 = fields.gaussian_spinor(DIMS, 190, flavours=2)
+    assert rel(ctx.apply(x2, tmg.OP_DND, F64), dirac.apply_DND(U, x2, ps, C)) < 1e-13
+    b2 = fields.gaussian_spinor(DIMS, 191, flavours=2)
+    assert rel(ctx.sap_nd(b2, 0.1 * x2, F64), HN.smooth(b2, 0.1 * x2)) < 1e-11
+    c1 = ctx.coarse_lat
+    xc = fields.gaussian_coarse((c1[3], c1[2], c1[1], c1[0]), 2 * NV, 192, n=2)
+    assert rel(ctx.coarse_apply_nd(xc, F64), HN.coarse_apply(xc)) < 1e-12
+    if levels == 3:
+        assert rel(ctx.kcycle_nd(xc, 0, F64), HN.coarse_solve(xc)) < 1e-9
+    else:
+        assert rel(ctx.coarse_solve_nd(xc, F64), HN.coarse_solve(xc)) < 1e-10
+    x, st = ctx.solve(b2, tol=1e-12, method=tmg.SOLVE_ND_MIXED)
+    assert rel(dirac.apply_DND(U, x, ps, C), b2) <= 1e-12
+    ctx.set_ndshift(0.0)
+    assert rel(ctx.apply(x2, tmg.OP_DND, F64), dirac.apply_DND(U, x2, p, C)) < 1e-13
