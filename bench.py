@@ -212,6 +212,12 @@ def run_kernel_case(args):
         print(json.dumps({"kernel_case": "coarse_tc", "norm": float(torch.linalg.vector_norm(yc)), "us_per_launch": round(us, 2),
                           "algo_bytes": algo, "gbs": round(algo / (us * 1e-6) / 1e9, 1),
                           "tflops": round(nc * 9 * (2 * nd) ** 2 * 2 * 20 / (us * 1e-6) / 1e12, 2)}))
+    elif args.kernel_case == "schur":
+        # the even-odd reduced operator, staged (eo_stage 1) then direct (eo_stage 0): two applications each
+        for stage in (1, 0):
+            ctx.tune("eo_stage", stage)
+            ms = ctx.bench_schur(tmg.PREC_F32, 1)
+        print(json.dumps({"kernel_case": "schur", "ms": ms}))
     elif args.kernel_case == "sap":
         prm = tmg.Context.mg_defaults()
         prm.nv, prm.n_init, prm.n_iter, prm.sap_sweeps = 2, 0, 0, 1
@@ -699,7 +705,7 @@ def main():
                     help="outer iterations the reference arm's per-solve estimate assumes")
     ap.add_argument("--ncu-solve", action="store_true", help="profile one solve only (for ncu)")
     ap.add_argument("--tune", action="append", default=[], help="launch-shape knob key=value (tmg_tune)")
-    ap.add_argument("--kernel-case", choices=["dslash", "sap", "coarse_tc"], default=None,
+    ap.add_argument("--kernel-case", choices=["dslash", "sap", "coarse_tc", "schur"], default=None,
                     help="run one kernel class on a 24^3 x 48 lattice (for ncu --set full)")
     args = ap.parse_args()
     if args.kernel_case:

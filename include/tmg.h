@@ -444,9 +444,9 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels), "coarse_overlap" (0, the default, or 1: the coarse GMRES updates the
- * Hessenberg column of step j on one warp per CTA while the other warps run the stencil of step
- * j+1; tmg_autotune tries both), "eo_stage" (1, the default: the FP32 even-odd kernels copy
+ * the basis for up to 10 basis vectors; 0: separate kernels), "coarse_overlap" (1, the default: the coarse GMRES updates the Hessenberg
+ * column of step j on one warp per CTA while the other warps run the stencil of step j+1; 0: the
+ * update follows each step and all warps run the stencil), "eo_stage" (1, the default: the FP32 even-odd kernels copy
  * each CTA's tile of the clover field / clover inverse into shared memory with bulk copies while
  * the neighbour loads run; 0: direct loads), "force_prec" (TMG_PREC_F64, the default: the force kernels of
  * tmg_force / tmg_force_xy / tmg_pf_force read FP64 X, Y and links; TMG_PREC_F32: they read FP32

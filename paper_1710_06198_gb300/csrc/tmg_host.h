@@ -223,8 +223,8 @@ struct Ctx {
   BatchWork bw;
   DBuf hmc_phi;                 // pseudofermions of the last HMC trajectory (hmc.cu)
   int hmc_nmono = 0;
-  int eo_stage = 1;
-  int coarse_overlap = 0;       // coarse GMRES: overlap the Hessenberg update with the next stencil             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
+  int eo_stage = 1;             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
+  int coarse_overlap = 1;       // coarse GMRES: overlap the Hessenberg update with the next stencil
 };
 
 // Records a start event on construction and an end event on destruction when profiling is on.
