@@ -282,6 +282,18 @@ def run_ours(args):
         torch.cuda.profiler.stop()
         print(json.dumps({"ncu_solve": True, "iterations": st["iterations"], "launches_total": tmg.launch_count(ctx)}))
         return
+    if args.ncu_batched:
+        # the lock-step solve of the point sources: one warm solve, then one inside the profiler range
+        bb = torch.from_numpy(np.ascontiguousarray(fields.point_sources(w["dims"])[:args.batch])).to(dev)
+        xb = torch.empty_like(bb)
+        ctx.solve(bb, tol=w["tol"], method=tmg.SOLVE_MG_BATCHED, out=xb)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, stb = ctx.solve(bb, tol=w["tol"], method=tmg.SOLVE_MG_BATCHED, out=xb)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_batched": True, "rhs": args.batch, "iterations": stb["iterations"]}))
+        return
 
     for _ in range(args.warmup):
         step()
@@ -704,6 +716,7 @@ def main():
     ap.add_argument("--ref-outer-iterations", type=int, default=14,
                     help="outer iterations the reference arm's per-solve estimate assumes")
     ap.add_argument("--ncu-solve", action="store_true", help="profile one solve only (for ncu)")
+    ap.add_argument("--ncu-batched", action="store_true", help="profile one batched solve only (for ncu)")
     ap.add_argument("--tune", action="append", default=[], help="launch-shape knob key=value (tmg_tune)")
     ap.add_argument("--kernel-case", choices=["dslash", "sap", "coarse_tc", "schur"], default=None,
                     help="run one kernel class on a 24^3 x 48 lattice (for ncu --set full)")

@@ -160,6 +160,16 @@ int tmg_coarse_apply_multi(tmg_ctx *ctx, const double *x, double *y, int n_rhs, 
 /* x ~= D_c(mu)^-1 b (Eq. 1's coarse solve): GMRES from zero with at most coarse_m steps, stopping
  * at relative residual coarse_rtol; coarse vectors [V_c][2 N_v], computed in precision prec. */
 int tmg_coarse_solve(tmg_ctx *ctx, const double *b, double *x, double mu, int prec, int where);
+/* X[n] ~= D_c(mu_n)^-1 B[n] for n_rhs (1..32) coarse right-hand sides [n_rhs][V_c][2 N_v] in
+ * lock-step (the coarse solve of the batched cycle, Sec. 1.2's multiple right-hand sides): GMRES
+ * from zero per column with its own Givens rotations and stopping test (coarse_m, coarse_rtol),
+ * FP32 vectors and FP64 reductions.  With "batched_coarse_tc" on (the default) and N_v one of 4,
+ * 8, 12, 16, 24, 32, D_c is applied to all columns at once on the tensor cores (as
+ * tmg_coarse_apply_multi); otherwise by one persistent CUDA-core kernel.  mu_per_col may be NULL
+ * (every column takes the context's mu).  Synchronises.  TMG_ERR_STATE before tmg_setup,
+ * TMG_ERR_ARG for a bad count or pointer, TMG_ERR_TIMEOUT if a tensor-core completion wait gave
+ * up. */
+int tmg_coarse_solve_multi(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double *mu_per_col, int where);
 
 /* ---- third level (Sec. 1.2 runs the method with three levels) ----
  * The level-1 operator D_c is aggregated again: level-2 aggregates are agg[0..3] blocks of
@@ -446,7 +456,10 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
  * the basis for up to 10 basis vectors; 0: separate kernels), "coarse_overlap" (1, the default: the coarse GMRES updates the Hessenberg
  * column of step j on one warp per CTA while the other warps run the stencil of step j+1; 0: the
- * update follows each step and all warps run the stencil), "eo_stage" (1, the default: the FP32 even-odd kernels copy
+ * update follows each step and all warps run the stencil), "batched_coarse_tc" (1, the default: the
+ * two-level batched solve's coarse GMRES applies D_c to all columns at once on the tensor cores,
+ * tcgen05 split TF32 as tmg_coarse_apply_multi, two launches per Arnoldi step; 0: one persistent
+ * CUDA-core kernel), "eo_stage" (1, the default: the FP32 even-odd kernels copy
  * each CTA's tile of the clover field / clover inverse into shared memory with bulk copies while
  * the neighbour loads run; 0: direct loads), "force_prec" (TMG_PREC_F64, the default: the force kernels of
  * tmg_force / tmg_force_xy / tmg_pf_force read FP64 X, Y and links; TMG_PREC_F32: they read FP32

@@ -95,6 +95,7 @@ _SIGS = {
     "tmg_cycle": [_P, _P, _P, _I],
     "tmg_coarse_solve": [_P, _P, _P, _D, _I, _I],
     "tmg_coarse_apply_multi": [_P, _P, _P, _I, _P, _I],
+    "tmg_coarse_solve_multi": [_P, _P, _P, _I, _P, _I],
     "tmg_coarse_solve_noalloc": [_P, _P, _P, _D, _I],
     "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
@@ -421,6 +422,19 @@ class Context:
             mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
         self._check(lib().tmg_coarse_apply_multi(self._h, px, py, n, mp, wh))
         return y
+
+    def coarse_solve_multi(self, b, mu_per_col=None):
+        """X[n] ~= D_c(mu_n)^-1 B[n] for b[n_rhs, ..., 2 Nv]: the batched coarse GMRES (FP32)."""
+        n = b.shape[0]
+        x = _empty_like(b, b.shape)
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        mp = None
+        if mu_per_col is not None:
+            mu_arr = np.ascontiguousarray(np.asarray(mu_per_col, dtype=np.float64).reshape(n))
+            mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
+        self._check(lib().tmg_coarse_solve_multi(self._h, pb, px, n, mp, wh))
+        return x
 
     def coarse_solve(self, c, mu=0.0, prec=PREC_F64):
         """x ~= D_c(mu)^-1 c by the coarse GMRES of the cycle."""

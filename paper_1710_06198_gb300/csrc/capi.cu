@@ -840,6 +840,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "coarse_grid" && v >= 0 && v <= 4096) ctx->c.coarse_grid = v;
     else if (k == "eo_stage" && (v == 0 || v == 1)) ctx->c.eo_stage = v;
     else if (k == "coarse_overlap" && (v == 0 || v == 1)) ctx->c.coarse_overlap = v;
+    else if (k == "batched_coarse_tc" && (v == 0 || v == 1)) ctx->c.batched_tc = v;
     else if (k == "outer_gs_fused" && (v == 0 || v == 1)) ctx->c.outer_gs_fused = v;
     else if (k == "force_prec" && (v == TMG_PREC_F64 || v == TMG_PREC_F32)) ctx->c.force_prec = v;
     else if (k == "kcycle_grid" && v >= 0 && v <= 4096) ctx->c.kcycle_grid = v;
@@ -1036,6 +1037,44 @@ int tmg_coarse_apply_multi(tmg_ctx* ctx, const double* x, double* y, int n_rhs, 
     stage_out_finish(c, c.stage_b, y, 2 * n * n_rhs, where);
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     if (herr) return fail(ctx, TMG_ERR_TIMEOUT, "tmg_coarse_apply_multi: a tensor-core completion wait gave up");
+    return TMG_OK;
+  });
+}
+
+int tmg_coarse_solve_multi(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double* mu_per_col, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || n_rhs < 1 || n_rhs > 32 || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_coarse_solve_multi: bad argument (1..32 columns)");
+    if (!c.mg_ready) return fail(ctx, TMG_ERR_STATE, "tmg_coarse_solve_multi: no setup");
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, b, 2 * n * n_rhs, where);
+    tmg::CField bi, xo;
+    bi.create(TMG_PREC_F32, n * n_rhs);
+    xo.create(TMG_PREC_F32, n * n_rhs);
+    convert_field(c, d, TMG_PREC_F64, bi.buf.p, TMG_PREC_F32, n * n_rhs);
+    std::vector<float> mus(n_rhs, (float)c.mu);
+    if (mu_per_col)
+      for (int j = 0; j < n_rhs; j++) mus[j] = (float)mu_per_col[j];
+    DBuf mu_dev;
+    mu_dev.alloc(sizeof(float) * 32);
+    TMG_CUDA(cudaMemcpyAsync(mu_dev.p, mus.data(), n_rhs * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    const bool tc = c.batched_tc && coarse_gmres_batched_tc_ok(c, n_rhs);
+    if (tc) {
+      if (!c.tc_err.p) c.tc_err.alloc(sizeof(int));
+      TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+      coarse_gmres_batched_tc(c, n_rhs, bi.buf.p, xo.buf.p, mu_dev.as<float>());
+    } else {
+      coarse_gmres_batched(c, n_rhs, bi.buf.p, xo.buf.p, mu_dev.as<float>());
+    }
+    TMG_CHECK_LAUNCH();
+    int herr = 0;
+    if (tc) TMG_CUDA(cudaMemcpyAsync(&herr, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    double* o = stage_out_ptr(c, c.stage_b, x, 2 * n * n_rhs, where);
+    convert_field(c, xo.buf.p, TMG_PREC_F32, o, TMG_PREC_F64, n * n_rhs);
+    stage_out_finish(c, c.stage_b, x, 2 * n * n_rhs, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (herr) return fail(ctx, TMG_ERR_TIMEOUT, "tmg_coarse_solve_multi: a tensor-core completion wait gave up");
     return TMG_OK;
   });
 }

@@ -45,25 +45,27 @@ __device__ __forceinline__ int colour_block_b(const Geom& g, int colour, int k) 
   return row * g.NB[0] + b0;
 }
 
+// CTA all-reduce of N floats, in FP32 throughout (red: shared scratch of at least 33 * N doubles)
 template <int N>
-__device__ __forceinline__ void cta_allreduce_f(float (&v)[N], double* red) {
+__device__ __forceinline__ void cta_allreduce_f(float (&v)[N], double* red_d) {
+  float* red = reinterpret_cast<float*>(red_d);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int i = 0; i < N; i++) {
     float a = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) red[w * N + i] = (double)a;
+    if (lane == 0) red[w * N + i] = a;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    double a = 0.0;
+    float a = 0.f;
     for (int k = 0; k < nw; k++) a += red[k * N + i];
     red[32 * N + i] = a;
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < N; i++) v[i] = (float)red[32 * N + i];
+  for (int i = 0; i < N; i++) v[i] = red[32 * N + i];
   __syncthreads();
 }
 

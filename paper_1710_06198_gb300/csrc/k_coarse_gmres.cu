@@ -3,10 +3,13 @@
 // reaches rtol; classical Gram-Schmidt with an optional second pass.
 //
 // Every CTA stays resident for the whole solve; phases are separated by grid-wide barriers of a
-// cooperative launch.  The small sequential work (Hessenberg column, Givens rotations, stopping
-// test) is repeated identically by every CTA from the same reduced values, so no extra barrier is
-// needed to broadcast it; CTA 0 alone keeps the rotated Hessenberg for the back substitution.
-// Vectors are in the coarse precision S (FP32 or FP64); all reductions finish in FP64.
+// cooperative launch (two per step: the dot products' partials, then w and its norm).  Each CTA
+// owns a range of coarse sites: it computes their stencil rows and owns those elements of every
+// vector, so the stencil needs no barrier of its own.  The small sequential work (Hessenberg
+// column, Givens rotations, stopping test) is repeated identically by every CTA from the same
+// reduced values, so no extra barrier is needed to broadcast it; CTA 0 alone keeps the rotated
+// Hessenberg for the back substitution.  Vectors, reductions and rotations are all in the coarse
+// precision S (FP32 or FP64): FP64 is far slower than FP32 on GB300, so the FP32 path uses none.
 #include <cooperative_groups.h>
 
 #include "tmg_host.h"
@@ -34,17 +37,19 @@ struct CgArgs {
   const typename CplxT<S>::T2* b;
   typename CplxT<S>::T2* x;
   typename CplxT<S>::T2* V;          // (m + 1) x n basis
-  typename CplxT<S>::T2* w;
-  typename CplxT<S>::T2* rows;       // [nc][9][nd] partial stencil rows
+  typename CplxT<S>::T2* w;          // 2 x n: w of even and of odd steps
+  typename CplxT<S>::T2* rows;       // [nf][nc][9][nd] partial stencil rows
   S mu;                              // twist (doublet: mubar, flavour 1 gets -mubar)
   S epsbar;                          // doublet flavour mixing -epsbar tau1 (unused for nf = 1)
   S delta;                           // shifted doublet: + i delta G5 x tau1 (0 for Eq. 2 itself)
   double rtol;
-  double2* part;                     // [CMAXM + 1][grid] dot partials
-  double* npart;                     // [grid] norm partials
-  double2* R;                        // rotated Hessenberg, column-major (CMAXM + 1) x CMAXM
-  double2* y;                        // solution coefficients
+  double2* part;                     // [2][CMAXM + 1][grid] dot partials (by pass parity; pairs of S)
+  double* npart;                     // [grid] norm partials (values of S)
+  double2* R;                        // rotated Hessenberg, column-major (CMAXM + 1) x CMAXM (pairs of S)
+  double2* y;                        // solution coefficients (pairs of S)
   int* counter;                      // accumulated step count
+  int rows_smem;                     // 1: the own sites' stencil rows live in dynamic shared memory
+                                     // (ceil(nc / grid) * nf * 9 * nd values); 0: in rows
   int overlap;                       // 1: the Hessenberg update of step j runs during the stencil of
                                      // step j+1 (warp 0 of every CTA); 0: after step j, all warps stencil
 };
@@ -53,14 +58,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
-// Sum of one double per thread over the CTA (result returned to every thread).
-__device__ __forceinline__ double cta_sum(double v, double* sh) {
+// Sum of one value per thread over the CTA (result returned to every thread).
+template <typename A>
+__device__ __forceinline__ A cta_sum(A v, A* sh) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  double t = 0.0;
+  A t = 0;
   for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
   __syncthreads();
   return t;
@@ -138,52 +148,83 @@ __device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __rest
   }
 }
 
+// Precision-generic helpers of the persistent solvers: the FP32 path keeps its reductions, Givens
+// rotations and least-squares solve in FP32 (GB300 issues FP64 at a small fraction of the FP32
+// rate, and one FP64 Givens chain per step costs more than the step's stencil).
+template <typename S>
+__device__ __forceinline__ typename CplxT<S>::T2 mk2(S x, S y) {
+  typename CplxT<S>::T2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+__device__ __forceinline__ float sq(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sq(double v) { return sqrt(v); }
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+
 // GMRES from zero on the operator of a (any level): grid-wide phases, the caller's grid must be a
 // cooperative launch; a.x is complete after the caller's next grid barrier.
 template <typename S>
 __device__ void gmres_dev(const CgArgs<S>& a) {
   using T2 = typename CplxT<S>::T2;
+  using A2 = T2;   // reductions, rotations and the least-squares solve in the vectors' precision
   cg::grid_group grid = cg::this_grid();
-  __shared__ double sh[32];
-  __shared__ double2 hcol[CMAXM + 2];
-  __shared__ double2 cs[CMAXM], sn[CMAXM], gv[CMAXM + 1];
-  __shared__ double2 hp[CMAXM + 1];
+  // the FP64-sized scratch of the launch holds the FP32 path's partials and rotations as well
+  A2* const part_base = reinterpret_cast<A2*>(a.part);
+  S* const npart = reinterpret_cast<S*>(a.npart);
+  A2* const Rm = reinterpret_cast<A2*>(a.R);
+  A2* const ym = reinterpret_cast<A2*>(a.y);
+  __shared__ S sh[32];
+  __shared__ A2 hcol[CMAXM + 2];
+  __shared__ A2 cs[CMAXM], sn[CMAXM], gv[CMAXM + 1];
+  __shared__ A2 hp[CMAXM + 1];
   __shared__ int s_done, s_k;
-  __shared__ double s_beta, s_hn;
+  __shared__ S s_beta, s_hn;
   const int n1 = a.nc * a.nd, n = a.nf * n1;
   const int G = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
-  // contiguous chunk of the vector owned by this CTA (the CTA that writes an element is the only
-  // one that reads it until the next grid barrier)
-  const int chunk = (n + G - 1) / G;
-  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  // Coarse sites [s0, s1) of every flavour belong to this CTA: it computes their stencil rows, sums
+  // them into w and is the only CTA that reads or writes those elements of the basis and of w until
+  // the next grid barrier.  Own element t in [0, nown) is flavour t / own, offset t % own.
+  const int s0 = (int)(((long long)blockIdx.x * a.nc) / G), s1 = (int)(((long long)(blockIdx.x + 1) * a.nc) / G);
+  const int own = (s1 - s0) * a.nd, nown = a.nf * own;
+#define GM_OWN_E(t) ((t) >= own ? n1 + s0 * a.nd + ((t) - own) : s0 * a.nd + (t))
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // stencil rows of (flavour f, own site): in shared memory when the launch provides it (the rows
+  // are written and read by this CTA only, so they never need a trip through L2), else global
+  extern __shared__ __align__(16) unsigned char gm_dyn[];
+  T2* const rows_sm = reinterpret_cast<T2*>(gm_dyn);
+  T2* const rows_g = a.rows_smem ? rows_sm : a.rows;          // (flavour, site) row block origin:
+  const int rows_site0 = a.rows_smem ? s0 : 0;                  // own sites only in shared memory
+  const int rows_nsite = a.rows_smem ? s1 - s0 : a.nc;
+#define GM_ROW_BASE(f, site) (rows_g + ((size_t)((f) * rows_nsite + (site) - rows_site0) * 9) * a.nd)
 
   // beta = ||b||
   {
     S nn = 0;
     for (int e = tid; e < n; e += nth) { const T2 v = a.b[e]; nn += v.x * v.x + v.y * v.y; }
-    const double t = cta_sum((double)nn, sh);
-    if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+    const S t = cta_sum((S)nn, sh);
+    if (threadIdx.x == 0) npart[blockIdx.x] = t;
   }
   grid.sync();
   if (warp == 0) {
-    double t = 0.0;
-    for (int q = lane; q < G; q += 32) t += a.npart[q];
+    S t = 0;
+    for (int q = lane; q < G; q += 32) t += npart[q];
     t = warp_sum(t);
-    if (lane == 0) s_beta = sqrt(t);
+    if (lane == 0) s_beta = sq(t);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_done = !(s_beta > 0.0);
+    s_done = !(s_beta > (S)0);
     s_k = 0;
     s_hn = 1.0;
-    for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
-    gv[0] = make_double2(s_beta, 0.0);
+    for (int i = 0; i <= CMAXM; i++) gv[i] = mk2<S>(0, 0);
+    gv[0] = mk2<S>(s_beta, (S)0);
   }
   __syncthreads();
   {
-    const S inv = s_beta > 0.0 ? (S)(1.0 / s_beta) : (S)0;
+    const S inv = s_beta > (S)0 ? (S)1 / s_beta : (S)0;
     for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
   }
   grid.sync();                                       // v_0 complete
@@ -192,36 +233,36 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   // the residual estimate and the stopping test.  Run by one thread of every CTA from the same
   // reduced values, so every CTA takes the same decision.
   auto hessenberg_update = [&](int j) {
-    const double hn = s_hn;
-    double2 x0 = hcol[0];
+    const S hn = s_hn;
+    A2 x0 = hcol[0];
     for (int i = 0; i < j; i++) {
-      const double2 x1 = hcol[i + 1];
-      const double2 c = cs[i], s = sn[i];
-      hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
-                             c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
-      x0 = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
-                        -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+      const A2 x1 = hcol[i + 1];
+      const A2 c = cs[i], s = sn[i];
+      hcol[i] = mk2<S>(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
+                       c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
+      x0 = mk2<S>(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                  -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
     }
     // one reciprocal square root instead of a square root and four divisions
-    const double2 p = x0;
-    const double n2 = p.x * p.x + p.y * p.y + hn * hn;
-    const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
-    const double den = n2 * inv;
-    const double2 c = n2 > 0.0 ? make_double2(p.x * inv, p.y * inv) : make_double2(1.0, 0.0);
-    const double2 sr = make_double2(hn * inv, 0.0);
+    const A2 p = x0;
+    const S n2 = p.x * p.x + p.y * p.y + hn * hn;
+    const S inv = n2 > (S)0 ? rsq(n2) : (S)0;
+    const S den = n2 * inv;
+    const A2 c = n2 > (S)0 ? mk2<S>(p.x * inv, p.y * inv) : mk2<S>(1, 0);
+    const A2 sr = mk2<S>(hn * inv, (S)0);
     cs[j] = c;
     sn[j] = sr;
-    hcol[j] = make_double2(den, 0.0);
-    hcol[j + 1] = make_double2(0.0, 0.0);
-    const double2 g = gv[j];
-    gv[j + 1] = make_double2(-(sr.x * g.x), -(sr.x * g.y));
-    gv[j] = make_double2(c.x * g.x + c.y * g.y, c.x * g.y - c.y * g.x);
+    hcol[j] = mk2<S>(den, (S)0);
+    hcol[j + 1] = mk2<S>(0, 0);
+    const A2 g = gv[j];
+    gv[j + 1] = mk2<S>(-(sr.x * g.x), -(sr.x * g.y));
+    gv[j] = mk2<S>(c.x * g.x + c.y * g.y, c.x * g.y - c.y * g.x);
     if (blockIdx.x == 0)
-      for (int i = 0; i <= j; i++) a.R[(size_t)j * (CMAXM + 1) + i] = hcol[i];
+      for (int i = 0; i <= j; i++) Rm[(size_t)j * (CMAXM + 1) + i] = hcol[i];
     s_k = j + 1;
-    const double res2 = gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y;
-    const double lim = a.rtol * s_beta;
-    if (res2 <= lim * lim || !(hn > 0.0) || !(den > 0.0) || j == a.m - 1) s_done = 1;
+    const S res2 = gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y;
+    const S lim = (S)a.rtol * s_beta;
+    if (res2 <= lim * lim || !(hn > (S)0) || !(den > (S)0) || j == a.m - 1) s_done = 1;
   };
   // Warp 0 of every CTA keeps out of the stencil products so that its first thread can update the
   // Hessenberg column of the previous step meanwhile: the stencil of step j only needs the norm
@@ -229,37 +270,41 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   // stencil rows of step j are simply not used.
   const bool ovl = a.overlap != 0;
   const int swarp = ovl ? warp - 1 : warp, snwarp = ovl ? nwarp - 1 : nwarp;
-  const int sgwarp = blockIdx.x * snwarp + swarp, snwarps_total = G * snwarp;
-  // s_done is read only right after a grid barrier (or before the loop, where it is settled): the
+  const int ntask = a.nf * (s1 - s0) * 9;
+  // s_done is read only right after a barrier (or before the loop, where it is settled): the
   // thread that updates the Hessenberg column may set it while other warps are still starting a
-  // step, and every thread must take the same number of grid barriers.
+  // step.  Every CTA sets it from the same reduced values, so all take the same grid barriers.
   const bool zero_rhs = s_done;
   for (int j = 0; j < a.m && !zero_rhs; j++) {
-    // v_j = v_0, or the previous step's orthogonalised w scaled by 1 / h_{j,j-1}.
-    const T2* src = j == 0 ? a.V : a.w;
-    const S scale = j == 0 ? (S)1 : (S)(1.0 / s_hn);
+    // v_j = v_0, or the previous step's orthogonalised w scaled by 1 / h_{j,j-1}.  w alternates
+    // between two buffers: a CTA writes w_j while its neighbours may still read w_{j-1} for
+    // their stencil rows.
+    const T2* src = j == 0 ? a.V : a.w + (size_t)((j - 1) & 1) * n;
+    T2* wj = a.w + (size_t)(j & 1) * n;
+    const S scale = j == 0 ? (S)1 : (S)1 / s_hn;
     T2* vj = a.V + (size_t)j * n;
     if (ovl && warp == 0) {
       if (lane == 0 && j > 0) hessenberg_update(j - 1);
     } else {
-      // (1) stencil products, one warp per (flavour, coarse site, stencil block) spread over the
-      //     grid's other warps: lanes are rows, so every column of a block is one coalesced read.
-      //     The doublet's flavour mixing is added to the self block's row here, while src is
-      //     read-only.
-      for (int task = sgwarp; task < a.nf * a.nc * 9; task += snwarps_total) {
-        const int f = task / (a.nc * 9), t9 = task - f * a.nc * 9;
+      // (1) stencil products of the own sites, one warp per (flavour, site, stencil block): lanes
+      //     are rows, so every column of a block is one coalesced read.  The doublet's flavour
+      //     mixing is added to the self block's row.
+      for (int t = swarp; t < ntask; t += snwarp) {
+        const int f = t / ((s1 - s0) * 9);
+        const int t9 = s0 * 9 + (t - f * (s1 - s0) * 9);
         const int site = t9 / 9;
-        const int nb = a.nbr[t9];
         const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
-        const T2* xv = src + (size_t)f * n1 + (size_t)nb * a.nd;
+        const T2* xv = src + (size_t)f * n1 + (size_t)a.nbr[t9] * a.nd;
         const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
-        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.delta, a.rows + (size_t)task * a.nd, lane);
+        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.delta,
+                        GM_ROW_BASE(f, site) + (size_t)(t9 - site * 9) * a.nd, lane);
       }
     }
-    grid.sync();                                     // partial rows and the previous column complete
+    __syncthreads();                                 // own rows and the previous column complete
     if (s_done) break;                               // the previous step met the stopping test
-    // (2) own chunk: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    // (2) own elements: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
+    for (int t = threadIdx.x; t < nown; t += blockDim.x) {
+      const int e = GM_OWN_E(t);
       const int f = e / n1, e1f = e - f * n1;
       const int site = e1f / a.nd, k = e1f - site * a.nd;
       T2 xs = src[e];
@@ -267,47 +312,52 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
       xs.y *= scale;
       if (j > 0) vj[e] = xs;
       S ar = 0, ai = 0;
-      const T2* rw = a.rows + ((size_t)(f * a.nc + site) * 9) * a.nd + k;
+      const T2* rw = GM_ROW_BASE(f, site) + k;
       for (int d = 0; d < 9; d++) { const T2 r = rw[(size_t)d * a.nd]; ar += r.x; ai += r.y; }
       const S tw = (k < a.nv) == (f == 0) ? a.mu : -a.mu;
       T2 o;
       o.x = ar - tw * xs.y;
       o.y = ai + tw * xs.x;
-      a.w[e] = o;
+      wj[e] = o;
     }
     if (threadIdx.x == 0)
-      for (int i = 0; i <= j + 1; i++) hcol[i] = make_double2(0.0, 0.0);
+      for (int i = 0; i <= j + 1; i++) hcol[i] = mk2<S>(0, 0);
     __syncthreads();
     for (int pass = 0; pass < a.passes; pass++) {
-      // partial <v_i, w> over the own chunk, one warp per basis vector
+      // partial <v_i, w> over the own chunk, one warp per basis vector.  Consecutive passes write
+      // alternate halves of the partials: only a CTA barrier separates one pass's reads from the
+      // next pass's writes, so a CTA may start pass p+1 while others still sum the partials of p.
+      A2* part = part_base + (size_t)(pass & 1) * (CMAXM + 1) * G;
       for (int i = warp; i <= j; i += nwarp) {
         const T2* vi = a.V + (size_t)i * n;
         S re = 0, im = 0;
-        for (int e = e0 + lane; e < e1; e += 32) {
-          const T2 p = vi[e], q = a.w[e];
+        for (int t = lane; t < nown; t += 32) {
+          const int e = GM_OWN_E(t);
+          const T2 p = vi[e], q = wj[e];
           re += p.x * q.x + p.y * q.y;
           im += p.x * q.y - p.y * q.x;
         }
-        const double dre = warp_sum((double)re), dim = warp_sum((double)im);
-        if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
+        const S dre = warp_sum((S)re), dim = warp_sum((S)im);
+        if (lane == 0) part[(size_t)i * G + blockIdx.x] = mk2<S>(dre, dim);
       }
       grid.sync();                                   // partials complete
       for (int i = warp; i <= j; i += nwarp) {
-        double re = 0.0, im = 0.0;
+        S re = 0, im = 0;
 #pragma unroll 8
-        for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
+        for (int q = lane; q < G; q += 32) { const A2 v = part[(size_t)i * G + q]; re += v.x; im += v.y; }
         re = warp_sum(re);
         im = warp_sum(im);
         if (lane == 0) {
-          hp[i] = make_double2(re, im);
-          hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+          hp[i] = mk2<S>(re, im);
+          hcol[i] = mk2<S>(hcol[i].x + re, hcol[i].y + im);
         }
       }
       __syncthreads();
       // w -= sum_i h_i v_i on the own chunk and, in the last pass, ||w||^2
       S nn = 0;
-      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        T2 q = a.w[e];
+      for (int t = threadIdx.x; t < nown; t += blockDim.x) {
+        const int e = GM_OWN_E(t);
+        T2 q = wj[e];
         S qr = q.x, qi = q.y;
         #pragma unroll 4
         for (int i = 0; i <= j; i++) {
@@ -318,24 +368,24 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
         }
         q.x = qr;
         q.y = qi;
-        a.w[e] = q;
+        wj[e] = q;
         nn += qr * qr + qi * qi;
       }
       if (pass == a.passes - 1) {
-        const double t = cta_sum((double)nn, sh);
-        if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+        const S t = cta_sum((S)nn, sh);
+        if (threadIdx.x == 0) npart[blockIdx.x] = t;
       } else {
         __syncthreads();
       }
     }
     grid.sync();                                     // w and norm partials complete
     if (warp == 0) {
-      double t = 0.0;
+      S t = 0;
 #pragma unroll 8
-      for (int q = lane; q < G; q += 32) t += a.npart[q];
+      for (int q = lane; q < G; q += 32) t += npart[q];
       t = warp_sum(t);
       if (lane == 0) {
-        s_hn = sqrt(t);
+        s_hn = sq(t);
         s_k = j + 1;
         // without overlap, and for the last allowed step (no following stencil to hide it behind),
         // the column update runs here
@@ -351,22 +401,22 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   const int k = s_k;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = k - 1; i >= 0; i--) {
-      double2 acc = gv[i];
+      A2 acc = gv[i];
       for (int l = i + 1; l < k; l++) {
-        const double2 h = a.R[(size_t)l * (CMAXM + 1) + i], yl = a.y[l];
+        const A2 h = Rm[(size_t)l * (CMAXM + 1) + i], yl = ym[l];
         acc.x -= h.x * yl.x - h.y * yl.y;
         acc.y -= h.x * yl.y + h.y * yl.x;
       }
-      const double2 d = a.R[(size_t)i * (CMAXM + 1) + i];
-      const double dn = d.x * d.x + d.y * d.y;
-      a.y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
-                        : make_double2(0.0, 0.0);
+      const A2 d = Rm[(size_t)i * (CMAXM + 1) + i];
+      const S dn = d.x * d.x + d.y * d.y;
+      ym[i] = dn > (S)0 ? mk2<S>((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : mk2<S>(0, 0);
     }
     if (a.counter) *a.counter += k;
   }
   grid.sync();                                       // coefficients ready
   __shared__ S yr[CMAXM], yi[CMAXM];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = (S)a.y[i].x; yi[i] = (S)a.y[i].y; }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = ym[i].x; yi[i] = ym[i].y; }
   __syncthreads();
   for (int e = tid; e < n; e += nth) {
     S xr = 0, xi = 0;
@@ -382,6 +432,9 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     a.x[e] = o;
   }
 }
+
+#undef GM_OWN_E
+#undef GM_ROW_BASE
 
 template <typename S>
 __global__ void __launch_bounds__(256, 2) k_coarse_gmres(CgArgs<S> a) {
@@ -407,7 +460,7 @@ struct KcArgs {
   T2* t;               // D_c z work vector
   int kr, passes, mode;
   double krtol;
-  double2* part;       // [KMAXR + 1][G]
+  double2* part;       // [2][KMAXR + 1][G] (by pass parity)
   double* npart;       // [G]
   double2* R;          // (KMAXR + 1) x KMAXR rotated Hessenberg (CTA 0)
   double2* y;          // [KMAXR]
@@ -547,11 +600,16 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
     l1_cycle_dev(a, a.b, a.x);
     return;
   }
-  __shared__ double sh[32];
-  __shared__ double2 hcol[KMAXR + 2], hp[KMAXR + 1];
-  __shared__ double2 cs[KMAXR], sn[KMAXR], gv[KMAXR + 1];
+  using A2 = T2;                  // reductions and rotations in the vectors' precision, as gmres_dev
+  A2* const part_base = reinterpret_cast<A2*>(a.part);
+  S* const npart = reinterpret_cast<S*>(a.npart);
+  A2* const Rm = reinterpret_cast<A2*>(a.R);
+  A2* const ym = reinterpret_cast<A2*>(a.y);
+  __shared__ S sh[32];
+  __shared__ A2 hcol[KMAXR + 2], hp[KMAXR + 1];
+  __shared__ A2 cs[KMAXR], sn[KMAXR], gv[KMAXR + 1];
   __shared__ int s_done, s_k;
-  __shared__ double s_beta, s_hn;
+  __shared__ S s_beta, s_hn;
   const int n = a.sm.nf * a.q.nc1 * a.q.nd1;
   const int G = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = G * blockDim.x;
@@ -561,26 +619,26 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
   {
     S nn = 0;
     for (int e = tid; e < n; e += nth) { const T2 v = a.b[e]; nn += v.x * v.x + v.y * v.y; }
-    const double t = cta_sum((double)nn, sh);
-    if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+    const S t = cta_sum((S)nn, sh);
+    if (threadIdx.x == 0) npart[blockIdx.x] = t;
   }
   grid.sync();
   if (warp == 0) {
-    double t = 0.0;
-    for (int q = lane; q < G; q += 32) t += a.npart[q];
+    S t = 0;
+    for (int q = lane; q < G; q += 32) t += npart[q];
     t = warp_sum(t);
-    if (lane == 0) s_beta = sqrt(t);
+    if (lane == 0) s_beta = sq(t);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_done = !(s_beta > 0.0);
+    s_done = !(s_beta > (S)0);
     s_k = 0;
-    for (int i = 0; i <= KMAXR; i++) gv[i] = make_double2(0.0, 0.0);
-    gv[0] = make_double2(s_beta, 0.0);
+    for (int i = 0; i <= KMAXR; i++) gv[i] = mk2<S>(0, 0);
+    gv[0] = mk2<S>(s_beta, (S)0);
   }
   __syncthreads();
   {
-    const S inv = s_beta > 0.0 ? (S)(1.0 / s_beta) : (S)0;
+    const S inv = s_beta > (S)0 ? (S)1 / s_beta : (S)0;
     for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
   }
   grid.sync();
@@ -591,9 +649,10 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
     stencil_dev(a.sm, zj, a.t, (const T2*)nullptr);  // w = D_c z_j
     grid.sync();
     if (threadIdx.x == 0)
-      for (int i = 0; i <= j + 1; i++) hcol[i] = make_double2(0.0, 0.0);
+      for (int i = 0; i <= j + 1; i++) hcol[i] = mk2<S>(0, 0);
     __syncthreads();
     for (int pass = 0; pass < a.passes; pass++) {
+      A2* part = part_base + (size_t)(pass & 1) * (KMAXR + 1) * G;   // alternate halves, as in gmres_dev
       for (int i = warp; i <= j; i += nwarp) {
         const T2* vi = a.V + (size_t)i * n;
         S re = 0, im = 0;
@@ -602,18 +661,18 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
           re += p.x * q.x + p.y * q.y;
           im += p.x * q.y - p.y * q.x;
         }
-        const double dre = warp_sum((double)re), dim = warp_sum((double)im);
-        if (lane == 0) a.part[(size_t)i * G + blockIdx.x] = make_double2(dre, dim);
+        const S dre = warp_sum((S)re), dim = warp_sum((S)im);
+        if (lane == 0) part[(size_t)i * G + blockIdx.x] = mk2<S>(dre, dim);
       }
       grid.sync();
       for (int i = warp; i <= j; i += nwarp) {
-        double re = 0.0, im = 0.0;
-        for (int q = lane; q < G; q += 32) { const double2 v = a.part[(size_t)i * G + q]; re += v.x; im += v.y; }
+        S re = 0, im = 0;
+        for (int q = lane; q < G; q += 32) { const A2 v = part[(size_t)i * G + q]; re += v.x; im += v.y; }
         re = warp_sum(re);
         im = warp_sum(im);
         if (lane == 0) {
-          hp[i] = make_double2(re, im);
-          hcol[i] = make_double2(hcol[i].x + re, hcol[i].y + im);
+          hp[i] = mk2<S>(re, im);
+          hcol[i] = mk2<S>(hcol[i].x + re, hcol[i].y + im);
         }
       }
       __syncthreads();
@@ -633,49 +692,49 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
         nn += qr * qr + qi * qi;
       }
       if (pass == a.passes - 1) {
-        const double t = cta_sum((double)nn, sh);
-        if (threadIdx.x == 0) a.npart[blockIdx.x] = t;
+        const S t = cta_sum((S)nn, sh);
+        if (threadIdx.x == 0) npart[blockIdx.x] = t;
       } else {
         __syncthreads();
       }
     }
     grid.sync();
     if (warp == 0) {
-      double t = 0.0;
-      for (int q = lane; q < G; q += 32) t += a.npart[q];
+      S t = 0;
+      for (int q = lane; q < G; q += 32) t += npart[q];
       t = warp_sum(t);
-      if (lane == 0) s_hn = sqrt(t);
+      if (lane == 0) s_hn = sq(t);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double hn = s_hn;
-      hcol[j + 1] = make_double2(hn, 0.0);
+      const S hn = s_hn;
+      hcol[j + 1] = mk2<S>(hn, (S)0);
       for (int i = 0; i < j; i++) {
-        const double2 x0 = hcol[i], x1 = hcol[i + 1];
-        const double2 c = cs[i], s = sn[i];
-        hcol[i] = make_double2(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
-                               c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
-        hcol[i + 1] = make_double2(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
-                                   -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
+        const A2 x0 = hcol[i], x1 = hcol[i + 1];
+        const A2 c = cs[i], s = sn[i];
+        hcol[i] = mk2<S>(c.x * x0.x + c.y * x0.y + s.x * x1.x + s.y * x1.y,
+                         c.x * x0.y - c.y * x0.x + s.x * x1.y - s.y * x1.x);
+        hcol[i + 1] = mk2<S>(-(s.x * x0.x - s.y * x0.y) + (c.x * x1.x - c.y * x1.y),
+                             -(s.x * x0.y + s.y * x0.x) + (c.x * x1.y + c.y * x1.x));
       }
-      const double2 p = hcol[j], q = hcol[j + 1];
-      const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
-      cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
-      sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
-      hcol[j] = make_double2(den, 0.0);
-      hcol[j + 1] = make_double2(0.0, 0.0);
-      const double2 g = gv[j];
-      gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
-      gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+      const A2 p = hcol[j], q = hcol[j + 1];
+      const S den = sq(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+      cs[j] = den > (S)0 ? mk2<S>(p.x / den, p.y / den) : mk2<S>(1, 0);
+      sn[j] = den > (S)0 ? mk2<S>(q.x / den, q.y / den) : mk2<S>(0, 0);
+      hcol[j] = mk2<S>(den, (S)0);
+      hcol[j + 1] = mk2<S>(0, 0);
+      const A2 g = gv[j];
+      gv[j + 1] = mk2<S>(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
+      gv[j] = mk2<S>(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
       if (blockIdx.x == 0)
-        for (int i = 0; i <= j; i++) a.R[(size_t)j * (KMAXR + 1) + i] = hcol[i];
+        for (int i = 0; i <= j; i++) Rm[(size_t)j * (KMAXR + 1) + i] = hcol[i];
       s_k = j + 1;
-      const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
-      if (res <= a.krtol * s_beta || !(hn > 0.0) || !(den > 0.0) || j == a.kr - 1) s_done = 1;
+      const S res = sq(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+      if (res <= (S)a.krtol * s_beta || !(hn > (S)0) || !(den > (S)0) || j == a.kr - 1) s_done = 1;
     }
     __syncthreads();
     if (!s_done) {                                   // v_{j+1} = w / h_{j+1,j} on the own chunk
-      const S inv = (S)(1.0 / s_hn);
+      const S inv = (S)1 / s_hn;
       T2* vn = a.V + (size_t)(j + 1) * n;
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         T2 q = a.t[e];
@@ -689,22 +748,22 @@ __global__ void __launch_bounds__(256) k_kcycle(KcArgs<S> a) {
   const int k = s_k;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = k - 1; i >= 0; i--) {
-      double2 acc = gv[i];
+      A2 acc = gv[i];
       for (int l = i + 1; l < k; l++) {
-        const double2 h = a.R[(size_t)l * (KMAXR + 1) + i], yl = a.y[l];
+        const A2 h = Rm[(size_t)l * (KMAXR + 1) + i], yl = ym[l];
         acc.x -= h.x * yl.x - h.y * yl.y;
         acc.y -= h.x * yl.y + h.y * yl.x;
       }
-      const double2 d = a.R[(size_t)i * (KMAXR + 1) + i];
-      const double dn = d.x * d.x + d.y * d.y;
-      a.y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
-                        : make_double2(0.0, 0.0);
+      const A2 d = Rm[(size_t)i * (KMAXR + 1) + i];
+      const S dn = d.x * d.x + d.y * d.y;
+      ym[i] = dn > (S)0 ? mk2<S>((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : mk2<S>(0, 0);
     }
     if (a.counter) *a.counter += k;
   }
   grid.sync();
   __shared__ S yr[KMAXR], yi[KMAXR];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = (S)a.y[i].x; yi[i] = (S)a.y[i].y; }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) { yr[i] = ym[i].x; yi[i] = ym[i].y; }
   __syncthreads();
   for (int e = tid; e < n; e += nth) {
     S xr = 0, xi = 0;
@@ -737,21 +796,21 @@ struct CgbArgs {
   float2* w;
   float2* rows;
   const float* mu;       // [ncol]
-  double rtol;
-  double2* part;         // [ncol][CMAXM + 1][G]
-  double* npart;         // [ncol][G]
-  double2* R;            // [ncol][(CMAXM + 1) * CMAXM]
-  double2* y;            // [ncol][CMAXM]
+  float rtol;
+  float2* part;          // [ncol][CMAXM + 1][G]
+  float* npart;          // [ncol][G]
+  float2* R;             // [ncol][(CMAXM + 1) * CMAXM]
+  float2* y;             // [ncol][CMAXM]
   int* counter;
 };
 
 __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ double2 bsm[];
+  extern __shared__ float2 bsm[];
   // per column: cs[CMAXM], sn[CMAXM], gv[CMAXM + 1], hcol[CMAXM + 2], hp[CMAXM + 1]
   const int per = 5 * CMAXM + 4;
-  __shared__ double sh[32];
-  __shared__ double s_beta[BMAXC], s_hn[BMAXC];
+  __shared__ float sh[32];
+  __shared__ float s_beta[BMAXC], s_hn[BMAXC];
   __shared__ int s_done[BMAXC], s_k[BMAXC], s_all;
   const int n = a.nc * a.nd;
   const int G = gridDim.x;
@@ -770,27 +829,27 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
   for (int c = 0; c < a.ncol; c++) {
     float nn = 0;
     for (int e = tid; e < n; e += nth) { const float2 v = a.b[(size_t)c * n + e]; nn += v.x * v.x + v.y * v.y; }
-    const double t = cta_sum((double)nn, sh);
+    const float t = cta_sum(nn, sh);
     if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
   }
   grid.sync();
   for (int c = warp; c < a.ncol; c += nwarp) {
-    double t = 0.0;
+    float t = 0.f;
     for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
     t = warp_sum(t);
     if (lane == 0) {
-      s_beta[c] = sqrt(t);
-      s_done[c] = !(s_beta[c] > 0.0);
+      s_beta[c] = sqrtf(t);
+      s_done[c] = !(s_beta[c] > 0.f);
       s_k[c] = 0;
-      s_hn[c] = 1.0;
-      double2* gv = GV(c);
-      for (int i = 0; i <= CMAXM; i++) gv[i] = make_double2(0.0, 0.0);
-      gv[0] = make_double2(s_beta[c], 0.0);
+      s_hn[c] = 1.f;
+      float2* gv = GV(c);
+      for (int i = 0; i <= CMAXM; i++) gv[i] = make_float2(0.f, 0.f);
+      gv[0] = make_float2(s_beta[c], 0.f);
     }
   }
   __syncthreads();
   for (int c = 0; c < a.ncol; c++) {
-    const float inv = s_beta[c] > 0.0 ? (float)(1.0 / s_beta[c]) : 0.f;
+    const float inv = s_beta[c] > 0.f ? 1.f / s_beta[c] : 0.f;
     for (int e = tid; e < n; e += nth) {
       float2 v = a.b[(size_t)c * n + e];
       v.x *= inv;
@@ -814,7 +873,7 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
       for (int c0 = 0; c0 < a.ncol; c0 += CB) {
         float sc[CB];
 #pragma unroll
-        for (int q = 0; q < CB; q++) sc[q] = (c0 + q < a.ncol && j > 0) ? (float)(1.0 / s_hn[c0 + q]) : 1.f;
+        for (int q = 0; q < CB; q++) sc[q] = (c0 + q < a.ncol && j > 0) ? 1.f / s_hn[c0 + q] : 1.f;
         for (int k = lane; k < a.nd; k += 32) {
           float ar[CB], ai[CB];
 #pragma unroll
@@ -841,7 +900,7 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
     grid.sync();
     // (2) own chunk: v_j, w = sum of rows + twist, per column
     for (int c = 0; c < a.ncol; c++) {
-      const float scale = j == 0 ? 1.f : (float)(1.0 / s_hn[c]);
+      const float scale = j == 0 ? 1.f : 1.f / s_hn[c];
       const float mu = a.mu[c];
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int site = e / a.nd, k = e - site * a.nd;
@@ -860,7 +919,7 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
       }
     }
     for (int c = threadIdx.x; c < a.ncol; c += blockDim.x)
-      for (int i = 0; i <= j + 1; i++) HC(c)[i] = make_double2(0.0, 0.0);
+      for (int i = 0; i <= j + 1; i++) HC(c)[i] = make_float2(0.f, 0.f);
     __syncthreads();
     // (3) dots <v_i, w> per column, partials per CTA
     for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
@@ -873,30 +932,30 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
         re += p.x * q.x + p.y * q.y;
         im += p.x * q.y - p.y * q.x;
       }
-      const double dre = warp_sum((double)re), dim = warp_sum((double)im);
-      if (lane == 0) a.part[((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x] = make_double2(dre, dim);
+      const float dre = warp_sum(re), dim = warp_sum(im);
+      if (lane == 0) a.part[((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x] = make_float2(dre, dim);
     }
     grid.sync();
     for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
       const int i = t / a.ncol, c = t - i * a.ncol;
-      double re = 0.0, im = 0.0;
+      float re = 0.f, im = 0.f;
       for (int q = lane; q < G; q += 32) {
-        const double2 v = a.part[((size_t)c * (CMAXM + 1) + i) * G + q];
+        const float2 v = a.part[((size_t)c * (CMAXM + 1) + i) * G + q];
         re += v.x;
         im += v.y;
       }
       re = warp_sum(re);
       im = warp_sum(im);
       if (lane == 0) {
-        HP(c)[i] = make_double2(re, im);
-        HC(c)[i] = make_double2(HC(c)[i].x + re, HC(c)[i].y + im);
+        HP(c)[i] = make_float2(re, im);
+        HC(c)[i] = make_float2(HC(c)[i].x + re, HC(c)[i].y + im);
       }
     }
     __syncthreads();
     // (4) update and norms on the own chunk
     for (int c = 0; c < a.ncol; c++) {
       float nn = 0.f;
-      const double2* hp = HP(c);
+      const float2* hp = HP(c);
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         float2 q = a.w[(size_t)c * n + e];
         for (int i = 0; i <= j; i++) {
@@ -908,46 +967,46 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
         a.w[(size_t)c * n + e] = q;
         nn += q.x * q.x + q.y * q.y;
       }
-      const double t = cta_sum((double)nn, sh);
+      const float t = cta_sum(nn, sh);
       if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
     }
     grid.sync();
     // (5) per column: norm, Givens, stopping test (one warp per column)
     for (int c = warp; c < a.ncol; c += nwarp) {
-      double t = 0.0;
+      float t = 0.f;
       for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
       t = warp_sum(t);
       if (lane == 0 && !s_done[c]) {
-        const double hn = sqrt(t);
-        s_hn[c] = hn > 0.0 ? hn : 1.0;   // a broken-down column is finished; keep its scale finite
-        double2* hcol = HC(c);
-        double2* cs = CS(c);
-        double2* sn = SN(c);
-        double2* gv = GV(c);
-        hcol[j + 1] = make_double2(hn, 0.0);
+        const float hn = sqrtf(t);
+        s_hn[c] = hn > 0.f ? hn : 1.f;   // a broken-down column is finished; keep its scale finite
+        float2* hcol = HC(c);
+        float2* cs = CS(c);
+        float2* sn = SN(c);
+        float2* gv = GV(c);
+        hcol[j + 1] = make_float2(hn, 0.f);
         for (int i = 0; i < j; i++) {
-          const double2 x0 = hcol[i], x1 = hcol[i + 1];
-          const double2 cc = cs[i], ss = sn[i];
-          hcol[i] = make_double2(cc.x * x0.x + cc.y * x0.y + ss.x * x1.x + ss.y * x1.y,
+          const float2 x0 = hcol[i], x1 = hcol[i + 1];
+          const float2 cc = cs[i], ss = sn[i];
+          hcol[i] = make_float2(cc.x * x0.x + cc.y * x0.y + ss.x * x1.x + ss.y * x1.y,
                                  cc.x * x0.y - cc.y * x0.x + ss.x * x1.y - ss.y * x1.x);
-          hcol[i + 1] = make_double2(-(ss.x * x0.x - ss.y * x0.y) + (cc.x * x1.x - cc.y * x1.y),
+          hcol[i + 1] = make_float2(-(ss.x * x0.x - ss.y * x0.y) + (cc.x * x1.x - cc.y * x1.y),
                                      -(ss.x * x0.y + ss.y * x0.x) + (cc.x * x1.y + cc.y * x1.x));
         }
-        const double2 p = hcol[j], q = hcol[j + 1];
-        const double den = sqrt(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
-        cs[j] = den > 0.0 ? make_double2(p.x / den, p.y / den) : make_double2(1.0, 0.0);
-        sn[j] = den > 0.0 ? make_double2(q.x / den, q.y / den) : make_double2(0.0, 0.0);
-        hcol[j] = make_double2(den, 0.0);
-        const double2 g = gv[j];
-        gv[j + 1] = make_double2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
-        gv[j] = make_double2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
+        const float2 p = hcol[j], q = hcol[j + 1];
+        const float den = sqrtf(p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+        cs[j] = den > 0.f ? make_float2(p.x / den, p.y / den) : make_float2(1.f, 0.f);
+        sn[j] = den > 0.f ? make_float2(q.x / den, q.y / den) : make_float2(0.f, 0.f);
+        hcol[j] = make_float2(den, 0.f);
+        const float2 g = gv[j];
+        gv[j + 1] = make_float2(-(sn[j].x * g.x - sn[j].y * g.y), -(sn[j].x * g.y + sn[j].y * g.x));
+        gv[j] = make_float2(cs[j].x * g.x + cs[j].y * g.y, cs[j].x * g.y - cs[j].y * g.x);
         if (blockIdx.x == 0)
           for (int i = 0; i <= j; i++) a.R[(size_t)c * (CMAXM + 1) * CMAXM + (size_t)j * (CMAXM + 1) + i] = hcol[i];
         s_k[c] = j + 1;
-        const double res = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
-        if (res <= a.rtol * s_beta[c] || !(hn > 0.0) || !(den > 0.0)) s_done[c] = 1;
+        const float res = sqrtf(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+        if (res <= (float)a.rtol * s_beta[c] || !(hn > 0.f) || !(den > 0.f)) s_done[c] = 1;
       } else if (lane == 0) {
-        s_hn[c] = s_hn[c] > 0.0 ? s_hn[c] : 1.0;   // a finished column keeps a harmless scale
+        s_hn[c] = s_hn[c] > 0.f ? s_hn[c] : 1.f;   // a finished column keeps a harmless scale
       }
     }
     __syncthreads();
@@ -963,20 +1022,20 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
     for (int c = warp; c < a.ncol; c += nwarp) {
       if (lane != 0) continue;
       const int k = s_k[c];
-      const double2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM;
-      double2* y = a.y + (size_t)c * CMAXM;
-      const double2* gv = GV(c);
+      const float2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM;
+      float2* y = a.y + (size_t)c * CMAXM;
+      const float2* gv = GV(c);
       for (int i = k - 1; i >= 0; i--) {
-        double2 acc = gv[i];
+        float2 acc = gv[i];
         for (int l = i + 1; l < k; l++) {
-          const double2 h = R[(size_t)l * (CMAXM + 1) + i], yl = y[l];
+          const float2 h = R[(size_t)l * (CMAXM + 1) + i], yl = y[l];
           acc.x -= h.x * yl.x - h.y * yl.y;
           acc.y -= h.x * yl.y + h.y * yl.x;
         }
-        const double2 d = R[(size_t)i * (CMAXM + 1) + i];
-        const double dn = d.x * d.x + d.y * d.y;
-        y[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
-                        : make_double2(0.0, 0.0);
+        const float2 d = R[(size_t)i * (CMAXM + 1) + i];
+        const float dn = d.x * d.x + d.y * d.y;
+        y[i] = dn > 0.f ? make_float2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : make_float2(0.f, 0.f);
       }
       if (a.counter) atomicAdd(a.counter, k);
     }
@@ -984,7 +1043,7 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
   grid.sync();
   for (int c = 0; c < a.ncol; c++) {
     const int k = s_k[c];
-    const double2* y = a.y + (size_t)c * CMAXM;
+    const float2* y = a.y + (size_t)c * CMAXM;
     for (int e = tid; e < n; e += nth) {
       float xr = 0.f, xi = 0.f;
       for (int i = 0; i < k; i++) {
@@ -1010,6 +1069,24 @@ int coarse_grid_ctas(Ctx& c) {
                            : std::max(1, std::min(c.cl.nc, c.sms * std::max(1, std::min(mps, c.coarse_ctas_per_sm))));
 }
 
+// Dynamic shared memory for the own sites' stencil rows of a grid of G CTAs, or 0 when they do not
+// fit (above 48 KB, or too large for every CTA of the grid to stay resident): then they go to the
+// global rows buffer.
+template <typename S>
+size_t rows_smem_bytes(Ctx& c, int G, int nf) {
+  using T2 = typename CplxT<S>::T2;
+  const size_t per_cta = (size_t)((c.cl.nc + G - 1) / G) * nf * 9 * c.cl.nd * sizeof(T2);
+  if (per_cta > 48 * 1024) return 0;
+  static size_t cached_bytes[2] = {(size_t)-1, (size_t)-1};
+  static int cached_mps[2] = {0, 0};
+  const int t = sizeof(S) == 8;
+  if (cached_bytes[t] != per_cta) {
+    TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_mps[t], k_coarse_gmres<S>, 256, per_cta));
+    cached_bytes[t] = per_cta;
+  }
+  return (size_t)cached_mps[t] * c.sms >= (size_t)G ? per_cta : 0;
+}
+
 template <typename S>
 void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 1, double epsbar = 0.0) {
   using T2 = typename CplxT<S>::T2;
@@ -1017,8 +1094,8 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   const size_t n = (size_t)nf * c.cl.nc * c.cl.nd;
   const int G = coarse_grid_ctas<S>(c);
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
-  c.cw_w.alloc(10 * n * sizeof(T2));
-  c.cw_part.alloc(sizeof(double2) * ((size_t)(CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
+  c.cw_w.alloc(11 * n * sizeof(T2));
+  c.cw_part.alloc(sizeof(double2) * ((size_t)2 * (CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
   if (!c.coarse_iter_dev.p) {
     c.coarse_iter_dev.alloc(sizeof(int));
     TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
@@ -1032,6 +1109,8 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   a.epsbar = (S)epsbar;
   a.delta = nf == 2 ? (S)c.ndshift : (S)0;
   a.overlap = c.coarse_overlap;
+  const size_t smem = rows_smem_bytes<S>(c, G, nf);
+  a.rows_smem = smem > 0;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1039,29 +1118,29 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   a.x = (T2*)x;
   a.V = c.cw_V.as<T2>();
   a.w = c.cw_w.as<T2>();
-  a.rows = a.w + n;
+  a.rows = a.w + 2 * n;
   a.mu = (S)mu;
   a.rtol = c.mg.coarse_rtol;
   a.part = c.cw_part.as<double2>();
-  a.R = a.part + (size_t)(CMAXM + 1) * G;
+  a.R = a.part + (size_t)2 * (CMAXM + 1) * G;
   a.y = a.R + (size_t)(CMAXM + 1) * CMAXM;
   a.npart = reinterpret_cast<double*>(a.y + CMAXM);
   a.counter = c.coarse_iter_dev.as<int>();
   void* args[] = {&a};
   ++c.launches;
-  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, smem, c.stream));
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Scratch layout used by coarse_gmres_on_scratch: basis V, w and the 9 partial stencil rows, dot partials, R, y, norm partials,
+// Scratch layout used by coarse_gmres_on_scratch: basis V, the two w buffers and the 9 partial stencil rows, dot partials, R, y, norm partials,
 // step counter, each 256-byte aligned.
 template <typename S>
 size_t scratch_layout(const Ctx& c, int G, size_t off[8]) {
   using T2 = typename CplxT<S>::T2;
   const int m = std::min(c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)c.cl.nc * c.cl.nd;
-  const size_t sz[7] = {(m + 1) * n * sizeof(T2), 10 * n * sizeof(T2), sizeof(double2) * (CMAXM + 1) * G,
+  const size_t sz[7] = {(m + 1) * n * sizeof(T2), 11 * n * sizeof(T2), sizeof(double2) * 2 * (CMAXM + 1) * G,
                         sizeof(double2) * (CMAXM + 1) * CMAXM, sizeof(double2) * CMAXM, sizeof(double) * G, sizeof(int)};
   size_t o = 0;
   for (int i = 0; i < 7; i++) {
@@ -1086,6 +1165,8 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.epsbar = (S)0;
   a.delta = (S)0;
   a.overlap = c.coarse_overlap;
+  const size_t smem = rows_smem_bytes<S>(c, G, 1);
+  a.rows_smem = smem > 0;
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1093,7 +1174,7 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.x = (T2*)x;
   a.V = (T2*)(scratch + off[0]);
   a.w = (T2*)(scratch + off[1]);
-  a.rows = a.w + (size_t)c.cl.nc * c.cl.nd;
+  a.rows = a.w + 2 * (size_t)c.cl.nc * c.cl.nd;
   a.part = (double2*)(scratch + off[2]);
   a.R = (double2*)(scratch + off[3]);
   a.y = (double2*)(scratch + off[4]);
@@ -1104,7 +1185,7 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   TMG_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), c.stream));   // the shared scratch keeps old contents
   void* args[] = {&a};
   ++c.launches;
-  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, 0, c.stream));
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gmres<S>, dim3(G), dim3(256), args, smem, c.stream));
 }
 
 }  // namespace
@@ -1124,7 +1205,7 @@ void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float*
   ProfScope ps(c, PK_COARSE_SOLVE);
   const int m = std::min(c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)c.cl.nc * c.cl.nd;
-  const size_t smem = sizeof(double2) * (size_t)ncol * (5 * CMAXM + 4);
+  const size_t smem = sizeof(float2) * (size_t)ncol * (5 * CMAXM + 4);
   if (smem > 48 * 1024)
     TMG_CUDA(cudaFuncSetAttribute(k_coarse_gmres_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int mps = 0;
@@ -1154,10 +1235,10 @@ void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float*
   a.rows = a.w + n * ncol;
   a.mu = mu_dev;
   a.rtol = c.mg.coarse_rtol;
-  a.part = c.cw_part.as<double2>();
+  a.part = c.cw_part.as<float2>();
   a.R = a.part + (size_t)ncol * (CMAXM + 1) * G;
   a.y = a.R + (size_t)ncol * (CMAXM + 1) * CMAXM;
-  a.npart = reinterpret_cast<double*>(a.y + (size_t)ncol * CMAXM);
+  a.npart = reinterpret_cast<float*>(a.y + (size_t)ncol * CMAXM);
   a.counter = c.coarse_iter_dev.as<int>();
   void* args[] = {&a};
   ++c.launches;
@@ -1174,6 +1255,328 @@ void coarse_gmres_persistent_nd(Ctx& c, int cp, const void* b, void* x) {
   ProfScope ps(c, PK_COARSE_SOLVE);
   if (cp == TMG_PREC_F64) launch<double>(c, b, x, c.mubar, c.cl.Dc64.p, 2, c.epsbar);
   else launch<float>(c, b, x, c.mubar, c.cl.Dc32.p, 2, c.epsbar);
+}
+
+namespace {
+
+// ---- batched coarse GMRES with the stencil on the tensor cores.  Each Arnoldi step is two
+// launches: the tcgen05 multi-RHS coarse operator W = D_c(mu_col) V_j for all columns (every
+// stencil block is read once per step for all columns), then one cooperative kernel that
+// orthogonalises W against V_0..V_j per column (two grid barriers), writes V_{j+1} and, on CTA 0,
+// advances every unfinished column's Givens rotations and stopping test.  The rotations live in
+// global memory between launches; once every column has stopped, the remaining launches of the
+// step sequence return at once (a flag both kernels read on entry).  Same arithmetic as
+// k_coarse_gmres_batched: one classical Gram-Schmidt pass, FP32 vectors, FP64 reductions.
+struct BgtArgs {
+  int nd, nv, nc, m, ncol;
+  const float2* b;
+  float2* x;
+  float2* V;             // [(m + 1)][ncol][n]
+  float2* W;             // [ncol][n]
+  float rtol;
+  float2* part;          // [ncol][CMAXM + 1][G]
+  float* npart;          // [ncol][G]
+  float2* cs;            // [ncol][CMAXM]
+  float2* sn;            // [ncol][CMAXM]
+  float2* gv;            // [ncol][CMAXM + 1]
+  float2* R;             // [ncol][(CMAXM + 1) * CMAXM]
+  float2* y;             // [ncol][CMAXM]
+  float* beta;           // [ncol]
+  int* done;             // [ncol]
+  int* kk;               // [ncol]: Krylov dimension reached
+  int* all_done;
+  int* counter;
+};
+
+__global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ float sh[32];
+  __shared__ float s_beta[BMAXC];
+  const int n = a.nc * a.nd, G = gridDim.x;
+  const int chunk = (n + G - 1) / G;
+  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int c = 0; c < a.ncol; c++) {
+    float nn = 0.f;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const float2 v = a.b[(size_t)c * n + e];
+      nn += v.x * v.x + v.y * v.y;
+    }
+    const float t = cta_sum(nn, sh);
+    if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+  }
+  grid.sync();
+  for (int c = warp; c < a.ncol; c += nwarp) {
+    float t = 0.f;
+    for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
+    t = warp_sum(t);
+    if (lane == 0) s_beta[c] = sqrtf(t);
+  }
+  __syncthreads();
+  for (int c = 0; c < a.ncol; c++) {
+    const float inv = s_beta[c] > 0.f ? 1.f / s_beta[c] : 0.f;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      float2 v = a.b[(size_t)c * n + e];
+      v.x *= inv;
+      v.y *= inv;
+      a.V[(size_t)c * n + e] = v;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int c = threadIdx.x; c < a.ncol; c += blockDim.x) {
+      a.beta[c] = s_beta[c];
+      a.done[c] = !(s_beta[c] > 0.f);
+      a.kk[c] = 0;
+      float2* gv = a.gv + (size_t)c * (CMAXM + 1);
+      for (int i = 0; i <= CMAXM; i++) gv[i] = make_float2(0.f, 0.f);
+      gv[0] = make_float2(s_beta[c], 0.f);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int all = 1;
+      for (int c = 0; c < a.ncol; c++) all &= a.done[c];
+      *a.all_done = all;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
+  if (*a.all_done) return;                           // the same value in every CTA: set by an earlier launch
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ float2 hsm[];                   // [ncol][CMAXM + 1]
+  __shared__ float sh[32];
+  __shared__ float s_hn[BMAXC];
+  const int n = a.nc * a.nd, G = gridDim.x;
+  const size_t cn = (size_t)a.ncol * n;
+  const int chunk = (n + G - 1) / G;
+  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // (1) partial <v_i, w> per column over the own chunk, one warp per (basis vector, column)
+  for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
+    const int i = t / a.ncol, c = t - i * a.ncol;
+    const float2* vi = a.V + (size_t)i * cn + (size_t)c * n;
+    const float2* wc = a.W + (size_t)c * n;
+    float re = 0.f, im = 0.f;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const float2 p = vi[e], q = wc[e];
+      re += p.x * q.x + p.y * q.y;
+      im += p.x * q.y - p.y * q.x;
+    }
+    const float dre = warp_sum(re), dim = warp_sum(im);
+    if (lane == 0) a.part[((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x] = make_float2(dre, dim);
+  }
+  grid.sync();
+  for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
+    const int i = t / a.ncol, c = t - i * a.ncol;
+    float re = 0.f, im = 0.f;
+    for (int q = lane; q < G; q += 32) {
+      const float2 v = a.part[((size_t)c * (CMAXM + 1) + i) * G + q];
+      re += v.x;
+      im += v.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) hsm[c * (CMAXM + 1) + i] = make_float2(re, im);
+  }
+  __syncthreads();
+  // (2) w -= sum_i h_i v_i and ||w||^2 on the own chunk, per column
+  for (int c = 0; c < a.ncol; c++) {
+    float nn = 0.f;
+    const float2* hp = hsm + c * (CMAXM + 1);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      float2 q = a.W[(size_t)c * n + e];
+      for (int i = 0; i <= j; i++) {
+        const float2 p = a.V[(size_t)i * cn + (size_t)c * n + e];
+        const float hr = (float)hp[i].x, hi = (float)hp[i].y;
+        q.x -= hr * p.x - hi * p.y;
+        q.y -= hr * p.y + hi * p.x;
+      }
+      a.W[(size_t)c * n + e] = q;
+      nn += q.x * q.x + q.y * q.y;
+    }
+    const float t = cta_sum(nn, sh);
+    if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+  }
+  grid.sync();
+  for (int c = warp; c < a.ncol; c += nwarp) {
+    float t = 0.f;
+    for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
+    t = warp_sum(t);
+    if (lane == 0) s_hn[c] = sqrtf(t);
+  }
+  __syncthreads();
+  // (3) v_{j+1} = w / h_{j+1,j} on the own chunk (zero for a column whose w vanished)
+  for (int c = 0; c < a.ncol; c++) {
+    const float inv = s_hn[c] > 0.f ? 1.f / s_hn[c] : 0.f;
+    float2* vn = a.V + (size_t)(j + 1) * cn + (size_t)c * n;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      float2 q = a.W[(size_t)c * n + e];
+      q.x *= inv;
+      q.y *= inv;
+      vn[e] = q;
+    }
+  }
+  // (4) CTA 0: Hessenberg column j of every unfinished column, rotated by the column's previous
+  //     Givens rotations, the new rotation, the residual estimate and the stopping test
+  if (blockIdx.x != 0) return;
+  for (int c = threadIdx.x; c < a.ncol; c += blockDim.x) {
+    if (a.done[c]) continue;
+    float2* hcol = hsm + c * (CMAXM + 1);           // j + 2 entries: the shared row has CMAXM + 1
+    float2* cs = a.cs + (size_t)c * CMAXM;
+    float2* sn = a.sn + (size_t)c * CMAXM;
+    float2* gv = a.gv + (size_t)c * (CMAXM + 1);
+    const float hn = s_hn[c];
+    float2 x0 = hcol[0];
+    for (int i = 0; i < j; i++) {
+      const float2 x1 = hcol[i + 1];
+      const float2 cc = cs[i], ss = sn[i];
+      hcol[i] = make_float2(cc.x * x0.x + cc.y * x0.y + ss.x * x1.x + ss.y * x1.y,
+                             cc.x * x0.y - cc.y * x0.x + ss.x * x1.y - ss.y * x1.x);
+      x0 = make_float2(-(ss.x * x0.x - ss.y * x0.y) + (cc.x * x1.x - cc.y * x1.y),
+                        -(ss.x * x0.y + ss.y * x0.x) + (cc.x * x1.y + cc.y * x1.x));
+    }
+    const float den = sqrtf(x0.x * x0.x + x0.y * x0.y + hn * hn);
+    const float2 cj = den > 0.f ? make_float2(x0.x / den, x0.y / den) : make_float2(1.f, 0.f);
+    const float2 sj = den > 0.f ? make_float2(hn / den, 0.f) : make_float2(0.f, 0.f);
+    cs[j] = cj;
+    sn[j] = sj;
+    hcol[j] = make_float2(den, 0.f);
+    const float2 g = gv[j];
+    gv[j + 1] = make_float2(-(sj.x * g.x - sj.y * g.y), -(sj.x * g.y + sj.y * g.x));
+    gv[j] = make_float2(cj.x * g.x + cj.y * g.y, cj.x * g.y - cj.y * g.x);
+    float2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM + (size_t)j * (CMAXM + 1);
+    for (int i = 0; i <= j; i++) R[i] = hcol[i];
+    a.kk[c] = j + 1;
+    const float res = sqrtf(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
+    if (res <= (float)a.rtol * a.beta[c] || !(hn > 0.f) || !(den > 0.f)) a.done[c] = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int c = 0; c < a.ncol; c++) all &= a.done[c];
+    *a.all_done = all || (j == a.m - 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bgt_finish(BgtArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int n = a.nc * a.nd;
+  const size_t cn = (size_t)a.ncol * n;
+  if (blockIdx.x == 0) {
+    for (int c = threadIdx.x; c < a.ncol; c += blockDim.x) {
+      const int k = a.kk[c];
+      const float2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM;
+      const float2* gv = a.gv + (size_t)c * (CMAXM + 1);
+      float2* y = a.y + (size_t)c * CMAXM;
+      for (int i = k - 1; i >= 0; i--) {
+        float2 acc = gv[i];
+        for (int l = i + 1; l < k; l++) {
+          const float2 h = R[(size_t)l * (CMAXM + 1) + i], yl = y[l];
+          acc.x -= h.x * yl.x - h.y * yl.y;
+          acc.y -= h.x * yl.y + h.y * yl.x;
+        }
+        const float2 d = R[(size_t)i * (CMAXM + 1) + i];
+        const float dn = d.x * d.x + d.y * d.y;
+        y[i] = dn > 0.f ? make_float2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                        : make_float2(0.f, 0.f);
+      }
+      if (a.counter) atomicAdd(a.counter, k);
+    }
+  }
+  grid.sync();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int c = 0; c < a.ncol; c++) {
+    const int k = a.kk[c];
+    const float2* y = a.y + (size_t)c * CMAXM;
+    for (int e = tid; e < n; e += nth) {
+      float xr = 0.f, xi = 0.f;
+      for (int i = 0; i < k; i++) {
+        const float2 v = a.V[(size_t)i * cn + (size_t)c * n + e];
+        const float yr = (float)y[i].x, yi = (float)y[i].y;
+        xr += yr * v.x - yi * v.y;
+        xi += yr * v.y + yi * v.x;
+      }
+      a.x[(size_t)c * n + e] = make_float2(xr, xi);
+    }
+  }
+}
+
+}  // namespace
+
+// Whether the tensor-core batched coarse solve covers this level: the tcgen05 coarse apply's block
+// widths (2 N_v = 8 .. 64) and at most 32 columns.
+bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol) {
+  const int nd = c.cl.nd;
+  return ncol >= 1 && ncol <= 32 && (nd == 8 || nd == 16 || nd == 24 || nd == 32 || nd == 48 || nd == 64);
+}
+
+void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (!coarse_gmres_batched_tc_ok(c, ncol)) throw Error{TMG_ERR_ARG, "tensor-core batched coarse solve: unsupported shape"};
+  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+  static int mps[3] = {-1, -1, -1};
+  if (mps[0] < 0) {
+    TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps[0], k_bgt_start, 256, 0));
+    TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps[1], k_bgt_arnoldi, 256,
+                                                           sizeof(float2) * BMAXC * (CMAXM + 1)));
+    TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps[2], k_bgt_finish, 256, 0));
+  }
+  const int per_sm = std::min(2, std::min(mps[0], std::min(mps[1], mps[2])));
+  if (per_sm < 1) throw Error{TMG_ERR_CUDA, "tensor-core batched coarse solve: kernels cannot be resident"};
+  const int G = std::max(1, std::min((int)((n + 255) / 256), c.sms * per_sm));
+  const size_t hsm = sizeof(float2) * (size_t)ncol * (CMAXM + 1);
+  if (hsm > 48 * 1024)
+    TMG_CUDA(cudaFuncSetAttribute(k_bgt_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+  c.cw_V.alloc((m + 1) * n * ncol * sizeof(float2));
+  c.cw_w.alloc(n * ncol * sizeof(float2));
+  // one state allocation: part, cs, sn, gv, R, y, npart, beta, done, kk, all_done
+  const size_t d2 = (size_t)ncol * ((CMAXM + 1) * G + 2 * CMAXM + (CMAXM + 1) + (CMAXM + 1) * CMAXM + CMAXM);
+  const size_t bytes = sizeof(float2) * d2 + sizeof(float) * ((size_t)ncol * G + ncol) + sizeof(int) * (2 * (size_t)ncol + 1);
+  c.cw_state.alloc(bytes);
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  if (!c.tc_err.p) {
+    c.tc_err.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+  }
+  BgtArgs a;
+  a.nd = c.cl.nd;
+  a.nv = c.cl.nv;
+  a.nc = c.cl.nc;
+  a.m = m;
+  a.ncol = ncol;
+  a.b = (const float2*)b;
+  a.x = (float2*)x;
+  a.V = c.cw_V.as<float2>();
+  a.W = c.cw_w.as<float2>();
+  a.rtol = c.mg.coarse_rtol;
+  a.part = c.cw_state.as<float2>();
+  a.cs = a.part + (size_t)ncol * (CMAXM + 1) * G;
+  a.sn = a.cs + (size_t)ncol * CMAXM;
+  a.gv = a.sn + (size_t)ncol * CMAXM;
+  a.R = a.gv + (size_t)ncol * (CMAXM + 1);
+  a.y = a.R + (size_t)ncol * (CMAXM + 1) * CMAXM;
+  a.npart = reinterpret_cast<float*>(a.y + (size_t)ncol * CMAXM);
+  a.beta = a.npart + (size_t)ncol * G;
+  a.done = reinterpret_cast<int*>(a.beta + ncol);
+  a.kk = a.done + ncol;
+  a.all_done = a.kk + ncol;
+  a.counter = c.coarse_iter_dev.as<int>();
+  int* tc_err = c.tc_err.as<int>();
+  void* args[] = {&a};
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_start, dim3(G), dim3(256), args, 0, c.stream));
+  for (int j = 0; j < m; j++) {
+    coarse_apply_tc(c, ncol, a.V + (size_t)j * ncol * n, a.W, mu_dev, tc_err, a.all_done);
+    void* sargs[] = {&a, &j};
+    ++c.launches;
+    TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_arnoldi, dim3(G), dim3(256), sargs, hsm, c.stream));
+  }
+  ++c.launches;
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_finish, dim3(G), dim3(256), args, 0, c.stream));
 }
 
 }  // namespace tmg
@@ -1195,11 +1598,11 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
                                   : c.sms * std::max(1, std::min(mps, c.kcycle_ctas_per_sm));
   const int sm_m = std::min(p.smooth_m, CMAXM), cm = std::min(p.coarse_m, CMAXM), kr = std::min(p.k_restart, KMAXR);
   // one scratch allocation, carved 256-byte aligned
-  const size_t vec_elems[] = {(kr + 1) * n1, kr * n1, n1, n1, n1, (sm_m + 1) * n1, 10 * n1, n2, n2, (cm + 1) * n2, 10 * n2};
+  const size_t vec_elems[] = {(kr + 1) * n1, kr * n1, n1, n1, n1, (sm_m + 1) * n1, 11 * n1, n2, n2, (cm + 1) * n2, 11 * n2};
   const size_t nvec = sizeof(vec_elems) / sizeof(vec_elems[0]);
-  const size_t d2_elems[] = {(size_t)(KMAXR + 1) * G, (size_t)(KMAXR + 1) * KMAXR, KMAXR,
-                             (size_t)(CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM,
-                             (size_t)(CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM};
+  const size_t d2_elems[] = {(size_t)2 * (KMAXR + 1) * G, (size_t)(KMAXR + 1) * KMAXR, KMAXR,
+                             (size_t)2 * (CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM,
+                             (size_t)2 * (CMAXM + 1) * G, (size_t)(CMAXM + 1) * CMAXM, CMAXM};
   const size_t nd2 = sizeof(d2_elems) / sizeof(d2_elems[0]);
   size_t off[32], o = 0;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
@@ -1233,6 +1636,7 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   s.epsbar = (S)epsbar;
   s.delta = nf == 2 ? (S)c.ndshift : (S)0;
   s.overlap = c.coarse_overlap;
+  s.rows_smem = 0;
   s.passes = passes;
   s.Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
   s.nbr = c.cl.nbr.as<int>();
@@ -1240,7 +1644,7 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   s.x = mode == 2 ? (T2*)x : vec(4);
   s.V = vec(5);
   s.w = vec(6);
-  s.rows = s.w + n1;
+  s.rows = s.w + 2 * n1;
   s.mu = (S)mu;
   s.rtol = 0.0;
   s.part = d2(3);
@@ -1257,6 +1661,7 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   l.epsbar = (S)epsbar;
   l.delta = nf == 2 ? (S)c.ndshift : (S)0;
   l.overlap = c.coarse_overlap;
+  l.rows_smem = 0;
   l.passes = passes;
   l.Dc = (const T2*)(sizeof(S) == 8 ? c.cl2.Dc64.p : c.cl2.Dc32.p);
   l.nbr = c.cl2.nbr.as<int>();
@@ -1264,7 +1669,7 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   l.x = vec(8);
   l.V = vec(9);
   l.w = vec(10);
-  l.rows = l.w + n2;
+  l.rows = l.w + 2 * n2;
   l.mu = (S)mu;
   l.rtol = p.coarse_rtol;
   l.part = d2(6);

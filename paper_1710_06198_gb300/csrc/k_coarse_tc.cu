@@ -190,7 +190,10 @@ template <int ND, int NPAD, int R>
 __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int ncol, const float2* __restrict__ Dc,
                                                          const int* __restrict__ nbr, const float2* __restrict__ X,
                                                          float2* __restrict__ Y, const float* __restrict__ mu,
-                                                         int* __restrict__ err) {
+                                                         int* __restrict__ err, const int* __restrict__ skip) {
+  // a caller's "nothing left to do" flag, written by an earlier launch: every thread reads the same
+  // value and returns before any tensor memory is allocated
+  if (skip && *skip) return;
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int KP = ((2 * ND + 7) / 8) * 8;             // K padded to the MMA step
   constexpr int nsteps = KP / 8;                          // K = 8 MMA steps per stencil block
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
 }
 
 template <int ND, int NPAD, int R>
-void launch_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+void launch_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
   constexpr int KP = ((2 * ND + 7) / 8) * 8;
   constexpr int cols = ((KP / 8 + R - 1) / R) * NPAD;
   const size_t smem = sizeof(float) * (size_t)(2 * TC_M * KP + 2 * NPAD * KP) + 32;
@@ -329,36 +332,37 @@ void launch_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, in
   TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<ND, NPAD, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ++c.launches, k_coarse_apply_tc<ND, NPAD, R><<<grid, 128, smem, c.stream>>>(c.cl.nc, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
                                                                            c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
-                                                                           mu_dev, err_dev);
+                                                                           mu_dev, err_dev, skip);
 }
 
 template <int ND, int NPAD>
-void launch_tc_r(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
-  if (c.tc_steps_per_range >= 4) launch_tc<ND, NPAD, 4>(c, ncol, X, Y, mu_dev, err_dev);
-  else if (c.tc_steps_per_range == 2) launch_tc<ND, NPAD, 2>(c, ncol, X, Y, mu_dev, err_dev);
-  else launch_tc<ND, NPAD, 1>(c, ncol, X, Y, mu_dev, err_dev);
+void launch_tc_r(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
+  if (c.tc_steps_per_range >= 4) launch_tc<ND, NPAD, 4>(c, ncol, X, Y, mu_dev, err_dev, skip);
+  else if (c.tc_steps_per_range == 2) launch_tc<ND, NPAD, 2>(c, ncol, X, Y, mu_dev, err_dev, skip);
+  else launch_tc<ND, NPAD, 1>(c, ncol, X, Y, mu_dev, err_dev, skip);
 }
 
 template <int ND>
-void launch_tc_nd(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
-  if (ncol <= 16) launch_tc_r<ND, 16>(c, ncol, X, Y, mu_dev, err_dev);
-  else launch_tc_r<ND, 32>(c, ncol, X, Y, mu_dev, err_dev);
+void launch_tc_nd(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
+  if (ncol <= 16) launch_tc_r<ND, 16>(c, ncol, X, Y, mu_dev, err_dev, skip);
+  else launch_tc_r<ND, 32>(c, ncol, X, Y, mu_dev, err_dev, skip);
 }
 
 }  // namespace
 
-// Y = D_c(mu_col) X for ncol FP32 coarse vectors ([col][nc * nd] complex) on the tensor cores.
-void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev) {
+// Y = D_c(mu_col) X for ncol FP32 coarse vectors ([col][nc * nd] complex) on the tensor cores; the
+// launch does nothing when skip is given and *skip is nonzero on the device.
+void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
   ProfScope ps(c, PK_COARSE);
   const int nd = c.cl.nd;
   if (ncol < 1 || ncol > 32) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns"};
   switch (nd) {
-    case 8: launch_tc_nd<8>(c, ncol, X, Y, mu_dev, err_dev); break;
-    case 16: launch_tc_nd<16>(c, ncol, X, Y, mu_dev, err_dev); break;
-    case 24: launch_tc_nd<24>(c, ncol, X, Y, mu_dev, err_dev); break;
-    case 32: launch_tc_nd<32>(c, ncol, X, Y, mu_dev, err_dev); break;
-    case 48: launch_tc_nd<48>(c, ncol, X, Y, mu_dev, err_dev); break;
-    case 64: launch_tc_nd<64>(c, ncol, X, Y, mu_dev, err_dev); break;
+    case 8: launch_tc_nd<8>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
+    case 16: launch_tc_nd<16>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
+    case 24: launch_tc_nd<24>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
+    case 32: launch_tc_nd<32>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
+    case 48: launch_tc_nd<48>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
+    case 64: launch_tc_nd<64>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
     default: throw Error{TMG_ERR_ARG, "tensor-core coarse apply: N_v must be 4, 8, 12, 16, 24 or 32"};
   }
   TMG_CHECK_LAUNCH();

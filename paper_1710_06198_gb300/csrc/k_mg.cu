@@ -15,27 +15,29 @@
 namespace tmg {
 
 // Reduction of N values (per thread) over the CTA; every thread gets the totals.  Warp sums use
-// shuffles in the kernel's precision; the cross-warp sum is done by one thread per value.
+// shuffles and the cross-warp sum (one thread per value) runs in the kernel's precision R: the
+// FP32 kernels use no FP64 arithmetic, which GB300 issues at a small fraction of the FP32 rate.
 // red: shared scratch of at least 33 * N doubles.
 template <int N, typename R>
-__device__ __forceinline__ void cta_allreduce(R (&v)[N], double* red) {
+__device__ __forceinline__ void cta_allreduce(R (&v)[N], double* red_d) {
+  R* red = reinterpret_cast<R*>(red_d);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int i = 0; i < N; i++) {
     R a = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) red[w * N + i] = (double)a;
+    if (lane == 0) red[w * N + i] = a;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    double a = 0.0;
+    R a = 0;
     for (int k = 0; k < nw; k++) a += red[k * N + i];
     red[32 * N + i] = a;
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < N; i++) v[i] = (R)red[32 * N + i];
+  for (int i = 0; i < N; i++) v[i] = red[32 * N + i];
   __syncthreads();
 }
 
@@ -423,27 +425,29 @@ __global__ void __launch_bounds__(256) k_restrict(Geom g, S r, S W, int nv, OUT2
       }
     }
     // warp sums by a butterfly in which every lane ends up holding the sum of one of the 32 values
-    // (31 shuffles instead of 32 x 5), then one FP64 sum over the warps per value
+    // (31 shuffles instead of 32 x 5), then one sum over the warps per value, in the kernel's
+    // precision R (no FP64 arithmetic in the FP32 kernel)
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     warp_transpose_reduce<16>(v, lane);
     warp_transpose_reduce<8>(v, lane);
     warp_transpose_reduce<4>(v, lane);
     warp_transpose_reduce<2>(v, lane);
     warp_transpose_reduce<1>(v, lane);
-    red[wp * 32 + lane] = (double)v[0];
+    R* redr = reinterpret_cast<R*>(red);
+    redr[wp * 32 + lane] = v[0];
     __syncthreads();
     if (threadIdx.x < 32) {
-      double t = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k * 32 + threadIdx.x];
-      red[32 * 32 + threadIdx.x] = t;
+      R t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += redr[k * 32 + threadIdx.x];
+      redr[32 * 32 + threadIdx.x] = t;
     }
     __syncthreads();
     if (threadIdx.x < 16) {
       const int chi = threadIdx.x / 8, jj = threadIdx.x % 8, j = j0 + jj;
       if (j < nv) {
         OUT2 o;
-        o.x = red[32 * 32 + (chi * 8 + jj) * 2];
-        o.y = red[32 * 32 + (chi * 8 + jj) * 2 + 1];
+        o.x = redr[32 * 32 + (chi * 8 + jj) * 2];
+        o.y = redr[32 * 32 + (chi * 8 + jj) * 2 + 1];
         out[(size_t)blk * nd + chi * nv + j] = o;
       }
     }

@@ -1237,6 +1237,8 @@ static void batched_cycle_p(Ctx& c, int pf, int ncol, const void* v, void* z, vo
     const size_t nco = (size_t)c.cl.nc * c.cl.nd;
     for (int col = 0; col < ncol; col++)
       kcycle(c, TMG_PREC_F32, (const float2*)cr + col * nco, (float2*)ce + col * nco, mu[col], 0);
+  } else if (c.batched_tc && coarse_gmres_batched_tc_ok(c, ncol)) {
+    coarse_gmres_batched_tc(c, ncol, cr, ce, mu_dev);
   } else {
     coarse_gmres_batched(c, ncol, cr, ce, mu_dev);
   }
@@ -1257,6 +1259,7 @@ static void batched_cycle_run(Ctx& c, int pf, int ncol, const void* v, void* z, 
     auto u = [](const void* p) { return (unsigned long long)(uintptr_t)p; };
     k.push_back(0xBA7C4ull);
     k.push_back((unsigned long long)ncol);
+    k.push_back((unsigned long long)c.batched_tc);
     k.push_back(u(cr));
     k.push_back(u(ce));
     k.push_back(u(mu_dev));
@@ -1341,6 +1344,7 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
   TMG_CUDA(cudaMemcpyAsync(mu_dev.p, muf.data(), ncol * sizeof(float), cudaMemcpyHostToDevice, c.stream));
   int c0 = 0, c1 = 0;
   if (c.coarse_iter_dev.p) TMG_CUDA(cudaMemcpyAsync(&c0, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  if (c.tc_err.p) TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
   std::vector<double> bn(ncol), rn(ncol);
   for (int j = 0; j < ncol; j++) {
     const char* bj = (const char*)b64 + j * n * 16;
@@ -1482,6 +1486,12 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
     TMG_CUDA(cudaMemcpyAsync(&c1, c.coarse_iter_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     st.coarse_iterations = c1 - c0;
+  }
+  if (c.tc_err.p) {
+    int herr = 0;
+    TMG_CUDA(cudaMemcpyAsync(&herr, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (herr) throw Error{TMG_ERR_TIMEOUT, "batched solve: a tensor-core completion wait gave up"};
   }
   return rc;
 }

@@ -225,6 +225,8 @@ struct Ctx {
   int hmc_nmono = 0;
   int eo_stage = 1;             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
   int coarse_overlap = 1;       // coarse GMRES: overlap the Hessenberg update with the next stencil
+  int batched_tc = 1;           // batched coarse solve: stencil on the tensor cores (k_coarse_tc.cu)
+  DBuf tc_err;                  // set by a tensor-core completion wait that gave up (batched solve)
 };
 
 // Records a start event on construction and an end event on destruction when profiling is on.
@@ -335,7 +337,10 @@ void restrict_mrhs(Ctx& c, int ncol, const void* r, void* cvec);
 void prolong_mrhs(Ctx& c, int ncol, const void* cvec, void* e);
 // Y = D_c(mu_col) X for ncol <= 32 FP32 coarse vectors on the tensor cores (k_coarse_tc.cu);
 // err_dev (device int) is set to 1 if a bounded wait gave up
-void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev);
+void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
+                     const int* skip = nullptr);
+bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol);
+void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev);
 // The same solve on caller-provided device scratch (no allocation): bytes needed, and the launch.
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
 void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);

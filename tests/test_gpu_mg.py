@@ -104,6 +104,51 @@ def test_coarse_solve(small, prec):
     assert rel(ctx.coarse_solve(c, p.mu, prec), want) < tol
 
 
+@pytest.mark.parametrize("overlap", [0, 1])
+@pytest.mark.parametrize("passes", [1, 2])
+def test_coarse_solve_launch_variants(small, overlap, passes):
+    """The persistent coarse GMRES with the Hessenberg update overlapped or not, one or two
+    Gram-Schmidt passes and grids of 1, 3, 7 and 16 CTAs (ragged vector chunks, CTAs owning
+    nothing): every variant gives the oracle's Krylov solution."""
+    ctx, H, U, p = small
+    c = fields.gaussian_coarse((2, 2, 2, 2), 2 * ctx.nv, 43)
+    want = H.coarse_solve(c, p.mu)
+    try:
+        ctx.tune("coarse_overlap", overlap)
+        ctx.tune("coarse_gs_passes", passes)
+        for g in (1, 3, 7, 16):
+            ctx.tune("coarse_grid", g)
+            # one classical Gram-Schmidt pass loses a little orthogonality against the oracle's
+            # modified Gram-Schmidt
+            assert rel(ctx.coarse_solve(c, p.mu, F64), want) < (1e-10 if passes == 2 else 1e-8), (g, overlap, passes)
+    finally:
+        ctx.tune("coarse_grid", 0)
+        ctx.tune("coarse_gs_passes", 0)
+        ctx.tune("coarse_overlap", 1)
+
+
+@pytest.fixture(scope="module")
+def nv8():
+    return build((8, 8, 4, 4), (4, 4, 2, 2), 8, 0.5, 44, prec_fine=F32, prec_coarse=F32)
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_coarse_solve_multi(nv8, tc):
+    """The batched coarse GMRES (rtol 0: exactly coarse_m lock-step steps) for 5 columns with their
+    own twists, with D_c applied on the tensor cores (split TF32, all columns per launch) and by the
+    CUDA-core kernel: every column is the oracle's Krylov solution to FP32 accuracy."""
+    ctx, H, U, p = nv8
+    c = fields.gaussian_coarse((2, 2, 2, 2), 2 * ctx.nv, 45, n=5)
+    mus = [p.mu, -p.mu, 0.0, 0.2, -0.07]
+    try:
+        ctx.tune("batched_coarse_tc", tc)
+        x = ctx.coarse_solve_multi(c, mus)
+    finally:
+        ctx.tune("batched_coarse_tc", 1)
+    for j, m in enumerate(mus):
+        assert rel(x[j], H.coarse_solve(c[j], m)) < 1e-4, j
+
+
 def test_cycle_f64(small):
     ctx, H, U, p = small
     r = fields.gaussian_spinor(ctx.dims, 39)

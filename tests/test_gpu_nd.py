@@ -129,8 +129,14 @@ def test_two_level_doublet_solve(method):
     assert rel(x, xo) < 1e-8
 
 
-def test_level1_doublet_kcycle():
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_level1_doublet_kcycle(overlap):
+    """Smoother, one level-1 cycle and the K-cycle solve of the doublet, with the Hessenberg update
+    of the persistent GMRES overlapped with the next stencil and after it; FP64 takes two
+    Gram-Schmidt passes per step, so this also covers partials written by one pass while other
+    CTAs still read the previous pass's."""
     ctx, HN, U, p = build(levels=3, coarse_rtol=5e-2, coarse_m=30)
+    ctx.tune("coarse_overlap", overlap)
     b = _coarse2(ctx, 189)
     L = HN.L1
     assert rel(ctx.kcycle_nd(b, 2, F64), L.smooth(b, np.zeros_like(b))) < 1e-10
