@@ -141,6 +141,22 @@ def kernel_sha(kind):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def stored_traffic(kind):
+    """DRAM bytes per launch of a kernel class from an ncu capture summarised under profiles/ (a line
+    'traffic: <kind> <bytes> bytes per launch, source sha <sha>'), or None when no summary has one
+    or the kernel's source changed since the capture."""
+    import glob
+    import re
+    pat = re.compile(r"^traffic: (\S+) (\d+) bytes per launch, source sha (\w+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                m = pat.match(line.strip())
+                if m and m.group(1) == kind and m.group(3) == kernel_sha(kind):
+                    return int(m.group(2))
+    return None
+
+
 def algorithmic_bytes(kind, V, nv, nc, nd):
     """Bytes one launch of a kernel class must move at least (each input read once, each output
     written once); per-site figures are listed in the design notes."""
@@ -462,13 +478,7 @@ def run_ours(args):
         dsl.append(ctx.bench_dslash(tmg.PREC_F32, 1))
     dsl_ms = statistics.median(dsl)
     dsl_gbs = algorithmic_bytes("dslash_f32", V, 0, 0, 0) / (dsl_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tr = json.load(f).get(dom)
-        if tr and tr.get("kernel_sha") == kernel_sha(dom):
-            traffic = tr["bytes_per_launch"]
+    traffic = stored_traffic(dom)
     # the kernel class with the largest share of the solve's device time, against the measured HBM
     # copy peak with its algorithmic bytes per launch
     roof = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",

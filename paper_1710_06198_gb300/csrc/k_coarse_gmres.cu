@@ -1262,7 +1262,8 @@ namespace {
 // ---- batched coarse GMRES with the stencil on the tensor cores.  Each Arnoldi step is two
 // launches: the tcgen05 multi-RHS coarse operator W = D_c(mu_col) V_j for all columns (every
 // stencil block is read once per step for all columns), then one cooperative kernel that
-// orthogonalises W against V_0..V_j per column (two grid barriers), writes V_{j+1} and, on CTA 0,
+// orthogonalises W against V_0..V_j per column (three grid barriers: per-CTA dot partials, their
+// totals reduced once across the grid, the norms), writes V_{j+1} and, on CTA 0,
 // advances every unfinished column's Givens rotations and stopping test.  The rotations live in
 // global memory between launches; once every column has stopped, the remaining launches of the
 // step sequence return at once (a flag both kernels read on entry).  Same arithmetic as
@@ -1281,6 +1282,7 @@ struct BgtArgs {
   float2* gv;            // [ncol][CMAXM + 1]
   float2* R;             // [ncol][(CMAXM + 1) * CMAXM]
   float2* y;             // [ncol][CMAXM]
+  float2* htot;          // [ncol][CMAXM + 1] Gram-Schmidt coefficients of the current step
   float* beta;           // [ncol]
   int* done;             // [ncol]
   int* kk;               // [ncol]: Krylov dimension reached
@@ -1288,22 +1290,51 @@ struct BgtArgs {
   int* counter;
 };
 
+// Lane l of the warp ends with the warp sum of v[l] (a butterfly over the five lane bits: at bit O
+// each lane keeps one half of its values and adds the partner's copy of the same half).
+template <int O>
+__device__ __forceinline__ void transpose_sum_level(float (&v)[32], int lane) {
+  const bool upper = (lane & O) != 0;
+#pragma unroll
+  for (int i = 0; i < O; i++) {
+    const float mine = upper ? v[i + O] : v[i];
+    const float other = upper ? v[i] : v[i + O];
+    v[i] = mine + __shfl_xor_sync(0xffffffffu, other, O);
+  }
+}
+__device__ __forceinline__ void warp_transpose_sum(float (&v)[32], int lane) {
+  transpose_sum_level<16>(v, lane);
+  transpose_sum_level<8>(v, lane);
+  transpose_sum_level<4>(v, lane);
+  transpose_sum_level<2>(v, lane);
+  transpose_sum_level<1>(v, lane);
+}
+
+// Every CTA owns elements [e0, e1) of every column; the column loops below give whole columns to
+// warps (lanes over the own elements), so the columns proceed in parallel.
+struct BgtChunk {
+  int e0, e1;
+  __device__ BgtChunk(int n) {
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    e0 = min(n, (int)blockIdx.x * chunk);
+    e1 = min(n, e0 + chunk);
+  }
+};
+
 __global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ float sh[32];
   __shared__ float s_beta[BMAXC];
   const int n = a.nc * a.nd, G = gridDim.x;
-  const int chunk = (n + G - 1) / G;
-  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const BgtChunk ch(n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int c = 0; c < a.ncol; c++) {
+  for (int c = warp; c < a.ncol; c += nwarp) {
     float nn = 0.f;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
       const float2 v = a.b[(size_t)c * n + e];
       nn += v.x * v.x + v.y * v.y;
     }
-    const float t = cta_sum(nn, sh);
-    if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+    nn = warp_sum(nn);
+    if (lane == 0) a.npart[(size_t)c * G + blockIdx.x] = nn;
   }
   grid.sync();
   for (int c = warp; c < a.ncol; c += nwarp) {
@@ -1313,9 +1344,9 @@ __global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
     if (lane == 0) s_beta[c] = sqrtf(t);
   }
   __syncthreads();
-  for (int c = 0; c < a.ncol; c++) {
+  for (int c = warp; c < a.ncol; c += nwarp) {
     const float inv = s_beta[c] > 0.f ? 1.f / s_beta[c] : 0.f;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
       float2 v = a.b[(size_t)c * n + e];
       v.x *= inv;
       v.y *= inv;
@@ -1340,34 +1371,45 @@ __global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
+__global__ void __launch_bounds__(256, 2) k_bgt_arnoldi(BgtArgs a, int j) {
   if (*a.all_done) return;                           // the same value in every CTA: set by an earlier launch
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ float2 hsm[];                   // [ncol][CMAXM + 1]
-  __shared__ float sh[32];
+  extern __shared__ float2 hsm[];                    // [ncol][CMAXM + 1]
   __shared__ float s_hn[BMAXC];
   const int n = a.nc * a.nd, G = gridDim.x;
   const size_t cn = (size_t)a.ncol * n;
-  const int chunk = (n + G - 1) / G;
-  const int e0 = min(n, blockIdx.x * chunk), e1 = min(n, e0 + chunk);
+  const BgtChunk ch(n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  // (1) partial <v_i, w> per column over the own chunk, one warp per (basis vector, column)
-  for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
-    const int i = t / a.ncol, c = t - i * a.ncol;
-    const float2* vi = a.V + (size_t)i * cn + (size_t)c * n;
-    const float2* wc = a.W + (size_t)c * n;
-    float re = 0.f, im = 0.f;
-    for (int e = e0 + lane; e < e1; e += 32) {
-      const float2 p = vi[e], q = wc[e];
-      re += p.x * q.x + p.y * q.y;
-      im += p.x * q.y - p.y * q.x;
+  const int ngrp = (j + 16) / 16;                    // groups of 16 basis vectors
+  float* const partf = reinterpret_cast<float*>(a.part);
+  // (1) per-CTA partials of <v_i, w>: one warp per (column, group of 16 basis vectors), every lane
+  //     accumulating 16 complex products over its elements; one transpose-sum leaves value l of
+  //     the group on lane l
+  for (int t = warp; t < a.ncol * ngrp; t += nwarp) {
+    const int c = t / ngrp, g0 = (t - c * ngrp) * 16;
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) v[q] = 0.f;
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
+      const float2 w = a.W[(size_t)c * n + e];
+#pragma unroll
+      for (int ii = 0; ii < 16; ii++) {
+        if (g0 + ii <= j) {
+          const float2 p = a.V[(size_t)(g0 + ii) * cn + (size_t)c * n + e];
+          v[2 * ii] += p.x * w.x + p.y * w.y;
+          v[2 * ii + 1] += p.x * w.y - p.y * w.x;
+        }
+      }
     }
-    const float dre = warp_sum(re), dim = warp_sum(im);
-    if (lane == 0) a.part[((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x] = make_float2(dre, dim);
+    warp_transpose_sum(v, lane);
+    const int i = g0 + (lane >> 1);
+    if (i <= j) partf[(((size_t)c * (CMAXM + 1) + i) * G + blockIdx.x) * 2 + (lane & 1)] = v[0];
   }
   grid.sync();
-  for (int t = warp; t < (j + 1) * a.ncol; t += nwarp) {
-    const int i = t / a.ncol, c = t - i * a.ncol;
+  // (2) totals h_{i,j} per column: the (column, i) pairs spread over all warps of the grid
+  const int npair = a.ncol * (j + 1);
+  for (int p = blockIdx.x * nwarp + warp; p < npair; p += G * nwarp) {
+    const int c = p / (j + 1), i = p - c * (j + 1);
     float re = 0.f, im = 0.f;
     for (int q = lane; q < G; q += 32) {
       const float2 v = a.part[((size_t)c * (CMAXM + 1) + i) * G + q];
@@ -1376,28 +1418,36 @@ __global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
     }
     re = warp_sum(re);
     im = warp_sum(im);
-    if (lane == 0) hsm[c * (CMAXM + 1) + i] = make_float2(re, im);
+    if (lane == 0) a.htot[(size_t)c * (CMAXM + 1) + i] = make_float2(re, im);
+  }
+  grid.sync();
+  // (3) w -= sum_i h_i v_i and the ||w||^2 partials on the own elements, a warp per column
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    const int c = p / (j + 1), i = p - c * (j + 1);
+    hsm[c * (CMAXM + 1) + i] = a.htot[(size_t)c * (CMAXM + 1) + i];
   }
   __syncthreads();
-  // (2) w -= sum_i h_i v_i and ||w||^2 on the own chunk, per column
-  for (int c = 0; c < a.ncol; c++) {
-    float nn = 0.f;
+  for (int c = warp; c < a.ncol; c += nwarp) {
     const float2* hp = hsm + c * (CMAXM + 1);
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    float nn = 0.f;
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
       float2 q = a.W[(size_t)c * n + e];
+#pragma unroll 4
       for (int i = 0; i <= j; i++) {
         const float2 p = a.V[(size_t)i * cn + (size_t)c * n + e];
-        const float hr = (float)hp[i].x, hi = (float)hp[i].y;
-        q.x -= hr * p.x - hi * p.y;
-        q.y -= hr * p.y + hi * p.x;
+        const float2 h = hp[i];
+        q.x -= h.x * p.x - h.y * p.y;
+        q.y -= h.x * p.y + h.y * p.x;
       }
       a.W[(size_t)c * n + e] = q;
       nn += q.x * q.x + q.y * q.y;
     }
-    const float t = cta_sum(nn, sh);
-    if (threadIdx.x == 0) a.npart[(size_t)c * G + blockIdx.x] = t;
+    nn = warp_sum(nn);
+    if (lane == 0) a.npart[(size_t)c * G + blockIdx.x] = nn;
   }
   grid.sync();
+  // (4) h_{j+1,j} per column, then v_{j+1} = w / h_{j+1,j} on the own elements (zero for a column
+  //     whose w vanished)
   for (int c = warp; c < a.ncol; c += nwarp) {
     float t = 0.f;
     for (int q = lane; q < G; q += 32) t += a.npart[(size_t)c * G + q];
@@ -1405,23 +1455,22 @@ __global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
     if (lane == 0) s_hn[c] = sqrtf(t);
   }
   __syncthreads();
-  // (3) v_{j+1} = w / h_{j+1,j} on the own chunk (zero for a column whose w vanished)
-  for (int c = 0; c < a.ncol; c++) {
+  for (int c = warp; c < a.ncol; c += nwarp) {
     const float inv = s_hn[c] > 0.f ? 1.f / s_hn[c] : 0.f;
     float2* vn = a.V + (size_t)(j + 1) * cn + (size_t)c * n;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
       float2 q = a.W[(size_t)c * n + e];
       q.x *= inv;
       q.y *= inv;
       vn[e] = q;
     }
   }
-  // (4) CTA 0: Hessenberg column j of every unfinished column, rotated by the column's previous
+  // (5) CTA 0: Hessenberg column j of every unfinished column, rotated by the column's previous
   //     Givens rotations, the new rotation, the residual estimate and the stopping test
   if (blockIdx.x != 0) return;
   for (int c = threadIdx.x; c < a.ncol; c += blockDim.x) {
     if (a.done[c]) continue;
-    float2* hcol = hsm + c * (CMAXM + 1);           // j + 2 entries: the shared row has CMAXM + 1
+    float2* hcol = hsm + c * (CMAXM + 1);
     float2* cs = a.cs + (size_t)c * CMAXM;
     float2* sn = a.sn + (size_t)c * CMAXM;
     float2* gv = a.gv + (size_t)c * (CMAXM + 1);
@@ -1431,9 +1480,9 @@ __global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
       const float2 x1 = hcol[i + 1];
       const float2 cc = cs[i], ss = sn[i];
       hcol[i] = make_float2(cc.x * x0.x + cc.y * x0.y + ss.x * x1.x + ss.y * x1.y,
-                             cc.x * x0.y - cc.y * x0.x + ss.x * x1.y - ss.y * x1.x);
+                            cc.x * x0.y - cc.y * x0.x + ss.x * x1.y - ss.y * x1.x);
       x0 = make_float2(-(ss.x * x0.x - ss.y * x0.y) + (cc.x * x1.x - cc.y * x1.y),
-                        -(ss.x * x0.y + ss.y * x0.x) + (cc.x * x1.y + cc.y * x1.x));
+                       -(ss.x * x0.y + ss.y * x0.x) + (cc.x * x1.y + cc.y * x1.x));
     }
     const float den = sqrtf(x0.x * x0.x + x0.y * x0.y + hn * hn);
     const float2 cj = den > 0.f ? make_float2(x0.x / den, x0.y / den) : make_float2(1.f, 0.f);
@@ -1448,7 +1497,7 @@ __global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
     for (int i = 0; i <= j; i++) R[i] = hcol[i];
     a.kk[c] = j + 1;
     const float res = sqrtf(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y);
-    if (res <= (float)a.rtol * a.beta[c] || !(hn > 0.f) || !(den > 0.f)) a.done[c] = 1;
+    if (res <= a.rtol * a.beta[c] || !(hn > 0.f) || !(den > 0.f)) a.done[c] = 1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1460,9 +1509,13 @@ __global__ void __launch_bounds__(256) k_bgt_arnoldi(BgtArgs a, int j) {
 
 __global__ void __launch_bounds__(256) k_bgt_finish(BgtArgs a) {
   cg::grid_group grid = cg::this_grid();
+  __shared__ float2 ys[BMAXC][CMAXM];
   const int n = a.nc * a.nd;
   const size_t cn = (size_t)a.ncol * n;
+  const BgtChunk ch(n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (blockIdx.x == 0) {
+    // back substitution R y = g, one thread per column
     for (int c = threadIdx.x; c < a.ncol; c += blockDim.x) {
       const int k = a.kk[c];
       const float2* R = a.R + (size_t)c * (CMAXM + 1) * CMAXM;
@@ -1484,17 +1537,22 @@ __global__ void __launch_bounds__(256) k_bgt_finish(BgtArgs a) {
     }
   }
   grid.sync();
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (int c = 0; c < a.ncol; c++) {
+  for (int p = threadIdx.x; p < a.ncol * CMAXM; p += blockDim.x) {
+    const int c = p / CMAXM, i = p - c * CMAXM;
+    ys[c][i] = i < a.kk[c] ? a.y[(size_t)c * CMAXM + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // x = sum_i y_i v_i on the own elements, a warp per column
+  for (int c = warp; c < a.ncol; c += nwarp) {
     const int k = a.kk[c];
-    const float2* y = a.y + (size_t)c * CMAXM;
-    for (int e = tid; e < n; e += nth) {
+    for (int e = ch.e0 + lane; e < ch.e1; e += 32) {
       float xr = 0.f, xi = 0.f;
+#pragma unroll 4
       for (int i = 0; i < k; i++) {
         const float2 v = a.V[(size_t)i * cn + (size_t)c * n + e];
-        const float yr = (float)y[i].x, yi = (float)y[i].y;
-        xr += yr * v.x - yi * v.y;
-        xi += yr * v.y + yi * v.x;
+        const float2 y = ys[c][i];
+        xr += y.x * v.x - y.y * v.y;
+        xi += y.x * v.y + y.y * v.x;
       }
       a.x[(size_t)c * n + e] = make_float2(xr, xi);
     }
@@ -1524,14 +1582,14 @@ void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const flo
   }
   const int per_sm = std::min(2, std::min(mps[0], std::min(mps[1], mps[2])));
   if (per_sm < 1) throw Error{TMG_ERR_CUDA, "tensor-core batched coarse solve: kernels cannot be resident"};
-  const int G = std::max(1, std::min((int)((n + 255) / 256), c.sms * per_sm));
+  const int G = std::max(1, std::min((int)((n + 31) / 32), c.sms * per_sm));
   const size_t hsm = sizeof(float2) * (size_t)ncol * (CMAXM + 1);
   if (hsm > 48 * 1024)
     TMG_CUDA(cudaFuncSetAttribute(k_bgt_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
   c.cw_V.alloc((m + 1) * n * ncol * sizeof(float2));
   c.cw_w.alloc(n * ncol * sizeof(float2));
-  // one state allocation: part, cs, sn, gv, R, y, npart, beta, done, kk, all_done
-  const size_t d2 = (size_t)ncol * ((CMAXM + 1) * G + 2 * CMAXM + (CMAXM + 1) + (CMAXM + 1) * CMAXM + CMAXM);
+  // one state allocation: part, cs, sn, gv, R, y, htot, npart, beta, done, kk, all_done
+  const size_t d2 = (size_t)ncol * ((CMAXM + 1) * G + 2 * CMAXM + (CMAXM + 1) + (CMAXM + 1) * CMAXM + CMAXM + (CMAXM + 1));
   const size_t bytes = sizeof(float2) * d2 + sizeof(float) * ((size_t)ncol * G + ncol) + sizeof(int) * (2 * (size_t)ncol + 1);
   c.cw_state.alloc(bytes);
   if (!c.coarse_iter_dev.p) {
@@ -1559,7 +1617,8 @@ void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const flo
   a.gv = a.sn + (size_t)ncol * CMAXM;
   a.R = a.gv + (size_t)ncol * (CMAXM + 1);
   a.y = a.R + (size_t)ncol * (CMAXM + 1) * CMAXM;
-  a.npart = reinterpret_cast<float*>(a.y + (size_t)ncol * CMAXM);
+  a.htot = a.y + (size_t)ncol * CMAXM;
+  a.npart = reinterpret_cast<float*>(a.htot + (size_t)ncol * (CMAXM + 1));
   a.beta = a.npart + (size_t)ncol * G;
   a.done = reinterpret_cast<int*>(a.beta + ncol);
   a.kk = a.done + ncol;
