@@ -270,6 +270,7 @@ def run_ours(args):
         ctx.tune(k, float(v))
     prm = tmg.Context.mg_defaults()
     prm.nv = w["nv"]
+    prm.sap_mr = w.get("sap_mr", prm.sap_mr)
     prm.prec_fine = tmg.PREC_F16 if args.fine == "f16" else tmg.PREC_F32
     prm.prec_coarse = tmg.PREC_F32
     torch.cuda.synchronize()
@@ -566,7 +567,7 @@ def workload_config(w, kappa, kinfo, args, world):
     return {"workload": w["name"], "lattice": list(w["dims"]), "kappa": kappa,
             "kappa_source": kinfo.get("source"), "sigma_min_DW": kinfo.get("sigma_min"),
             "sigma_min_lattice": kinfo.get("sigma_lattice"), "sigma_target": w["sigma_target"], "csw": w["csw"],
-            "mu": w["mu"], "levels": 2, "sap_block": list(w["block"]), "aggregate": list(w["block"]), "nv": w["nv"],
+            "mu": w["mu"], "levels": 2, "sap_block": list(w["block"]), "aggregate": list(w["block"]), "nv": w["nv"], "sap_mr": w.get("sap_mr", 4),
             "fine_precision": args.fine, "tol": w["tol"], "rhs": 1, "rhs_per_step": world, "tune": args.tune,
             "l2": "flushed (512 MB write) between steps", "parallelism": "replicas" if world > 1 else "single"}
 

@@ -87,6 +87,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// 16 consecutive TMEM columns of the warp's 32 lanes into registers, without waiting (the caller
+// issues tmem_wait_ld before reading them), so several loads can be in flight at once
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 template <int NPAD>
 __device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[NPAD]);
 
@@ -234,13 +245,20 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
 #pragma unroll
   for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
 
-  RawTile<ND, NPAD> raw;
+  // two raw tiles in registers (when they fit: up to 16 float2 per thread each): tile t + 2's global
+  // loads are issued as soon as tile t has been stored to shared memory, so each load has two
+  // tiles' worth of MMAs and TMEM reads to land; larger tiles keep one register tile, loaded one
+  // tile ahead
+  constexpr bool kTwoAhead = RawTile<ND, NPAD>::kA + RawTile<ND, NPAD>::kB <= 16;
+  RawTile<ND, NPAD> rawA, rawB;
   auto tile_site = [&](int t) { return blockIdx.x + (t / 9) * gridDim.x; };
-  if (ntiles > 0) {
-    const int s0 = tile_site(0);
-    load_tile<ND, NPAD>(raw, Dc + (size_t)(s0 * 9) * ND * ND, X, n, nbr[s0 * 9], ncol, tid);
-  }
-  for (int t = 0; t < ntiles && ok; t++) {
+  auto load_t = [&](RawTile<ND, NPAD>& r, int t) {
+    const int st = tile_site(t), dt = t % 9;
+    load_tile<ND, NPAD>(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X, n, nbr[st * 9 + dt], ncol, tid);
+  };
+  if (ntiles > 0) load_t(rawA, 0);
+  if (kTwoAhead && ntiles > 1) load_t(rawB, 1);
+  auto tile_step = [&](int t, RawTile<ND, NPAD>& raw, int tnext) {
     const int site = tile_site(t), d = t % 9;
     store_tile<ND, NPAD>(raw, Ahi, Alo, Bhi, Blo, ncol, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
@@ -265,11 +283,8 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                    : "memory");
     }
-    // the next tile's global loads overlap the MMAs of this one
-    if (t + 1 < ntiles) {
-      const int s1 = tile_site(t + 1), d1 = (t + 1) % 9;
-      load_tile<ND, NPAD>(raw, Dc + (size_t)(s1 * 9 + d1) * ND * ND, X, n, nbr[s1 * 9 + d1], ncol, tid);
-    }
+    // the loads of tile tnext go out into the registers this tile has just left
+    if (tnext < ntiles) load_t(raw, tnext);
     // the MMAs read shared memory asynchronously: thread 0 waits (bounded) for their completion,
     // then the whole CTA learns the outcome at one barrier, so every thread leaves the loop together
     if (tid == 0) {
@@ -282,13 +297,26 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && warp * 32 < 2 * ND) {
       // warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the real-embedded result), one column
-      // range per K step, and sums them in FP32 (warps above row 2 ND hold only padding)
+      // range per K step, and sums them in FP32 (warps above row 2 ND hold only padding); up to 64
+      // columns are loaded before each wait
+      constexpr int X16 = NPAD / 16, RB = 4 / X16;
 #pragma unroll
-      for (int s2 = 0; s2 < nranges; s2++) {
-        float part[NPAD];
-        tmem_load<NPAD>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s2 * NPAD), part);
+      for (int s2 = 0; s2 < nranges; s2 += RB) {
+        uint32_t r[RB * X16][16];
 #pragma unroll
-        for (int i = 0; i < NPAD; i++) acc[i] += part[i];
+        for (int q = 0; q < RB; q++)
+          if (s2 + q < nranges)
+#pragma unroll
+            for (int h = 0; h < X16; h++)
+              tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((s2 + q) * NPAD + h * 16), r[q * X16 + h]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < RB; q++)
+          if (s2 + q < nranges)
+#pragma unroll
+            for (int h = 0; h < X16; h++)
+#pragma unroll
+              for (int i = 0; i < 16; i++) acc[h * 16 + i] += __uint_as_float(r[q * X16 + h][i]);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -311,6 +339,14 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
 #pragma unroll
       for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
     }
+  };
+  if (kTwoAhead) {
+    for (int t = 0; t < ntiles && ok; t += 2) {
+      tile_step(t, rawA, t + 2);
+      if (t + 1 < ntiles && ok) tile_step(t + 1, rawB, t + 3);
+    }
+  } else {
+    for (int t = 0; t < ntiles && ok; t++) tile_step(t, rawA, t + 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
