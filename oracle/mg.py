@@ -29,10 +29,16 @@ project adopts (listed with their reasons in the design notes):
   x = 0; build P and D_c; then n_iter passes of v_j <- normalise(cycle(v_j)) with P and D_c
   rebuilt after each pass (the adaptive setup iterations of Sec. 2).
 
+* Optionally the coarse solve runs on the odd-even reduced system (not in the paper; an addition of
+  this project): with even coarse extents, S x_o = b_o - A_oe A_ee^-1 b_e with the Schur complement
+  S = A_oo - A_oe A_ee^-1 A_eo, then x_e = A_ee^-1 (b_e - A_eo x_o).
+
 Pinned by (tests/test_oracle_mg.py): P^dag P = I, G5 P = P G5_c, D_c x_c = P^dag D P x_c,
 D_c(mu) - D_c(0) = i mu G5_c, D_c^dag = G5_c D_c G5_c, the dense SAP error propagator, exact
-coarse correction with full-rank P, dense LU solutions, and the cycle's dense error propagator
-I - C D = (I - M D)^k (I - P D_c^-1 P^dag D) of Eq. 1 with exact inner solves.
+coarse correction with full-rank P, dense LU solutions, the cycle's dense error propagator
+I - C D = (I - M D)^k (I - P D_c^-1 P^dag D) of Eq. 1 with exact inner solves, and for the
+odd-even coarse solve: D_c applied to (x_o, -A_ee^-1 A_eo x_o) equals (S x_o, 0), the assembled
+dense S equals the dense block elimination, and a full-dimension cycle equals the dense solve.
 
 Parity unpinned: Hierarchy.setup.  The adaptive setup has many correct results (any test vectors
 that span the near-null space do); it is compared only through what it feeds, never by value.
@@ -299,6 +305,58 @@ def coarse_apply(Dc: CoarseOp, x, mu=0.0):
     return y + 1j * mu * coarse_gamma5(Dc.nv) * x
 
 
+def coarse_parity(Dc: CoarseOp):
+    """Parity (0 even, 1 odd) of every coarse site, from the sum of its coarse coordinates."""
+    lat = Dc.self_blk.shape[:-2]
+    if any(n % 2 for n in lat):
+        raise ValueError("odd-even splitting of the coarse lattice needs even extents")
+    return np.indices(lat).sum(axis=0) % 2
+
+
+def coarse_hops(Dc: CoarseOp, x):
+    """The nearest-neighbour part of D_c: y(a) = sum_mu [A_+mu(a) x(a+mu) + A_-mu(a) x(a-mu)]."""
+    y = np.zeros_like(x)
+    for m in range(4):
+        y += np.einsum("...kl,...l->...k", Dc.fwd[m], _cshift(x, m, +1))
+        y += np.einsum("...kl,...l->...k", Dc.bwd[m], _cshift(x, m, -1))
+    return y
+
+
+def coarse_site_term(Dc: CoarseOp, x, mu=0.0):
+    """The site-local part of D_c(mu): A_self(a) x(a) + i mu G5_c x(a)."""
+    return np.einsum("...kl,...l->...k", Dc.self_blk, x) + 1j * mu * coarse_gamma5(Dc.nv) * x
+
+
+def coarse_site_inverse(Dc: CoarseOp, mu=0.0):
+    """(A_self(a) + i mu G5_c)^-1 for every coarse site (dense inverse of each block)."""
+    nd = Dc.self_blk.shape[-1]
+    blk = Dc.self_blk + 1j * mu * np.diag(coarse_gamma5(Dc.nv)).reshape((1,) * (Dc.self_blk.ndim - 2) + (nd, nd))
+    return np.linalg.inv(blk)
+
+
+def coarse_schur_apply(Dc: CoarseOp, x, mu, inv=None):
+    """S x on the odd sites, S = A_oo - A_oe A_ee^-1 A_eo: the Schur complement of D_c(mu) after
+    eliminating the even sites (with even coarse extents every hop joins sites of opposite parity,
+    so A_ee and A_oo are the site-local blocks).  x and the result carry zeros on the even sites."""
+    par = coarse_parity(Dc)[..., None]
+    inv = coarse_site_inverse(Dc, mu) if inv is None else inv
+    t = np.einsum("...kl,...l->...k", inv, coarse_hops(Dc, x)) * (par == 0)
+    return (coarse_site_term(Dc, x, mu) - coarse_hops(Dc, t)) * (par == 1)
+
+
+def coarse_solve_eo(Dc: CoarseOp, b, mu, m, rtol):
+    """D_c(mu)^-1 b by odd-even reduction: one GMRES cycle from zero (at most m steps, stop at
+    relative residual rtol of the reduced system) on S x_o = b_o - A_oe A_ee^-1 b_e, then
+    x_e = A_ee^-1 (b_e - A_eo x_o)."""
+    par = coarse_parity(Dc)[..., None]
+    inv = coarse_site_inverse(Dc, mu)
+    te = np.einsum("...kl,...l->...k", inv, b * (par == 0))
+    rhs = (b - coarse_hops(Dc, te)) * (par == 1)
+    xo, k = krylov.gmres_fixed(lambda v: coarse_schur_apply(Dc, v, mu, inv), rhs, m, rtol)
+    xe = np.einsum("...kl,...l->...k", inv, (b - coarse_hops(Dc, xo)) * (par == 0)) * (par == 0)
+    return xo * (par == 1) + xe
+
+
 def coarse_apply_definition(U, p, clover, P, x, mu=None):
     """D_c(mu) x = P^dag D(mu) P x, straight from the definition (Sec. 1.1)."""
     return restrict(P, dirac.apply_D(U, prolong(P, x), p, mu, clover))
@@ -334,6 +392,7 @@ class MGParams:
     n_init: int = 5                   # initial SAP inverse-iteration passes
     n_iter: int = 3                   # adaptive setup iterations
     restart: int = 10                 # outer FGMRES restart length
+    coarse_eo: bool = False           # coarse solve on the odd-even reduced system (coarse_solve_eo)
 
 
 class Hierarchy:
@@ -358,6 +417,8 @@ class Hierarchy:
 
     def coarse_solve(self, c, mu=None):
         mu = self.p.mu if mu is None else mu
+        if self.mg.coarse_eo:
+            return coarse_solve_eo(self.Dc, c, mu, self.mg.coarse_m, self.mg.coarse_rtol)
         e, _ = krylov.gmres_fixed(lambda v: coarse_apply(self.Dc, v, mu), c, self.mg.coarse_m,
                                   self.mg.coarse_rtol)
         return e

@@ -246,3 +246,69 @@ def test_cycle_error_propagator_is_eq1_product():
         assert rel(got, want) < 1e-10
         for name, Wp in wrong.items():
             assert rel(Wp @ e, want) > 1e-3, name
+
+
+def _coarse_small(mu=0.07):
+    """A coarse operator on a 2^4 coarse lattice (4^4 fine lattice, 2^4 aggregates, N_v = 2)."""
+    dims, adims, nv = (4, 4, 4, 4), (2, 2, 2, 2), 2
+    U = fields.gauge_field(dims, 0.4, 71)
+    p = dirac.Params(kappa=dirac.kappa_from_m0(-0.4), csw=1.2, mu=mu, tbc=-1)
+    H = mg.Hierarchy(U, p, mg.MGParams(block=adims, agg=adims, nv=nv))
+    H.set_vectors(fields.gaussian_spinor(dims, 72, n=nv))
+    return H.Dc, mu
+
+
+def _dense_coarse(Dc, mu):
+    shp = Dc.self_blk.shape[:-1]
+    N = int(np.prod(shp))
+    A = np.zeros((N, N), dtype=complex)
+    for i in range(N):
+        e = np.zeros(N, dtype=complex)
+        e[i] = 1.0
+        A[:, i] = mg.coarse_apply(Dc, e.reshape(shp), mu).reshape(-1)
+    return A, shp
+
+
+def test_coarse_schur_complement_is_block_elimination():
+    """D_c(mu) applied to (x_o, -A_ee^-1 A_eo x_o) gives S x_o on the odd sites and zero on the even
+    ones, and the assembled S equals A_oo - A_oe A_ee^-1 A_eo of the dense operator."""
+    Dc, mu = _coarse_small()
+    par = mg.coarse_parity(Dc)[..., None]
+    rng = np.random.default_rng(73)
+    shp = Dc.self_blk.shape[:-1]
+    xo = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)) * (par == 1)
+    inv = mg.coarse_site_inverse(Dc, mu)
+    xe = -np.einsum("...kl,...l->...k", inv, mg.coarse_hops(Dc, xo)) * (par == 0)
+    y = mg.coarse_apply(Dc, xo + xe, mu)
+    assert np.abs(y * (par == 0)).max() < 1e-12 * np.abs(y).max()
+    assert rel(y * (par == 1), mg.coarse_schur_apply(Dc, xo, mu)) < 1e-13
+    A, _ = _dense_coarse(Dc, mu)
+    odd = np.broadcast_to(par == 1, shp).reshape(-1)
+    E, O = np.where(~odd)[0], np.where(odd)[0]
+    S_dense = A[np.ix_(O, O)] - A[np.ix_(O, E)] @ np.linalg.solve(A[np.ix_(E, E)], A[np.ix_(E, O)])
+    S_op = np.zeros((len(O), len(O)), dtype=complex)
+    for c, i in enumerate(O):
+        e = np.zeros(int(np.prod(shp)), dtype=complex)
+        e[i] = 1.0
+        S_op[:, c] = mg.coarse_schur_apply(Dc, e.reshape(shp), mu).reshape(-1)[O]
+    assert rel(S_op, S_dense) < 1e-12
+
+
+def test_coarse_eo_solve_full_dimension_equals_dense_solve():
+    """A reduced-system GMRES cycle as long as the odd dimension is exact: the odd-even coarse solve
+    then equals the dense solution of D_c(mu) x = b (and a short cycle is not)."""
+    Dc, mu = _coarse_small()
+    A, shp = _dense_coarse(Dc, mu)
+    rng = np.random.default_rng(74)
+    b = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    want = np.linalg.solve(A, b.reshape(-1)).reshape(shp)
+    n_odd = A.shape[0] // 2
+    assert rel(mg.coarse_solve_eo(Dc, b, mu, n_odd, 0.0), want) < 1e-9
+    assert rel(mg.coarse_solve_eo(Dc, b, mu, 3, 0.0), want) > 1e-4
+
+
+def test_coarse_parity_needs_even_extents():
+    Dc, _ = _coarse_small()
+    odd = mg.CoarseOp(Dc.self_blk[:1], Dc.fwd[:, :1], Dc.bwd[:, :1], Dc.nv)
+    with pytest.raises(ValueError):
+        mg.coarse_parity(odd)
