@@ -454,12 +454,23 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
- * the basis for up to 10 basis vectors; 0: separate kernels), "coarse_overlap" (1, the default: the coarse GMRES updates the Hessenberg
+ * the basis for up to 10 basis vectors; 0: separate kernels), "outer_gs_passes" (1, the default, or 2:
+ * classical Gram-Schmidt passes of the outer FGMRES and of the batched solve), "coarse_overlap" (1, the default: the coarse GMRES updates the Hessenberg
  * column of step j on one warp per CTA while the other warps run the stencil of step j+1; 0: the
  * update follows each step and all warps run the stencil), "batched_coarse_tc" (1, the default: the
  * two-level batched solve's coarse GMRES applies D_c to all columns at once on the tensor cores,
  * tcgen05 split TF32 as tmg_coarse_apply_multi, two launches per Arnoldi step; 0: one persistent
- * CUDA-core kernel), "eo_stage" (1, the default: the FP32 even-odd kernels copy
+ * CUDA-core kernel), "coarse_block_cache" (1, the default: each CTA of the persistent coarse GMRES
+ * copies as many of its own coarse sites' stencil blocks as fit into shared memory once per solve,
+ * with one bounded bulk copy, and reads them from there at every step; 0: every step reads the
+ * stencil from L2), "coarse_eo" (0, the default, or 1: the coarse GMRES of the single-flavour
+ * cycle solves the odd-even reduced system S x_o = b_o - A_oe A_ee^-1 b_e, S = A_oo - A_oe A_ee^-1
+ * A_eo, with per-site inverses (A_self + i mu G5_c)^-1 computed on the GPU for each twist and kept
+ * for up to 16 (twist, precision) pairs, then sets x_e = A_ee^-1 (b_e - A_eo x_o); needs even
+ * coarse extents, else the plain form runs; not a construction of the paper; the allocation-free
+ * tmg_coarse_solve_noalloc keeps the plain form), "batched_coarse_m" (0, the default: the batched
+ * solve's coarse GMRES takes at most coarse_m steps; 1..64: at most that many, e.g. when coarse_m
+ * is sized for the odd-even reduced single-column solve), "eo_stage" (1, the default: the FP32 even-odd kernels copy
  * each CTA's tile of the clover field / clover inverse into shared memory with bulk copies while
  * the neighbour loads run; 0: direct loads), "force_prec" (TMG_PREC_F64, the default: the force kernels of
  * tmg_force / tmg_force_xy / tmg_pf_force read FP64 X, Y and links; TMG_PREC_F32: they read FP32

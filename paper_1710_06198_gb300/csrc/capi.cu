@@ -841,7 +841,11 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "eo_stage" && (v == 0 || v == 1)) ctx->c.eo_stage = v;
     else if (k == "coarse_overlap" && (v == 0 || v == 1)) ctx->c.coarse_overlap = v;
     else if (k == "batched_coarse_tc" && (v == 0 || v == 1)) ctx->c.batched_tc = v;
+    else if (k == "coarse_block_cache" && (v == 0 || v == 1)) ctx->c.coarse_block_cache = v;
+    else if (k == "coarse_eo" && (v == 0 || v == 1)) ctx->c.coarse_eo = v;
+    else if (k == "batched_coarse_m" && v >= 0 && v <= 64) ctx->c.batched_coarse_m = v;
     else if (k == "outer_gs_fused" && (v == 0 || v == 1)) ctx->c.outer_gs_fused = v;
+    else if (k == "outer_gs_passes" && (v == 1 || v == 2)) ctx->c.outer_gs_passes = v;
     else if (k == "force_prec" && (v == TMG_PREC_F64 || v == TMG_PREC_F32)) ctx->c.force_prec = v;
     else if (k == "kcycle_grid" && v >= 0 && v <= 4096) ctx->c.kcycle_grid = v;
     else if (k == "cycle_graph" && (v == 0 || v == 1)) {

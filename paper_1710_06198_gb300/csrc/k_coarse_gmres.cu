@@ -50,6 +50,13 @@ struct CgArgs {
   int* counter;                      // accumulated step count
   int rows_smem;                     // 1: the own sites' stencil rows live in dynamic shared memory
                                      // (ceil(nc / grid) * nf * 9 * nd values); 0: in rows
+  int blk_cache;                     // own stencil blocks copied once per launch into dynamic shared
+  int cache_off;                     // memory (from the first own block on), at byte offset cache_off
+  int eo;                            // 1: solve the odd-even reduced system (nf = 1, even extents)
+  int cg[4];                         // coarse lattice extents (site = x + X (y + Y (z + Z t)))
+  const typename CplxT<S>::T2* inv;  // eo: per-site (A_self + i mu G5_c)^-1, [nc][nd(l)][nd(k)]
+  typename CplxT<S>::T2* te;         // eo: even-site intermediate A_ee^-1 (...) [n]
+  typename CplxT<S>::T2* rb;         // eo: reduced right-hand side [n]
   int overlap;                       // 1: the Hessenberg update of step j runs during the stencil of
                                      // step j+1 (warp 0 of every CTA); 0: after step j, all warps stencil
 };
@@ -148,6 +155,44 @@ __device__ __forceinline__ void stencil_task(const typename CplxT<S>::T2* __rest
   }
 }
 
+// One-dimensional bulk copy global -> shared memory completing on an mbarrier, and a wait on it
+// that gives up after about a second (the caller then falls back to global loads).
+__device__ __forceinline__ uint32_t gm_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void gm_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  const uint32_t b = gm_smem_addr(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(gm_smem_addr(dst)), "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+__device__ __forceinline__ bool gm_bulk_wait(uint64_t* bar) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+  for (unsigned it = 0; it < (1u << 26); it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(gm_smem_addr(bar)), "r"(0u), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+  return false;
+}
+
+// Parity of a coarse site from its coordinates (x fastest).
+__device__ __forceinline__ int coarse_site_parity(const int cg[4], int site) {
+  const int x = site % cg[0];
+  site /= cg[0];
+  const int y = site % cg[1];
+  site /= cg[1];
+  const int z = site % cg[2];
+  return (x + y + z + site / cg[2]) & 1;
+}
+
 // Precision-generic helpers of the persistent solvers: the FP32 path keeps its reductions, Givens
 // rotations and least-squares solve in FP32 (GB300 issues FP64 at a small fraction of the FP32
 // rate, and one FP64 Givens chain per step costs more than the step's stencil).
@@ -165,7 +210,7 @@ __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
 // GMRES from zero on the operator of a (any level): grid-wide phases, the caller's grid must be a
 // cooperative launch; a.x is complete after the caller's next grid barrier.
-template <typename S>
+template <typename S, bool EO = false>
 __device__ void gmres_dev(const CgArgs<S>& a) {
   using T2 = typename CplxT<S>::T2;
   using A2 = T2;   // reductions, rotations and the least-squares solve in the vectors' precision
@@ -199,11 +244,66 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   const int rows_site0 = a.rows_smem ? s0 : 0;                  // own sites only in shared memory
   const int rows_nsite = a.rows_smem ? s1 - s0 : a.nc;
 #define GM_ROW_BASE(f, site) (rows_g + ((size_t)((f) * rows_nsite + (site) - rows_site0) * 9) * a.nd)
+  // The stencil does not change during the solve: the CTA's first ncache own blocks (contiguous in
+  // Dc) are copied once into shared memory and read from there at every step; the rest come from
+  // L2.  The copy runs while the right-hand side's norm is reduced.
+  __shared__ __align__(8) uint64_t s_cache_bar;
+  __shared__ int s_cache_ok;
+  T2* const blk_sm = reinterpret_cast<T2*>(gm_dyn + a.cache_off);
+  const int ncache = min(a.blk_cache, (s1 - s0) * 9);
+  if (ncache > 0) {
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gm_smem_addr(&s_cache_bar)), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      gm_bulk_copy(blk_sm, a.Dc + (size_t)s0 * 9 * a.nd * a.nd, (uint32_t)((size_t)ncache * a.nd * a.nd * sizeof(T2)),
+                   &s_cache_bar);
+    }
+  }
 
-  // beta = ||b||
+  // ---- odd-even reduced system (a.eo, one flavour, even coarse extents): the basis and w live on
+  // the odd sites (their even entries stay zero).  GM_HOP_ROWS: hop products (blocks d = 1..8) of the
+  // own sites of parity P applied to X, scaled by SC, into those sites' rows (the first NCACHED own
+  // blocks from shared memory); GM_INV_TASKS: per own even site, OUT = A_ee^-1 IN.
+#define GM_HOP_ROWS(P, X, SC, W0, NW, NCACHED)                                                        \
+  for (int t = (W0); t < (s1 - s0) * 8; t += (NW)) {                                                 \
+    const int site = s0 + t / 8, d = 1 + (t & 7);                                                    \
+    if (coarse_site_parity(a.cg, site) != (P)) continue;                                             \
+    const int t9 = site * 9 + d, lb = t9 - s0 * 9;                                                   \
+    const T2* blk = lb < (NCACHED) ? blk_sm + (size_t)lb * a.nd * a.nd : a.Dc + (size_t)t9 * a.nd * a.nd; \
+    stencil_task<S>(blk, (X) + (size_t)a.nbr[t9] * a.nd, a.nd, (SC), nullptr, (S)0, (S)0,            \
+                    GM_ROW_BASE(0, site) + (size_t)d * a.nd, lane);                                  \
+  }
+#define GM_INV_TASKS(IN, OUT)                                                                        \
+  for (int t = warp; t < s1 - s0; t += nwarp) {                                                      \
+    const int site = s0 + t;                                                                         \
+    if (coarse_site_parity(a.cg, site) != 0) continue;                                               \
+    stencil_task<S>(a.inv + (size_t)site * a.nd * a.nd, (IN), a.nd, (S)1, nullptr, (S)0, (S)0, (OUT), lane); \
+  }
+  const T2* bsrc = a.b;
+  if (EO) {
+    // reduced right-hand side r_o = b_o - A_oe A_ee^-1 b_e
+    GM_INV_TASKS(a.b + (size_t)site * a.nd, a.te + (size_t)site * a.nd);
+    grid.sync();                                     // A_ee^-1 b_e complete
+    GM_HOP_ROWS(1, a.te, (S)-1, warp, nwarp, 0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nown; t += blockDim.x) {
+      const int e = GM_OWN_E(t), site = e / a.nd, k = e - site * a.nd;
+      T2 o = mk2<S>(0, 0);
+      if (coarse_site_parity(a.cg, site) == 1) {
+        o = a.b[e];
+        const T2* rw = GM_ROW_BASE(0, site) + k;
+        for (int d = 1; d < 9; d++) { const T2 r = rw[(size_t)d * a.nd]; o.x += r.x; o.y += r.y; }
+      }
+      a.rb[e] = o;
+    }
+    grid.sync();                                     // r_o complete
+    bsrc = a.rb;
+  }
+
+  // beta = ||b|| (of the reduced right-hand side for the odd-even system)
   {
     S nn = 0;
-    for (int e = tid; e < n; e += nth) { const T2 v = a.b[e]; nn += v.x * v.x + v.y * v.y; }
+    for (int e = tid; e < n; e += nth) { const T2 v = bsrc[e]; nn += v.x * v.x + v.y * v.y; }
     const S t = cta_sum((S)nn, sh);
     if (threadIdx.x == 0) npart[blockIdx.x] = t;
   }
@@ -225,7 +325,7 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   __syncthreads();
   {
     const S inv = s_beta > (S)0 ? (S)1 / s_beta : (S)0;
-    for (int e = tid; e < n; e += nth) { T2 v = a.b[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
+    for (int e = tid; e < n; e += nth) { T2 v = bsrc[e]; v.x *= inv; v.y *= inv; a.V[e] = v; }
   }
   grid.sync();                                       // v_0 complete
   // Hessenberg column j: previous rotations [[conj c, conj s], [-s, c]] applied down the new column
@@ -271,6 +371,12 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
   const bool ovl = a.overlap != 0;
   const int swarp = ovl ? warp - 1 : warp, snwarp = ovl ? nwarp - 1 : nwarp;
   const int ntask = a.nf * (s1 - s0) * 9;
+  int cached = 0;                                    // own blocks readable from shared memory
+  if (ncache > 0) {
+    if (threadIdx.x == 0) s_cache_ok = gm_bulk_wait(&s_cache_bar) ? 1 : 0;
+    __syncthreads();
+    cached = s_cache_ok ? ncache : 0;
+  }
   // s_done is read only right after a barrier (or before the loop, where it is settled): the
   // thread that updates the Hessenberg column may set it while other warps are still starting a
   // step.  Every CTA sets it from the same reduced values, so all take the same grid barriers.
@@ -283,30 +389,69 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     T2* wj = a.w + (size_t)(j & 1) * n;
     const S scale = j == 0 ? (S)1 : (S)1 / s_hn;
     T2* vj = a.V + (size_t)j * n;
-    if (ovl && warp == 0) {
-      if (lane == 0 && j > 0) hessenberg_update(j - 1);
-    } else {
-      // (1) stencil products of the own sites, one warp per (flavour, site, stencil block): lanes
-      //     are rows, so every column of a block is one coalesced read.  The doublet's flavour
-      //     mixing is added to the self block's row.
-      for (int t = swarp; t < ntask; t += snwarp) {
-        const int f = t / ((s1 - s0) * 9);
-        const int t9 = s0 * 9 + (t - f * (s1 - s0) * 9);
-        const int site = t9 / 9;
-        const T2* blk = a.Dc + (size_t)t9 * a.nd * a.nd;
-        const T2* xv = src + (size_t)f * n1 + (size_t)a.nbr[t9] * a.nd;
-        const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
-        stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.delta,
-                        GM_ROW_BASE(f, site) + (size_t)(t9 - site * 9) * a.nd, lane);
+    if (EO) {
+      // (1a) t_e = A_ee^-1 A_eo src on the own even sites (unscaled: the scale enters in 1b)
+      if (ovl && warp == 0) {
+        if (lane == 0 && j > 0) hessenberg_update(j - 1);
+      } else {
+        GM_HOP_ROWS(0, src, (S)1, swarp, snwarp, cached);
       }
+      __syncthreads();                               // own rows and the previous column complete
+      if (s_done) break;                             // the previous step met the stopping test
+      for (int t = threadIdx.x; t < nown; t += blockDim.x) {
+        const int e = GM_OWN_E(t), site = e / a.nd, k = e - site * a.nd;
+        if (coarse_site_parity(a.cg, site) != 0) continue;
+        T2* rw = GM_ROW_BASE(0, site) + k;
+        S ar = 0, ai = 0;
+        for (int d = 1; d < 9; d++) { const T2 r = rw[(size_t)d * a.nd]; ar += r.x; ai += r.y; }
+        rw[0] = mk2<S>(ar, ai);                      // slot 0 of an even site: the input of A_ee^-1
+      }
+      __syncthreads();
+      GM_INV_TASKS(GM_ROW_BASE(0, site), a.te + (size_t)site * a.nd);
+      grid.sync();                                   // t_e complete
+      // (1b) rows of w_o = A_oo v_o - A_oe t_e on the own odd sites, v = scale * src
+      for (int t = warp; t < (s1 - s0) * 9; t += nwarp) {
+        const int site = s0 + t / 9, d = t - (t / 9) * 9;
+        if (coarse_site_parity(a.cg, site) != 1) continue;
+        const int t9 = site * 9 + d, lb = t9 - s0 * 9;
+        const T2* blk = lb < cached ? blk_sm + (size_t)lb * a.nd * a.nd : a.Dc + (size_t)t9 * a.nd * a.nd;
+        const T2* xv = d == 0 ? src + (size_t)site * a.nd : a.te + (size_t)a.nbr[t9] * a.nd;
+        stencil_task<S>(blk, xv, a.nd, d == 0 ? scale : -scale, nullptr, (S)0, (S)0,
+                        GM_ROW_BASE(0, site) + (size_t)d * a.nd, lane);
+      }
+      __syncthreads();
+    } else {
+      if (ovl && warp == 0) {
+        if (lane == 0 && j > 0) hessenberg_update(j - 1);
+      } else {
+        // (1) stencil products of the own sites, one warp per (flavour, site, stencil block): lanes
+        //     are rows, so every column of a block is one coalesced read.  The doublet's flavour
+        //     mixing is added to the self block's row.
+        for (int t = swarp; t < ntask; t += snwarp) {
+          const int f = t / ((s1 - s0) * 9);
+          const int t9 = s0 * 9 + (t - f * (s1 - s0) * 9);
+          const int site = t9 / 9;
+          const int lb = t9 - s0 * 9;                // own block index
+          const T2* blk = lb < cached ? blk_sm + (size_t)lb * a.nd * a.nd : a.Dc + (size_t)t9 * a.nd * a.nd;
+          const T2* xv = src + (size_t)f * n1 + (size_t)a.nbr[t9] * a.nd;
+          const T2* xo = (a.nf == 2 && t9 == site * 9) ? src + (size_t)(1 - f) * n1 + (size_t)site * a.nd : nullptr;
+          stencil_task<S>(blk, xv, a.nd, scale, xo, a.epsbar, a.delta,
+                          GM_ROW_BASE(f, site) + (size_t)(t9 - site * 9) * a.nd, lane);
+        }
+      }
+      __syncthreads();                               // own rows and the previous column complete
+      if (s_done) break;                             // the previous step met the stopping test
     }
-    __syncthreads();                                 // own rows and the previous column complete
-    if (s_done) break;                               // the previous step met the stopping test
     // (2) own elements: v_j, w = sum of the 9 partial rows + twist, then <v_i, w> partials
     for (int t = threadIdx.x; t < nown; t += blockDim.x) {
       const int e = GM_OWN_E(t);
       const int f = e / n1, e1f = e - f * n1;
       const int site = e1f / a.nd, k = e1f - site * a.nd;
+      if (EO && coarse_site_parity(a.cg, site) == 0) {   // reduced system: even entries stay zero
+        if (j > 0) vj[e] = mk2<S>(0, 0);
+        wj[e] = mk2<S>(0, 0);
+        continue;
+      }
       T2 xs = src[e];
       xs.x *= scale;
       xs.y *= scale;
@@ -431,14 +576,35 @@ __device__ void gmres_dev(const CgArgs<S>& a) {
     o.y = xi;
     a.x[e] = o;
   }
+  if (EO) {
+    // x_e = A_ee^-1 (b_e - A_eo x_o) on the own even sites (the loop above left x_e = 0)
+    grid.sync();                                     // x_o complete
+    GM_HOP_ROWS(0, a.x, (S)-1, warp, nwarp, cached);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nown; t += blockDim.x) {
+      const int e = GM_OWN_E(t), site = e / a.nd, k = e - site * a.nd;
+      if (coarse_site_parity(a.cg, site) != 0) continue;
+      T2* rw = GM_ROW_BASE(0, site) + k;
+      T2 o = a.b[e];
+      for (int d = 1; d < 9; d++) { const T2 r = rw[(size_t)d * a.nd]; o.x += r.x; o.y += r.y; }
+      rw[0] = o;
+    }
+    __syncthreads();
+    GM_INV_TASKS(GM_ROW_BASE(0, site), a.x + (size_t)site * a.nd);
+  }
+  // a copy that missed its deadline must still land before the CTA's shared memory goes away
+  if (ncache > 0 && !cached && threadIdx.x == 0) gm_bulk_wait(&s_cache_bar);
 }
 
 #undef GM_OWN_E
 #undef GM_ROW_BASE
+#undef GM_HOP_ROWS
+#undef GM_INV_TASKS
 
 template <typename S>
 __global__ void __launch_bounds__(256, 2) k_coarse_gmres(CgArgs<S> a) {
-  gmres_dev(a);
+  if (a.eo) gmres_dev<S, true>(a);
+  else gmres_dev<S, false>(a);
 }
 
 // ---- third level: the level-1 K-cycle as one persistent cooperative kernel.
@@ -1060,6 +1226,123 @@ __global__ void __launch_bounds__(256) k_coarse_gmres_batched(CgbArgs a) {
 // CTAs of the persistent coarse GMRES: the "coarse_grid" knob if set, else "coarse_ctas_per_sm" per
 // SM (at most one CTA per coarse site), both capped by the kernel's residency.  The allocating and
 // the allocation-free launch both size their grid here, so they reduce in the same order.
+// (A_self(a) + i mu G5_c)^-1 for every coarse site a, by Gauss-Jordan elimination with partial
+// pivoting on the augmented matrix [A | I] in shared memory, one CTA per site; the result is stored
+// like a stencil block (element (k, l) at l * nd + k).
+template <typename S>
+__global__ void __launch_bounds__(256) k_coarse_site_inverse(int nd, int nv, const typename CplxT<S>::T2* __restrict__ Dc,
+                                                             S mu, typename CplxT<S>::T2* __restrict__ inv) {
+  using T2 = typename CplxT<S>::T2;
+  extern __shared__ __align__(16) unsigned char sinv_raw[];
+  T2* const m = reinterpret_cast<T2*>(sinv_raw);   // [nd][2 nd], row-major
+  T2* const fac = m + (size_t)nd * 2 * nd;          // [nd] elimination factors of the current column
+  __shared__ int s_piv;
+  const int w2 = 2 * nd;
+  const T2* blk = Dc + (size_t)blockIdx.x * 9 * nd * nd;   // slot 0: the site's own block
+  for (int q = threadIdx.x; q < nd * w2; q += blockDim.x) {
+    const int r = q / w2, cc = q - r * w2;
+    T2 v = mk2<S>(0, 0);
+    if (cc < nd) {
+      v = blk[(size_t)cc * nd + r];
+      if (cc == r) v.y += r < nv ? mu : -mu;
+    } else if (cc - nd == r) {
+      v = mk2<S>(1, 0);
+    }
+    m[q] = v;
+  }
+  __syncthreads();
+  for (int p = 0; p < nd; p++) {
+    if (threadIdx.x == 0) {
+      int best = p;
+      S bv = m[(size_t)p * w2 + p].x * m[(size_t)p * w2 + p].x + m[(size_t)p * w2 + p].y * m[(size_t)p * w2 + p].y;
+      for (int r = p + 1; r < nd; r++) {
+        const T2 v = m[(size_t)r * w2 + p];
+        const S a2 = v.x * v.x + v.y * v.y;
+        if (a2 > bv) { bv = a2; best = r; }
+      }
+      s_piv = best;
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != p)
+      for (int cc = threadIdx.x; cc < w2; cc += blockDim.x) {
+        const T2 t = m[(size_t)p * w2 + cc];
+        m[(size_t)p * w2 + cc] = m[(size_t)pr * w2 + cc];
+        m[(size_t)pr * w2 + cc] = t;
+      }
+    __syncthreads();
+    const T2 d = m[(size_t)p * w2 + p];
+    const S dn = d.x * d.x + d.y * d.y;
+    const T2 di = mk2<S>(d.x / dn, -d.y / dn);
+    for (int r = threadIdx.x; r < nd; r += blockDim.x) fac[r] = m[(size_t)r * w2 + p];
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < w2; cc += blockDim.x) {
+      const T2 v = m[(size_t)p * w2 + cc];
+      m[(size_t)p * w2 + cc] = mk2<S>(v.x * di.x - v.y * di.y, v.x * di.y + v.y * di.x);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nd * w2; q += blockDim.x) {
+      const int r = q / w2, cc = q - r * w2;
+      if (r == p) continue;
+      const T2 f = fac[r], v = m[(size_t)p * w2 + cc];
+      T2 o = m[q];
+      o.x -= f.x * v.x - f.y * v.y;
+      o.y -= f.x * v.y + f.y * v.x;
+      m[q] = o;
+    }
+    __syncthreads();
+  }
+  T2* out = inv + (size_t)blockIdx.x * nd * nd;
+  for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) {
+    const int l = q / nd, k = q - l * nd;          // column l, row k
+    out[q] = m[(size_t)k * w2 + nd + l];
+  }
+}
+
+// The per-site inverses for mu in precision S, computed on first use and kept in one of the
+// context's slots (least recently used slot reused; the cycle graphs, which may point at it, are
+// dropped when a used slot is overwritten).
+template <typename S>
+const typename CplxT<S>::T2* site_inverse(Ctx& c, double mu) {
+  using T2 = typename CplxT<S>::T2;
+  const int prec = sizeof(S) == 8 ? TMG_PREC_F64 : TMG_PREC_F32;
+  SiteInverse* pick = nullptr;
+  for (auto& e : c.site_inv)
+    if (e.used && e.mu == mu && e.prec == prec && e.version == c.cl.version) {
+      e.stamp = ++c.site_inv_clock;
+      return e.buf.as<T2>();
+    }
+  for (auto& e : c.site_inv)
+    if (!pick || !e.used || (pick->used && e.stamp < pick->stamp)) {
+      pick = &e;
+      if (!e.used) break;
+    }
+  if (pick->used) c.graphs.clear();
+  const int nd = c.cl.nd;
+  pick->buf.alloc((size_t)c.cl.nc * nd * nd * sizeof(T2));
+  const size_t smem = sizeof(T2) * ((size_t)nd * 2 * nd + nd);
+  if (smem > 48 * 1024)
+    TMG_CUDA(cudaFuncSetAttribute(k_coarse_site_inverse<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const T2* Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
+  ++c.launches;
+  k_coarse_site_inverse<S><<<c.cl.nc, 256, smem, c.stream>>>(nd, c.cl.nv, Dc, (S)mu, pick->buf.as<T2>());
+  TMG_CHECK_LAUNCH();
+  pick->used = true;
+  pick->mu = mu;
+  pick->prec = prec;
+  pick->version = c.cl.version;
+  pick->stamp = ++c.site_inv_clock;
+  return pick->buf.as<T2>();
+}
+
+// Whether the odd-even coarse solve applies: asked for, one flavour, every coarse extent even.
+inline bool coarse_eo_on(const Ctx& c, int nf) {
+  if (!c.coarse_eo || nf != 1) return false;
+  for (int mu = 0; mu < 4; mu++)
+    if (c.cl.cgeom[mu] % 2) return false;
+  return true;
+}
+
 template <typename S>
 int coarse_grid_ctas(Ctx& c) {
   static int max_per_sm[2] = {-1, -1};
@@ -1087,6 +1370,36 @@ size_t rows_smem_bytes(Ctx& c, int G, int nf) {
   return (size_t)cached_mps[t] * c.sms >= (size_t)G ? per_cta : 0;
 }
 
+// Shared-memory layout of a coarse GMRES launch of G CTAs: the own sites' stencil rows (when they
+// fit), then as many of the own stencil blocks as the CTAs that share an SM leave room for.
+template <typename S>
+size_t coarse_smem_layout(Ctx& c, int G, int nf, CgArgs<S>& a) {
+  using T2 = typename CplxT<S>::T2;
+  const size_t rows = rows_smem_bytes<S>(c, G, nf);
+  auto al = [](size_t v) { return (v + 127) & ~(size_t)127; };
+  a.rows_smem = rows > 0;
+  a.blk_cache = 0;
+  const int per_sm = (G + c.sms - 1) / c.sms;
+  static int cached_per_sm[2] = {-1, -1};
+  static size_t cached_avail[2] = {0, 0};
+  const int t = sizeof(S) == 8;
+  if (cached_per_sm[t] != per_sm) {
+    size_t avail = 0;
+    TMG_CUDA(cudaOccupancyAvailableDynamicSMemPerBlock(&avail, k_coarse_gmres<S>, per_sm, 256));
+    cached_avail[t] = avail;
+    cached_per_sm[t] = per_sm;
+    TMG_CUDA(cudaFuncSetAttribute(k_coarse_gmres<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail));
+  }
+  const size_t avail = cached_avail[t];
+  const size_t off = al(rows);
+  a.cache_off = (int)off;
+  const size_t blk_bytes = (size_t)c.cl.nd * c.cl.nd * sizeof(T2);
+  if (!c.coarse_block_cache || avail <= off + blk_bytes) return rows;
+  const int own_max = ((c.cl.nc + G - 1) / G) * 9;
+  a.blk_cache = (int)std::min<size_t>((size_t)own_max, (avail - off) / blk_bytes);
+  return off + (size_t)a.blk_cache * blk_bytes;
+}
+
 template <typename S>
 void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 1, double epsbar = 0.0) {
   using T2 = typename CplxT<S>::T2;
@@ -1094,7 +1407,7 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   const size_t n = (size_t)nf * c.cl.nc * c.cl.nd;
   const int G = coarse_grid_ctas<S>(c);
   c.cw_V.alloc((m + 1) * n * sizeof(T2));
-  c.cw_w.alloc(11 * n * sizeof(T2));
+  c.cw_w.alloc(13 * n * sizeof(T2));   // w (two buffers), 9 rows, odd-even intermediate and right-hand side
   c.cw_part.alloc(sizeof(double2) * ((size_t)2 * (CMAXM + 1) * G + (CMAXM + 1) * CMAXM + CMAXM) + sizeof(double) * G);
   if (!c.coarse_iter_dev.p) {
     c.coarse_iter_dev.alloc(sizeof(int));
@@ -1109,8 +1422,7 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   a.epsbar = (S)epsbar;
   a.delta = nf == 2 ? (S)c.ndshift : (S)0;
   a.overlap = c.coarse_overlap;
-  const size_t smem = rows_smem_bytes<S>(c, G, nf);
-  a.rows_smem = smem > 0;
+  const size_t smem = coarse_smem_layout<S>(c, G, nf, a);
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1119,6 +1431,11 @@ void launch(Ctx& c, const void* b, void* x, double mu, const void* Dc, int nf = 
   a.V = c.cw_V.as<T2>();
   a.w = c.cw_w.as<T2>();
   a.rows = a.w + 2 * n;
+  a.te = a.w + 11 * n;
+  a.rb = a.w + 12 * n;
+  a.eo = coarse_eo_on(c, nf);
+  for (int q = 0; q < 4; q++) a.cg[q] = c.cl.cgeom[q];
+  a.inv = a.eo ? site_inverse<S>(c, mu) : nullptr;
   a.mu = (S)mu;
   a.rtol = c.mg.coarse_rtol;
   a.part = c.cw_part.as<double2>();
@@ -1165,8 +1482,7 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.epsbar = (S)0;
   a.delta = (S)0;
   a.overlap = c.coarse_overlap;
-  const size_t smem = rows_smem_bytes<S>(c, G, 1);
-  a.rows_smem = smem > 0;
+  const size_t smem = coarse_smem_layout<S>(c, G, 1, a);
   a.passes = c.coarse_gs_passes > 0 ? c.coarse_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   a.Dc = (const T2*)Dc;
   a.nbr = c.cl.nbr.as<int>();
@@ -1175,6 +1491,10 @@ void launch_on(Ctx& c, const void* b, void* x, double mu, const void* Dc, char* 
   a.V = (T2*)(scratch + off[0]);
   a.w = (T2*)(scratch + off[1]);
   a.rows = a.w + 2 * (size_t)c.cl.nc * c.cl.nd;
+  a.eo = 0;                          // the allocation-free call keeps the plain form
+  for (int q = 0; q < 4; q++) a.cg[q] = c.cl.cgeom[q];
+  a.inv = nullptr;
+  a.te = a.rb = nullptr;
   a.part = (double2*)(scratch + off[2]);
   a.R = (double2*)(scratch + off[3]);
   a.y = (double2*)(scratch + off[4]);
@@ -1203,7 +1523,7 @@ void coarse_gmres_on_scratch(Ctx& c, int cp, const void* b, void* x, double mu, 
 
 void coarse_gmres_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
   ProfScope ps(c, PK_COARSE_SOLVE);
-  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const int m = std::min(c.batched_coarse_m > 0 ? c.batched_coarse_m : c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)c.cl.nc * c.cl.nd;
   const size_t smem = sizeof(float2) * (size_t)ncol * (5 * CMAXM + 4);
   if (smem > 48 * 1024)
@@ -1571,7 +1891,7 @@ bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol) {
 void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
   ProfScope ps(c, PK_COARSE_SOLVE);
   if (!coarse_gmres_batched_tc_ok(c, ncol)) throw Error{TMG_ERR_ARG, "tensor-core batched coarse solve: unsupported shape"};
-  const int m = std::min(c.mg.coarse_m, CMAXM);
+  const int m = std::min(c.batched_coarse_m > 0 ? c.batched_coarse_m : c.mg.coarse_m, CMAXM);
   const size_t n = (size_t)c.cl.nc * c.cl.nd;
   static int mps[3] = {-1, -1, -1};
   if (mps[0] < 0) {
@@ -1696,6 +2016,11 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   s.delta = nf == 2 ? (S)c.ndshift : (S)0;
   s.overlap = c.coarse_overlap;
   s.rows_smem = 0;
+  s.blk_cache = 0;
+  s.cache_off = 0;
+  s.eo = 0;
+  s.inv = nullptr;
+  s.te = s.rb = nullptr;
   s.passes = passes;
   s.Dc = (const T2*)(sizeof(S) == 8 ? c.cl.Dc64.p : c.cl.Dc32.p);
   s.nbr = c.cl.nbr.as<int>();
@@ -1721,6 +2046,11 @@ void kcycle_launch(Ctx& c, const void* b, void* x, double mu, int mode, int nf, 
   l.delta = nf == 2 ? (S)c.ndshift : (S)0;
   l.overlap = c.coarse_overlap;
   l.rows_smem = 0;
+  l.blk_cache = 0;
+  l.cache_off = 0;
+  l.eo = 0;
+  l.inv = nullptr;
+  l.te = l.rb = nullptr;
   l.passes = passes;
   l.Dc = (const T2*)(sizeof(S) == 8 ? c.cl2.Dc64.p : c.cl2.Dc32.p);
   l.nbr = c.cl2.nbr.as<int>();

@@ -135,19 +135,28 @@ struct RawTile {
   float2 b[kB];
 };
 
+// Element assignment shared by load_tile and store_tile: chunk q * 4 + warp of a tile is one 8 x 4
+// patch (8 rows of the result, 4 consecutive K) and lane L takes element (L / 4, L % 4) of it, so
+// each warp-wide shared-memory store fills one 128-byte core matrix (no bank conflicts).
 template <int ND, int NPAD>
 __device__ __forceinline__ void load_tile(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ X,
                                           size_t n, int nbr_site, int ncol, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
   for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
-    const int i = q * 128 + tid;
-    if (i < ND * ND) t.a[q] = blk[i];
+    const int ch = q * 4 + warp;                   // patch of the block: rows kb*8.., columns lb*4..
+    if (ch < ND * ND / 32) {
+      const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
+      t.a[q] = blk[(size_t)l * ND + k];
+    }
   }
 #pragma unroll
   for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
-    const int i = q * 128 + tid;
-    const int col = i / ND, l = i - col * ND;
-    if (col < ncol) t.b[q] = X[(size_t)col * n + (size_t)nbr_site * ND + l];
+    const int ch = q * 4 + warp;                   // patch of the columns: col cb*8.., entries lb*4..
+    if (ch < NPAD * ND / 32) {
+      const int col = (ch % (NPAD / 8)) * 8 + (lane >> 2), l = (ch / (NPAD / 8)) * 4 + (lane & 3);
+      if (col < ncol) t.b[q] = X[(size_t)col * n + (size_t)nbr_site * ND + l];
+    }
   }
 }
 
@@ -155,12 +164,13 @@ template <int ND, int NPAD>
 __device__ __forceinline__ void store_tile(const RawTile<ND, NPAD>& t, float* Ahi, float* Alo, float* Bhi, float* Blo, int ncol,
                                            int tid) {
   constexpr int KP = ((2 * ND + 7) / 8) * 8;
+  const int warp = tid >> 5, lane = tid & 31;
   // A real embedding: row r < ND -> (Re, -Im); row ND + r -> (Im, Re)
 #pragma unroll
   for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
-    const int i = q * 128 + tid;
-    if (i < ND * ND) {
-      const int l = i / ND, k = i - l * ND;
+    const int ch = q * 4 + warp;
+    if (ch < ND * ND / 32) {
+      const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
       const float2 z = t.a[q];
       const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
       const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
@@ -179,16 +189,18 @@ __device__ __forceinline__ void store_tile(const RawTile<ND, NPAD>& t, float* Ah
   // B: column vectors of the neighbour (NPAD rows of K-major data)
 #pragma unroll
   for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
-    const int i = q * 128 + tid;
-    const int col = i / ND, l = i - col * ND;
-    if (col < ncol) {
-      const float2 z = t.b[q];
-      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
-      const int o0 = core_off(col, l, KP), o1 = core_off(col, ND + l, KP);
-      Bhi[o0] = re_h;
-      Bhi[o1] = im_h;
-      Blo[o0] = tf32_round(z.x - re_h);
-      Blo[o1] = tf32_round(z.y - im_h);
+    const int ch = q * 4 + warp;
+    if (ch < NPAD * ND / 32) {
+      const int col = (ch % (NPAD / 8)) * 8 + (lane >> 2), l = (ch / (NPAD / 8)) * 4 + (lane & 3);
+      if (col < ncol) {
+        const float2 z = t.b[q];
+        const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+        const int o0 = core_off(col, l, KP), o1 = core_off(col, ND + l, KP);
+        Bhi[o0] = re_h;
+        Bhi[o1] = im_h;
+        Blo[o0] = tf32_round(z.x - re_h);
+        Blo[o1] = tf32_round(z.y - im_h);
+      }
     }
   }
 }

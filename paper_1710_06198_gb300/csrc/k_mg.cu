@@ -719,6 +719,7 @@ __global__ void k_copy_convert(const A2* __restrict__ a, B2* __restrict__ b, siz
 
 void build_coarse(Ctx& c) {
   const int nd = c.cl.nd;
+  ++c.cl.version;                    // per-site inverses of the old stencil are stale
   {
     std::vector<int> nb((size_t)c.g.nblk * 9);
     for (int a = 0; a < c.g.nblk; a++) {

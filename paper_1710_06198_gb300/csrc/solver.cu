@@ -370,7 +370,9 @@ static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, c
                                        (unsigned long long)c.mg.sap_mr, (unsigned long long)c.mg.coarse_m, d(c.mg.coarse_rtol),
                                        (unsigned long long)c.coarse_ctas_per_sm, (unsigned long long)c.coarse_gs_passes,
                                        (unsigned long long)c.kcycle_ctas_per_sm, (unsigned long long)c.coarse_grid,
-                                       (unsigned long long)c.kcycle_grid, (unsigned long long)c.coarse_overlap, (unsigned long long)c.l2p.smooth_m,
+                                       (unsigned long long)c.kcycle_grid, (unsigned long long)c.coarse_overlap,
+                                       (unsigned long long)c.coarse_block_cache, (unsigned long long)c.coarse_eo,
+                                       (unsigned long long)(c.coarse_eo ? c.cl.version : 0), (unsigned long long)c.l2p.smooth_m,
                                        (unsigned long long)c.l2p.k_restart, d(c.l2p.k_rtol), (unsigned long long)c.l2p.coarse_m,
                                        d(c.l2p.coarse_rtol)};
   for (int i = 0; i < 3; i++) {
@@ -726,11 +728,14 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
     cycle_run(c, pf, pc, vj, zj, mu, nf);
     if (nf == 2) dslash_nd(c, op, c.fw_w.p, zj);
     else dslash(c, op, c.fw_w.p, zj, nullptr, mu, 0, 0);
-    std::vector<double2> hc(j + 1), hc2(j + 1);
+    std::vector<double2> hc(j + 1), hc2(j + 1, make_double2(0.0, 0.0));
     std::vector<double2> nn_parts(NPART);
+    // classical Gram-Schmidt, two passes (the second restores the orthogonality the first loses in
+    // FP32), or one pass when outer_gs_passes = 1
+    const int npass = c.outer_gs_passes == 1 ? 1 : 2;
     dispatch(sp, [&](auto tag) {
       using T2 = decltype(tag);
-      if (c.outer_gs_fused && j + 1 <= FUSED_MAX) {
+      if (npass == 2 && c.outer_gs_fused && j + 1 <= FUSED_MAX) {
         // classical Gram-Schmidt, two passes, with pass 1's update and pass 2's dots in one sweep
         ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
         ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev, nullptr);
@@ -740,17 +745,18 @@ static void fgmres_cycle(Ctx& c, int sp, int op, int pf, int pc, const void* r, 
                                                    part + NPART * (MAXM + 1), nullptr);
         TMG_CHECK_LAUNCH();
       } else {
-        for (int pass = 0; pass < 2; pass++) {
+        for (int pass = 0; pass < npass; pass++) {
           ++c.launches, k_mdot_partial<T2><<<dim3(rg, j + 1), 256, 0, c.stream>>>((const T2*)V, n, (const T2*)c.fw_w.p, n, part, nullptr);
           ++c.launches, k_mdot_final<<<j + 1, 256, 0, c.stream>>>(part, rg, j + 1, hdev + pass * (MAXM + 1), nullptr);
           ++c.launches, k_mgs_update<T2><<<rg, 256, 0, c.stream>>>((const T2*)V, n, j + 1, hdev + pass * (MAXM + 1), (T2*)c.fw_w.p, n,
-                                                     pass == 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
+                                                     pass == npass - 1 ? part + NPART * (MAXM + 1) : nullptr, nullptr);
           TMG_CHECK_LAUNCH();
         }
       }
     });
     TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
-    TMG_CUDA(cudaMemcpyAsync(hc2.data(), hdev + (MAXM + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
+    if (npass == 2)
+      TMG_CUDA(cudaMemcpyAsync(hc2.data(), hdev + (MAXM + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaMemcpyAsync(nn_parts.data(), part + NPART * (MAXM + 1), sizeof(double2) * rg, cudaMemcpyDeviceToHost, c.stream));
     TMG_CUDA(cudaStreamSynchronize(c.stream));
     double nn = 0.0;
@@ -1260,6 +1266,7 @@ static void batched_cycle_run(Ctx& c, int pf, int ncol, const void* v, void* z, 
     k.push_back(0xBA7C4ull);
     k.push_back((unsigned long long)ncol);
     k.push_back((unsigned long long)c.batched_tc);
+    k.push_back((unsigned long long)c.batched_coarse_m);
     k.push_back(u(cr));
     k.push_back(u(ce));
     k.push_back(u(mu_dev));
@@ -1403,18 +1410,20 @@ int solve_batched(Ctx& c, int ncol, const void* b64, void* x64, const double* mu
       // z = M v (one batched cycle, replayed as a graph)
       batched_cycle_run(c, pf, ncol, vj, zj, cr.p, ce.p, mu_dev.as<float>(), mu);
       dslash_mrhs(c, pf, ncol, w.p, zj, nullptr, mu_dev.as<float>(), 0);
-      for (int pass = 0; pass < 2; pass++) {
+      const int npass = c.outer_gs_passes == 1 ? 1 : 2;   // classical Gram-Schmidt passes
+      for (int pass = 0; pass < npass; pass++) {
         ++c.launches, k_mdot_partial_b<<<dim3(rg, it + 1, ncol), 256, 0, c.stream>>>(Vp, istride, w.as<float2>(), n, part.as<double2>());
         ++c.launches, k_mdot_final_b<<<dim3(it + 1, ncol), 256, 0, c.stream>>>(part.as<double2>(), rg,
                                                                                hdev.as<double2>() + (size_t)pass * ncol * (MAXM + 1));
         ++c.launches, k_mgs_update_b<<<dim3(rg, ncol), 256, 0, c.stream>>>(Vp, istride, it + 1,
                                                                             hdev.as<double2>() + (size_t)pass * ncol * (MAXM + 1),
-                                                                            w.as<float2>(), n, pass == 1 ? npart.as<double>() : nullptr);
+                                                                            w.as<float2>(), n, pass == npass - 1 ? npart.as<double>() : nullptr);
         TMG_CHECK_LAUNCH();
       }
-      std::vector<double2> hc((size_t)2 * ncol * (MAXM + 1));
+      std::vector<double2> hc((size_t)2 * ncol * (MAXM + 1), make_double2(0.0, 0.0));
       std::vector<double> nn((size_t)ncol * NPART);
-      TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev.p, sizeof(double2) * hc.size(), cudaMemcpyDeviceToHost, c.stream));
+      TMG_CUDA(cudaMemcpyAsync(hc.data(), hdev.p, sizeof(double2) * (size_t)npass * ncol * (MAXM + 1), cudaMemcpyDeviceToHost,
+                               c.stream));
       TMG_CUDA(cudaMemcpyAsync(nn.data(), npart.p, sizeof(double) * nn.size(), cudaMemcpyDeviceToHost, c.stream));
       TMG_CUDA(cudaStreamSynchronize(c.stream));
       k = it + 1;

@@ -99,7 +99,19 @@ struct Coarse {
   DBuf W64, W32;               // orthonormalised test vectors, F64 and F32 ([nv] spinor fields)
   DBuf Dc64, Dc32;             // coarse stencil [nc][9][nd(col l)][nd(row k)]
   DBuf nbr;                    // coarse neighbour table [nc][9] (slot 0 self, 1 + 2 mu: +mu, 2 + 2 mu: -mu)
+  unsigned long long version = 0;   // bumped whenever the stencil is rebuilt
 };
+
+// Per-site inverses (A_self + i mu G5_c)^-1 of the coarse stencil for the odd-even coarse solve,
+// kept for a few (mu, precision) pairs; a captured cycle refers to an entry by address.
+struct SiteInverse {
+  bool used = false;
+  double mu = 0.0;
+  int prec = 0;
+  unsigned long long version = 0, stamp = 0;
+  DBuf buf;
+};
+constexpr int kSiteInverseSlots = 16;
 
 // Level 2 of the three-level hierarchy: aggregates of level-1 sites (Sec. 1.2 runs three levels).
 struct Coarse2 {
@@ -213,6 +225,7 @@ struct Ctx {
   int kcycle_ctas_per_sm = 1;   // CTAs per SM of the persistent level-1 K-cycle
   int force_prec = TMG_PREC_F64;   // force kernels: all FP64 (TMG_PREC_F64) or FP32 inputs with FP64 sums
   int outer_gs_fused = 1;       // outer FGMRES: fuse pass 1's update with pass 2's dot products
+  int outer_gs_passes = 1;      // outer FGMRES: classical Gram-Schmidt passes (1 or 2)
   int coarse_grid = 0;          // CTAs of the persistent coarse GMRES (0: coarse_ctas_per_sm x SMs)
   int kcycle_grid = 0;          // CTAs of the persistent K-cycle (0: kcycle_ctas_per_sm x SMs)
   int tc_steps_per_range = 1;   // K steps sharing one TMEM accumulator range in the tensor-core coarse apply
@@ -226,6 +239,11 @@ struct Ctx {
   int eo_stage = 1;             // FP32 even-odd kernels stage the site-local clover stream by bulk copies
   int coarse_overlap = 1;       // coarse GMRES: overlap the Hessenberg update with the next stencil
   int batched_tc = 1;           // batched coarse solve: stencil on the tensor cores (k_coarse_tc.cu)
+  int coarse_block_cache = 1;   // coarse GMRES: own stencil blocks copied once into shared memory
+  int coarse_eo = 0;            // coarse GMRES on the odd-even reduced system (one flavour, even extents)
+  int batched_coarse_m = 0;     // GMRES steps of the batched coarse solve (0: the multigrid's coarse_m)
+  SiteInverse site_inv[kSiteInverseSlots];
+  unsigned long long site_inv_clock = 0;
   DBuf tc_err;                  // set by a tensor-core completion wait that gave up (batched solve)
 };
 

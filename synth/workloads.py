@@ -22,7 +22,8 @@ WORKLOADS = {
     # mixed-precision fine level with FP64 refinement (the timed workload)
     "tm_clover_16x16x16x32_mixed_2lvl": dict(
         dims=(16, 16, 16, 32), eps=0.35, seed=3, csw=1.5, mu=0.003, sigma_target=5e-4, block=(4, 4, 4, 4), nv=16,
-        restart=10, rhs_seed=4, setup_seed=103, levels=2, sap_mr=6),
+        restart=10, rhs_seed=4, setup_seed=103, levels=2, sap_mr=6, coarse_eo=1, coarse_m=15,
+        batched_coarse_m=30),
     # batched: 12 point sources + 8 shifted pseudofermion systems, three levels
     "tm_clover_24x24x24x48_batched_3lvl": dict(
         dims=(24, 24, 24, 48), eps=0.3, seed=4, csw=1.6, mu=0.002, sigma_target=5e-4, block=(4, 4, 4, 4), nv=24,

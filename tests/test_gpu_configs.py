@@ -40,6 +40,8 @@ def _context(w, U, p, prec_fine, prec_coarse, n_init=5, n_iter=3):
     prm = tmg.Context.mg_defaults()
     prm.nv, prm.restart, prm.n_init, prm.n_iter = w["nv"], w["restart"], n_init, n_iter
     prm.sap_mr = w.get("sap_mr", prm.sap_mr)
+    prm.coarse_m = w.get("coarse_m", prm.coarse_m)
+    ctx.tune("coarse_eo", w.get("coarse_eo", 0))
     prm.prec_fine, prm.prec_coarse = prec_fine, prec_coarse
     ctx.setup(fields.gaussian_spinor(w["dims"], w["seed"] + 100, n=w["nv"]), prm)
     return ctx, prm

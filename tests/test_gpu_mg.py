@@ -104,16 +104,19 @@ def test_coarse_solve(small, prec):
     assert rel(ctx.coarse_solve(c, p.mu, prec), want) < tol
 
 
+@pytest.mark.parametrize("cache", [1, 0])
 @pytest.mark.parametrize("overlap", [0, 1])
 @pytest.mark.parametrize("passes", [1, 2])
-def test_coarse_solve_launch_variants(small, overlap, passes):
+def test_coarse_solve_launch_variants(small, overlap, passes, cache):
     """The persistent coarse GMRES with the Hessenberg update overlapped or not, one or two
-    Gram-Schmidt passes and grids of 1, 3, 7 and 16 CTAs (ragged vector chunks, CTAs owning
-    nothing): every variant gives the oracle's Krylov solution."""
+    Gram-Schmidt passes, the own stencil blocks cached in shared memory or read from L2, and grids
+    of 1, 3, 7 and 16 CTAs (ragged site ranges, several sites per CTA): every variant gives the
+    oracle's Krylov solution."""
     ctx, H, U, p = small
     c = fields.gaussian_coarse((2, 2, 2, 2), 2 * ctx.nv, 43)
     want = H.coarse_solve(c, p.mu)
     try:
+        ctx.tune("coarse_block_cache", cache)
         ctx.tune("coarse_overlap", overlap)
         ctx.tune("coarse_gs_passes", passes)
         for g in (1, 3, 7, 16):
@@ -125,6 +128,7 @@ def test_coarse_solve_launch_variants(small, overlap, passes):
         ctx.tune("coarse_grid", 0)
         ctx.tune("coarse_gs_passes", 0)
         ctx.tune("coarse_overlap", 1)
+        ctx.tune("coarse_block_cache", 1)
 
 
 @pytest.fixture(scope="module")
@@ -147,6 +151,45 @@ def test_coarse_solve_multi(nv8, tc):
         ctx.tune("batched_coarse_tc", 1)
     for j, m in enumerate(mus):
         assert rel(x[j], H.coarse_solve(c[j], m)) < 1e-4, j
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_coarse_solve_odd_even(small, nv8, prec):
+    """The coarse GMRES on the odd-even reduced system (Schur complement of the even sites; rtol 0:
+    exactly coarse_m steps on S, then the even sites) against the oracle's odd-even coarse solve, on
+    two operators and on grids of 1, 3, 7 and 16 CTAs (several sites of both parities per CTA)."""
+    tol = 1e-10 if prec == F64 else 1e-4
+    # the FP64 solve on the FP64-built context; the FP32 solve also on the FP32-built N_v = 8 one
+    cases = ((small, 46),) if prec == F64 else ((small, 46), (nv8, 47))
+    for case, seed in cases:
+        ctx, H, U, p = case
+        c = fields.gaussian_coarse((2, 2, 2, 2), 2 * ctx.nv, seed)
+        for mu in (p.mu, -0.09):
+            want = mg.coarse_solve_eo(H.Dc, c, mu, H.mg.coarse_m, 0.0)
+            try:
+                ctx.tune("coarse_eo", 1)
+                for g in (1, 3, 7, 16):
+                    ctx.tune("coarse_grid", g)
+                    assert rel(ctx.coarse_solve(c, mu, prec), want) < tol, (g, mu)
+            finally:
+                ctx.tune("coarse_grid", 0)
+                ctx.tune("coarse_eo", 0)
+
+
+def test_mixed_solve_odd_even_coarse():
+    """The mixed-precision solve with the odd-even coarse solve inside every cycle reaches 1e-10,
+    measured with the oracle's operator, and agrees with the plain-coarse-solve solution."""
+    ctx, H, U, p = build((8, 8, 8, 8), (4, 4, 2, 2), 4, 0.45, 48, prec_fine=F32, prec_coarse=F32, n_init=3, n_iter=1)
+    b = fields.gaussian_spinor(ctx.dims, 49)
+    x0, st0 = ctx.solve(b, tol=1e-12, method=tmg.SOLVE_MG_MIXED)
+    try:
+        ctx.tune("coarse_eo", 1)
+        x1, st1 = ctx.solve(b, tol=1e-12, method=tmg.SOLVE_MG_MIXED)
+    finally:
+        ctx.tune("coarse_eo", 0)
+    assert rel(dirac.apply_D(U, x1, p, clover=H.clover), b) <= 1e-12
+    assert rel(x1, x0) < 1e-8
+    assert st1["iterations"] <= st0["iterations"] + 1
 
 
 def test_cycle_f64(small):
