@@ -142,6 +142,76 @@ def kernel_sha(kind):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def run_config3(dev):
+    """The 24^3 x 48 three-level workload: 12 point sources D(mu) x = b and the first solves
+    D(-mu_k) y = g5 phi of the 8 shifted systems, all 20 in one lock-step mixed-precision solve
+    (setup untimed), against the same 20 systems solved one after another by the FP64 multigrid and
+    by the mixed single-column solve."""
+    import torch
+
+    import paper_1710_06198_gb300 as tmg
+    from synth import fields
+    name = "tm_clover_24x24x24x48_batched_3lvl"
+    w = workloads.WORKLOADS[name]
+    kappa, _ = workloads.kappa(name)
+    dims = w["dims"]
+    U = fields.gauge_field(dims, w["eps"], w["seed"])
+    ctx = tmg.Context(dims, w["block"], device=dev.index or 0)
+    try:
+        ctx.set_params(kappa, w["csw"], w["mu"])
+        ctx.load_gauge(U, -1)
+        prm = tmg.Context.mg_defaults()
+        prm.nv, prm.restart = w["nv"], w["restart"]
+        t0 = time.time()
+        ctx.setup(fields.gaussian_spinor(dims, w["seed"] + 100, n=w["nv"]), prm)
+        q = tmg.Context.level2_defaults()
+        q.agg[:] = w["agg2"]
+        q.nv = w["nv2"]
+        c1 = ctx.coarse_lat
+        ctx.setup_level2(fields.gaussian_coarse((c1[3], c1[2], c1[1], c1[0]), 2 * w["nv"], w["seed"] + 200, n=w["nv2"]), q)
+        torch.cuda.synchronize()
+        setup_s = time.time() - t0
+        sig = workloads.shifts(w["n_shifts"])
+        mu_k = [float(np.sqrt(w["mu"] ** 2 + s_)) for s_ in sig]
+        ps = fields.point_sources(dims)
+        g5phi = fields.gaussian_spinor(dims, w["phi_seed"])
+        g5phi[..., 2:, :] *= -1.0          # gamma5 = diag(1, 1, -1, -1) in the chiral spin basis
+        b = torch.from_numpy(np.ascontiguousarray(np.concatenate([ps, np.broadcast_to(g5phi, (len(sig),) + g5phi.shape)]))).to(dev)
+        mus = [w["mu"]] * len(ps) + [-m for m in mu_k]
+        x = torch.empty_like(b)
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3, r
+
+        ctx.solve(b, tol=w.get("tol", 1e-10), method=tmg.SOLVE_MG_BATCHED, mu_per_col=mus, out=x)   # warm-up
+        tb, (_, stb) = timed(lambda: ctx.solve(b, tol=1e-10, method=tmg.SOLVE_MG_BATCHED, mu_per_col=mus, out=x))
+        rb = ctx.apply(x, tmg.OP_D, tmg.PREC_F64, mu_per_col=mus) - b
+        worst = max(float(torch.linalg.vector_norm(rb[j]) / torch.linalg.vector_norm(b[j])) for j in range(len(mus)))
+        x1 = torch.empty_like(b[0])
+        t64, it64, tmx, itmx = 0.0, 0, 0.0, 0
+        for j in range(len(mus)):
+            t, (_, s1) = timed(lambda: ctx.solve(b[j], tol=1e-10, method=tmg.SOLVE_MG_F64, mu_per_col=[mus[j]], out=x1))
+            t64 += t
+            it64 += s1["iterations"]
+            t, (_, s2) = timed(lambda: ctx.solve(b[j], tol=1e-10, method=tmg.SOLVE_MG_MIXED, mu_per_col=[mus[j]], out=x1))
+            tmx += t
+            itmx += s2["iterations"]
+        return {"lattice": list(dims), "levels": 3, "rhs": len(mus), "kinds": "12 point sources + 8 shifted systems",
+                "setup_s_untimed": round(setup_s, 2), "batched_mixed_s": round(tb, 4), "batched_iterations": stb["iterations"],
+                "batched_true_residual_max": worst, "sequential_fp64_multigrid_s": round(t64, 4),
+                "sequential_fp64_iterations_total": it64, "sequential_mixed_s": round(tmx, 4),
+                "sequential_mixed_iterations_total": itmx, "speedup_batched_vs_sequential_fp64": round(t64 / tb, 2),
+                "speedup_batched_vs_sequential_mixed": round(tmx / tb, 2)}
+    finally:
+        ctx.close()
+
+
 def stored_traffic(kind):
     """DRAM bytes per launch of a kernel class from an ncu capture summarised under profiles/ (a line
     'traffic: <kind> <bytes> bytes per launch, source sha <sha>'), or None when no summary has one
@@ -443,6 +513,12 @@ def run_ours(args):
                    "true_residual_max": worst, "per_rhs_over_single": round(tbm / nb / t_step, 3),
                    "kernels_one_solve": bprof}
 
+    # the 24^3 x 48 three-level workload: 12 point sources and 8 shifted systems in one lock-step
+    # mixed-precision solve, against the same 20 systems solved one at a time by the FP64 multigrid
+    config3 = None
+    if args.config3 and world == 1:
+        config3 = run_config3(dev)
+
     # one instrumented solve: device time of every kernel class
     flush.zero_()
     tmg.profile(ctx, True)
@@ -541,6 +617,7 @@ def run_ours(args):
         "autotune_coarse_ms": None if autotune_ms is None else round(autotune_ms, 4), "graphs": graphs,
         "fp64_solve_s": round(fp64_s, 4), "fp64_iterations": st64["iterations"],
         "batched": batched,
+        "batched_three_level_24x24x24x48": config3,
         "speedup_vs_fp64": {"mixed_single": round(fp64_s / t_step, 2),
                             "mixed_batched_per_rhs": round(fp64_s / batched["s_per_rhs"], 2) if batched else None},
         "cg_fp64": cg,
@@ -727,6 +804,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-large-dslash", action="store_true")
     ap.add_argument("--batch", type=int, default=12, help="right-hand sides of the batched solve (0: skip)")
+    ap.add_argument("--no-config3", dest="config3", action="store_false",
+                    help="skip the 24^3 x 48 three-level batched comparison")
     ap.add_argument("--cg-maxiter", type=int, default=50000)
     ap.add_argument("--shifts", type=int, default=8, help="shifted systems solved with and without Taylor guesses (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
