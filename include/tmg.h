@@ -218,6 +218,15 @@ int tmg_coarse_apply2(tmg_ctx *ctx, const double *x, double *y, double mu, int p
  * mode 2: x = smoother of b from zero (smooth_m GMRES steps). */
 int tmg_kcycle(tmg_ctx *ctx, const double *b, double *x, double mu, int mode, int prec, int where);
 
+/* The same K-cycle (modes 0 / 1 / 2, FP32) for n_rhs level-1 vectors b[n_rhs][V_c][2 N_v] in
+ * lock-step, column n with twist mu_per_col[n] (or the context's mu when mu_per_col is NULL): the
+ * coarse solve of the three-level batched solve.  Every D_c and D_cc application covers all columns
+ * in one tensor-core launch; Gram-Schmidt, Givens rotations and stopping tests are per column, as
+ * in tmg_kcycle.  Needs 1..32 columns and 2 N_v, 2 nv in {8, 16, 24, 32, 48, 64}.  Synchronises.
+ * TMG_ERR_STATE before tmg_setup_level2, TMG_ERR_ARG for a bad count, mode, shape or pointer,
+ * TMG_ERR_TIMEOUT if a tensor-core completion wait gave up. */
+int tmg_kcycle_multi(tmg_ctx *ctx, const double *b, double *x, int n_rhs, const double *mu_per_col, int mode, int where);
+
 /* ---- the non-degenerate doublet (Eq. 2, coarsened with P_ND = P x I2 as in Sec. 1.2) ----
  * Doublet vectors are flavour pairs: fine [2][V][4][3], coarse [2][V_c][2 N_v].  The operator
  * parameters are the context's mubar and epsbar; P (and P2 with three levels) come from the

@@ -96,6 +96,7 @@ _SIGS = {
     "tmg_coarse_solve": [_P, _P, _P, _D, _I, _I],
     "tmg_coarse_apply_multi": [_P, _P, _P, _I, _P, _I],
     "tmg_coarse_solve_multi": [_P, _P, _P, _I, _P, _I],
+    "tmg_kcycle_multi": [_P, _P, _P, _I, _P, _I, _I],
     "tmg_coarse_solve_noalloc": [_P, _P, _P, _D, _I],
     "tmg_solve": [_P, _P, _P, _I, _P, _D, _I, _I, ctypes.POINTER(Stats), _I],
     "tmg_bench_dslash": [_P, _I, _I, ctypes.POINTER(_D)],
@@ -500,6 +501,19 @@ class Context:
         pb, wh = _ptr(b)
         px, _ = _ptr(x)
         self._check(lib().tmg_kcycle(self._h, pb, px, float(mu), int(mode), prec, wh))
+        return x
+
+    def kcycle_multi(self, b, mu_per_col=None, mode=0):
+        """The K-cycle (FP32) on b[n_rhs, ..., 2 Nv] in lock-step, column n with twist mu_per_col[n]."""
+        n = b.shape[0]
+        x = _empty_like(b, b.shape)
+        pb, wh = _ptr(b)
+        px, _ = _ptr(x)
+        mp = None
+        if mu_per_col is not None:
+            mu_arr = np.ascontiguousarray(np.asarray(mu_per_col, dtype=np.float64).reshape(n))
+            mp = mu_arr.ctypes.data_as(ctypes.c_void_p)
+        self._check(lib().tmg_kcycle_multi(self._h, pb, px, n, mp, int(mode), wh))
         return x
 
     # ---- non-degenerate doublet (flavour pairs: fine [2, ..., 4, 3], coarse [2, ..., 2 Nv])

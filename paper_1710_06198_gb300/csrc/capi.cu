@@ -1083,6 +1083,39 @@ int tmg_coarse_solve_multi(tmg_ctx* ctx, const double* b, double* x, int n_rhs, 
   });
 }
 
+int tmg_kcycle_multi(tmg_ctx* ctx, const double* b, double* x, int n_rhs, const double* mu_per_col, int mode, int where) {
+  return guarded(ctx, [&]() -> int {
+    Ctx& c = ctx->c;
+    if (!b || !x || n_rhs < 1 || n_rhs > 32 || mode < 0 || mode > 2 || !valid_where(where))
+      return fail(ctx, TMG_ERR_ARG, "tmg_kcycle_multi: bad argument (1..32 columns, mode 0..2)");
+    if (!c.mg_ready || !c.l2_ready) return fail(ctx, TMG_ERR_STATE, "tmg_kcycle_multi: no level-2 setup");
+    if (!kcycle_batched_ok(c, n_rhs)) return fail(ctx, TMG_ERR_ARG, "tmg_kcycle_multi: level shapes not covered by the tensor-core apply");
+    const size_t n = (size_t)c.cl.nc * c.cl.nd;
+    const double* d = stage_in(c, c.stage_a, b, 2 * n * n_rhs, where);
+    tmg::CField bi, xo;
+    bi.create(TMG_PREC_F32, n * n_rhs);
+    xo.create(TMG_PREC_F32, n * n_rhs);
+    convert_field(c, d, TMG_PREC_F64, bi.buf.p, TMG_PREC_F32, n * n_rhs);
+    std::vector<float> mus(n_rhs, (float)c.mu);
+    if (mu_per_col)
+      for (int j = 0; j < n_rhs; j++) mus[j] = (float)mu_per_col[j];
+    DBuf mu_dev;
+    mu_dev.alloc(sizeof(float) * 32);
+    TMG_CUDA(cudaMemcpyAsync(mu_dev.p, mus.data(), n_rhs * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    if (!c.tc_err.p) c.tc_err.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+    kcycle_batched(c, n_rhs, bi.buf.p, xo.buf.p, mu_dev.as<float>(), mode);
+    int herr = 0;
+    TMG_CUDA(cudaMemcpyAsync(&herr, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    double* o = stage_out_ptr(c, c.stage_b, x, 2 * n * n_rhs, where);
+    convert_field(c, xo.buf.p, TMG_PREC_F32, o, TMG_PREC_F64, n * n_rhs);
+    stage_out_finish(c, c.stage_b, x, 2 * n * n_rhs, where);
+    TMG_CUDA(cudaStreamSynchronize(c.stream));
+    if (herr) return fail(ctx, TMG_ERR_TIMEOUT, "tmg_kcycle_multi: a tensor-core completion wait gave up");
+    return TMG_OK;
+  });
+}
+
 int tmg_coarse_solve(tmg_ctx* ctx, const double* b, double* x, double mu, int prec, int where) {
   return guarded(ctx, [&]() -> int {
     Ctx& c = ctx->c;

@@ -1608,6 +1608,7 @@ struct BgtArgs {
   int* kk;               // [ncol]: Krylov dimension reached
   int* all_done;
   int* counter;
+  const int* skip_outer; // an enclosing solve's all-done flag (or null): every launch returns at once
 };
 
 // Lane l of the warp ends with the warp sum of v[l] (a butterfly over the five lane bits: at bit O
@@ -1642,6 +1643,7 @@ struct BgtChunk {
 };
 
 __global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
+  if (a.skip_outer && *a.skip_outer) return;         // the same value in every CTA
   cg::grid_group grid = cg::this_grid();
   __shared__ float s_beta[BMAXC];
   const int n = a.nc * a.nd, G = gridDim.x;
@@ -1692,7 +1694,7 @@ __global__ void __launch_bounds__(256) k_bgt_start(BgtArgs a) {
 }
 
 __global__ void __launch_bounds__(256, 2) k_bgt_arnoldi(BgtArgs a, int j) {
-  if (*a.all_done) return;                           // the same value in every CTA: set by an earlier launch
+  if (*a.all_done || (a.skip_outer && *a.skip_outer)) return;   // the same values in every CTA: set by earlier launches
   cg::grid_group grid = cg::this_grid();
   extern __shared__ float2 hsm[];                    // [ncol][CMAXM + 1]
   __shared__ float s_hn[BMAXC];
@@ -1828,6 +1830,7 @@ __global__ void __launch_bounds__(256, 2) k_bgt_arnoldi(BgtArgs a, int j) {
 }
 
 __global__ void __launch_bounds__(256) k_bgt_finish(BgtArgs a) {
+  if (a.skip_outer && *a.skip_outer) return;
   cg::grid_group grid = cg::this_grid();
   __shared__ float2 ys[BMAXC][CMAXM];
   const int n = a.nc * a.nd;
@@ -1883,18 +1886,21 @@ __global__ void __launch_bounds__(256) k_bgt_finish(BgtArgs a) {
 
 // Whether the tensor-core batched coarse solve covers this level: the tcgen05 coarse apply's block
 // widths (2 N_v = 8 .. 64) and at most 32 columns.
-bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol) {
-  const int nd = c.cl.nd;
-  return ncol >= 1 && ncol <= 32 && (nd == 8 || nd == 16 || nd == 24 || nd == 32 || nd == 48 || nd == 64);
-}
+bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol) { return tc_level_ok(c.cl.nd, ncol); }
 
-void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
-  ProfScope ps(c, PK_COARSE_SOLVE);
-  if (!coarse_gmres_batched_tc_ok(c, ncol)) throw Error{TMG_ERR_ARG, "tensor-core batched coarse solve: unsupported shape"};
-  const int m = std::min(c.batched_coarse_m > 0 ? c.batched_coarse_m : c.mg.coarse_m, CMAXM);
-  const size_t n = (size_t)c.cl.nc * c.cl.nd;
+namespace {
+
+// Launch shape of the three batched-GMRES kernels for vectors of n elements: a cooperative grid of
+// at most two CTAs per SM and no more CTAs than 32-element chunks.
+struct BgtPlan {
+  int G;
+  size_t hsm;
+};
+BgtPlan bgt_plan(Ctx& c, size_t n, int ncol) {
   static int mps[3] = {-1, -1, -1};
   if (mps[0] < 0) {
+    TMG_CUDA(cudaFuncSetAttribute(k_bgt_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float2) * BMAXC * (CMAXM + 1))));
     TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps[0], k_bgt_start, 256, 0));
     TMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mps[1], k_bgt_arnoldi, 256,
                                                            sizeof(float2) * BMAXC * (CMAXM + 1)));
@@ -1902,36 +1908,21 @@ void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const flo
   }
   const int per_sm = std::min(2, std::min(mps[0], std::min(mps[1], mps[2])));
   if (per_sm < 1) throw Error{TMG_ERR_CUDA, "tensor-core batched coarse solve: kernels cannot be resident"};
-  const int G = std::max(1, std::min((int)((n + 31) / 32), c.sms * per_sm));
-  const size_t hsm = sizeof(float2) * (size_t)ncol * (CMAXM + 1);
-  if (hsm > 48 * 1024)
-    TMG_CUDA(cudaFuncSetAttribute(k_bgt_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-  c.cw_V.alloc((m + 1) * n * ncol * sizeof(float2));
-  c.cw_w.alloc(n * ncol * sizeof(float2));
-  // one state allocation: part, cs, sn, gv, R, y, htot, npart, beta, done, kk, all_done
+  BgtPlan p;
+  p.G = std::max(1, std::min((int)((n + 31) / 32), c.sms * per_sm));
+  p.hsm = sizeof(float2) * (size_t)ncol * (CMAXM + 1);
+  return p;
+}
+
+// Bytes of one solve's state (part, cs, sn, gv, R, y, htot, npart, beta, done, kk, all_done) and
+// its carving from one allocation.
+size_t bgt_state_bytes(int ncol, int G) {
   const size_t d2 = (size_t)ncol * ((CMAXM + 1) * G + 2 * CMAXM + (CMAXM + 1) + (CMAXM + 1) * CMAXM + CMAXM + (CMAXM + 1));
   const size_t bytes = sizeof(float2) * d2 + sizeof(float) * ((size_t)ncol * G + ncol) + sizeof(int) * (2 * (size_t)ncol + 1);
-  c.cw_state.alloc(bytes);
-  if (!c.coarse_iter_dev.p) {
-    c.coarse_iter_dev.alloc(sizeof(int));
-    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
-  }
-  if (!c.tc_err.p) {
-    c.tc_err.alloc(sizeof(int));
-    TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
-  }
-  BgtArgs a;
-  a.nd = c.cl.nd;
-  a.nv = c.cl.nv;
-  a.nc = c.cl.nc;
-  a.m = m;
-  a.ncol = ncol;
-  a.b = (const float2*)b;
-  a.x = (float2*)x;
-  a.V = c.cw_V.as<float2>();
-  a.W = c.cw_w.as<float2>();
-  a.rtol = c.mg.coarse_rtol;
-  a.part = c.cw_state.as<float2>();
+  return (bytes + 255) & ~(size_t)255;
+}
+void bgt_carve(BgtArgs& a, void* state, int ncol, int G) {
+  a.part = reinterpret_cast<float2*>(state);
   a.cs = a.part + (size_t)ncol * (CMAXM + 1) * G;
   a.sn = a.cs + (size_t)ncol * CMAXM;
   a.gv = a.sn + (size_t)ncol * CMAXM;
@@ -1943,19 +1934,189 @@ void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const flo
   a.done = reinterpret_cast<int*>(a.beta + ncol);
   a.kk = a.done + ncol;
   a.all_done = a.kk + ncol;
-  a.counter = c.coarse_iter_dev.as<int>();
+}
+
+void ensure_counters(Ctx& c) {
+  if (!c.coarse_iter_dev.p) {
+    c.coarse_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.coarse_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  if (!c.tc_err.p) {
+    c.tc_err.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+  }
+}
+
+// A whole batched GMRES on level L: start, a.m Arnoldi steps (tensor-core apply of V_j, then the
+// orthogonalisation kernel), and the solution x = V y.
+void bgt_run(Ctx& c, const TcLevel& L, BgtArgs& a, const BgtPlan& pl, const float* mu_dev) {
+  const size_t n = (size_t)L.nc * L.nd;
   int* tc_err = c.tc_err.as<int>();
   void* args[] = {&a};
   ++c.launches;
-  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_start, dim3(G), dim3(256), args, 0, c.stream));
-  for (int j = 0; j < m; j++) {
-    coarse_apply_tc(c, ncol, a.V + (size_t)j * ncol * n, a.W, mu_dev, tc_err, a.all_done);
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_start, dim3(pl.G), dim3(256), args, 0, c.stream));
+  for (int j = 0; j < a.m; j++) {
+    coarse_apply_tc_level(c, L, a.ncol, a.V + (size_t)j * a.ncol * n, a.W, mu_dev, tc_err, a.all_done, a.skip_outer);
     void* sargs[] = {&a, &j};
     ++c.launches;
-    TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_arnoldi, dim3(G), dim3(256), sargs, hsm, c.stream));
+    TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_arnoldi, dim3(pl.G), dim3(256), sargs, pl.hsm, c.stream));
   }
   ++c.launches;
-  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_finish, dim3(G), dim3(256), args, 0, c.stream));
+  TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_finish, dim3(pl.G), dim3(256), args, 0, c.stream));
+}
+
+BgtArgs bgt_args(const TcLevel& L, int ncol, int m, float rtol, const void* b, void* x, float2* V, float2* W, int* counter,
+                 const int* skip_outer) {
+  BgtArgs a;
+  a.nd = L.nd;
+  a.nv = L.nv;
+  a.nc = L.nc;
+  a.m = m;
+  a.ncol = ncol;
+  a.b = (const float2*)b;
+  a.x = (float2*)x;
+  a.V = V;
+  a.W = W;
+  a.rtol = rtol;
+  a.counter = counter;
+  a.skip_outer = skip_outer;
+  return a;
+}
+
+}  // namespace
+
+void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (!coarse_gmres_batched_tc_ok(c, ncol)) throw Error{TMG_ERR_ARG, "tensor-core batched coarse solve: unsupported shape"};
+  const int m = std::min(c.batched_coarse_m > 0 ? c.batched_coarse_m : c.mg.coarse_m, CMAXM);
+  const TcLevel L = tc_level1(c);
+  const size_t n = (size_t)L.nc * L.nd;
+  const BgtPlan pl = bgt_plan(c, n, ncol);
+  c.cw_V.alloc((m + 1) * n * ncol * sizeof(float2));
+  c.cw_w.alloc(n * ncol * sizeof(float2));
+  c.cw_state.alloc(bgt_state_bytes(ncol, pl.G));
+  ensure_counters(c);
+  BgtArgs a = bgt_args(L, ncol, m, (float)c.mg.coarse_rtol, b, x, c.cw_V.as<float2>(), c.cw_w.as<float2>(),
+                       c.coarse_iter_dev.as<int>(), nullptr);
+  bgt_carve(a, c.cw_state.p, ncol, pl.G);
+  bgt_run(c, L, a, pl, mu_dev);
+}
+
+// ---- the level-1 K-cycle for ncol columns in lock-step (three levels, batched solve).  The same
+// algorithm as k_kcycle (FGMRES on D_c, right-preconditioned by the level-1 cycle z = P2 gmres_L2(P2^dag v)
+// followed by smooth_m GMRES steps on D_c from zero), with every column advancing together: each
+// operator application is one tensor-core launch for all columns (every stencil block read once per
+// step), every Gram-Schmidt step one cooperative launch, and the restriction, prolongation and
+// vector updates one launch each.  Once every column of the FGMRES has stopped, the remaining
+// launches return at once (they read its all-done flag).
+namespace {
+
+__global__ void __launch_bounds__(256) k_kb_restrict2(L2Geom q, const float2* __restrict__ W2, const float2* __restrict__ v,
+                                                      float2* __restrict__ c2, size_t n1, size_t n2, const int* skip) {
+  if (skip && *skip) return;
+  restrict2_dev<float>(q, W2, v + blockIdx.y * n1, c2 + blockIdx.y * n2);
+}
+
+__global__ void __launch_bounds__(256) k_kb_prolong2(L2Geom q, const float2* __restrict__ W2, const float2* __restrict__ c2,
+                                                     float2* __restrict__ z, size_t n1, size_t n2, const int* skip) {
+  if (skip && *skip) return;
+  prolong2_dev<float>(q, W2, c2 + blockIdx.y * n2, z + blockIdx.y * n1);
+}
+
+// out = u + s v (elementwise over n complex values)
+__global__ void __launch_bounds__(256) k_kb_axpy(const float2* u, const float2* __restrict__ v, float2* out, size_t n, float s,
+                                                 const int* skip) {
+  if (skip && *skip) return;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 a = u[e], b = v[e];
+    out[e] = make_float2(a.x + s * b.x, a.y + s * b.y);
+  }
+}
+
+}  // namespace
+
+bool kcycle_batched_ok(const Ctx& c, int ncol) {
+  return c.l2_ready && c.batched_tc && tc_level_ok(c.cl.nd, ncol) && tc_level_ok(c.cl2.nd, ncol);
+}
+
+void kcycle_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev, int mode) {
+  ProfScope ps(c, PK_COARSE_SOLVE);
+  if (!kcycle_batched_ok(c, ncol)) throw Error{TMG_ERR_ARG, "batched K-cycle: unsupported shape"};
+  const tmg_level2_params& p = c.l2p;
+  const TcLevel L1 = tc_level1(c), L2 = tc_level2(c);
+  const size_t n1 = (size_t)L1.nc * L1.nd, n2 = (size_t)L2.nc * L2.nd, m1 = n1 * ncol, m2 = n2 * ncol;
+  const int sm_m = std::max(1, std::min(p.smooth_m, CMAXM)), cm = std::max(1, std::min(p.coarse_m, CMAXM));
+  const int kr = std::max(1, std::min(p.k_restart, KMAXR));
+  const BgtPlan P1 = bgt_plan(c, n1, ncol), P2 = bgt_plan(c, n2, ncol);
+  // one allocation: FGMRES basis V, preconditioned vectors Z and w; smoother basis and w; the
+  // smoother's right-hand side and solution; the level-2 right-hand side, solution, basis and w;
+  // the three solves' states
+  const size_t vec[] = {(kr + 1) * m1, kr * m1, m1, (sm_m + 1) * m1, m1, m1, m1, m2, m2, (cm + 1) * m2, m2};
+  const size_t nvec = sizeof(vec) / sizeof(vec[0]);
+  size_t off[16], o = 0;
+  for (size_t i = 0; i < nvec; i++) { off[i] = o; o += ((vec[i] * sizeof(float2)) + 255) & ~(size_t)255; }
+  const size_t so = o, s1b = bgt_state_bytes(ncol, P1.G), s2b = bgt_state_bytes(ncol, P2.G);
+  o += 2 * s1b + s2b;
+  c.kbw.alloc(o);
+  ensure_counters(c);
+  if (!c.l2_iter_dev.p) {
+    c.l2_iter_dev.alloc(sizeof(int));
+    TMG_CUDA(cudaMemsetAsync(c.l2_iter_dev.p, 0, sizeof(int), c.stream));
+  }
+  char* base = (char*)c.kbw.p;
+  auto v = [&](int i) { return (float2*)(base + off[i]); };
+  float2 *oV = v(0), *oZ = v(1), *oW = v(2), *sV = v(3), *sW = v(4), *r1 = v(5), *es = v(6), *c2 = v(7), *e2 = v(8),
+         *bV = v(9), *bW = v(10);
+  const float2* W2 = c.cl2.W32.as<float2>();
+  const L2Geom q = l2geom(c);
+  auto smoother = [&](const void* rhs, void* out, const int* skip) {
+    BgtArgs S = bgt_args(L1, ncol, sm_m, 0.f, rhs, out, sV, sW, nullptr, skip);
+    bgt_carve(S, base + so + s1b, ncol, P1.G);
+    bgt_run(c, L1, S, P1, mu_dev);
+  };
+  const int eb = 256;
+  auto grid_for = [&](size_t n) { return (unsigned)std::max<size_t>(1, std::min<size_t>((n + eb - 1) / eb, (size_t)8 * c.sms)); };
+  // z = level-1 cycle of v (all columns): level-2 correction, then the smoother on the residual
+  auto l1_cycle = [&](const float2* vin, float2* z, const int* skip) {
+    ++c.launches;
+    k_kb_restrict2<<<dim3(grid_for(n2), ncol), eb, 0, c.stream>>>(q, W2, vin, c2, n1, n2, skip);
+    BgtArgs B = bgt_args(L2, ncol, cm, (float)p.coarse_rtol, c2, e2, bV, bW, c.l2_iter_dev.as<int>(), skip);
+    bgt_carve(B, base + so + 2 * s1b, ncol, P2.G);
+    bgt_run(c, L2, B, P2, mu_dev);
+    ++c.launches;
+    k_kb_prolong2<<<dim3(grid_for(n1), ncol), eb, 0, c.stream>>>(q, W2, e2, z, n1, n2, skip);
+    coarse_apply_tc_level(c, L1, ncol, z, sW, mu_dev, c.tc_err.as<int>(), skip, nullptr);
+    ++c.launches;
+    k_kb_axpy<<<grid_for(m1), eb, 0, c.stream>>>(vin, sW, r1, m1, -1.f, skip);
+    smoother(r1, es, skip);
+    ++c.launches;
+    k_kb_axpy<<<grid_for(m1), eb, 0, c.stream>>>(z, es, z, m1, 1.f, skip);
+  };
+  if (mode == 2) {
+    smoother(b, x, nullptr);
+  } else if (mode == 1) {
+    l1_cycle((const float2*)b, (float2*)x, nullptr);
+  } else {
+    BgtArgs A = bgt_args(L1, ncol, kr, (float)p.k_rtol, b, x, oV, oW, c.coarse_iter_dev.as<int>(), nullptr);
+    bgt_carve(A, base + so, ncol, P1.G);
+    void* args[] = {&A};
+    ++c.launches;
+    TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_start, dim3(P1.G), dim3(256), args, 0, c.stream));
+    for (int j = 0; j < kr; j++) {
+      float2* zj = oZ + (size_t)j * m1;
+      l1_cycle(oV + (size_t)j * m1, zj, A.all_done);
+      coarse_apply_tc_level(c, L1, ncol, zj, oW, mu_dev, c.tc_err.as<int>(), A.all_done, nullptr);
+      void* sargs[] = {&A, &j};
+      ++c.launches;
+      TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_arnoldi, dim3(P1.G), dim3(256), sargs, P1.hsm, c.stream));
+    }
+    BgtArgs F = A;                                   // flexible GMRES: x = Z y
+    F.V = oZ;
+    void* fargs[] = {&F};
+    ++c.launches;
+    TMG_CUDA(cudaLaunchCooperativeKernel((const void*)k_bgt_finish, dim3(P1.G), dim3(256), fargs, 0, c.stream));
+  }
+  TMG_CHECK_LAUNCH();
 }
 
 }  // namespace tmg

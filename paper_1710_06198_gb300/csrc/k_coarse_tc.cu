@@ -213,10 +213,11 @@ template <int ND, int NPAD, int R>
 __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int ncol, const float2* __restrict__ Dc,
                                                          const int* __restrict__ nbr, const float2* __restrict__ X,
                                                          float2* __restrict__ Y, const float* __restrict__ mu,
-                                                         int* __restrict__ err, const int* __restrict__ skip) {
-  // a caller's "nothing left to do" flag, written by an earlier launch: every thread reads the same
-  // value and returns before any tensor memory is allocated
-  if (skip && *skip) return;
+                                                         int* __restrict__ err, const int* __restrict__ skip,
+                                                         const int* __restrict__ skip2) {
+  // the caller's "nothing left to do" flags, written by earlier launches: every thread reads the
+  // same values and returns before any tensor memory is allocated
+  if ((skip && *skip) || (skip2 && *skip2)) return;
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int KP = ((2 * ND + 7) / 8) * 8;             // K padded to the MMA step
   constexpr int nsteps = KP / 8;                          // K = 8 MMA steps per stencil block
@@ -369,51 +370,64 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
 }
 
 template <int ND, int NPAD, int R>
-void launch_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
+void launch_tc(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip,
+               const int* skip2) {
   constexpr int KP = ((2 * ND + 7) / 8) * 8;
   constexpr int cols = ((KP / 8 + R - 1) / R) * NPAD;
   const size_t smem = sizeof(float) * (size_t)(2 * TC_M * KP + 2 * NPAD * KP) + 32;
   // persistent CTAs, as many as can be resident: tensor memory (512 columns per SM) holds two CTAs
   // when one needs at most 256 columns, shared memory two when one needs at most 113 KB
   const int per_sm = (cols <= 256 && smem <= 113 * 1024) ? 2 : 1;
-  const int grid = std::max(1, std::min(c.cl.nc, per_sm * c.sms));
+  const int grid = std::max(1, std::min(L.nc, per_sm * c.sms));
   TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc<ND, NPAD, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ++c.launches, k_coarse_apply_tc<ND, NPAD, R><<<grid, 128, smem, c.stream>>>(c.cl.nc, c.cl.nv, ncol, c.cl.Dc32.as<float2>(),
-                                                                           c.cl.nbr.as<int>(), (const float2*)X, (float2*)Y,
-                                                                           mu_dev, err_dev, skip);
+  ++c.launches, k_coarse_apply_tc<ND, NPAD, R><<<grid, 128, smem, c.stream>>>(L.nc, L.nv, ncol, L.Dc, L.nbr, (const float2*)X,
+                                                                           (float2*)Y, mu_dev, err_dev, skip, skip2);
 }
 
 template <int ND, int NPAD>
-void launch_tc_r(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
-  if (c.tc_steps_per_range >= 4) launch_tc<ND, NPAD, 4>(c, ncol, X, Y, mu_dev, err_dev, skip);
-  else if (c.tc_steps_per_range == 2) launch_tc<ND, NPAD, 2>(c, ncol, X, Y, mu_dev, err_dev, skip);
-  else launch_tc<ND, NPAD, 1>(c, ncol, X, Y, mu_dev, err_dev, skip);
+void launch_tc_r(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
+                 const int* skip, const int* skip2) {
+  if (c.tc_steps_per_range >= 4) launch_tc<ND, NPAD, 4>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
+  else if (c.tc_steps_per_range == 2) launch_tc<ND, NPAD, 2>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
+  else launch_tc<ND, NPAD, 1>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
 }
 
 template <int ND>
-void launch_tc_nd(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
-  if (ncol <= 16) launch_tc_r<ND, 16>(c, ncol, X, Y, mu_dev, err_dev, skip);
-  else launch_tc_r<ND, 32>(c, ncol, X, Y, mu_dev, err_dev, skip);
+void launch_tc_nd(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
+                  const int* skip, const int* skip2) {
+  if (ncol <= 16) launch_tc_r<ND, 16>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
+  else launch_tc_r<ND, 32>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
 }
 
 }  // namespace
 
-// Y = D_c(mu_col) X for ncol FP32 coarse vectors ([col][nc * nd] complex) on the tensor cores; the
-// launch does nothing when skip is given and *skip is nonzero on the device.
-void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
+bool tc_level_ok(int nd, int ncol) {
+  return ncol >= 1 && ncol <= 32 && (nd == 8 || nd == 16 || nd == 24 || nd == 32 || nd == 48 || nd == 64);
+}
+
+TcLevel tc_level1(const Ctx& c) { return TcLevel{c.cl.nc, c.cl.nv, c.cl.nd, c.cl.Dc32.as<float2>(), c.cl.nbr.as<int>()}; }
+TcLevel tc_level2(const Ctx& c) { return TcLevel{c.cl2.nc, c.cl2.nv, c.cl2.nd, c.cl2.Dc32.as<float2>(), c.cl2.nbr.as<int>()}; }
+
+// Y = D(mu_col) X for ncol FP32 vectors ([col][nc * nd] complex) of level L on the tensor cores;
+// the launch does nothing when a skip flag is given and nonzero on the device.
+void coarse_apply_tc_level(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
+                           const int* skip, const int* skip2) {
   ProfScope ps(c, PK_COARSE);
-  const int nd = c.cl.nd;
-  if (ncol < 1 || ncol > 32) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns"};
-  switch (nd) {
-    case 8: launch_tc_nd<8>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    case 16: launch_tc_nd<16>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    case 24: launch_tc_nd<24>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    case 32: launch_tc_nd<32>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    case 48: launch_tc_nd<48>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    case 64: launch_tc_nd<64>(c, ncol, X, Y, mu_dev, err_dev, skip); break;
-    default: throw Error{TMG_ERR_ARG, "tensor-core coarse apply: N_v must be 4, 8, 12, 16, 24 or 32"};
+  if (!tc_level_ok(L.nd, ncol)) throw Error{TMG_ERR_ARG, "tensor-core coarse apply: 1..32 columns, N_v 4, 8, 12, 16, 24 or 32"};
+  switch (L.nd) {
+    case 8: launch_tc_nd<8>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
+    case 16: launch_tc_nd<16>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
+    case 24: launch_tc_nd<24>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
+    case 32: launch_tc_nd<32>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
+    case 48: launch_tc_nd<48>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
+    default: launch_tc_nd<64>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2); break;
   }
   TMG_CHECK_LAUNCH();
+}
+
+// Y = D_c(mu_col) X on level 1
+void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip) {
+  coarse_apply_tc_level(c, tc_level1(c), ncol, X, Y, mu_dev, err_dev, skip, nullptr);
 }
 
 }  // namespace tmg

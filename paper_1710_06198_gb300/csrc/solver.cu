@@ -382,7 +382,7 @@ static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, c
   }
   for (const DBuf* b : {&c.cl.W64, &c.cl.W32, &c.cl.Dc64, &c.cl.Dc32, &c.cl.nbr, &c.cl2.W64, &c.cl2.W32, &c.cl2.Dc64,
                         &c.cl2.Dc32, &c.cl2.nbr, &c.cw_cr, &c.cw_ce, &c.cw_V, &c.cw_w, &c.cw_part, &c.coarse_iter_dev,
-                        &c.kw, &c.l2_iter_dev}) {
+                        &c.kw, &c.kbw, &c.l2_iter_dev, &c.tc_err}) {
     k.push_back(u(b->p));
     k.push_back((unsigned long long)b->bytes);
   }
@@ -1234,12 +1234,15 @@ double sigma_min_lanczos(Ctx& c, const void* start, double mu_s, int k, double r
 }
 
 // ---------------------------------------------------------------- batched cycle (and its graph)
-// z = M v for ncol FP32 columns: P^dag, the batched coarse solve (three levels: one K-cycle per
-// column), P, SAP; one launch per operation for every column at two levels.
+// z = M v for ncol FP32 columns: P^dag, the batched coarse solve (three levels: the lock-step
+// K-cycle, or one K-cycle per column where the tensor-core apply does not cover the level shapes),
+// P, SAP; one launch per operation for every column.
 static void batched_cycle_p(Ctx& c, int pf, int ncol, const void* v, void* z, void* cr, void* ce, const float* mu_dev,
                             const double* mu) {
   restrict_mrhs(c, ncol, v, cr);
-  if (c.l2_ready) {
+  if (c.l2_ready && kcycle_batched_ok(c, ncol)) {
+    kcycle_batched(c, ncol, cr, ce, mu_dev, 0);
+  } else if (c.l2_ready) {
     const size_t nco = (size_t)c.cl.nc * c.cl.nd;
     for (int col = 0; col < ncol; col++)
       kcycle(c, TMG_PREC_F32, (const float2*)cr + col * nco, (float2*)ce + col * nco, mu[col], 0);

@@ -205,6 +205,7 @@ struct Ctx {
   bool l2_ready = false;   // level 2 built: the coarse solve of the cycle is the level-1 K-cycle
   Coarse2 cl2;
   DBuf kw;                 // K-cycle scratch (k_coarse_gmres.cu)
+  DBuf kbw;                // batched K-cycle scratch (k_coarse_gmres.cu)
   DBuf sv2;                // raw level-1 test vectors of the level-2 setup
   DBuf l2_iter_dev;        // device counter of level-2 GMRES steps (K-cycle steps go to coarse_iter_dev)
   // solver workspaces (solver.cu)
@@ -359,6 +360,18 @@ void coarse_apply_tc(Ctx& c, int ncol, const void* X, void* Y, const float* mu_d
                      const int* skip = nullptr);
 bool coarse_gmres_batched_tc_ok(const Ctx& c, int ncol);
 void coarse_gmres_batched_tc(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev);
+// One coarse level as the tensor-core apply sees it: sites, test vectors, dofs per site, FP32
+// stencil [nc][9][nd][nd] and neighbour table [nc][9].
+struct TcLevel {
+  int nc, nv, nd;
+  const float2* Dc;
+  const int* nbr;
+};
+bool tc_level_ok(int nd, int ncol);
+TcLevel tc_level1(const Ctx& c);
+TcLevel tc_level2(const Ctx& c);
+void coarse_apply_tc_level(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
+                           const int* skip, const int* skip2);
 // The same solve on caller-provided device scratch (no allocation): bytes needed, and the launch.
 size_t coarse_gmres_scratch_bytes(Ctx& c, int cprec);
 void coarse_gmres_on_scratch(Ctx& c, int cprec, const void* b, void* x, double mu, void* scratch);
@@ -381,6 +394,10 @@ void coarse_apply_c(Ctx& c, int prec, const void* x, void* y, double mu);
 //         nf = 2: the same on doublet vectors [2][nc1][nd1] with D_ND,c and D_ND,cc (mu = mubar, the
 //         context's epsbar).
 void kcycle(Ctx& c, int prec, const void* b, void* x, double mu, int mode, int nf = 1);
+// The same (one flavour, FP32, modes 0 / 1 / 2) for ncol columns [col][nc1 * nd1] in lock-step, each
+// with its twist mu_dev[col] on the device: the operator applications on the tensor cores.
+bool kcycle_batched_ok(const Ctx& c, int ncol);
+void kcycle_batched(Ctx& c, int ncol, const void* b, void* x, const float* mu_dev, int mode);
 
 }  // namespace tmg
 

@@ -67,6 +67,8 @@ def test_level2_defaults_and_null_context(L):
     assert L.tmg_level2_defaults(None) == -1
     assert L.tmg_setup_level2(None, ctypes.byref(q), None, 0) == -1
     assert L.tmg_kcycle(None, None, None, 0.0, 0, 0, 0) == -1
+    assert L.tmg_kcycle_multi(None, None, None, 1, None, 0, 0) == -1
+    assert L.tmg_coarse_solve_multi(None, None, None, 1, None, 0) == -1
     assert L.tmg_coarse_apply2(None, None, None, 0.0, 0, 0) == -1
 
 
