@@ -164,9 +164,7 @@ def run_config3(dev):
         prm.nv, prm.restart = w["nv"], w["restart"]
         t0 = time.time()
         ctx.setup(fields.gaussian_spinor(dims, w["seed"] + 100, n=w["nv"]), prm)
-        q = tmg.Context.level2_defaults()
-        q.agg[:] = w["agg2"]
-        q.nv = w["nv2"]
+        q = workloads.level2_params(w, tmg.Context.level2_defaults())
         c1 = ctx.coarse_lat
         ctx.setup_level2(fields.gaussian_coarse((c1[3], c1[2], c1[1], c1[0]), 2 * w["nv"], w["seed"] + 200, n=w["nv2"]), q)
         torch.cuda.synchronize()
@@ -203,6 +201,7 @@ def run_config3(dev):
             tmx += t
             itmx += s2["iterations"]
         return {"lattice": list(dims), "levels": 3, "rhs": len(mus), "kinds": "12 point sources + 8 shifted systems",
+                "kcycle": {"smooth_m": q.smooth_m, "k_rtol": q.k_rtol, "level2_gmres_m": q.coarse_m, "form": "lock-step, tensor-core applies"},
                 "setup_s_untimed": round(setup_s, 2), "batched_mixed_s": round(tb, 4), "batched_iterations": stb["iterations"],
                 "batched_true_residual_max": worst, "sequential_fp64_multigrid_s": round(t64, 4),
                 "sequential_fp64_iterations_total": it64, "sequential_mixed_s": round(tmx, 4),

@@ -56,8 +56,12 @@ __device__ __forceinline__ int colour_block(const Geom& g, int colour, int k) {
 // minimal-residual steps e += a r, r -= a D_B r with the Dirichlet block operator D_B (hops that
 // leave the block are dropped), then x += e.  Blocks of one colour never touch, so the CTAs of a
 // launch are independent; the other colour's x is only read.
-template <typename R, class S, class G, class C>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom g, int colour, S x, S b, G U, C A, R tw, int n_mr) {
+// Multi-column form (MC): CTA (block, column) = (blockIdx.x / ncol, blockIdx.x % ncol),
+// column c of x and b with twist mu_col[c]; the columns of a block run on neighbouring CTAs, so
+// its links and clover come from DRAM about once per launch.
+template <typename R, class S, class G, class C, bool MC = false>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom g, int colour, S x, S b, G U, C A, R tw, int n_mr,
+                                                                           int ncol, const float* __restrict__ mu_col) {
   // shared memory: r [12][VB] complex; for FP32 arithmetic also the block's links, reconstructed
   // once to 18 reals, [4][9][VB] complex (the MR steps then never touch global memory for links)
   extern __shared__ double smem_d[];
@@ -65,7 +69,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
   constexpr bool kCacheLinks = sizeof(R) == 4;
   cpx<R>* ls = rs + 12 * g.VB;
   double* red = smem_d + (sizeof(cpx<R>) * (kCacheLinks ? 48 : 12) * g.VB) / sizeof(double);
-  const int blk = colour_block(g, colour, blockIdx.x);
+  int kblk = blockIdx.x;
+  if constexpr (MC) {
+    const int col = blockIdx.x % ncol;
+    kblk = blockIdx.x / ncol;
+    x = x.column(col);
+    b = b.column(col);
+    tw = (R)mu_col[col];
+  }
+  const int blk = colour_block(g, colour, kblk);
   const int t = threadIdx.x;
   const int s = blk * g.VB + t;
   const SiteCoord sc = decode_site(g, s);
@@ -358,9 +370,38 @@ static void launch_sap(Ctx& c, S x, S b, G U, C A, R tw, int n_sweeps, int kind)
   for (int sw = 0; sw < n_sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
       ProfScope ps(c, kind);
-      ++c.launches, k_sap_block<R, S, G, C><<<c.g.nblk / 2, c.g.VB, smem, c.stream>>>(c.g, colour, x, b, U, A, tw, c.mg.sap_mr);
+      ++c.launches, k_sap_block<R, S, G, C><<<c.g.nblk / 2, c.g.VB, smem, c.stream>>>(c.g, colour, x, b, U, A, tw, c.mg.sap_mr,
+                                                                                   1, nullptr);
       TMG_CHECK_LAUNCH();
     }
+}
+
+// The same sweeps for ncol FP32 columns [col][12 V] (column c with twist mu_col_dev[c]), one launch
+// per colour for all columns.
+template <class G, class C>
+static void launch_sap_mrhs(Ctx& c, int ncol, float4* x, const float4* b, G U, C A, const float* mu_col_dev, int n_sweeps,
+                            int kind) {
+  using S = SpinorF32;
+  const size_t smem = sizeof(cpx<float>) * 48 * c.g.VB + 33 * 3 * sizeof(double);
+  if (smem > 48 * 1024)
+    TMG_CUDA(cudaFuncSetAttribute(k_sap_block<float, S, G, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)(c.g.nblk / 2) * (unsigned)ncol;
+  for (int sw = 0; sw < n_sweeps; sw++)
+    for (int colour = 0; colour < 2; colour++) {
+      ProfScope ps(c, kind);
+      ++c.launches, k_sap_block<float, S, G, C, true><<<grid, c.g.VB, smem, c.stream>>>(c.g, colour, S{x, c.g.V}, S{(float4*)b, c.g.V},
+                                                                                  U, A, 0.f, c.mg.sap_mr, ncol, mu_col_dev);
+      TMG_CHECK_LAUNCH();
+    }
+}
+
+void sap_mrhs(Ctx& c, int prec, int ncol, void* x, const void* b, const float* mu_col_dev, int n_sweeps) {
+  if (prec == TMG_PREC_F16)
+    launch_sap_mrhs(c, ncol, (float4*)x, (const float4*)b, GaugeF16{c.op[2].U.as<short4>(), c.g.V},
+                    CloverF16{c.op[2].A.as<short4>(), c.op[2].Ascale.as<float>(), c.g.V}, mu_col_dev, n_sweeps, PK_SAP_F16);
+  else
+    launch_sap_mrhs(c, ncol, (float4*)x, (const float4*)b, GaugeF32{c.op[1].U.as<float4>(), c.g.V},
+                    CloverF32{c.op[1].A.as<float4>(), c.g.V}, mu_col_dev, n_sweeps, PK_SAP_F32);
 }
 
 void sap_sweeps(Ctx& c, int prec, void* x, const void* b, void* /*r_scratch*/, double mu, int n_sweeps) {

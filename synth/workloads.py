@@ -27,7 +27,8 @@ WORKLOADS = {
     # batched: 12 point sources + 8 shifted pseudofermion systems, three levels
     "tm_clover_24x24x24x48_batched_3lvl": dict(
         dims=(24, 24, 24, 48), eps=0.3, seed=4, csw=1.6, mu=0.002, sigma_target=5e-4, block=(4, 4, 4, 4), nv=24,
-        agg2=(2, 2, 2, 2), nv2=32, restart=10, phi_seed=1004, n_shifts=8, levels=3),
+        agg2=(2, 2, 2, 2), nv2=32, restart=10, phi_seed=1004, n_shifts=8, levels=3,
+        smooth_m=4, k_rtol=0.2, coarse_m2=20),
     # pseudofermion action and force
     "tm_clover_16x16x16x16_force": dict(
         dims=(16, 16, 16, 16), eps=0.3, seed=5, csw=1.0, mu=0.005, sigma_target=1e-3, block=(4, 4, 4, 4), nv=16,
@@ -37,6 +38,17 @@ WORKLOADS = {
         dims=(48, 48, 48, 96), eps=0.3, seed=6, csw=1.7, mu=0.0, mubar=0.12, epsbar=0.13, sigma_target=2e-4,
         block=(4, 4, 4, 4), nv=24, agg2=(2, 2, 2, 2), nv2=24, restart=10, rhs_seeds=tuple(range(7, 15)), levels=3),
 }
+
+
+def level2_params(w, q):
+    """Copy a three-level workload's K-cycle parameters (smoother steps, K-cycle residual target,
+    level-2 GMRES steps) into a level-2 parameter struct; the others keep their defaults."""
+    q.agg[:] = w["agg2"]
+    q.nv = w["nv2"]
+    q.smooth_m = w.get("smooth_m", q.smooth_m)
+    q.k_rtol = w.get("k_rtol", q.k_rtol)
+    q.coarse_m = w.get("coarse_m2", q.coarse_m)
+    return q
 
 
 def shifts(n):

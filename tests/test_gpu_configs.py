@@ -103,9 +103,7 @@ def test_batched_three_level_24x24x24x48():
     U = fields.gauge_field(dims, w["eps"], w["seed"])
     ctx, prm = _context(w, U, p, F32, F32)
     _sampled_operator(ctx, U, p, dims, 161, precs=((F64, 1e-13), (F32, 1e-6)))
-    q = tmg.Context.level2_defaults()
-    q.agg[:] = w["agg2"]
-    q.nv = w["nv2"]
+    q = workloads.level2_params(w, tmg.Context.level2_defaults())
     c1 = ctx.coarse_lat
     ctx.setup_level2(fields.gaussian_coarse((c1[3], c1[2], c1[1], c1[0]), 2 * w["nv"], w["seed"] + 200, n=w["nv2"]), q)
     # 12 point sources D(mu) x = b, and the first step D(-mu_k) y = g5 phi of the 8 shifted systems
