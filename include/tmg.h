@@ -460,7 +460,10 @@ int tmg_profile_read(tmg_ctx *ctx, int kind, long long *count, double *ms_total)
  * cycle inside the outer FGMRES is captured once per set of buffers and parameters as a CUDA graph
  * and replayed with one launch; 0: launched kernel by kernel), "tc_steps_per_range" (1, 2 or 4 K = 8
  * steps accumulated in one tensor-memory range by tmg_coarse_apply_multi; 1 keeps FP32-level
- * accuracy for any N_v), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
+ * accuracy for any N_v), "tc_pipeline" (1, the default: for 2 N_v <= 32 the tensor-core apply stacks
+ * the hi and lo TF32 parts of each stencil block in one 128-row operand and the columns' parts in one
+ * operand, one MMA per K step, with double-buffered shared and tensor memory; 0: the unstacked
+ * kernel, three MMAs per K step), "coarse_grid" / "kcycle_grid" (absolute CTA count of the persistent coarse
  * GMRES / K-cycle, capped by residency; 0 = the per-SM knobs), "outer_gs_fused" (1, the default:
  * the outer FGMRES's first Gram-Schmidt update and second set of dot products share one sweep over
  * the basis for up to 10 basis vectors; 0: separate kernels), "outer_gs_passes" (1, the default, or 2:

@@ -837,6 +837,7 @@ int tmg_tune(tmg_ctx* ctx, const char* key, double value) {
     else if (k == "coarse_gs_passes" && (v >= 0 && v <= 2)) ctx->c.coarse_gs_passes = v;
     else if (k == "kcycle_ctas_per_sm" && v >= 1 && v <= 4) ctx->c.kcycle_ctas_per_sm = v;
     else if (k == "tc_steps_per_range" && (v == 1 || v == 2 || v == 4)) ctx->c.tc_steps_per_range = v;
+    else if (k == "tc_pipeline" && (v == 0 || v == 1)) ctx->c.tc_pipeline = v;
     else if (k == "coarse_grid" && v >= 0 && v <= 4096) ctx->c.coarse_grid = v;
     else if (k == "eo_stage" && (v == 0 || v == 1)) ctx->c.eo_stage = v;
     else if (k == "coarse_overlap" && (v == 0 || v == 1)) ctx->c.coarse_overlap = v;

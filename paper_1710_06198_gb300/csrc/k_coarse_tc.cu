@@ -16,6 +16,10 @@
 // accumulation rounding below the FP32 tolerance for any N_v.  The twist i mu_n G5_c is added in
 // the epilogue.
 //
+// For 2 N_v <= 32 a pipelined form (k_coarse_apply_tc2) stacks the split parts instead: one M = 128
+// operand [A_hi; A_lo], one N = 2 NPAD operand [B_hi | B_lo], one MMA per K step, and two operand and
+// accumulator buffers so that staging, MMAs and read-back of consecutive tiles overlap.
+//
 // Every wait on the MMA-completion mbarrier is bounded; a wait that gives up sets *err and the
 // CTA still frees its tensor memory before returning.
 #include <algorithm>
@@ -97,31 +101,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-template <int NPAD>
-__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[NPAD]);
-
-template <>
-__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
-}
-
-template <>
-__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
-  float a[16], b[16];
-  tmem_load<16>(taddr, a);
-  tmem_load<16>(taddr + 16, b);
-#pragma unroll
-  for (int i = 0; i < 16; i++) { v[i] = a[i]; v[16 + i] = b[i]; }
-}
 
 // Per-thread share of one raw tile: the stencil block (ND x ND complex) and the neighbour's column
 // vectors (ncol <= NPAD columns of ND complex) with 128 threads.  ND (= 2 N_v) and the padded K are
@@ -369,6 +348,257 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
   }
 }
 
+// ---- pipelined form for 4 ND <= 128 (N_v <= 16).  The hi and lo parts of the split stencil block
+// are stacked in one M = 128 operand, A' = [A_hi; A_lo] (rows 0 .. 2 ND - 1 and 2 ND .. 4 ND - 1 of
+// the real embedding), and the neighbour's columns side by side in one N = 2 NPAD operand,
+// B' = [B_hi | B_lo].  One MMA per K = 8 step then yields all four products A_hi B_hi, A_hi B_lo,
+// A_lo B_hi, A_lo B_lo (TMEM lanes: hi / lo rows; columns: hi / lo right-hand sides), whose sum is
+// the product of the split values; no row of the MMA is padding when N_v = 16.
+//
+// Two operand buffers in shared memory and two accumulator buffers in tensor memory, each with its
+// own completion mbarrier: while the MMAs of tile t run, the CTA reads tile t - 1's accumulators,
+// issues the global loads of tile t + 2 and, in the next iteration, stages tile t + 1 into the
+// other buffer.
+template <int ND, int NPAD>
+__device__ __forceinline__ void store_tile_stacked(const RawTile<ND, NPAD>& t, float* A, float* B, int ncol, int tid) {
+  constexpr int KP = 2 * ND;
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
+    const int ch = q * 4 + warp;
+    if (ch < ND * ND / 32) {
+      const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
+      const float2 z = t.a[q];
+      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+      const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
+      A[core_off(k, l, KP)] = re_h;
+      A[core_off(k, ND + l, KP)] = -im_h;
+      A[core_off(ND + k, l, KP)] = im_h;
+      A[core_off(ND + k, ND + l, KP)] = re_h;
+      A[core_off(2 * ND + k, l, KP)] = re_l;
+      A[core_off(2 * ND + k, ND + l, KP)] = -im_l;
+      A[core_off(3 * ND + k, l, KP)] = im_l;
+      A[core_off(3 * ND + k, ND + l, KP)] = re_l;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
+    const int ch = q * 4 + warp;
+    if (ch < NPAD * ND / 32) {
+      const int col = (ch % (NPAD / 8)) * 8 + (lane >> 2), l = (ch / (NPAD / 8)) * 4 + (lane & 3);
+      if (col < ncol) {
+        const float2 z = t.b[q];
+        const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+        B[core_off(col, l, KP)] = re_h;
+        B[core_off(col, ND + l, KP)] = im_h;
+        B[core_off(NPAD + col, l, KP)] = tf32_round(z.x - re_h);
+        B[core_off(NPAD + col, ND + l, KP)] = tf32_round(z.y - im_h);
+      }
+    }
+  }
+}
+
+__host__ __device__ constexpr uint32_t tmem_cols_pow2(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
+
+// Shared-memory bytes and TMEM columns of the pipelined kernel.
+template <int ND, int NPAD, int R>
+struct Tc2Shape {
+  static constexpr int KP = 2 * ND, NS = KP / 8, NR = (NS + R - 1) / R, NB = 2 * NPAD;
+  static constexpr int TCOLS = NR * NB;                    // accumulator columns of one buffer
+  static constexpr int ASZ = TC_M * KP, BSZ = NB * KP;     // floats of one operand buffer
+  static constexpr int SCR = 2 * ND * (NPAD + 1);          // epilogue scratch (floats)
+  static constexpr size_t smem = sizeof(float) * (size_t)(2 * (ASZ + BSZ) + SCR) + 64;
+  static constexpr uint32_t cols = tmem_cols_pow2(2 * TCOLS);
+};
+
+template <int ND, int NPAD, int R>
+__global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int ncol, const float2* __restrict__ Dc,
+                                                          const int* __restrict__ nbr, const float2* __restrict__ X,
+                                                          float2* __restrict__ Y, const float* __restrict__ mu,
+                                                          int* __restrict__ err, const int* __restrict__ skip,
+                                                          const int* __restrict__ skip2) {
+  using Sh = Tc2Shape<ND, NPAD, R>;
+  static_assert(4 * ND <= TC_M, "stacked hi / lo rows must fit one M = 128 tile");
+  if ((skip && *skip) || (skip2 && *skip2)) return;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float* const opnd = reinterpret_cast<float*>(sm);        // [2][A' (ASZ) | B' (BSZ)]
+  float* const scratch = opnd + 2 * (Sh::ASZ + Sh::BSZ);   // [2 ND][NPAD + 1]
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(scratch + Sh::SCR);   // [2]
+  uint32_t* const tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  volatile int* const s_ok = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t n = (size_t)nc * ND;
+  const int my_sites = blockIdx.x < nc ? (nc - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int ntiles = 9 * my_sites;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(Sh::cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + 1)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // rows >= 4 ND of A' and columns >= ncol of either half of B' stay zero for the whole kernel
+  for (int i = tid; i < 2 * (Sh::ASZ + Sh::BSZ); i += blockDim.x) opnd[i] = 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = idesc_tf32(TC_M, Sh::NB);
+  constexpr uint32_t lbo = 128, sbo = (uint32_t)(Sh::KP / 4) * 128;
+  bool ok = true;
+  float acc[NPAD];
+#pragma unroll
+  for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
+
+  constexpr bool kTwoAhead = RawTile<ND, NPAD>::kA + RawTile<ND, NPAD>::kB <= 16;
+  RawTile<ND, NPAD> rawA, rawB;
+  auto tile_site = [&](int t) { return blockIdx.x + (t / 9) * gridDim.x; };
+  auto load_t = [&](RawTile<ND, NPAD>& r, int t) {
+    const int st = tile_site(t), dt = t % 9;
+    load_tile<ND, NPAD>(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X, n, nbr[st * 9 + dt], ncol, tid);
+  };
+  // thread 0 issues the MMAs of tile t (operand and accumulator buffer t & 1) once every thread's
+  // shared-memory stores are visible to the tensor core
+  auto issue = [&](int t) {
+    const int bb = t & 1;
+    float* const A = opnd + bb * (Sh::ASZ + Sh::BSZ);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t aA = smem_u32(A), aB = smem_u32(A + Sh::ASZ);
+#pragma unroll
+      for (int s = 0; s < Sh::NS; s++) {
+        const uint32_t koff = (uint32_t)s * 2 * 128;     // two core matrices per K = 8 step
+        const uint32_t dcol = tmem + (uint32_t)(bb * Sh::TCOLS + (s / R) * Sh::NB);
+        const uint64_t dA = smem_desc(aA + koff, lbo, sbo), dB = smem_desc(aB + koff, lbo, sbo);
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(dcol), "l"(dA), "l"(dB), "r"(idesc), "r"((s % R) ? 1u : 0u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar + bb))
+                   : "memory");
+    }
+  };
+  // site epilogue: rows 2 ND .. 4 ND - 1 (the lo part of A') hand their sums to rows 0 .. 2 ND - 1
+  // through shared memory; those add the twist and store
+  auto epilogue = [&](int site) {
+    const int L = warp * 32 + lane;
+    if (L >= 2 * ND && L < 4 * ND) {
+#pragma unroll
+      for (int i = 0; i < NPAD; i++) scratch[(L - 2 * ND) * (NPAD + 1) + i] = acc[i];
+    }
+    __syncthreads();
+    if (L < 2 * ND) {
+      const bool imag = L >= ND;
+      const int k = imag ? L - ND : L;
+#pragma unroll
+      for (int col = 0; col < NPAD; col++) {
+        if (col < ncol) {
+          const float2 xs = X[(size_t)col * n + (size_t)site * ND + k];
+          const float tw = k < nv ? mu[col] : -mu[col];
+          const float v = acc[col] + scratch[L * (NPAD + 1) + col];
+          float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * ND + k);
+          if (!imag) yp[0] = v - tw * xs.y;
+          else yp[1] = v + tw * xs.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NPAD; i++) acc[i] = 0.f;
+  };
+  // wait (bounded) for tile u's MMAs, add its accumulators to acc, free its buffers
+  auto drain = [&](int u) {
+    const int bu = u & 1;
+    if (tid == 0) {
+      const bool done = mbar_wait(smem_u32(mbar + bu), (uint32_t)((u >> 1) & 1));
+      *s_ok = done ? 1 : 0;
+      if (!done) atomicExch(err, 1);
+    }
+    __syncthreads();
+    ok = *s_ok != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && warp * 32 < 4 * ND) {
+      constexpr int X16 = Sh::NB / 16, RB = X16 >= 4 ? 1 : 4 / X16;
+#pragma unroll
+      for (int s2 = 0; s2 < Sh::NR; s2 += RB) {
+        uint32_t r[RB * X16][16];
+#pragma unroll
+        for (int q = 0; q < RB; q++)
+          if (s2 + q < Sh::NR)
+#pragma unroll
+            for (int h = 0; h < X16; h++)
+              tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bu * Sh::TCOLS + (s2 + q) * Sh::NB + h * 16),
+                        r[q * X16 + h]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < RB; q++)
+          if (s2 + q < Sh::NR)
+#pragma unroll
+            for (int h = 0; h < X16 / 2; h++)
+#pragma unroll
+              for (int i = 0; i < 16; i++)
+                acc[h * 16 + i] += __uint_as_float(r[q * X16 + h][i]) + __uint_as_float(r[q * X16 + X16 / 2 + h][i]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (ok && u % 9 == 8) epilogue(tile_site(u));
+  };
+  int issued = 0, drained = 0;   // tiles whose MMAs were issued / whose accumulators were read
+  auto step = [&](int t, RawTile<ND, NPAD>& raw) {
+    float* const A = opnd + (t & 1) * (Sh::ASZ + Sh::BSZ);
+    store_tile_stacked<ND, NPAD>(raw, A, A + Sh::ASZ, ncol, tid);   // buffer t & 1: tile t - 2 drained
+    issue(t);
+    issued = t + 1;
+    const int tn = kTwoAhead ? t + 2 : t + 1;        // the registers just stored take the next loads
+    if (tn < ntiles) load_t(raw, tn);
+    if (t >= 1) {
+      drain(t - 1);
+      if (ok) drained = t;
+    }
+  };
+  if (ntiles > 0) load_t(rawA, 0);
+  if (kTwoAhead && ntiles > 1) load_t(rawB, 1);
+  if (kTwoAhead) {
+    for (int t = 0; t < ntiles && ok; t += 2) {
+      step(t, rawA);
+      if (t + 1 < ntiles && ok) step(t + 1, rawB);
+    }
+  } else {
+    for (int t = 0; t < ntiles && ok; t++) step(t, rawA);
+  }
+  if (ok && ntiles > 0) {
+    drain(ntiles - 1);
+    if (ok) drained = ntiles;
+  }
+  // after a wait that gave up, let every issued MMA finish (bounded) before the tensor memory goes
+  if (tid == 0)
+    for (int u = drained; u < issued; u++) mbar_wait(smem_u32(mbar + (u & 1)), (uint32_t)((u >> 1) & 1));
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::cols));
+  }
+}
+
+template <int ND, int NPAD>
+void launch_tc2(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip,
+                const int* skip2) {
+  constexpr int R = NPAD <= 16 ? 2 : 4;   // K steps per accumulator range: at most 32 products per TMEM sum
+  using Sh = Tc2Shape<ND, NPAD, R>;
+  // persistent CTAs: two per SM when both tensor memory (512 columns) and shared memory allow
+  const int per_sm = (Sh::cols <= 256 && Sh::smem <= 113 * 1024) ? 2 : 1;
+  const int grid = std::max(1, std::min(L.nc, per_sm * c.sms));
+  TMG_CUDA(cudaFuncSetAttribute(k_coarse_apply_tc2<ND, NPAD, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem));
+  ++c.launches, k_coarse_apply_tc2<ND, NPAD, R><<<grid, 128, Sh::smem, c.stream>>>(L.nc, L.nv, ncol, L.Dc, L.nbr, (const float2*)X,
+                                                                                (float2*)Y, mu_dev, err_dev, skip, skip2);
+}
+
 template <int ND, int NPAD, int R>
 void launch_tc(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev, const int* skip,
                const int* skip2) {
@@ -395,6 +625,13 @@ void launch_tc_r(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, con
 template <int ND>
 void launch_tc_nd(Ctx& c, const TcLevel& L, int ncol, const void* X, void* Y, const float* mu_dev, int* err_dev,
                   const int* skip, const int* skip2) {
+  if constexpr (4 * ND <= TC_M) {
+    if (c.tc_pipeline) {
+      if (ncol <= 16) launch_tc2<ND, 16>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
+      else launch_tc2<ND, 32>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
+      return;
+    }
+  }
   if (ncol <= 16) launch_tc_r<ND, 16>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
   else launch_tc_r<ND, 32>(c, L, ncol, X, Y, mu_dev, err_dev, skip, skip2);
 }

@@ -230,6 +230,7 @@ struct Ctx {
   int coarse_grid = 0;          // CTAs of the persistent coarse GMRES (0: coarse_ctas_per_sm x SMs)
   int kcycle_grid = 0;          // CTAs of the persistent K-cycle (0: kcycle_ctas_per_sm x SMs)
   int tc_steps_per_range = 1;   // K steps sharing one TMEM accumulator range in the tensor-core coarse apply
+  int tc_pipeline = 1;          // tensor-core coarse apply for 2 N_v <= 32: stacked hi / lo operands, double-buffered
   int cycle_graphs = 1;         // replay the preconditioner cycle of the outer FGMRES as a CUDA graph
   GraphCache graphs;
   Prof prof;
