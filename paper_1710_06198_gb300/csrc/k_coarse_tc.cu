@@ -320,12 +320,20 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
       if (r < 2 * ND) {
         const bool imag = r >= ND;
         const int k = imag ? r - ND : r;
-        for (int col = 0; col < ncol; col++) {
-          const float2 xs = X[(size_t)col * n + (size_t)site * ND + k];
-          const float tw = k < nv ? mu[col] : -mu[col];
-          float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * ND + k);
-          if (!imag) yp[0] = acc[col] - tw * xs.y;
-          else yp[1] = acc[col] + tw * xs.x;
+        float xo[NPAD];
+#pragma unroll
+        for (int col = 0; col < NPAD; col++) {
+          const float2* xp = X + (size_t)col * n + (size_t)site * ND + k;
+          xo[col] = col < ncol ? (imag ? xp->x : xp->y) : 0.f;
+        }
+#pragma unroll
+        for (int col = 0; col < NPAD; col++) {
+          if (col < ncol) {
+            const float tw = k < nv ? mu[col] : -mu[col];
+            float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * ND + k);
+            if (!imag) yp[0] = acc[col] - tw * xo[col];
+            else yp[1] = acc[col] + tw * xo[col];
+          }
         }
       }
 #pragma unroll
@@ -359,44 +367,78 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
 // own completion mbarrier: while the MMAs of tile t run, the CTA reads tile t - 1's accumulators,
 // issues the global loads of tile t + 2 and, in the next iteration, stages tile t + 1 into the
 // other buffer.
+// Per-thread element map of the stacked form, computed once per kernel (the same element assignment
+// as load_tile / store_tile): for each register slot of a raw tile, its offset in the global block
+// or column vector and its shared-memory offset in A' / B' (-1: nothing to load or store).  The other
+// copies of an element (Im rows, lo rows, Im columns) sit at compile-time distances from it.
 template <int ND, int NPAD>
-__device__ __forceinline__ void store_tile_stacked(const RawTile<ND, NPAD>& t, float* A, float* B, int ncol, int tid) {
-  constexpr int KP = 2 * ND;
-  const int warp = tid >> 5, lane = tid & 31;
+struct StackedMap {
+  static constexpr int kA = RawTile<ND, NPAD>::kA, kB = RawTile<ND, NPAD>::kB, KP = 2 * ND;
+  static constexpr int CC = (ND / 4) * 32;               // + ND along K
+  static constexpr int CR = (ND / 8) * (KP / 4) * 32;    // + ND rows
+  static constexpr int CB = (NPAD / 8) * (KP / 4) * 32;  // + NPAD rows (columns of B')
+  int sa[kA], ga[kA], sb[kB];
+  size_t gb[kB];
+  __device__ __forceinline__ StackedMap(int tid, int ncol, size_t n) {
+    const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-  for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
-    const int ch = q * 4 + warp;
-    if (ch < ND * ND / 32) {
+    for (int q = 0; q < kA; q++) {
+      const int ch = q * 4 + warp;
       const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
-      const float2 z = t.a[q];
-      const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
-      const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
-      A[core_off(k, l, KP)] = re_h;
-      A[core_off(k, ND + l, KP)] = -im_h;
-      A[core_off(ND + k, l, KP)] = im_h;
-      A[core_off(ND + k, ND + l, KP)] = re_h;
-      A[core_off(2 * ND + k, l, KP)] = re_l;
-      A[core_off(2 * ND + k, ND + l, KP)] = -im_l;
-      A[core_off(3 * ND + k, l, KP)] = im_l;
-      A[core_off(3 * ND + k, ND + l, KP)] = re_l;
+      const bool in = ch < ND * ND / 32;
+      sa[q] = in ? core_off(k, l, KP) : -1;
+      ga[q] = in ? l * ND + k : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kB; q++) {
+      const int ch = q * 4 + warp;
+      const int col = (ch % (NPAD / 8)) * 8 + (lane >> 2), l = (ch / (NPAD / 8)) * 4 + (lane & 3);
+      const bool in = ch < NPAD * ND / 32 && col < ncol;
+      sb[q] = in ? core_off(col, l, KP) : -1;
+      gb[q] = in ? (size_t)col * n + l : 0;
     }
   }
+  __device__ __forceinline__ void load(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ xv) const {
 #pragma unroll
-  for (int q = 0; q < RawTile<ND, NPAD>::kB; q++) {
-    const int ch = q * 4 + warp;
-    if (ch < NPAD * ND / 32) {
-      const int col = (ch % (NPAD / 8)) * 8 + (lane >> 2), l = (ch / (NPAD / 8)) * 4 + (lane & 3);
-      if (col < ncol) {
+    for (int q = 0; q < kA; q++)
+      if (sa[q] >= 0) t.a[q] = blk[ga[q]];
+#pragma unroll
+    for (int q = 0; q < kB; q++)
+      if (sb[q] >= 0) t.b[q] = xv[gb[q]];
+  }
+  // A' = [A_hi; A_lo] (real embedding rows (Re, -Im) / (Im, Re)), B' = [B_hi | B_lo]
+  __device__ __forceinline__ void store(const RawTile<ND, NPAD>& t, float* A, float* B) const {
+#pragma unroll
+    for (int q = 0; q < kA; q++) {
+      if (sa[q] >= 0) {
+        const float2 z = t.a[q];
+        const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
+        const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
+        float* a = A + sa[q];
+        a[0] = re_h;
+        a[CC] = -im_h;
+        a[CR] = im_h;
+        a[CR + CC] = re_h;
+        a[2 * CR] = re_l;
+        a[2 * CR + CC] = -im_l;
+        a[3 * CR] = im_l;
+        a[3 * CR + CC] = re_l;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kB; q++) {
+      if (sb[q] >= 0) {
         const float2 z = t.b[q];
         const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
-        B[core_off(col, l, KP)] = re_h;
-        B[core_off(col, ND + l, KP)] = im_h;
-        B[core_off(NPAD + col, l, KP)] = tf32_round(z.x - re_h);
-        B[core_off(NPAD + col, ND + l, KP)] = tf32_round(z.y - im_h);
+        float* b = B + sb[q];
+        b[0] = re_h;
+        b[CC] = im_h;
+        b[CB] = tf32_round(z.x - re_h);
+        b[CB + CC] = tf32_round(z.y - im_h);
       }
     }
   }
-}
+};
 
 __host__ __device__ constexpr uint32_t tmem_cols_pow2(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
 
@@ -456,9 +498,10 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
   constexpr bool kTwoAhead = RawTile<ND, NPAD>::kA + RawTile<ND, NPAD>::kB <= 16;
   RawTile<ND, NPAD> rawA, rawB;
   auto tile_site = [&](int t) { return blockIdx.x + (t / 9) * gridDim.x; };
+  const StackedMap<ND, NPAD> map(tid, ncol, n);
   auto load_t = [&](RawTile<ND, NPAD>& r, int t) {
     const int st = tile_site(t), dt = t % 9;
-    load_tile<ND, NPAD>(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X, n, nbr[st * 9 + dt], ncol, tid);
+    map.load(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X + (size_t)nbr[st * 9 + dt] * ND);
   };
   // thread 0 issues the MMAs of tile t (operand and accumulator buffer t & 1) once every thread's
   // shared-memory stores are visible to the tensor core
@@ -470,12 +513,12 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aA = smem_u32(A), aB = smem_u32(A + Sh::ASZ);
+      // the descriptor's address field counts 16-byte units: K step s adds 2 * 128 / 16
+      const uint64_t dA0 = smem_desc(smem_u32(A), lbo, sbo), dB0 = smem_desc(smem_u32(A + Sh::ASZ), lbo, sbo);
 #pragma unroll
       for (int s = 0; s < Sh::NS; s++) {
-        const uint32_t koff = (uint32_t)s * 2 * 128;     // two core matrices per K = 8 step
         const uint32_t dcol = tmem + (uint32_t)(bb * Sh::TCOLS + (s / R) * Sh::NB);
-        const uint64_t dA = smem_desc(aA + koff, lbo, sbo), dB = smem_desc(aB + koff, lbo, sbo);
+        const uint64_t dA = dA0 + (uint64_t)(s * 16), dB = dB0 + (uint64_t)(s * 16);
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
                      ::"r"(dcol), "l"(dA), "l"(dB), "r"(idesc), "r"((s % R) ? 1u : 0u));
       }
@@ -495,15 +538,21 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
     if (L < 2 * ND) {
       const bool imag = L >= ND;
       const int k = imag ? L - ND : L;
+      // the site's own entries for the twist term: all loads in flight before the first use
+      float xo[NPAD];
+#pragma unroll
+      for (int col = 0; col < NPAD; col++) {
+        const float2* xp = X + (size_t)col * n + (size_t)site * ND + k;
+        xo[col] = col < ncol ? (imag ? xp->x : xp->y) : 0.f;
+      }
 #pragma unroll
       for (int col = 0; col < NPAD; col++) {
         if (col < ncol) {
-          const float2 xs = X[(size_t)col * n + (size_t)site * ND + k];
           const float tw = k < nv ? mu[col] : -mu[col];
           const float v = acc[col] + scratch[L * (NPAD + 1) + col];
           float* yp = reinterpret_cast<float*>(Y + (size_t)col * n + (size_t)site * ND + k);
-          if (!imag) yp[0] = v - tw * xs.y;
-          else yp[1] = v + tw * xs.x;
+          if (!imag) yp[0] = v - tw * xo[col];
+          else yp[1] = v + tw * xo[col];
         }
       }
     }
@@ -544,14 +593,15 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
                 acc[h * 16 + i] += __uint_as_float(r[q * X16 + h][i]) + __uint_as_float(r[q * X16 + X16 / 2 + h][i]);
       }
     }
+    // no CTA barrier here: the next issue's barrier orders these TMEM reads before the MMAs that
+    // reuse the buffer, and this tile's operand buffer is free since the wait above
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
     if (ok && u % 9 == 8) epilogue(tile_site(u));
   };
   int issued = 0, drained = 0;   // tiles whose MMAs were issued / whose accumulators were read
   auto step = [&](int t, RawTile<ND, NPAD>& raw) {
     float* const A = opnd + (t & 1) * (Sh::ASZ + Sh::BSZ);
-    store_tile_stacked<ND, NPAD>(raw, A, A + Sh::ASZ, ncol, tid);   // buffer t & 1: tile t - 2 drained
+    map.store(raw, A, A + Sh::ASZ);                  // buffer t & 1: tile t - 2 drained
     issue(t);
     issued = t + 1;
     const int tn = kTwoAhead ? t + 2 : t + 1;        // the registers just stored take the next loads

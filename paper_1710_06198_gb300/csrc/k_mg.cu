@@ -41,6 +41,31 @@ __device__ __forceinline__ void cta_allreduce(R (&v)[N], double* red_d) {
   __syncthreads();
 }
 
+// One-barrier variant for the block solvers (at most 8 warps): the warp sums go to half `parity`
+// of the scratch (8 N values of R each) and, after one barrier, every thread adds the warps' values
+// itself.  Consecutive calls alternate the parity; any two calls with the same parity must be
+// separated by another CTA barrier of the caller (the block solvers have one before each MR step's
+// operator), so no warp overwrites a half that another is still reading.
+template <int N, typename R>
+__device__ __forceinline__ void cta_allreduce_db(R (&v)[N], double* red_d, int parity) {
+  R* red = reinterpret_cast<R*>(red_d) + parity * 8 * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    R a = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[w * N + i] = a;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    R a = 0;
+    for (int k = 0; k < nw; k++) a += red[k * N + i];
+    v[i] = a;
+  }
+}
+
 // k-th block of the given colour (colour = parity of the block coordinates; NB[0] is even).
 __device__ __forceinline__ int colour_block(const Geom& g, int colour, int k) {
   const int half = g.NB[0] >> 1;
@@ -163,7 +188,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_sap_block(Geom 
       v[1] += q.re;
       v[2] += q.im;
     }
-    cta_allreduce<3, R>(v, red);
+    cta_allreduce_db<3, R>(v, red, it & 1);
     const cpx<R> alpha = v[0] > R(0) ? mk(v[1] / v[0], v[2] / v[0]) : mk<R>(0, 0);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -302,7 +327,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_block_nd(Geom g, int colour, S x
         v[1] += w.re;
         v[2] += w.im;
       }
-    cta_allreduce<3, R>(v, red);
+    cta_allreduce_db<3, R>(v, red, it & 1);
     const cpx<R> alpha = v[0] > R(0) ? mk(v[1] / v[0], v[2] / v[0]) : mk<R>(0, 0);
 #pragma unroll
     for (int f = 0; f < 2; f++)
