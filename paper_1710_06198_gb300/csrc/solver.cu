@@ -374,7 +374,8 @@ static std::vector<unsigned long long> cycle_key(const Ctx& c, int pf, int pc, c
                                        (unsigned long long)c.coarse_block_cache, (unsigned long long)c.coarse_eo,
                                        (unsigned long long)(c.coarse_eo ? c.cl.version : 0), (unsigned long long)c.l2p.smooth_m,
                                        (unsigned long long)c.l2p.k_restart, d(c.l2p.k_rtol), (unsigned long long)c.l2p.coarse_m,
-                                       d(c.l2p.coarse_rtol)};
+                                       d(c.l2p.coarse_rtol), (unsigned long long)c.tc_pipeline,
+                                       (unsigned long long)c.tc_steps_per_range};
   for (int i = 0; i < 3; i++) {
     k.push_back(u(c.op[i].U.p));
     k.push_back(u(c.op[i].A.p));

@@ -58,3 +58,27 @@ def test_autotune_keeps_a_working_shape(levels):
     assert 0.0 < ms < 1e4
     x, st = ctx.solve(b, tol=1e-10)
     assert rel(dirac.apply_D(U, x, p), b) <= 1.01e-10
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_batched_graph_follows_tensor_core_knob(levels):
+    """The batched cycle's graph is keyed on the tensor-core kernel form: switching tc_pipeline after
+    a capture leads to a new capture, and both forms give the same converged columns (N_v = 4, so the
+    lock-step K-cycle and the batched coarse GMRES run on the tensor cores)."""
+    ctx, U, p = _ctx(levels)
+    b = np.stack([fields.gaussian_spinor(DIMS, 215 + j) for j in range(3)])
+    mus = [p.mu, -p.mu, 0.5 * p.mu]
+    xs = []
+    for pipe in (1, 0):
+        ctx.tune("tc_pipeline", pipe)
+        ctx.solve(b, tol=1e-10, method=tmg.SOLVE_MG_BATCHED, mu_per_col=mus)     # eager run, then capture
+        g0 = tmg.graph_count(ctx)
+        x, st = ctx.solve(b, tol=1e-10, method=tmg.SOLVE_MG_BATCHED, mu_per_col=mus)
+        assert tmg.graph_count(ctx) >= g0
+        xs.append((x, g0))
+    assert xs[1][1] > xs[0][1]     # the second form was captured, not replayed from the first
+    for j, mu in enumerate(mus):
+        pj = dirac.Params(kappa=p.kappa, csw=p.csw, mu=mu, tbc=-1)
+        for x, _ in xs:
+            assert rel(dirac.apply_D(U, x[j], pj), b[j]) <= 1.5e-10
+        assert rel(xs[0][0][j], xs[1][0][j]) < 1e-8
