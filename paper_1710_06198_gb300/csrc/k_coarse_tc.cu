@@ -114,19 +114,27 @@ struct RawTile {
   float2 b[kB];
 };
 
+// The backward-hop blocks are not read: by the Gamma5_c-hermiticity of D_c (twist excluded) the
+// block of site x for the hop -mu is G5_c B^dag G5_c with B the +mu block of site x - mu (the
+// stencil's slot 2 + 2 mu holds the -mu hop, slot 1 + 2 mu the +mu hop, for every coarse extent), so
+// a backward tile is staged from that forward block: transposed addresses at load, and at store the
+// conjugate with the sign s_k s_l of the chirality halves.  Only the self and forward blocks (5 of
+// 9) are read from memory.
+__device__ __forceinline__ bool tc_backward(int d) { return d >= 2 && (d & 1) == 0; }
+
 // Element assignment shared by load_tile and store_tile: chunk q * 4 + warp of a tile is one 8 x 4
 // patch (8 rows of the result, 4 consecutive K) and lane L takes element (L / 4, L % 4) of it, so
 // each warp-wide shared-memory store fills one 128-byte core matrix (no bank conflicts).
 template <int ND, int NPAD>
 __device__ __forceinline__ void load_tile(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ X,
-                                          size_t n, int nbr_site, int ncol, int tid) {
+                                          size_t n, int nbr_site, int ncol, int tid, bool tr) {
   const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
   for (int q = 0; q < RawTile<ND, NPAD>::kA; q++) {
     const int ch = q * 4 + warp;                   // patch of the block: rows kb*8.., columns lb*4..
     if (ch < ND * ND / 32) {
       const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
-      t.a[q] = blk[(size_t)l * ND + k];
+      t.a[q] = blk[tr ? (size_t)k * ND + l : (size_t)l * ND + k];
     }
   }
 #pragma unroll
@@ -141,7 +149,7 @@ __device__ __forceinline__ void load_tile(RawTile<ND, NPAD>& t, const float2* __
 
 template <int ND, int NPAD>
 __device__ __forceinline__ void store_tile(const RawTile<ND, NPAD>& t, float* Ahi, float* Alo, float* Bhi, float* Blo, int ncol,
-                                           int tid) {
+                                           int tid, bool tr) {
   constexpr int KP = ((2 * ND + 7) / 8) * 8;
   const int warp = tid >> 5, lane = tid & 31;
   // A real embedding: row r < ND -> (Re, -Im); row ND + r -> (Im, Re)
@@ -150,7 +158,11 @@ __device__ __forceinline__ void store_tile(const RawTile<ND, NPAD>& t, float* Ah
     const int ch = q * 4 + warp;
     if (ch < ND * ND / 32) {
       const int k = (ch % (ND / 8)) * 8 + (lane >> 2), l = (ch / (ND / 8)) * 4 + (lane & 3);
-      const float2 z = t.a[q];
+      float2 z = t.a[q];
+      if (tr) {                                    // backward hop: s_k s_l conj(B_lk)
+        const float sg = ((k < ND / 2) == (l < ND / 2)) ? 1.f : -1.f;
+        z = make_float2(sg * z.x, -sg * z.y);
+      }
       const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
       const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
       const int o00 = core_off(k, l, KP), o01 = core_off(k, ND + l, KP);
@@ -246,13 +258,15 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc(int nc, int nv, int nco
   auto tile_site = [&](int t) { return blockIdx.x + (t / 9) * gridDim.x; };
   auto load_t = [&](RawTile<ND, NPAD>& r, int t) {
     const int st = tile_site(t), dt = t % 9;
-    load_tile<ND, NPAD>(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X, n, nbr[st * 9 + dt], ncol, tid);
+    const int nb = nbr[st * 9 + dt];
+    const bool bw = tc_backward(dt);
+    load_tile<ND, NPAD>(r, Dc + (size_t)(bw ? nb * 9 + dt - 1 : st * 9 + dt) * ND * ND, X, n, nb, ncol, tid, bw);
   };
   if (ntiles > 0) load_t(rawA, 0);
   if (kTwoAhead && ntiles > 1) load_t(rawB, 1);
   auto tile_step = [&](int t, RawTile<ND, NPAD>& raw, int tnext) {
     const int site = tile_site(t), d = t % 9;
-    store_tile<ND, NPAD>(raw, Ahi, Alo, Bhi, Blo, ncol, tid);
+    store_tile<ND, NPAD>(raw, Ahi, Alo, Bhi, Blo, ncol, tid, tc_backward(d));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -377,7 +391,8 @@ struct StackedMap {
   static constexpr int CC = (ND / 4) * 32;               // + ND along K
   static constexpr int CR = (ND / 8) * (KP / 4) * 32;    // + ND rows
   static constexpr int CB = (NPAD / 8) * (KP / 4) * 32;  // + NPAD rows (columns of B')
-  int sa[kA], ga[kA], sb[kB];
+  int sa[kA], ga[kA], gt[kA], sb[kB];
+  float sg[kA];                                          // chirality sign s_k s_l of a backward tile
   size_t gb[kB];
   __device__ __forceinline__ StackedMap(int tid, int ncol, size_t n) {
     const int warp = tid >> 5, lane = tid & 31;
@@ -388,6 +403,8 @@ struct StackedMap {
       const bool in = ch < ND * ND / 32;
       sa[q] = in ? core_off(k, l, KP) : -1;
       ga[q] = in ? l * ND + k : 0;
+      gt[q] = in ? k * ND + l : 0;
+      sg[q] = ((k < ND / 2) == (l < ND / 2)) ? 1.f : -1.f;
     }
 #pragma unroll
     for (int q = 0; q < kB; q++) {
@@ -398,20 +415,22 @@ struct StackedMap {
       gb[q] = in ? (size_t)col * n + l : 0;
     }
   }
-  __device__ __forceinline__ void load(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ xv) const {
+  __device__ __forceinline__ void load(RawTile<ND, NPAD>& t, const float2* __restrict__ blk, const float2* __restrict__ xv,
+                                       bool tr) const {
 #pragma unroll
     for (int q = 0; q < kA; q++)
-      if (sa[q] >= 0) t.a[q] = blk[ga[q]];
+      if (sa[q] >= 0) t.a[q] = blk[tr ? gt[q] : ga[q]];
 #pragma unroll
     for (int q = 0; q < kB; q++)
       if (sb[q] >= 0) t.b[q] = xv[gb[q]];
   }
   // A' = [A_hi; A_lo] (real embedding rows (Re, -Im) / (Im, Re)), B' = [B_hi | B_lo]
-  __device__ __forceinline__ void store(const RawTile<ND, NPAD>& t, float* A, float* B) const {
+  __device__ __forceinline__ void store(const RawTile<ND, NPAD>& t, float* A, float* B, bool tr) const {
 #pragma unroll
     for (int q = 0; q < kA; q++) {
       if (sa[q] >= 0) {
-        const float2 z = t.a[q];
+        float2 z = t.a[q];
+        if (tr) z = make_float2(sg[q] * z.x, -sg[q] * z.y);   // backward hop: s_k s_l conj(B_lk)
         const float re_h = tf32_round(z.x), im_h = tf32_round(z.y);
         const float re_l = tf32_round(z.x - re_h), im_l = tf32_round(z.y - im_h);
         float* a = A + sa[q];
@@ -501,7 +520,9 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
   const StackedMap<ND, NPAD> map(tid, ncol, n);
   auto load_t = [&](RawTile<ND, NPAD>& r, int t) {
     const int st = tile_site(t), dt = t % 9;
-    map.load(r, Dc + (size_t)(st * 9 + dt) * ND * ND, X + (size_t)nbr[st * 9 + dt] * ND);
+    const int nb = nbr[st * 9 + dt];
+    const bool bw = tc_backward(dt);
+    map.load(r, Dc + (size_t)(bw ? nb * 9 + dt - 1 : st * 9 + dt) * ND * ND, X + (size_t)nb * ND, bw);
   };
   // thread 0 issues the MMAs of tile t (operand and accumulator buffer t & 1) once every thread's
   // shared-memory stores are visible to the tensor core
@@ -601,7 +622,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc2(int nc, int nv, int nc
   int issued = 0, drained = 0;   // tiles whose MMAs were issued / whose accumulators were read
   auto step = [&](int t, RawTile<ND, NPAD>& raw) {
     float* const A = opnd + (t & 1) * (Sh::ASZ + Sh::BSZ);
-    map.store(raw, A, A + Sh::ASZ);                  // buffer t & 1: tile t - 2 drained
+    map.store(raw, A, A + Sh::ASZ, tc_backward(t % 9));   // buffer t & 1: tile t - 2 drained
     issue(t);
     issued = t + 1;
     const int tn = kTwoAhead ? t + 2 : t + 1;        // the registers just stored take the next loads
