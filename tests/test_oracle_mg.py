@@ -71,6 +71,24 @@ def test_coarse_gamma5_hermiticity():
     assert np.abs(A.conj().T - (g[:, None] * A * g[None, :])).max() < 1e-13
 
 
+def test_coarse_backward_blocks_from_forward_blocks():
+    """Per stencil slot: the -mu block of site a equals G5_c (+mu block of a - mu)^dag G5_c, also on
+    coarse extents 2 (where a + mu = a - mu but the two hops are separate slots) and 3, with the
+    antiperiodic time boundary.  The tensor-core coarse apply reads only the self and forward
+    blocks and builds the backward ones from this relation."""
+    dims, adims, nv = (6, 4, 4, 4), (2, 2, 2, 2), 2          # coarse lattice 3 x 2 x 2 x 2
+    U, P = _prolongator(dims, adims, nv, 51)
+    p = _params(mu=0.0)
+    Dc = mg.build_coarse(U, p, dirac.clover_term(U, p.csw), P)
+    g = mg.coarse_gamma5(nv)
+    for m in range(4):
+        f = np.roll(Dc.fwd[m], 1, axis=-3 - m)               # the +mu block of site a - mu, at a
+        want = g[:, None] * np.swapaxes(f.conj(), -1, -2) * g[None, :]
+        assert np.abs(Dc.bwd[m] - want).max() < 1e-13 * np.abs(Dc.bwd[m]).max(), m
+        # a dropped sign or conjugation does not pass
+        assert np.abs(Dc.bwd[m] - np.swapaxes(f.conj(), -1, -2)).max() > 1e-6, m
+
+
 def test_coarse_correction_basis_invariance():
     """I - P D_c^-1 P^dag D depends on span(P) only: mixing the test vectors by any invertible
     matrix leaves the coarse-grid correction unchanged."""
