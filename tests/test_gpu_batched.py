@@ -74,7 +74,7 @@ def test_batched_solve_fp16_links():
 def test_shifted_solves_with_taylor_guesses(case):
     """tmg_solve_shifts: D(mu_k) x_k = b for twists mu_k = sqrt(mu^2 + sigma_k) (shifted normal
     equations, Sec. 1.1), with zero, previous-solution and first-order Taylor (Sec. 3) initial
-    guesses.  Every system reaches 1e-10 with the oracle's operator as the judge; the three guesses
+    guesses.  Every system reaches 1e-10 measured with the oracle's operator; the three guesses
     give the same solutions; the Taylor guess leaves the systems after the first no more outer
     iterations than the zero guess."""
     ctx, U, p, C = case

@@ -5,7 +5,7 @@ At these sizes the oracle cannot solve, so parity is checked on what it can comp
 * the 8^4 FP64 workload is small enough for the oracle's CG and its own two-level DD-alpha-AMG:
   both GPU solves (FP64 multigrid, FP64 CG) agree with both oracle solves;
 * elsewhere the operator is compared with the oracle site by site on sampled sites (tests.sampled),
-  and solutions are judged by their true residual, computed with the oracle's operator on the
+  and solutions are checked by their true residual, computed with the oracle's operator on the
   whole lattice where that is affordable (16^3 x 32, 16^4) and with the GPU FP64 operator (itself
   compared site by site with the oracle at the same size) on 24^3 x 48;
 * the force on 16^4 (FP64 force kernels, mixed-precision solves) against central finite

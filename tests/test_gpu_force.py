@@ -144,7 +144,7 @@ def test_pf_action_and_force_match_oracle():
 
 def test_setup_update_after_rotation():
     """Rotate the field, update the setup by one iteration (Sec. 2), and solve to 1e-10 with the
-    oracle's operator on the rotated field as the judge of the residual."""
+    oracle's operator on the rotated field measuring the residual."""
     U = fields.gauge_field(DIMS, 0.4, 98)
     p = dirac.Params(kappa=dirac.kappa_from_m0(-0.25), csw=1.0, mu=0.05, tbc=-1)
     ctx = _ctx(U, p)

@@ -161,7 +161,7 @@ def test_shifted_doublet_pieces_and_solve(levels):
     """The shifted doublet D_ND + i delta (G5 x tau1) of the rational approximation's systems
     (Sec. 3): fine operator, SAP, coarse operator and coarse solve (or K-cycle) in FP64 against the
     oracle with the same delta, and a mixed-precision doublet solve to 1e-12 with the oracle's
-    operator as the judge."""
+    operator as the reference."""
     import dataclasses
     ctx, HN, U, p = build(levels=levels)
     delta = 0.04
